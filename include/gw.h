@@ -1,0 +1,162 @@
+/*
+ * gw.h -- C ABI of the GB300 contour-deformation G0W0 library (libgw.so).
+ *
+ * Method: arXiv 2107.10423, "Scalable Molecular GW Calculations: Valence and
+ * Core Spectra".  Closed-shell G0W0 in an orthonormal (Coulomb-metric)
+ * auxiliary basis (Sec. 3.1): the input is the fitted three-index tensor
+ * B_{P,pq} = (P|pq) restricted to the two slices the method touches:
+ *
+ *   B_ia : [n_aux][n_occ*n_virt], row-major, pair index ia = i*n_virt + a
+ *          (i occupied, a virtual).  Builds Pi (Sec. 3.3, equation after
+ *          "wauxbas").
+ *   B_nm : [n_targets][n_bas][n_aux], row-major: the rows b_nm = (P|nm) of
+ *          each target state n against every state m.  W_nm enters Sigma_nn
+ *          (eqs. "inn" and "rnn").
+ *
+ * All energies are in Hartree.  KS energies eps[n_bas] are ascending, the
+ * first n_occ occupied (closed shell, n_bas = n_occ + n_virt).
+ *
+ * Ownership: the caller owns every array it passes.  gw_plan_create copies
+ * the inputs into device memory owned by the plan, unless
+ * GW_BORROW_DEVICE_PTRS is given (then B_ia and B_nm must be device pointers
+ * that stay valid until gw_plan_destroy).  Output arrays are host arrays
+ * that the caller allocates.  Every call returns a gw_status; no call aborts
+ * or throws.  A plan is used by one host thread at a time; work runs on the
+ * stream given at creation (or a stream the plan creates).  Every call
+ * synchronises that stream before returning.
+ */
+#ifndef GW_H
+#define GW_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GW_OK = 0,
+  GW_ERR_ARG = 1,              /* bad argument (sizes, NULL pointers, unsorted energies) */
+  GW_ERR_OOM = 2,              /* device allocation failed */
+  GW_ERR_CUDA = 3,             /* a CUDA call or kernel failed; see gw_last_error */
+  GW_ERR_NOT_CONVERGED = 4,    /* a solver stopped at its iteration cap (results still written) */
+  GW_ERR_TIMEOUT = 5,          /* a bounded device wait ran out */
+  GW_ERR_UNIMPLEMENTED = 6,
+  GW_ERR_NUMERIC = 7           /* a factorisation met a non-positive pivot, or NaN input */
+} gw_status;
+
+typedef enum {
+  GW_PREC_FP64 = 0,            /* every step in FP64 */
+  GW_PREC_MIXED = 1            /* Pi and the W table on tcgen05 tensor cores with BF16 hi+lo split
+                                  products (FP32 accumulate); MINRES operator in FP32, Lanczos
+                                  recurrences, quadrature and QP search in FP64 */
+} gw_precision;
+
+typedef enum {
+  GW_QP_LINEARISED = 0,        /* one Newton step from eps_n (Sec. 3.4) */
+  GW_QP_STEPTREE = 1           /* iterative solver with the step-selection tree (Sec. 3.4, Fig. "steptree") */
+} gw_qp_mode;
+
+/* Flags for gw_plan_create. */
+#define GW_INPUT_ON_DEVICE     1u   /* B_ia and B_nm are device pointers (copied device-to-device) */
+#define GW_BORROW_DEVICE_PTRS  2u   /* B_ia and B_nm are device pointers used in place (not copied) */
+
+typedef struct {
+  int n_occ, n_virt, n_aux;    /* sizes; n_bas = n_occ + n_virt */
+  int n_freq;                  /* imaginary grid points (modified Gauss-Legendre, Sec. 3.3) */
+  double x0;                   /* grid scale: xi = x0 (1+t)/(1-t) */
+  double eta;                  /* real-axis broadening in Pi(x) (Ha) */
+  int precision;               /* gw_precision */
+  int minres_maxit;            /* MINRES iteration cap (paper default 25) */
+  double minres_tol;           /* MINRES stop: ||r|| <= tol ||rhs|| (paper 5e-5) */
+  double minres_fallback_tol;  /* dense solve if ||r||/||rhs|| > this after maxit (paper 1e-4) */
+  int qp_maxit;                /* QP iterations (step tree) */
+  double qp_tol;               /* QP convergence |f| < qp_tol (Ha) */
+  int static_subtraction;      /* 1: I term with the W(0) sgn(a)/2 rewrite (exact); 0: literal quadrature */
+  int max_rhs_batch;           /* residue right-hand sides per batched MINRES launch (0 = automatic) */
+} gw_config;
+
+typedef struct gw_plan* gw_plan_t;
+
+/* Fill *cfg with defaults: n_freq 128, x0 0.5, eta 1e-3, FP64, MINRES 25 / 5e-5 / 1e-4,
+ * qp_maxit 50, qp_tol 1e-8, static_subtraction 1.  Sizes are set to 0. */
+void gw_config_default(gw_config* cfg);
+
+/* Create a plan (Algorithm 1, Init).
+ *   eps      [n_bas] host, ascending.
+ *   B_ia     [n_aux][n_occ*n_virt]; B_nm [n_targets][n_bas][n_aux] (host unless flags say device).
+ *   targets  [n_targets] host, state indices in [0, n_bas).
+ *   vxc      [n_targets] host or NULL.  NULL means V_xc := Sigma_x, so e_QP = e + Re Sigma_c(e_QP).
+ *   xi, wt   [n_freq] host imaginary grid and weights, or NULL for the built-in grid.
+ *   stream   cudaStream_t to run on, or NULL for a plan-owned stream.
+ * Computes Sigma_x_nn = -sum_i sum_P B_P,ni^2 (Algorithm 1, Init).
+ * On failure *out is NULL and gw_last_error(NULL) describes the error. */
+gw_status gw_plan_create(const gw_config* cfg, const double* eps, const double* B_ia, const double* B_nm,
+                         const int* targets, int n_targets, const double* vxc, const double* xi,
+                         const double* wt, unsigned flags, void* stream, gw_plan_t* out);
+
+/* Polarizability on the imaginary axis (Sec. 3.3, equation after "wauxbas", eta = 0):
+ *   Pi_PQ(i xi) = -4 sum_ia B_P,ia B_Q,ia D_ia / (D_ia^2 + xi^2),  D_ia = e_a - e_i.
+ * With xi != NULL: builds Pi for the n_xi given frequencies and, if pi_out != NULL, writes
+ * them to pi_out [n_xi][n_aux][n_aux] (host, full symmetric).
+ * With xi == NULL: runs the imaginary-axis stage of Algorithm 1 on the plan's grid: Pi(i xi_g)
+ * for every grid point and xi = 0, the factorisation of eps(i xi) = 1 - Pi (SPD), and the
+ * table W^c_nm(i xi_g) = b_nm^T [eps^-1 - 1] b_nm for every target n and state m (kept on the
+ * device for gw_sigma_cd / gw_qp_solve); pi_out must then be NULL. */
+gw_status gw_polarizability(gw_plan_t plan, const double* xi, int n_xi, double* pi_out);
+
+/* Correlation self-energy by contour deformation (eqs. "R", "I", "inn", "rnn"):
+ *   Re Sigma^c_nn(omega_n) = R_nn(omega_n) - I_nn(omega_n)
+ * for every target n at its own frequency omega[n_targets] (host), with the omega-derivative.
+ * Builds the imaginary-axis table first if gw_polarizability(plan, NULL, ...) has not run.
+ * Residues by batched MINRES (with dense fallback).  sigma_x may be NULL.
+ * Returns GW_ERR_NOT_CONVERGED if a residue solve stayed above minres_fallback_tol even after the
+ * dense fallback (values are still written). */
+gw_status gw_sigma_cd(gw_plan_t plan, const double* omega, double* sigma_c, double* dsigma_c,
+                      double* sigma_x);
+
+/* Residue terms (eq. "rnn") for an explicit list of n_rhs right-hand sides:
+ *   W_nm(x) = b_nm^T [(1 - Pi(x))^-1 - 1] b_nm,  Pi(x) = 2 sum_ia B B [1/(x-D+i eta) + 1/(-x-D+i eta)]
+ * solved matrix-free by MINRES on the real symmetric 2 n_aux embedding of the complex-symmetric
+ * system, for target_idx[k] (index into the plan's targets), state m[k] and real frequency x[k].
+ * Outputs (host, [n_rhs]): w_re, w_im, dw_re = Re dW/dx, iters, resnorm (relative), used_fallback.
+ * Any output pointer may be NULL. */
+gw_status gw_residues_minres(gw_plan_t plan, int n_rhs, const int* target_idx, const int* m, const double* x,
+                             double* w_re, double* w_im, double* dw_re, int* iters, double* resnorm,
+                             int* used_fallback);
+
+/* Quasiparticle energies (Sec. 3.4, eq. "qpeqn"): e_QP = e_n + Sigma_x - V_xc + Re Sigma^c(e_QP).
+ * Outputs (host, [n_targets]): e_qp, z_factor = 1/(1 - dSigma^c/domega) at the solution, and
+ * state_status (0 converged, 1 not converged, 2 converged but a residue used the dense fallback).
+ * Returns GW_ERR_NOT_CONVERGED if any state did not converge. */
+gw_status gw_qp_solve(gw_plan_t plan, gw_qp_mode mode, double* e_qp, double* z_factor, int* state_status);
+
+/* Timing and counters of the last calls (host, milliseconds / counts); any pointer may be NULL. */
+typedef struct {
+  double ms_screening;         /* Pi + factorisation + W table */
+  double ms_pi;                /* Pi build alone (inside ms_screening) */
+  double ms_sigma_imag;        /* I-term quadrature */
+  double ms_residues;          /* batched MINRES + fallback */
+  double ms_qp;                /* whole gw_qp_solve */
+  long long n_rhs_solved;      /* residue right-hand sides solved */
+  long long n_minres_iters;    /* sum over right-hand sides */
+  long long n_fallback;        /* dense fallback solves */
+  long long n_sigma_evals;     /* Sigma(omega) evaluations (per target) */
+  long long n_kernel_launches; /* kernels this plan launched */
+} gw_stats;
+gw_status gw_get_stats(gw_plan_t plan, gw_stats* out);
+
+/* The built-in imaginary-frequency grid (host only, no GPU needed): modified Gauss-Legendre
+ * (Sec. 3.3, text after eq. "inn"): Legendre nodes t_k on [-1, 1] mapped by
+ * xi_k = x0 (1 + t_k)/(1 - t_k), weights w_k = 2 x0 w_GL,k/(1 - t_k)^2, ascending.
+ * xi, wt: [n] host arrays owned by the caller.  Returns GW_ERR_ARG for n <= 0, x0 <= 0 or NULL. */
+gw_status gw_grid(int n, double x0, double* xi, double* wt);
+
+/* Release every device buffer the plan owns.  NULL is ignored. */
+void gw_plan_destroy(gw_plan_t plan);
+
+/* Last error message of this plan (or of the last failed gw_plan_create when plan is NULL). */
+const char* gw_last_error(gw_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GW_H */

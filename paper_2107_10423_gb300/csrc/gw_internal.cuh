@@ -1,0 +1,102 @@
+// Internal declarations of libgw: kernel launchers shared between translation units.
+// Not part of the public ABI (include/gw.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace gw {
+
+// ---------------------------------------------------------------- dense kernels (kernels_dense.cu)
+// Pi_PQ(i xi_g) = -4 sum_k B[P][k] B[Q][k] D_k/(D_k^2 + xi_g^2)  (Sec. 3.3, eta = 0), for n_xi points.
+// mode 0 writes Pi, mode 1 writes eps = 1 - Pi.  out: [n_xi][n_aux][n_aux] full symmetric.
+template <typename T>
+void launch_pi_syrk(const T* B, const double* eps, int n_occ, int n_virt, int n_aux, const double* xi, int n_xi,
+                    T* out, int mode, cudaStream_t s);
+
+// Dense complex real-axis matrix A = 1 - Pi(x) as two real [n_aux][n_aux] halves (dense fallback).
+void launch_pi_complex_dense(const double* B, const double* eps, int n_occ, int n_virt, int n_aux, double x,
+                             double eta, double* Ar, double* Ai, cudaStream_t s);
+
+// In-place lower Cholesky of `batch` SPD matrices A[b] = base + b*stride (row-major n x n).
+// info[b] = 0 on success, j+1 if pivot j was not positive.
+template <typename T>
+void launch_cholesky(T* base, int n, long stride, int batch, int* info, cudaStream_t s);
+
+// W table from Cholesky factors: for matrices g in [0, n_g): y = L_g^-1 b_r for rows r of Bn [R][n],
+// W[r*w_ld + g_out[g]] = |y|^2 - |b|^2 = b^T(eps^-1 - 1)b.  scratch: [n_cta][n][64] elements of T.
+template <typename T>
+void launch_trsm_w(const T* Lbase, long Lstride, int n, int n_g, const int* g_out, const T* Bn, int R, double* W,
+                   int w_ld, T* scratch, int n_cta, cudaStream_t s);
+template <typename T>
+size_t trsm_w_scratch_elems(int n, int n_cta);
+int trsm_w_default_ctas();
+
+// Matrix-free operator of the residue systems (MINRES), for a batch of nr right-hand sides.
+// V: [2nr][n_aux] pairs (u, v) encoding z = u - i v.
+// gemm1: U[2j..2j+1][k] = c_k(x_j) * t_k (mode 0) or c'_k(x_j) * t_k^2 (mode 1), t = B^T z
+//   with c_k(x) = 2[1/(x-D_k+i eta) + 1/(-x-D_k+i eta)], c' its x-derivative.
+// gemm2: S[r][P] = sum_k U[r][k] B[P][k]; mode 0 writes S (= [Re; Im] of Pi z),
+//   mode 1 writes the real embedding [u - S_re; -v - S_im] of (1 - Pi) z.
+template <typename T>
+void launch_op_gemm1(const T* V, const T* B, const double* eps, int n_occ, int n_virt, int n_aux, const double* x,
+                     double eta, int nr, T* U, int mode, cudaStream_t s);
+template <typename T>
+void launch_op_gemm2(const T* U, const T* B, int n_aux, int n_ov, int nr, const T* V, T* out, int mode,
+                     cudaStream_t s);
+
+// ---------------------------------------------------------------- CD kernels (kernels_cd.cu)
+void launch_sigma_x(const double* B_nm, int n_t, int n_bas, int n_aux, int n_occ, double* sx, cudaStream_t s);
+
+// I term (eq. "inn") with optional static subtraction, per target t at omega[t].
+void launch_sigma_imag(const double* W, int n_t, int n_bas, int n_g, const double* eps, const double* xi,
+                       const double* wt, const double* omega, int static_sub, double* I, double* dI,
+                       const unsigned char* active, cudaStream_t s);
+
+struct MinresState {
+  double beta, c2, s2, c1, s1, phibar, beta1, pad;
+  int iters, done, pad0, pad1;
+};
+
+// Gather b_j = B_nm[t_j][m_j] into V as (u, v) = (b, 0); T is the operator precision.
+template <typename T>
+void launch_gather_rhs(const double* B_nm, int n_bas, int n_aux, const int* rhs_t, const int* rhs_m, int nr, T* V,
+                       cudaStream_t s);
+// From S = [Re; Im](Pi b): initialise MINRES (v_1 = rhs/|rhs|) and write v_1 into V.
+template <typename T>
+void launch_minres_init(const T* S, int nr, int n_aux, double* vprev, double* v, double* d1, double* d2, double* x,
+                        MinresState* st, T* V, cudaStream_t s);
+// One MINRES step given P = E v (embedding matvec output).  Writes the next Lanczos vector into V.
+template <typename T>
+void launch_minres_step(const T* P, int nr, int n_aux, double tol, double* vprev, double* v, double* d1, double* d2,
+                        double* x, MinresState* st, T* V, int* n_active, cudaStream_t s);
+// After MINRES: W = b^T delta; y = b + delta written into V as (u, v) = (y_r, -y_i) for the derivative pass.
+template <typename T>
+void launch_minres_finish(const double* B_nm, int n_bas, int n_aux, const int* rhs_t, const int* rhs_m, int nr,
+                          const double* x, const MinresState* st, double* w_re, double* w_im, int* iters,
+                          double* resnorm, T* V, cudaStream_t s);
+// dW_j = sum_k U[2j][k] + i U[2j+1][k] (derivative pass output); writes Re into dw_re.
+template <typename T>
+void launch_rowsum_pairs(const T* U, int nr, int n_ov, double* dw_re, double* dw_im, cudaStream_t s);
+
+// Dense fallback: solve (Ar + i Ai) y = b for one right-hand side by complex Gaussian elimination
+// with partial pivoting (single CTA), then W = b^T (y - b), dW = y^T Pi'(x) y.
+void launch_dense_residue(double* Ar, double* Ai, int n, const double* b, double* work, double* result,
+                          int* info, cudaStream_t s);
+
+// R term reduction per target over its right-hand sides [start[t], start[t+1]).
+void launch_residue_reduce(const int* start, int n_t, const double* coef, const double* w_re, const double* dw_re,
+                           double* R, double* dR, cudaStream_t s);
+
+struct QPState {
+  double omega, f_prev, omega_prev, Z;
+  double a, fa, b, fb, x, fx;
+  double sigma, dsigma;
+  int br_kind, has_prev, iter, status;   // status: 0 running, 1 converged, 2 not converged
+};
+void launch_qp_init(QPState* st, const double* e_n, int n, cudaStream_t s);
+// sigma = R - I, dsigma = dR - dI for active states, then one step-tree step.
+void launch_qp_step(QPState* st, const double* R, const double* dR, const double* I, const double* dI,
+                    const double* e_n, const double* shift, double tol, int maxit, int n, int linearised,
+                    cudaStream_t s);
+
+}  // namespace gw

@@ -1,0 +1,774 @@
+// C ABI of libgw (include/gw.h): plan lifetime, device memory, and the host-side orchestration of
+// Algorithm 1 (imaginary-axis screening, then the per-state QP loop with batched residue solves).
+#include "gw.h"
+#include "gw_internal.cuh"
+#include "pi_tc.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using gw::MinresState;
+using gw::QPState;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct gw_plan {
+  gw_config cfg{};
+  int n_bas = 0, n_ov = 0, n_t = 0, n_g = 0;
+  unsigned flags = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<double> h_eps, h_xi, h_wt, h_shift, h_sx, h_en;
+  std::vector<int> h_targets;
+  double* d_eps = nullptr;
+  double* d_B_ia = nullptr;
+  double* d_B_nm = nullptr;
+  bool own_B = true;
+  double* d_xi = nullptr;     // [n_g + 1], last entry 0 (static point)
+  double* d_wt = nullptr;     // [n_g]
+  double* d_sx = nullptr;
+  double* d_shift = nullptr;
+  double* d_en = nullptr;
+  double* d_W = nullptr;      // [n_t][n_bas][n_g + 1]
+  float* d_B_ia_f = nullptr;  // mixed: FP32 copy of B_ia
+  float* d_B_nm_f = nullptr;  // mixed: FP32 copy of B_nm
+  bool screening_done = false;
+  std::vector<DevBuf*> bufs;
+  DevBuf ws_mat, ws_info, ws_scratch, ws_gout, ws_tc, ws_xi;
+  DevBuf mr_V, mr_U, mr_S, mr_vprev, mr_v, mr_d1, mr_d2, mr_x, mr_st, mr_rt, mr_rm, mr_xf, mr_wre, mr_wim,
+      mr_dwre, mr_it, mr_res, mr_cnt;
+  DevBuf sg_I, sg_dI, sg_R, sg_dR, sg_om, sg_start, sg_coef, sg_act, qp_st;
+  DevBuf fb_Ar, fb_Ai, fb_work, fb_res, fb_info;
+  int* h_cnt = nullptr;       // pinned
+  std::string err;
+  gw_stats stats{};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+
+  gw_plan() {
+    DevBuf* all[] = {&ws_mat, &ws_info, &ws_scratch, &ws_gout, &ws_tc, &ws_xi, &mr_V, &mr_U, &mr_S, &mr_vprev,
+                     &mr_v, &mr_d1, &mr_d2, &mr_x, &mr_st, &mr_rt, &mr_rm, &mr_xf, &mr_wre, &mr_wim,
+                     &mr_dwre, &mr_it, &mr_res, &mr_cnt, &sg_I, &sg_dI, &sg_R, &sg_dR, &sg_om, &sg_start,
+                     &sg_coef, &sg_act, &qp_st, &fb_Ar, &fb_Ai, &fb_work, &fb_res, &fb_info};
+    bufs.assign(all, all + sizeof(all) / sizeof(all[0]));
+  }
+};
+
+namespace {
+
+gw_status fail(gw_plan* p, gw_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (p) p->err = buf; else g_create_error = buf;
+  return st;
+}
+
+#define CK(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) {                                                                       \
+      if (e_ == cudaErrorMemoryAllocation) { cudaGetLastError(); return fail(P, GW_ERR_OOM, "%s: %s", #call, cudaGetErrorString(e_)); } \
+      return fail(P, GW_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));                        \
+    }                                                                                              \
+  } while (0)
+
+#define LAUNCH(expr)                                                                               \
+  do {                                                                                             \
+    expr;                                                                                          \
+    P->stats.n_kernel_launches++;                                                                  \
+    cudaError_t e_ = cudaGetLastError();                                                           \
+    if (e_ != cudaSuccess) return fail(P, GW_ERR_CUDA, "launch %s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+#define TRY(call)                                                                                  \
+  do {                                                                                             \
+    gw_status s_ = (call);                                                                         \
+    if (s_ != GW_OK) return s_;                                                                    \
+  } while (0)
+
+gw_status ensure(gw_plan* P, DevBuf& b, size_t bytes) {
+  if (b.bytes >= bytes && b.p) return GW_OK;
+  if (b.p) {
+    CK(cudaStreamSynchronize(P->stream));
+    cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  if (bytes == 0) bytes = 16;
+  CK(cudaMalloc(&b.p, bytes));
+  b.bytes = bytes;
+  return GW_OK;
+}
+
+template <typename T>
+T* as(DevBuf& b) { return reinterpret_cast<T*>(b.p); }
+
+double now_ms(gw_plan* P, cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  return (double)ms;
+}
+
+// ---------------------------------------------------------------- imaginary-axis screening
+template <typename T>
+gw_status screening_T(gw_plan* P, const T* B, const T* Bn) {
+  const int n = P->cfg.n_aux;
+  const int n_g1 = P->n_g + 1;
+  const int R = P->n_t * P->n_bas;
+  // chunk of frequency matrices held at once: <= 8 GiB and <= n_g1
+  const size_t per = (size_t)n * n * sizeof(T);
+  int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_g1, ((size_t)8 << 30) / per));
+  TRY(ensure(P, P->ws_mat, per * chunk));
+  TRY(ensure(P, P->ws_info, sizeof(int) * chunk));
+  TRY(ensure(P, P->ws_gout, sizeof(int) * n_g1));
+  const int n_cta = gw::trsm_w_default_ctas();
+  TRY(ensure(P, P->ws_scratch, sizeof(T) * gw::trsm_w_scratch_elems<T>(n, n_cta)));
+  std::vector<int> gout(n_g1);
+  for (int g = 0; g < n_g1; ++g) gout[g] = g;
+  CK(cudaMemcpyAsync(P->ws_gout.p, gout.data(), sizeof(int) * n_g1, cudaMemcpyHostToDevice, P->stream));
+  std::vector<int> info(chunk);
+  double ms_pi = 0.0;
+  for (int g0 = 0; g0 < n_g1; g0 += chunk) {
+    const int nc = std::min(chunk, n_g1 - g0);
+    CK(cudaEventRecord(P->ev0, P->stream));
+    bool tc = false;
+    if (P->cfg.precision == GW_PREC_MIXED && sizeof(T) == 4) {
+      gw_status st = gw::pi_tc_build(P->d_B_ia_f, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, P->d_xi + g0, nc,
+                                     reinterpret_cast<float*>(P->ws_mat.p), 1, &P->ws_tc.p, &P->ws_tc.bytes,
+                                     P->stream, &tc);
+      if (st != GW_OK) return fail(P, st, "tensor-core Pi build failed");
+      if (tc) P->stats.n_kernel_launches += 2;
+    }
+    if (!tc) {
+      LAUNCH(gw::launch_pi_syrk<T>(B, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, P->d_xi + g0, nc,
+                                   as<T>(P->ws_mat), 1, P->stream));
+    }
+    CK(cudaEventRecord(P->ev1, P->stream));
+    LAUNCH(gw::launch_cholesky<T>(as<T>(P->ws_mat), n, (long)n * n, nc, as<int>(P->ws_info), P->stream));
+    LAUNCH(gw::launch_trsm_w<T>(as<T>(P->ws_mat), (long)n * n, n, nc, as<int>(P->ws_gout) + g0, Bn, R, P->d_W,
+                                n_g1, as<T>(P->ws_scratch), n_cta, P->stream));
+    CK(cudaMemcpyAsync(info.data(), P->ws_info.p, sizeof(int) * nc, cudaMemcpyDeviceToHost, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+    ms_pi += now_ms(P, P->ev0, P->ev1);
+    for (int i = 0; i < nc; ++i)
+      if (info[i] != 0)
+        return fail(P, GW_ERR_NUMERIC, "Cholesky of eps(i xi) failed at frequency %d, pivot %d", g0 + i, info[i]);
+  }
+  P->stats.ms_pi = ms_pi;
+  return GW_OK;
+}
+
+gw_status ensure_screening(gw_plan* P) {
+  if (P->screening_done) return GW_OK;
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  CK(cudaEventRecord(a, P->stream));
+  gw_status st;
+  if (P->cfg.precision == GW_PREC_MIXED)
+    st = screening_T<float>(P, P->d_B_ia_f, P->d_B_nm_f);
+  else
+    st = screening_T<double>(P, P->d_B_ia, P->d_B_nm);
+  if (st != GW_OK) { cudaEventDestroy(a); cudaEventDestroy(b); return st; }
+  CK(cudaEventRecord(b, P->stream));
+  CK(cudaEventSynchronize(b));
+  P->stats.ms_screening = now_ms(P, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  P->screening_done = true;
+  return GW_OK;
+}
+
+// ---------------------------------------------------------------- batched residue solves
+// Device arrays in: rt, rm (target index, state), xf (frequency); out: w_re, w_im, dw_re, iters, resnorm.
+template <typename T>
+gw_status residues_T(gw_plan* P, int nr_total, const int* d_rt, const int* d_rm, const double* d_xf, double* w_re,
+                     double* w_im, double* dw_re, int* iters, double* resnorm, int* h_fallback) {
+  const T* B = (sizeof(T) == 8) ? reinterpret_cast<const T*>(P->d_B_ia) : reinterpret_cast<const T*>(P->d_B_ia_f);
+  const int n = P->cfg.n_aux, n_ov = P->n_ov;
+  int batch = P->cfg.max_rhs_batch;
+  if (batch <= 0) {
+    // keep the U buffer (2 batch x n_ov) within ~4 GiB
+    size_t cap = ((size_t)4 << 30) / ((size_t)2 * n_ov * sizeof(T));
+    batch = (int)std::max<size_t>(1, std::min<size_t>(cap, 2048));
+  }
+  batch = std::min(batch, std::max(1, nr_total));
+  TRY(ensure(P, P->mr_V, sizeof(T) * 2 * (size_t)batch * n));
+  TRY(ensure(P, P->mr_S, sizeof(T) * 2 * (size_t)batch * n));
+  TRY(ensure(P, P->mr_U, sizeof(T) * 2 * (size_t)batch * n_ov));
+  for (DevBuf* b : {&P->mr_vprev, &P->mr_v, &P->mr_d1, &P->mr_d2, &P->mr_x})
+    TRY(ensure(P, *b, sizeof(double) * 2 * (size_t)batch * n));
+  TRY(ensure(P, P->mr_st, sizeof(MinresState) * batch));
+  TRY(ensure(P, P->mr_cnt, sizeof(int)));
+  const double eta = P->cfg.eta;
+  std::vector<double> h_res;
+  for (int j0 = 0; j0 < nr_total; j0 += batch) {
+    const int nr = std::min(batch, nr_total - j0);
+    const int* rt = d_rt + j0;
+    const int* rm = d_rm + j0;
+    const double* xf = d_xf + j0;
+    LAUNCH(gw::launch_gather_rhs<T>(P->d_B_nm, P->n_bas, n, rt, rm, nr, as<T>(P->mr_V), P->stream));
+    // rhs = Pi(x) b
+    LAUNCH(gw::launch_op_gemm1<T>(as<T>(P->mr_V), B, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, xf, eta, nr,
+                                  as<T>(P->mr_U), 0, P->stream));
+    LAUNCH(gw::launch_op_gemm2<T>(as<T>(P->mr_U), B, n, n_ov, nr, as<T>(P->mr_V), as<T>(P->mr_S), 0, P->stream));
+    LAUNCH(gw::launch_minres_init<T>(as<T>(P->mr_S), nr, n, as<double>(P->mr_vprev), as<double>(P->mr_v),
+                                     as<double>(P->mr_d1), as<double>(P->mr_d2), as<double>(P->mr_x),
+                                     as<MinresState>(P->mr_st), as<T>(P->mr_V), P->stream));
+    for (int it = 0; it < P->cfg.minres_maxit; ++it) {
+      LAUNCH(gw::launch_op_gemm1<T>(as<T>(P->mr_V), B, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, xf, eta, nr,
+                                    as<T>(P->mr_U), 0, P->stream));
+      LAUNCH(gw::launch_op_gemm2<T>(as<T>(P->mr_U), B, n, n_ov, nr, as<T>(P->mr_V), as<T>(P->mr_S), 1,
+                                    P->stream));
+      CK(cudaMemsetAsync(P->mr_cnt.p, 0, sizeof(int), P->stream));
+      LAUNCH(gw::launch_minres_step<T>(as<T>(P->mr_S), nr, n, P->cfg.minres_tol, as<double>(P->mr_vprev),
+                                       as<double>(P->mr_v), as<double>(P->mr_d1), as<double>(P->mr_d2),
+                                       as<double>(P->mr_x), as<MinresState>(P->mr_st), as<T>(P->mr_V),
+                                       as<int>(P->mr_cnt), P->stream));
+      CK(cudaMemcpyAsync(P->h_cnt, P->mr_cnt.p, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+      CK(cudaStreamSynchronize(P->stream));
+      if (*P->h_cnt == 0) break;
+    }
+    LAUNCH(gw::launch_minres_finish<T>(P->d_B_nm, P->n_bas, n, rt, rm, nr, as<double>(P->mr_x),
+                                       as<MinresState>(P->mr_st), w_re + j0, w_im + j0, iters + j0, resnorm + j0,
+                                       as<T>(P->mr_V), P->stream));
+    // dense fallback for right-hand sides above the fallback threshold (Sec. 3.3, MINRES defaults paragraph)
+    h_res.resize(nr);
+    CK(cudaMemcpyAsync(h_res.data(), resnorm + j0, sizeof(double) * nr, cudaMemcpyDeviceToHost, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+    std::vector<int> need;
+    for (int j = 0; j < nr; ++j) {
+      bool bad = !(h_res[j] <= P->cfg.minres_fallback_tol);
+      if (h_fallback) h_fallback[j0 + j] = bad ? 1 : 0;
+      if (bad) need.push_back(j);
+    }
+    if (!need.empty()) {
+      std::vector<int> ht(nr), hm(nr);
+      std::vector<double> hx(nr);
+      CK(cudaMemcpyAsync(ht.data(), rt, sizeof(int) * nr, cudaMemcpyDeviceToHost, P->stream));
+      CK(cudaMemcpyAsync(hm.data(), rm, sizeof(int) * nr, cudaMemcpyDeviceToHost, P->stream));
+      CK(cudaMemcpyAsync(hx.data(), xf, sizeof(double) * nr, cudaMemcpyDeviceToHost, P->stream));
+      TRY(ensure(P, P->fb_Ar, sizeof(double) * (size_t)n * n));
+      TRY(ensure(P, P->fb_Ai, sizeof(double) * (size_t)n * n));
+      TRY(ensure(P, P->fb_work, sizeof(double) * 2 * (size_t)n));
+      TRY(ensure(P, P->fb_res, sizeof(double) * 2));
+      TRY(ensure(P, P->fb_info, sizeof(int)));
+      CK(cudaStreamSynchronize(P->stream));
+      for (int j : need) {
+        const double* b = P->d_B_nm + ((size_t)ht[j] * P->n_bas + hm[j]) * n;
+        LAUNCH(gw::launch_pi_complex_dense(P->d_B_ia, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, hx[j], eta,
+                                           as<double>(P->fb_Ar), as<double>(P->fb_Ai), P->stream));
+        LAUNCH(gw::launch_dense_residue(as<double>(P->fb_Ar), as<double>(P->fb_Ai), n, b, as<double>(P->fb_work),
+                                        as<double>(P->fb_res), as<int>(P->fb_info), P->stream));
+        double res[2];
+        int info = 0;
+        std::vector<double> y(2 * (size_t)n);
+        CK(cudaMemcpyAsync(res, P->fb_res.p, sizeof(res), cudaMemcpyDeviceToHost, P->stream));
+        CK(cudaMemcpyAsync(&info, P->fb_info.p, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+        CK(cudaMemcpyAsync(y.data(), P->fb_work.p, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, P->stream));
+        CK(cudaStreamSynchronize(P->stream));
+        if (info != 0) return fail(P, GW_ERR_NUMERIC, "dense residue solve: singular pivot");
+        CK(cudaMemcpyAsync(w_re + j0 + j, &res[0], sizeof(double), cudaMemcpyHostToDevice, P->stream));
+        CK(cudaMemcpyAsync(w_im + j0 + j, &res[1], sizeof(double), cudaMemcpyHostToDevice, P->stream));
+        double zero = 0.0;
+        CK(cudaMemcpyAsync(resnorm + j0 + j, &zero, sizeof(double), cudaMemcpyHostToDevice, P->stream));
+        std::vector<T> yt(2 * (size_t)n);
+        for (size_t i = 0; i < yt.size(); ++i) yt[i] = (T)y[i];
+        CK(cudaMemcpyAsync(as<T>(P->mr_V) + (size_t)2 * j * n, yt.data(), sizeof(T) * 2 * n,
+                           cudaMemcpyHostToDevice, P->stream));
+        CK(cudaStreamSynchronize(P->stream));
+        P->stats.n_fallback++;
+      }
+    }
+    // dW/dx = y^T Pi'(x) y
+    LAUNCH(gw::launch_op_gemm1<T>(as<T>(P->mr_V), B, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, xf, eta, nr,
+                                  as<T>(P->mr_U), 1, P->stream));
+    LAUNCH(gw::launch_rowsum_pairs<T>(as<T>(P->mr_U), nr, n_ov, dw_re + j0, nullptr, P->stream));
+  }
+  return GW_OK;
+}
+
+gw_status residues(gw_plan* P, int nr, const int* d_rt, const int* d_rm, const double* d_xf, double* w_re,
+                   double* w_im, double* dw_re, int* iters, double* resnorm, int* h_fallback) {
+  if (nr <= 0) return GW_OK;
+  CK(cudaEventRecord(P->ev2, P->stream));
+  gw_status st = (P->cfg.precision == GW_PREC_MIXED)
+                     ? residues_T<float>(P, nr, d_rt, d_rm, d_xf, w_re, w_im, dw_re, iters, resnorm, h_fallback)
+                     : residues_T<double>(P, nr, d_rt, d_rm, d_xf, w_re, w_im, dw_re, iters, resnorm, h_fallback);
+  if (st != GW_OK) return st;
+  CK(cudaEventRecord(P->ev1, P->stream));
+  CK(cudaEventSynchronize(P->ev1));
+  P->stats.ms_residues += now_ms(P, P->ev2, P->ev1);
+  P->stats.n_rhs_solved += nr;
+  std::vector<int> it(nr);
+  CK(cudaMemcpy(it.data(), iters, sizeof(int) * nr, cudaMemcpyDeviceToHost));
+  for (int v : it) P->stats.n_minres_iters += v;
+  return GW_OK;
+}
+
+// Residues of eq. "rnn" at omega_t for the active targets: (t, m, x = e_m - omega_t, coef = sign * theta).
+void build_residue_list(gw_plan* P, const std::vector<double>& omega, const std::vector<unsigned char>& active,
+                        std::vector<int>& rt, std::vector<int>& rm, std::vector<double>& xf,
+                        std::vector<double>& coef, std::vector<int>& start) {
+  rt.clear(); rm.clear(); xf.clear(); coef.clear();
+  start.assign(P->n_t + 1, 0);
+  for (int t = 0; t < P->n_t; ++t) {
+    start[t] = (int)rt.size();
+    if (!active[t]) continue;
+    const double w = omega[t];
+    for (int m = 0; m < P->n_bas; ++m) {
+      const double e = P->h_eps[m];
+      double th;
+      double sg;
+      if (m < P->cfg.n_occ) {
+        th = (e > w) ? 1.0 : (e == w ? 0.5 : 0.0);
+        sg = -1.0;
+      } else {
+        th = (w > e) ? 1.0 : (w == e ? 0.5 : 0.0);
+        sg = 1.0;
+      }
+      if (th == 0.0) continue;
+      rt.push_back(t);
+      rm.push_back(m);
+      xf.push_back(e - w);
+      coef.push_back(sg * th);
+    }
+  }
+  start[P->n_t] = (int)rt.size();
+}
+
+// Sigma_c = R - I (and derivative) at omega for active targets, into sg_R/sg_dR/sg_I/sg_dI.
+gw_status sigma_eval(gw_plan* P, const std::vector<double>& omega, const std::vector<unsigned char>& active,
+                     int* n_fallback_out) {
+  const int n_t = P->n_t;
+  TRY(ensure(P, P->sg_I, sizeof(double) * n_t));
+  TRY(ensure(P, P->sg_dI, sizeof(double) * n_t));
+  TRY(ensure(P, P->sg_R, sizeof(double) * n_t));
+  TRY(ensure(P, P->sg_dR, sizeof(double) * n_t));
+  TRY(ensure(P, P->sg_om, sizeof(double) * n_t));
+  TRY(ensure(P, P->sg_act, n_t));
+  TRY(ensure(P, P->sg_start, sizeof(int) * (n_t + 1)));
+  CK(cudaMemcpyAsync(P->sg_om.p, omega.data(), sizeof(double) * n_t, cudaMemcpyHostToDevice, P->stream));
+  CK(cudaMemcpyAsync(P->sg_act.p, active.data(), n_t, cudaMemcpyHostToDevice, P->stream));
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  CK(cudaEventRecord(a, P->stream));
+  LAUNCH(gw::launch_sigma_imag(P->d_W, n_t, P->n_bas, P->n_g, P->d_eps, P->d_xi, P->d_wt, as<double>(P->sg_om),
+                               P->cfg.static_subtraction, as<double>(P->sg_I), as<double>(P->sg_dI),
+                               as<unsigned char>(P->sg_act), P->stream));
+  CK(cudaEventRecord(b, P->stream));
+  std::vector<int> rt, rm, start;
+  std::vector<double> xf, coef;
+  build_residue_list(P, omega, active, rt, rm, xf, coef, start);
+  const int nr = (int)rt.size();
+  TRY(ensure(P, P->mr_rt, sizeof(int) * std::max(1, nr)));
+  TRY(ensure(P, P->mr_rm, sizeof(int) * std::max(1, nr)));
+  TRY(ensure(P, P->mr_xf, sizeof(double) * std::max(1, nr)));
+  TRY(ensure(P, P->sg_coef, sizeof(double) * std::max(1, nr)));
+  TRY(ensure(P, P->mr_wre, sizeof(double) * std::max(1, nr)));
+  TRY(ensure(P, P->mr_wim, sizeof(double) * std::max(1, nr)));
+  TRY(ensure(P, P->mr_dwre, sizeof(double) * std::max(1, nr)));
+  TRY(ensure(P, P->mr_it, sizeof(int) * std::max(1, nr)));
+  TRY(ensure(P, P->mr_res, sizeof(double) * std::max(1, nr)));
+  if (nr > 0) {
+    CK(cudaMemcpyAsync(P->mr_rt.p, rt.data(), sizeof(int) * nr, cudaMemcpyHostToDevice, P->stream));
+    CK(cudaMemcpyAsync(P->mr_rm.p, rm.data(), sizeof(int) * nr, cudaMemcpyHostToDevice, P->stream));
+    CK(cudaMemcpyAsync(P->mr_xf.p, xf.data(), sizeof(double) * nr, cudaMemcpyHostToDevice, P->stream));
+    CK(cudaMemcpyAsync(P->sg_coef.p, coef.data(), sizeof(double) * nr, cudaMemcpyHostToDevice, P->stream));
+  }
+  CK(cudaMemcpyAsync(P->sg_start.p, start.data(), sizeof(int) * (n_t + 1), cudaMemcpyHostToDevice, P->stream));
+  std::vector<int> fb(std::max(1, nr), 0);
+  TRY(residues(P, nr, as<int>(P->mr_rt), as<int>(P->mr_rm), as<double>(P->mr_xf), as<double>(P->mr_wre),
+               as<double>(P->mr_wim), as<double>(P->mr_dwre), as<int>(P->mr_it), as<double>(P->mr_res), fb.data()));
+  LAUNCH(gw::launch_residue_reduce(as<int>(P->sg_start), n_t, as<double>(P->sg_coef), as<double>(P->mr_wre),
+                                   as<double>(P->mr_dwre), as<double>(P->sg_R), as<double>(P->sg_dR), P->stream));
+  CK(cudaStreamSynchronize(P->stream));
+  P->stats.ms_sigma_imag += now_ms(P, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  int nf = 0;
+  for (int j = 0; j < nr; ++j) nf += fb[j];
+  if (n_fallback_out) *n_fallback_out = nf;
+  for (int t = 0; t < n_t; ++t) P->stats.n_sigma_evals += active[t] ? 1 : 0;
+  return GW_OK;
+}
+
+__global__ void convert_f64_f32_kernel(const double* __restrict__ a, float* __restrict__ b, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+}  // namespace
+
+// ==================================================================== C ABI
+extern "C" {
+
+void gw_config_default(gw_config* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof(*c));
+  c->n_freq = 128;
+  c->x0 = 0.5;
+  c->eta = 1e-3;
+  c->precision = GW_PREC_FP64;
+  c->minres_maxit = 25;
+  c->minres_tol = 5e-5;
+  c->minres_fallback_tol = 1e-4;
+  c->qp_maxit = 50;
+  c->qp_tol = 1e-8;
+  c->static_subtraction = 1;
+  c->max_rhs_batch = 0;
+}
+
+static void free_plan(gw_plan* P) {
+  if (!P) return;
+  if (P->stream) cudaStreamSynchronize(P->stream);
+  for (DevBuf* b : P->bufs)
+    if (b->p) cudaFree(b->p);
+  double* owned[] = {P->d_eps, P->d_xi, P->d_wt, P->d_sx, P->d_shift, P->d_en, P->d_W};
+  for (double* p : owned)
+    if (p) cudaFree(p);
+  if (P->own_B) {
+    if (P->d_B_ia) cudaFree(P->d_B_ia);
+    if (P->d_B_nm) cudaFree(P->d_B_nm);
+  }
+  if (P->d_B_ia_f) cudaFree(P->d_B_ia_f);
+  if (P->d_B_nm_f) cudaFree(P->d_B_nm_f);
+  if (P->h_cnt) cudaFreeHost(P->h_cnt);
+  if (P->ev0) cudaEventDestroy(P->ev0);
+  if (P->ev1) cudaEventDestroy(P->ev1);
+  if (P->ev2) cudaEventDestroy(P->ev2);
+  if (P->own_stream && P->stream) cudaStreamDestroy(P->stream);
+  delete P;
+}
+
+static gw_status plan_create_impl(gw_plan* P, const gw_config* cfg, const double* eps, const double* B_ia,
+                                  const double* B_nm, const int* targets, int n_targets, const double* vxc,
+                                  const double* xi, const double* wt, unsigned flags, void* stream) {
+  P->cfg = *cfg;
+  P->flags = flags;
+  P->n_bas = cfg->n_occ + cfg->n_virt;
+  P->n_ov = cfg->n_occ * cfg->n_virt;
+  P->n_t = n_targets;
+  P->n_g = cfg->n_freq;
+  if (stream) {
+    P->stream = (cudaStream_t)stream;
+  } else {
+    CK(cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking));
+    P->own_stream = true;
+  }
+  CK(cudaEventCreate(&P->ev0));
+  CK(cudaEventCreate(&P->ev1));
+  CK(cudaEventCreate(&P->ev2));
+  CK(cudaMallocHost(&P->h_cnt, sizeof(int)));
+  const int n = cfg->n_aux;
+  P->h_eps.assign(eps, eps + P->n_bas);
+  P->h_targets.assign(targets, targets + n_targets);
+  // grid
+  P->h_xi.resize(P->n_g);
+  P->h_wt.resize(P->n_g);
+  if (xi && wt) {
+    for (int g = 0; g < P->n_g; ++g) { P->h_xi[g] = xi[g]; P->h_wt[g] = wt[g]; }
+  } else {
+    gw_grid(P->n_g, cfg->x0, P->h_xi.data(), P->h_wt.data());
+  }
+  std::vector<double> xi_all(P->h_xi);
+  xi_all.push_back(0.0);
+  CK(cudaMalloc(&P->d_eps, sizeof(double) * P->n_bas));
+  CK(cudaMalloc(&P->d_xi, sizeof(double) * (P->n_g + 1)));
+  CK(cudaMalloc(&P->d_wt, sizeof(double) * std::max(1, P->n_g)));
+  CK(cudaMalloc(&P->d_sx, sizeof(double) * std::max(1, n_targets)));
+  CK(cudaMalloc(&P->d_shift, sizeof(double) * std::max(1, n_targets)));
+  CK(cudaMalloc(&P->d_en, sizeof(double) * std::max(1, n_targets)));
+  CK(cudaMalloc(&P->d_W, sizeof(double) * (size_t)n_targets * P->n_bas * (P->n_g + 1)));
+  CK(cudaMemcpyAsync(P->d_eps, eps, sizeof(double) * P->n_bas, cudaMemcpyHostToDevice, P->stream));
+  CK(cudaMemcpyAsync(P->d_xi, xi_all.data(), sizeof(double) * (P->n_g + 1), cudaMemcpyHostToDevice, P->stream));
+  CK(cudaMemcpyAsync(P->d_wt, P->h_wt.data(), sizeof(double) * P->n_g, cudaMemcpyHostToDevice, P->stream));
+  const size_t nB = (size_t)n * P->n_ov, nBn = (size_t)n_targets * P->n_bas * n;
+  if (flags & GW_BORROW_DEVICE_PTRS) {
+    P->own_B = false;
+    P->d_B_ia = const_cast<double*>(B_ia);
+    P->d_B_nm = const_cast<double*>(B_nm);
+  } else {
+    P->own_B = true;
+    CK(cudaMalloc(&P->d_B_ia, sizeof(double) * nB));
+    CK(cudaMalloc(&P->d_B_nm, sizeof(double) * nBn));
+    cudaMemcpyKind kind = (flags & GW_INPUT_ON_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(P->d_B_ia, B_ia, sizeof(double) * nB, kind, P->stream));
+    CK(cudaMemcpyAsync(P->d_B_nm, B_nm, sizeof(double) * nBn, kind, P->stream));
+  }
+  if (cfg->precision == GW_PREC_MIXED) {
+    CK(cudaMalloc(&P->d_B_ia_f, sizeof(float) * nB));
+    CK(cudaMalloc(&P->d_B_nm_f, sizeof(float) * nBn));
+    LAUNCH((convert_f64_f32_kernel<<<1024, 256, 0, P->stream>>>(P->d_B_ia, P->d_B_ia_f, nB)));
+    LAUNCH((convert_f64_f32_kernel<<<1024, 256, 0, P->stream>>>(P->d_B_nm, P->d_B_nm_f, nBn)));
+  }
+  LAUNCH(gw::launch_sigma_x(P->d_B_nm, n_targets, P->n_bas, n, cfg->n_occ, P->d_sx, P->stream));
+  P->h_sx.resize(n_targets);
+  CK(cudaMemcpyAsync(P->h_sx.data(), P->d_sx, sizeof(double) * n_targets, cudaMemcpyDeviceToHost, P->stream));
+  CK(cudaStreamSynchronize(P->stream));
+  P->h_shift.resize(n_targets);
+  P->h_en.resize(n_targets);
+  for (int t = 0; t < n_targets; ++t) {
+    P->h_shift[t] = vxc ? P->h_sx[t] - vxc[t] : 0.0;
+    P->h_en[t] = eps[targets[t]];
+  }
+  CK(cudaMemcpyAsync(P->d_shift, P->h_shift.data(), sizeof(double) * n_targets, cudaMemcpyHostToDevice, P->stream));
+  CK(cudaMemcpyAsync(P->d_en, P->h_en.data(), sizeof(double) * n_targets, cudaMemcpyHostToDevice, P->stream));
+  CK(cudaStreamSynchronize(P->stream));
+  return GW_OK;
+}
+
+gw_status gw_plan_create(const gw_config* cfg, const double* eps, const double* B_ia, const double* B_nm,
+                         const int* targets, int n_targets, const double* vxc, const double* xi, const double* wt,
+                         unsigned flags, void* stream, gw_plan_t* out) {
+  gw_plan* P = nullptr;
+  if (!out) return fail(nullptr, GW_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!cfg || !eps || !B_ia || !B_nm || !targets) return fail(nullptr, GW_ERR_ARG, "NULL input pointer");
+  if (cfg->n_occ <= 0 || cfg->n_virt <= 0 || cfg->n_aux <= 0 || n_targets <= 0 || cfg->n_freq <= 0)
+    return fail(nullptr, GW_ERR_ARG, "sizes must be positive (n_occ %d n_virt %d n_aux %d n_targets %d n_freq %d)",
+                cfg->n_occ, cfg->n_virt, cfg->n_aux, n_targets, cfg->n_freq);
+  if ((long)cfg->n_occ * cfg->n_virt > 2147483647L) return fail(nullptr, GW_ERR_ARG, "n_occ*n_virt too large");
+  if (cfg->precision != GW_PREC_FP64 && cfg->precision != GW_PREC_MIXED)
+    return fail(nullptr, GW_ERR_ARG, "unknown precision %d", cfg->precision);
+  if ((xi == nullptr) != (wt == nullptr)) return fail(nullptr, GW_ERR_ARG, "xi and wt must both be given or both NULL");
+  if (!(cfg->x0 > 0.0) && !xi) return fail(nullptr, GW_ERR_ARG, "x0 must be positive");
+  if (!(cfg->eta >= 0.0)) return fail(nullptr, GW_ERR_ARG, "eta must be >= 0");
+  if (cfg->minres_maxit < 0 || cfg->qp_maxit <= 0) return fail(nullptr, GW_ERR_ARG, "bad iteration caps");
+  const int n_bas = cfg->n_occ + cfg->n_virt;
+  for (int i = 0; i < n_bas; ++i) {
+    if (!std::isfinite(eps[i])) return fail(nullptr, GW_ERR_ARG, "eps[%d] is not finite", i);
+    if (i > 0 && eps[i] < eps[i - 1]) return fail(nullptr, GW_ERR_ARG, "eps must be ascending (index %d)", i);
+  }
+  if (eps[cfg->n_occ] <= eps[cfg->n_occ - 1]) return fail(nullptr, GW_ERR_ARG, "no gap between HOMO and LUMO");
+  for (int t = 0; t < n_targets; ++t)
+    if (targets[t] < 0 || targets[t] >= n_bas) return fail(nullptr, GW_ERR_ARG, "target %d out of range", targets[t]);
+  if ((flags & GW_BORROW_DEVICE_PTRS) && cfg->precision == GW_PREC_MIXED) {
+    // the FP32 copies are made from the borrowed FP64 arrays; fine
+  }
+  P = new (std::nothrow) gw_plan();
+  if (!P) return fail(nullptr, GW_ERR_OOM, "host allocation failed");
+  gw_status st = plan_create_impl(P, cfg, eps, B_ia, B_nm, targets, n_targets, vxc, xi, wt, flags, stream);
+  if (st != GW_OK) {
+    g_create_error = P->err;
+    free_plan(P);
+    return st;
+  }
+  *out = P;
+  return GW_OK;
+}
+
+gw_status gw_polarizability(gw_plan_t P, const double* xi, int n_xi, double* pi_out) {
+  if (!P) return GW_ERR_ARG;
+  if (!xi) {
+    if (pi_out) return fail(P, GW_ERR_ARG, "pi_out must be NULL when building the plan grid");
+    return ensure_screening(P);
+  }
+  if (n_xi <= 0) return fail(P, GW_ERR_ARG, "n_xi must be positive");
+  const int n = P->cfg.n_aux;
+  DevBuf& dxi = P->ws_xi;
+  gw_status st = ensure(P, dxi, sizeof(double) * n_xi);
+  if (st != GW_OK) return st;
+  CK(cudaMemcpyAsync(dxi.p, xi, sizeof(double) * n_xi, cudaMemcpyHostToDevice, P->stream));
+  CK(cudaEventRecord(P->ev0, P->stream));
+  if (P->cfg.precision == GW_PREC_MIXED) {
+    TRY(ensure(P, P->ws_mat, sizeof(float) * (size_t)n * n * n_xi));
+    bool tc = false;
+    st = gw::pi_tc_build(P->d_B_ia_f, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, as<double>(dxi), n_xi,
+                         as<float>(P->ws_mat), 0, &P->ws_tc.p, &P->ws_tc.bytes, P->stream, &tc);
+    if (st != GW_OK) return fail(P, st, "tensor-core Pi build failed");
+    if (!tc)
+      LAUNCH(gw::launch_pi_syrk<float>(P->d_B_ia_f, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, as<double>(dxi), n_xi,
+                                       as<float>(P->ws_mat), 0, P->stream));
+    else
+      P->stats.n_kernel_launches += 2;
+    CK(cudaEventRecord(P->ev1, P->stream));
+    if (pi_out) {
+      std::vector<float> h((size_t)n * n * n_xi);
+      CK(cudaMemcpyAsync(h.data(), P->ws_mat.p, sizeof(float) * h.size(), cudaMemcpyDeviceToHost, P->stream));
+      CK(cudaStreamSynchronize(P->stream));
+      for (size_t i = 0; i < h.size(); ++i) pi_out[i] = h[i];
+    }
+  } else {
+    TRY(ensure(P, P->ws_mat, sizeof(double) * (size_t)n * n * n_xi));
+    LAUNCH(gw::launch_pi_syrk<double>(P->d_B_ia, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, as<double>(dxi), n_xi,
+                                      as<double>(P->ws_mat), 0, P->stream));
+    CK(cudaEventRecord(P->ev1, P->stream));
+    if (pi_out)
+      CK(cudaMemcpyAsync(pi_out, P->ws_mat.p, sizeof(double) * (size_t)n * n * n_xi, cudaMemcpyDeviceToHost,
+                         P->stream));
+  }
+  CK(cudaStreamSynchronize(P->stream));
+  P->stats.ms_pi = now_ms(P, P->ev0, P->ev1);
+  return GW_OK;
+}
+
+gw_status gw_sigma_cd(gw_plan_t P, const double* omega, double* sigma_c, double* dsigma_c, double* sigma_x) {
+  if (!P || !omega) return P ? fail(P, GW_ERR_ARG, "omega is NULL") : GW_ERR_ARG;
+  TRY(ensure_screening(P));
+  const int n_t = P->n_t;
+  std::vector<double> om(omega, omega + n_t);
+  std::vector<unsigned char> act(n_t, 1);
+  int nf = 0;
+  TRY(sigma_eval(P, om, act, &nf));
+  std::vector<double> R(n_t), dR(n_t), I(n_t), dI(n_t);
+  CK(cudaMemcpy(R.data(), P->sg_R.p, sizeof(double) * n_t, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(dR.data(), P->sg_dR.p, sizeof(double) * n_t, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(I.data(), P->sg_I.p, sizeof(double) * n_t, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(dI.data(), P->sg_dI.p, sizeof(double) * n_t, cudaMemcpyDeviceToHost));
+  for (int t = 0; t < n_t; ++t) {
+    if (sigma_c) sigma_c[t] = R[t] - I[t];
+    if (dsigma_c) dsigma_c[t] = dR[t] - dI[t];
+    if (sigma_x) sigma_x[t] = P->h_sx[t];
+  }
+  return GW_OK;
+}
+
+gw_status gw_residues_minres(gw_plan_t P, int n_rhs, const int* target_idx, const int* m, const double* x,
+                             double* w_re, double* w_im, double* dw_re, int* iters, double* resnorm,
+                             int* used_fallback) {
+  if (!P) return GW_ERR_ARG;
+  if (n_rhs < 0 || (n_rhs > 0 && (!target_idx || !m || !x))) return fail(P, GW_ERR_ARG, "bad right-hand side list");
+  if (n_rhs == 0) return GW_OK;
+  for (int j = 0; j < n_rhs; ++j) {
+    if (target_idx[j] < 0 || target_idx[j] >= P->n_t) return fail(P, GW_ERR_ARG, "target_idx[%d] out of range", j);
+    if (m[j] < 0 || m[j] >= P->n_bas) return fail(P, GW_ERR_ARG, "m[%d] out of range", j);
+    if (!std::isfinite(x[j])) return fail(P, GW_ERR_ARG, "x[%d] not finite", j);
+  }
+  TRY(ensure(P, P->mr_rt, sizeof(int) * n_rhs));
+  TRY(ensure(P, P->mr_rm, sizeof(int) * n_rhs));
+  TRY(ensure(P, P->mr_xf, sizeof(double) * n_rhs));
+  TRY(ensure(P, P->mr_wre, sizeof(double) * n_rhs));
+  TRY(ensure(P, P->mr_wim, sizeof(double) * n_rhs));
+  TRY(ensure(P, P->mr_dwre, sizeof(double) * n_rhs));
+  TRY(ensure(P, P->mr_it, sizeof(int) * n_rhs));
+  TRY(ensure(P, P->mr_res, sizeof(double) * n_rhs));
+  CK(cudaMemcpyAsync(P->mr_rt.p, target_idx, sizeof(int) * n_rhs, cudaMemcpyHostToDevice, P->stream));
+  CK(cudaMemcpyAsync(P->mr_rm.p, m, sizeof(int) * n_rhs, cudaMemcpyHostToDevice, P->stream));
+  CK(cudaMemcpyAsync(P->mr_xf.p, x, sizeof(double) * n_rhs, cudaMemcpyHostToDevice, P->stream));
+  std::vector<int> fb(n_rhs, 0);
+  TRY(residues(P, n_rhs, as<int>(P->mr_rt), as<int>(P->mr_rm), as<double>(P->mr_xf), as<double>(P->mr_wre),
+               as<double>(P->mr_wim), as<double>(P->mr_dwre), as<int>(P->mr_it), as<double>(P->mr_res), fb.data()));
+  if (w_re) CK(cudaMemcpy(w_re, P->mr_wre.p, sizeof(double) * n_rhs, cudaMemcpyDeviceToHost));
+  if (w_im) CK(cudaMemcpy(w_im, P->mr_wim.p, sizeof(double) * n_rhs, cudaMemcpyDeviceToHost));
+  if (dw_re) CK(cudaMemcpy(dw_re, P->mr_dwre.p, sizeof(double) * n_rhs, cudaMemcpyDeviceToHost));
+  if (iters) CK(cudaMemcpy(iters, P->mr_it.p, sizeof(int) * n_rhs, cudaMemcpyDeviceToHost));
+  if (resnorm) CK(cudaMemcpy(resnorm, P->mr_res.p, sizeof(double) * n_rhs, cudaMemcpyDeviceToHost));
+  if (used_fallback) std::memcpy(used_fallback, fb.data(), sizeof(int) * n_rhs);
+  return GW_OK;
+}
+
+gw_status gw_qp_solve(gw_plan_t P, gw_qp_mode mode, double* e_qp, double* z_factor, int* state_status) {
+  if (!P) return GW_ERR_ARG;
+  if (mode != GW_QP_LINEARISED && mode != GW_QP_STEPTREE) return fail(P, GW_ERR_ARG, "unknown QP mode %d", (int)mode);
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  CK(cudaEventRecord(a, P->stream));
+  TRY(ensure_screening(P));
+  const int n_t = P->n_t;
+  TRY(ensure(P, P->qp_st, sizeof(QPState) * n_t));
+  LAUNCH(gw::launch_qp_init(as<QPState>(P->qp_st), P->d_en, n_t, P->stream));
+  std::vector<QPState> hs(n_t);
+  std::vector<double> om(n_t);
+  std::vector<unsigned char> act(n_t);
+  std::vector<int> any_fb(n_t, 0);
+  const int lin = (mode == GW_QP_LINEARISED) ? 1 : 0;
+  const int maxit = lin ? 1 : P->cfg.qp_maxit;
+  for (int it = 0; it < maxit; ++it) {
+    CK(cudaMemcpyAsync(hs.data(), P->qp_st.p, sizeof(QPState) * n_t, cudaMemcpyDeviceToHost, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+    int n_act = 0;
+    for (int t = 0; t < n_t; ++t) {
+      om[t] = hs[t].omega;
+      act[t] = hs[t].status == 0 ? 1 : 0;
+      n_act += act[t];
+    }
+    if (n_act == 0) break;
+    int nf = 0;
+    TRY(sigma_eval(P, om, act, &nf));
+    if (nf > 0)
+      for (int t = 0; t < n_t; ++t)
+        if (act[t]) any_fb[t] = 1;   // conservative: flag the active states of an evaluation that fell back
+    LAUNCH(gw::launch_qp_step(as<QPState>(P->qp_st), as<double>(P->sg_R), as<double>(P->sg_dR),
+                              as<double>(P->sg_I), as<double>(P->sg_dI), P->d_en, P->d_shift, P->cfg.qp_tol,
+                              P->cfg.qp_maxit, n_t, lin, P->stream));
+  }
+  CK(cudaMemcpyAsync(hs.data(), P->qp_st.p, sizeof(QPState) * n_t, cudaMemcpyDeviceToHost, P->stream));
+  CK(cudaEventRecord(b, P->stream));
+  CK(cudaStreamSynchronize(P->stream));
+  P->stats.ms_qp = now_ms(P, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  bool all_ok = true;
+  for (int t = 0; t < n_t; ++t) {
+    if (e_qp) e_qp[t] = hs[t].omega;
+    if (z_factor) z_factor[t] = hs[t].Z;
+    int s = hs[t].status == 1 ? (any_fb[t] ? 2 : 0) : 1;
+    if (hs[t].status != 1) all_ok = false;
+    if (state_status) state_status[t] = s;
+  }
+  return all_ok ? GW_OK : GW_ERR_NOT_CONVERGED;
+}
+
+gw_status gw_grid(int N, double x0, double* xi, double* wt) {
+  if (N <= 0 || !(x0 > 0.0) || !xi || !wt) return GW_ERR_ARG;
+  // P_N(t) and P_N'(t) by the three-term recurrence
+  auto legendre = [N](double t, double* dp) {
+    double p0 = 1.0, p1 = t;
+    for (int l = 2; l <= N; ++l) {
+      double p2 = ((2.0 * l - 1.0) * t * p1 - (l - 1.0) * p0) / l;
+      p0 = p1;
+      p1 = p2;
+    }
+    *dp = N * (t * p1 - p0) / (t * t - 1.0);
+    return p1;
+  };
+  for (int k = 0; k < N; ++k) {
+    double t = -std::cos(M_PI * (k + 0.75) / (N + 0.5));   // Newton from the asymptotic node estimate
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p = legendre(t, &dp);
+      double dt = p / dp;
+      t -= dt;
+      if (std::fabs(dt) < 1e-16) break;
+    }
+    legendre(t, &dp);
+    double wgl = 2.0 / ((1.0 - t * t) * dp * dp);
+    xi[k] = x0 * (1.0 + t) / (1.0 - t);
+    wt[k] = 2.0 * x0 * wgl / ((1.0 - t) * (1.0 - t));
+  }
+  return GW_OK;
+}
+
+gw_status gw_get_stats(gw_plan_t P, gw_stats* out) {
+  if (!P || !out) return GW_ERR_ARG;
+  *out = P->stats;
+  return GW_OK;
+}
+
+void gw_plan_destroy(gw_plan_t P) { free_plan(P); }
+
+const char* gw_last_error(gw_plan_t P) {
+  if (!P) return g_create_error.c_str();
+  return P->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,537 @@
+// Contour-deformation kernels: exchange self-energy, the imaginary-axis quadrature (eq. "inn"),
+// batched MINRES recurrences for the residue systems (eq. "rnn", Sec. 3.3), the dense fallback
+// solve, and the step-tree QP search (Sec. 3.4, Fig. "steptree").  All arithmetic here is FP64.
+#include "gw_internal.cuh"
+
+#include <cmath>
+
+namespace gw {
+
+namespace {
+
+constexpr int RT = 256;   // threads for per-vector kernels
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum; every thread receives the total.  `buf` holds >= 32 doubles.
+__device__ double block_sum(double v, double* buf) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) buf[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < nw; ++w) t += buf[w];
+  return t;
+}
+
+// Sigma_x_nn = -sum_{m < n_occ} sum_P B_nm[t][m][P]^2  (Algorithm 1, Init)
+__global__ void sigma_x_kernel(const double* __restrict__ B_nm, int n_bas, int n_aux, int n_occ,
+                               double* __restrict__ sx) {
+  __shared__ double buf[32];
+  const double* b = B_nm + (long)blockIdx.x * n_bas * n_aux;
+  double acc = 0.0;
+  for (long i = threadIdx.x; i < (long)n_occ * n_aux; i += blockDim.x) acc += b[i] * b[i];
+  acc = block_sum(acc, buf);
+  if (threadIdx.x == 0) sx[blockIdx.x] = -acc;
+}
+
+// I_nn(omega) = sum_m [(1/pi) sum_g w_g (W_g - W_0) a/(a^2 + xi_g^2) + W_0 sgn(a)/2], a = omega - e_m,
+// and dI/domega = (1/pi) sum_m sum_g w_g (W_g - W_0)(xi_g^2 - a^2)/(a^2 + xi_g^2)^2.
+// W layout: [t][m][g], g in [0, n_g) the grid, g = n_g the static point xi = 0.
+__global__ void sigma_imag_kernel(const double* __restrict__ W, int n_bas, int n_g, const double* __restrict__ eps,
+                                  const double* __restrict__ xi, const double* __restrict__ wt,
+                                  const double* __restrict__ omega, int static_sub, double* __restrict__ I,
+                                  double* __restrict__ dI, const unsigned char* __restrict__ active) {
+  __shared__ double buf[32];
+  const int t = blockIdx.x;
+  if (active && !active[t]) return;
+  const double w0 = omega[t];
+  const int ld = n_g + 1;
+  double si = 0.0, sd = 0.0, sj = 0.0;
+  // one warp per state m, lanes over grid points
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int m = wid; m < n_bas; m += nw) {
+    const double a = w0 - eps[m];
+    const double* Wm = W + ((long)t * n_bas + m) * ld;
+    const double Ws = static_sub ? Wm[n_g] : 0.0;
+    double pi_acc = 0.0, pd_acc = 0.0;
+    for (int g = lane; g < n_g; g += 32) {
+      double x2 = xi[g] * xi[g];
+      double den = a * a + x2;
+      double dW = Wm[g] - Ws;
+      pi_acc += wt[g] * dW * a / den;
+      pd_acc += wt[g] * dW * (x2 - a * a) / (den * den);
+    }
+    si += pi_acc;
+    sd += pd_acc;
+    if (lane == 0 && static_sub) sj += Ws * (a > 0.0 ? 0.5 : (a < 0.0 ? -0.5 : 0.0));
+  }
+  si = block_sum(si, buf);
+  sd = block_sum(sd, buf);
+  sj = block_sum(sj, buf);
+  if (threadIdx.x == 0) {
+    I[t] = si / M_PI + sj;
+    dI[t] = sd / M_PI;
+  }
+}
+
+template <typename T>
+__global__ void gather_rhs_kernel(const double* __restrict__ B_nm, int n_bas, int n_aux, const int* __restrict__ rt,
+                                  const int* __restrict__ rm, T* __restrict__ V) {
+  const int j = blockIdx.x;
+  const double* b = B_nm + ((long)rt[j] * n_bas + rm[j]) * n_aux;
+  T* u = V + (long)(2 * j) * n_aux;
+  for (int i = threadIdx.x; i < n_aux; i += blockDim.x) {
+    u[i] = (T)b[i];
+    u[n_aux + i] = T(0);
+  }
+}
+
+template <typename T>
+__global__ void minres_init_kernel(const T* __restrict__ S, int n_aux, double* vprev, double* v, double* d1,
+                                   double* d2, double* x, MinresState* st, T* V) {
+  __shared__ double buf[32];
+  const int j = blockIdx.x;
+  const long n2 = 2L * n_aux, off = (long)j * n2;
+  double acc = 0.0;
+  for (long i = threadIdx.x; i < n2; i += blockDim.x) {
+    double r = (double)S[off + i];
+    acc += r * r;
+  }
+  const double beta1 = sqrt(block_sum(acc, buf));
+  const double inv = beta1 > 0.0 ? 1.0 / beta1 : 0.0;
+  for (long i = threadIdx.x; i < n2; i += blockDim.x) {
+    double vi = (double)S[off + i] * inv;
+    v[off + i] = vi;
+    vprev[off + i] = 0.0;
+    d1[off + i] = 0.0;
+    d2[off + i] = 0.0;
+    x[off + i] = 0.0;
+    V[off + i] = (T)vi;
+  }
+  if (threadIdx.x == 0) {
+    MinresState s;
+    s.beta = 0.0; s.c2 = 1.0; s.s2 = 0.0; s.c1 = 1.0; s.s1 = 0.0;
+    s.phibar = beta1; s.beta1 = beta1; s.pad = 0.0;
+    s.iters = 0; s.done = beta1 > 0.0 ? 0 : 1; s.pad0 = s.pad1 = 0;
+    st[j] = s;
+  }
+}
+
+// One Paige-Saunders MINRES step for right-hand side j (CTA j).  P = E v_k from the operator GEMMs.
+template <typename T>
+__global__ void minres_step_kernel(const T* __restrict__ P, int n_aux, double tol, double* vprev, double* v,
+                                   double* d1, double* d2, double* x, MinresState* st, T* V, int* n_active) {
+  __shared__ double buf[32];
+  const int j = blockIdx.x;
+  MinresState s = st[j];
+  if (s.done) return;
+  const long n2 = 2L * n_aux, off = (long)j * n2;
+  // alpha = v . (P - beta vprev)
+  double acc = 0.0;
+  for (long i = threadIdx.x; i < n2; i += blockDim.x)
+    acc += v[off + i] * ((double)P[off + i] - s.beta * vprev[off + i]);
+  const double alpha = block_sum(acc, buf);
+  acc = 0.0;
+  for (long i = threadIdx.x; i < n2; i += blockDim.x) {
+    double p = (double)P[off + i] - s.beta * vprev[off + i] - alpha * v[off + i];
+    acc += p * p;
+  }
+  const double beta_next = sqrt(block_sum(acc, buf));
+  // QR of the tridiagonal by Givens rotations
+  const double eps_k = s.s2 * s.beta;
+  const double dbar = s.c2 * s.beta;
+  const double delta = s.c1 * dbar + s.s1 * alpha;
+  const double gbar = -s.s1 * dbar + s.c1 * alpha;
+  const double gamma = hypot(gbar, beta_next);
+  bool breakdown = !(gamma > 0.0);
+  const double c = breakdown ? 1.0 : gbar / gamma;
+  const double sn = breakdown ? 0.0 : beta_next / gamma;
+  const double tau = c * s.phibar;
+  const double phibar = -sn * s.phibar;
+  const double ginv = breakdown ? 0.0 : 1.0 / gamma;
+  const bool done = breakdown || fabs(phibar) <= tol * s.beta1 || beta_next == 0.0;
+  const double binv = done ? 0.0 : 1.0 / beta_next;
+  for (long i = threadIdx.x; i < n2; i += blockDim.x) {
+    const double vi = v[off + i];
+    const double d = (vi - delta * d1[off + i] - eps_k * d2[off + i]) * ginv;
+    x[off + i] += tau * d;
+    d2[off + i] = d1[off + i];
+    d1[off + i] = d;
+    if (!done) {
+      const double p = (double)P[off + i] - s.beta * vprev[off + i] - alpha * vi;
+      const double vn = p * binv;
+      vprev[off + i] = vi;
+      v[off + i] = vn;
+      V[off + i] = (T)vn;
+    }
+  }
+  if (threadIdx.x == 0) {
+    s.beta = beta_next;
+    s.c2 = s.c1; s.s2 = s.s1; s.c1 = c; s.s1 = sn;
+    s.phibar = phibar;
+    s.iters += 1;
+    s.done = done ? 1 : 0;
+    st[j] = s;
+    if (!done) atomicAdd(n_active, 1);
+  }
+}
+
+template <typename T>
+__global__ void minres_finish_kernel(const double* __restrict__ B_nm, int n_bas, int n_aux,
+                                     const int* __restrict__ rt, const int* __restrict__ rm,
+                                     const double* __restrict__ x, const MinresState* __restrict__ st,
+                                     double* w_re, double* w_im, int* iters, double* resnorm, T* V) {
+  __shared__ double buf[32];
+  const int j = blockIdx.x;
+  const double* b = B_nm + ((long)rt[j] * n_bas + rm[j]) * n_aux;
+  const long off = (long)j * 2 * n_aux;
+  double ar = 0.0, ai = 0.0;
+  for (int i = threadIdx.x; i < n_aux; i += blockDim.x) {
+    const double x1 = x[off + i], x2 = x[off + n_aux + i];
+    ar += b[i] * x1;
+    ai += b[i] * x2;
+    V[off + i] = (T)(b[i] + x1);     // u = Re y = b + x1
+    V[off + n_aux + i] = (T)x2;      // v = -Im y = x2   (delta = x1 - i x2)
+  }
+  ar = block_sum(ar, buf);
+  ai = block_sum(ai, buf);
+  if (threadIdx.x == 0) {
+    w_re[j] = ar;
+    w_im[j] = -ai;
+    MinresState s = st[j];
+    iters[j] = s.iters;
+    resnorm[j] = s.beta1 > 0.0 ? fabs(s.phibar) / s.beta1 : 0.0;
+  }
+}
+
+template <typename T>
+__global__ void rowsum_pairs_kernel(const T* __restrict__ U, long n_ov, double* dw_re, double* dw_im) {
+  __shared__ double buf[32];
+  const int j = blockIdx.x;
+  const T* ur = U + (long)(2 * j) * n_ov;
+  const T* ui = ur + n_ov;
+  double sr = 0.0, si = 0.0;
+  for (long k = threadIdx.x; k < n_ov; k += blockDim.x) {
+    sr += (double)ur[k];
+    si += (double)ui[k];
+  }
+  sr = block_sum(sr, buf);
+  si = block_sum(si, buf);
+  if (threadIdx.x == 0) {
+    dw_re[j] = sr;
+    if (dw_im) dw_im[j] = si;
+  }
+}
+
+// Complex Gaussian elimination with partial pivoting, single CTA.  A = Ar + i Ai (n x n, destroyed),
+// right-hand side b (real).  result[0..1] = W = b^T(y - b); y written to work[0..2n) as (y_r, -y_i).
+__global__ void __launch_bounds__(1024) dense_residue_kernel(double* Ar, double* Ai, int n, const double* __restrict__ b,
+                                                             double* work, double* result, int* info) {
+  __shared__ double bv[32];
+  __shared__ int bi[32];
+  __shared__ int piv_s;
+  double* yr = work;            // rhs / solution, real part
+  double* yi = work + n;        // imaginary part
+  for (int i = threadIdx.x; i < n; i += blockDim.x) { yr[i] = b[i]; yi[i] = 0.0; }
+  if (threadIdx.x == 0) *info = 0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    // pivot search on column k
+    double best = -1.0;
+    int bidx = k;
+    for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+      double m = Ar[(long)i * n + k] * Ar[(long)i * n + k] + Ai[(long)i * n + k] * Ai[(long)i * n + k];
+      if (m > best) { best = m; bidx = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+      if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+    }
+    if ((threadIdx.x & 31) == 0) { bv[threadIdx.x >> 5] = best; bi[threadIdx.x >> 5] = bidx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double bb = -1.0;
+      int ii = k;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+        if (bv[w] > bb || (bv[w] == bb && bi[w] < ii)) { bb = bv[w]; ii = bi[w]; }
+      piv_s = ii;
+      if (!(bb > 0.0)) *info = 1;
+    }
+    __syncthreads();
+    const int p = piv_s;
+    if (p != k) {
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double t = Ar[(long)k * n + j]; Ar[(long)k * n + j] = Ar[(long)p * n + j]; Ar[(long)p * n + j] = t;
+        t = Ai[(long)k * n + j]; Ai[(long)k * n + j] = Ai[(long)p * n + j]; Ai[(long)p * n + j] = t;
+      }
+      if (threadIdx.x == 0) {
+        double t = yr[k]; yr[k] = yr[p]; yr[p] = t;
+        t = yi[k]; yi[k] = yi[p]; yi[p] = t;
+      }
+    }
+    __syncthreads();
+    const double pr = Ar[(long)k * n + k], pi = Ai[(long)k * n + k];
+    const double pd = pr * pr + pi * pi;
+    const double ipr = pd > 0.0 ? pr / pd : 0.0, ipi = pd > 0.0 ? -pi / pd : 0.0;   // 1/pivot
+    // eliminate rows below: one warp per row
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = k + 1 + wid; i < n; i += nw) {
+      const double ar = Ar[(long)i * n + k], ai = Ai[(long)i * n + k];
+      const double lr = ar * ipr - ai * ipi, li = ar * ipi + ai * ipr;
+      for (int j = k + 1 + lane; j < n; j += 32) {
+        const double ur = Ar[(long)k * n + j], ui = Ai[(long)k * n + j];
+        Ar[(long)i * n + j] -= lr * ur - li * ui;
+        Ai[(long)i * n + j] -= lr * ui + li * ur;
+      }
+      if (lane == 0) {
+        const double yrk = yr[k], yik = yi[k];
+        yr[i] -= lr * yrk - li * yik;
+        yi[i] -= lr * yik + li * yrk;
+      }
+    }
+    __syncthreads();
+  }
+  // back substitution
+  for (int k = n - 1; k >= 0; --k) {
+    double sr = 0.0, si = 0.0;
+    for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) {
+      const double ar = Ar[(long)k * n + j], ai = Ai[(long)k * n + j];
+      sr += ar * yr[j] - ai * yi[j];
+      si += ar * yi[j] + ai * yr[j];
+    }
+    sr = block_sum(sr, bv);
+    si = block_sum(si, bv);
+    if (threadIdx.x == 0) {
+      const double rr = yr[k] - sr, ri = yi[k] - si;
+      const double pr = Ar[(long)k * n + k], pi = Ai[(long)k * n + k];
+      const double pd = pr * pr + pi * pi;
+      yr[k] = pd > 0.0 ? (rr * pr + ri * pi) / pd : 0.0;
+      yi[k] = pd > 0.0 ? (ri * pr - rr * pi) / pd : 0.0;
+    }
+    __syncthreads();
+  }
+  // W = b^T y - b^T b; store (u, v) = (y_r, -y_i)
+  double wr = 0.0, wi = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    wr += b[i] * (yr[i] - b[i]);
+    wi += b[i] * yi[i];
+  }
+  wr = block_sum(wr, bv);
+  wi = block_sum(wi, bv);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) yi[i] = -yi[i];
+  if (threadIdx.x == 0) { result[0] = wr; result[1] = wi; }
+}
+
+__global__ void residue_reduce_kernel(const int* __restrict__ start, int n_t, const double* __restrict__ coef,
+                                      const double* __restrict__ w_re, const double* __restrict__ dw_re,
+                                      double* R, double* dR) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_t) return;
+  double r = 0.0, d = 0.0;
+  for (int j = start[t]; j < start[t + 1]; ++j) {
+    r += coef[j] * w_re[j];
+    d -= coef[j] * dw_re[j];     // d/domega W(e_m - omega) = -W'(x)
+  }
+  R[t] = r;
+  dR[t] = d;
+}
+
+// ------------------------------------------------------------------ QP step tree
+__device__ __forceinline__ double sgn(double v) { return v > 0.0 ? 1.0 : (v < 0.0 ? -1.0 : 0.0); }
+
+constexpr double kGold = 0.38196601125010515;   // (3 - sqrt 5)/2
+
+// bracket kinds: 0 none, 1 sign change, 2 same sign (golden-section minimisation of |f| around x)
+__device__ void update_bracket(QPState& s, double w1, double f1) {
+  if (s.br_kind != 0 && s.a < w1 && w1 < s.b) {
+    if (s.br_kind == 1) {
+      if (sgn(f1) == sgn(s.fa)) { s.a = w1; s.fa = f1; }
+      else { s.b = w1; s.fb = f1; }
+      return;
+    }
+    if (sgn(f1) != sgn(s.fx)) {
+      s.br_kind = 1;
+      if (w1 < s.x) { s.a = w1; s.fa = f1; s.b = s.x; s.fb = s.fx; }
+      else { s.a = s.x; s.fa = s.fx; s.b = w1; s.fb = f1; }
+      return;
+    }
+    if (fabs(f1) < fabs(s.fx)) {
+      if (w1 > s.x) { s.a = s.x; s.fa = s.fx; } else { s.b = s.x; s.fb = s.fx; }
+      s.x = w1; s.fx = f1;
+    } else {
+      if (w1 > s.x) { s.b = w1; s.fb = f1; } else { s.a = w1; s.fa = f1; }
+    }
+    return;
+  }
+  if (!s.has_prev) return;
+  const double w0 = s.omega_prev, f0 = s.f_prev;
+  if (sgn(f1) != sgn(f0)) {
+    s.br_kind = 1;
+    if (w0 < w1) { s.a = w0; s.fa = f0; s.b = w1; s.fb = f1; }
+    else { s.a = w1; s.fa = f1; s.b = w0; s.fb = f0; }
+    return;
+  }
+  if (s.br_kind == 0 && fabs(f1) > fabs(f0)) {
+    s.br_kind = 2;
+    if (w0 < w1) { s.a = w0; s.fa = f0; s.b = w1; s.fb = f1; }
+    else { s.a = w1; s.fa = f1; s.b = w0; s.fb = f0; }
+    s.x = w0; s.fx = f0;
+  }
+}
+
+__device__ double golden_point(const QPState& s) {
+  if (s.br_kind == 1) return fabs(s.fa) <= fabs(s.fb) ? s.a + kGold * (s.b - s.a) : s.b - kGold * (s.b - s.a);
+  return (s.b - s.x) >= (s.x - s.a) ? s.x + kGold * (s.b - s.x) : s.x - kGold * (s.x - s.a);
+}
+
+__global__ void qp_init_kernel(QPState* st, const double* e_n, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  QPState s;
+  s.omega = e_n[t]; s.f_prev = 0.0; s.omega_prev = 0.0; s.Z = 1.0;
+  s.a = s.fa = s.b = s.fb = s.x = s.fx = 0.0;
+  s.sigma = s.dsigma = 0.0;
+  s.br_kind = 0; s.has_prev = 0; s.iter = 0; s.status = 0;
+  st[t] = s;
+}
+
+__global__ void qp_step_kernel(QPState* st, const double* __restrict__ R, const double* __restrict__ dR,
+                               const double* __restrict__ I, const double* __restrict__ dI,
+                               const double* __restrict__ e_n, const double* __restrict__ shift, double tol, int maxit,
+                               int n, int linearised) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  QPState s = st[t];
+  if (s.status != 0) return;
+  const double sig = R[t] - I[t], dsig = dR[t] - dI[t];
+  s.sigma = sig;
+  s.dsigma = dsig;
+  const double Z = 1.0 / (1.0 - dsig);
+  s.Z = Z;
+  if (linearised) {
+    // e_QP = e + Z (shift + Sigma_c(e)), Z = 1/(1 - Sigma_c'(e))
+    s.omega = e_n[t] + Z * (shift[t] + sig);
+    s.status = 1;
+    s.iter = 1;
+    st[t] = s;
+    return;
+  }
+  const double w = s.omega;
+  const double f = e_n[t] + shift[t] + sig - w;
+  if (fabs(f) < tol) {
+    s.status = 1;
+    s.iter += 1;
+    st[t] = s;
+    return;
+  }
+  if (s.iter + 1 >= maxit) {
+    s.status = 2;
+    s.iter += 1;
+    st[t] = s;
+    return;
+  }
+  update_bracket(s, w, f);
+  double nw;
+  if (s.iter == 0) {
+    nw = w + fmin(1.0, 0.1 / fabs(f)) * f;       // scaled residual, step capped at 0.1 Ha
+  } else if (Z >= 0.3) {
+    nw = w + Z * f;                              // Newton
+  } else if (s.br_kind != 0) {
+    nw = golden_point(s);                        // golden section inside the bracket
+  } else if (Z >= 0.1) {
+    nw = w + 0.7 * Z * f;                        // scaled Newton
+  } else {
+    nw = w + fmin(1.0, 0.1 / fabs(f)) * f;       // scaled residual
+  }
+  s.omega_prev = w;
+  s.f_prev = f;
+  s.has_prev = 1;
+  s.omega = nw;
+  s.iter += 1;
+  st[t] = s;
+}
+
+}  // namespace
+
+void launch_sigma_x(const double* B_nm, int n_t, int n_bas, int n_aux, int n_occ, double* sx, cudaStream_t s) {
+  if (n_t > 0) sigma_x_kernel<<<n_t, RT, 0, s>>>(B_nm, n_bas, n_aux, n_occ, sx);
+}
+
+void launch_sigma_imag(const double* W, int n_t, int n_bas, int n_g, const double* eps, const double* xi,
+                       const double* wt, const double* omega, int static_sub, double* I, double* dI,
+                       const unsigned char* active, cudaStream_t s) {
+  if (n_t > 0) sigma_imag_kernel<<<n_t, RT, 0, s>>>(W, n_bas, n_g, eps, xi, wt, omega, static_sub, I, dI, active);
+}
+
+template <typename T>
+void launch_gather_rhs(const double* B_nm, int n_bas, int n_aux, const int* rhs_t, const int* rhs_m, int nr, T* V,
+                       cudaStream_t s) {
+  if (nr > 0) gather_rhs_kernel<T><<<nr, RT, 0, s>>>(B_nm, n_bas, n_aux, rhs_t, rhs_m, V);
+}
+
+template <typename T>
+void launch_minres_init(const T* S, int nr, int n_aux, double* vprev, double* v, double* d1, double* d2, double* x,
+                        MinresState* st, T* V, cudaStream_t s) {
+  if (nr > 0) minres_init_kernel<T><<<nr, RT, 0, s>>>(S, n_aux, vprev, v, d1, d2, x, st, V);
+}
+
+template <typename T>
+void launch_minres_step(const T* P, int nr, int n_aux, double tol, double* vprev, double* v, double* d1, double* d2,
+                        double* x, MinresState* st, T* V, int* n_active, cudaStream_t s) {
+  if (nr > 0) minres_step_kernel<T><<<nr, RT, 0, s>>>(P, n_aux, tol, vprev, v, d1, d2, x, st, V, n_active);
+}
+
+template <typename T>
+void launch_minres_finish(const double* B_nm, int n_bas, int n_aux, const int* rhs_t, const int* rhs_m, int nr,
+                          const double* x, const MinresState* st, double* w_re, double* w_im, int* iters,
+                          double* resnorm, T* V, cudaStream_t s) {
+  if (nr > 0)
+    minres_finish_kernel<T><<<nr, RT, 0, s>>>(B_nm, n_bas, n_aux, rhs_t, rhs_m, x, st, w_re, w_im, iters, resnorm, V);
+}
+
+template <typename T>
+void launch_rowsum_pairs(const T* U, int nr, int n_ov, double* dw_re, double* dw_im, cudaStream_t s) {
+  if (nr > 0) rowsum_pairs_kernel<T><<<nr, RT, 0, s>>>(U, (long)n_ov, dw_re, dw_im);
+}
+
+void launch_dense_residue(double* Ar, double* Ai, int n, const double* b, double* work, double* result, int* info,
+                          cudaStream_t s) {
+  dense_residue_kernel<<<1, 1024, 0, s>>>(Ar, Ai, n, b, work, result, info);
+}
+
+void launch_residue_reduce(const int* start, int n_t, const double* coef, const double* w_re, const double* dw_re,
+                           double* R, double* dR, cudaStream_t s) {
+  if (n_t > 0) residue_reduce_kernel<<<(n_t + 127) / 128, 128, 0, s>>>(start, n_t, coef, w_re, dw_re, R, dR);
+}
+
+void launch_qp_init(QPState* st, const double* e_n, int n, cudaStream_t s) {
+  if (n > 0) qp_init_kernel<<<(n + 127) / 128, 128, 0, s>>>(st, e_n, n);
+}
+
+void launch_qp_step(QPState* st, const double* R, const double* dR, const double* I, const double* dI,
+                    const double* e_n, const double* shift, double tol, int maxit, int n, int linearised,
+                    cudaStream_t s) {
+  if (n > 0) qp_step_kernel<<<(n + 127) / 128, 128, 0, s>>>(st, R, dR, I, dI, e_n, shift, tol, maxit, n, linearised);
+}
+
+#define GW_INST(T)                                                                                                \
+  template void launch_gather_rhs<T>(const double*, int, int, const int*, const int*, int, T*, cudaStream_t);     \
+  template void launch_minres_init<T>(const T*, int, int, double*, double*, double*, double*, double*,            \
+                                      MinresState*, T*, cudaStream_t);                                            \
+  template void launch_minres_step<T>(const T*, int, int, double, double*, double*, double*, double*, double*,    \
+                                      MinresState*, T*, int*, cudaStream_t);                                      \
+  template void launch_minres_finish<T>(const double*, int, int, const int*, const int*, int, const double*,      \
+                                        const MinresState*, double*, double*, int*, double*, T*, cudaStream_t);   \
+  template void launch_rowsum_pairs<T>(const T*, int, int, double*, double*, cudaStream_t);
+GW_INST(double)
+GW_INST(float)
+#undef GW_INST
+
+}  // namespace gw

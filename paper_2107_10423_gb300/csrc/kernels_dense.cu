@@ -1,0 +1,574 @@
+// Dense kernels of the CD-G0W0 path (SIMT, templated on the arithmetic type):
+//  * Pi(i xi) symmetric rank-N_ov update (Sec. 3.3, equation after "wauxbas"), lower tiles + mirror;
+//  * batched in-place Cholesky of eps(i xi) = 1 - Pi (SPD, Sec. 3.3 text after "inn");
+//  * triangular solves that turn the factors into the table W^c_nm(i xi) (Algorithm 1, imaginary-grid loop);
+//  * the two skinny GEMMs of the matrix-free residue operator 1 - Pi(x) (Sec. 3.3, MINRES paragraph).
+#include "gw_internal.cuh"
+
+#include <cstdio>
+
+namespace gw {
+
+namespace {
+
+constexpr int TM = 64;     // tile rows
+constexpr int TN = 64;     // tile cols
+constexpr int TK = 16;     // k step
+constexpr int NT = 256;    // threads per CTA (16 x 16, 4 x 4 outputs each)
+
+__device__ __forceinline__ double pair_energy(const double* eps, int n_occ, int n_virt, long k) {
+  int i = (int)(k / n_virt);
+  int a = (int)(k - (long)i * n_virt);
+  return eps[n_occ + a] - eps[i];
+}
+
+// ------------------------------------------------------------------ Pi(i xi) SYRK
+// grid.x: lower-triangular tile index (bi >= bj), grid.y: frequency index.
+template <typename T>
+__global__ void __launch_bounds__(NT) pi_syrk_kernel(const T* __restrict__ B, const double* __restrict__ eps,
+                                                     int n_occ, int n_virt, int n_aux,
+                                                     const double* __restrict__ xi, T* __restrict__ out, int mode) {
+  __shared__ T As[TK][TM + 4];
+  __shared__ T Bs[TK][TN + 4];
+  const long n_ov = (long)n_occ * n_virt;
+  // decode lower tile (bi, bj) from linear index t = bi*(bi+1)/2 + bj
+  int t = blockIdx.x;
+  int bi = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
+  while (bi * (bi + 1) / 2 > t) --bi;
+  int bj = t - bi * (bi + 1) / 2;
+  const int g = blockIdx.y;
+  const double x2 = xi[g] * xi[g];
+  const int p0 = bi * TM, q0 = bj * TN;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  const int lr = tid >> 2, lk = (tid & 3) * 4;
+  for (long k0 = 0; k0 < n_ov; k0 += TK) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      long k = k0 + lk + u;
+      T wa = T(0), va = T(0), vb = T(0);
+      if (k < n_ov) {
+        double D = pair_energy(eps, n_occ, n_virt, k);
+        wa = (T)(-4.0 * D / (D * D + x2));
+        if (p0 + lr < n_aux) va = B[(long)(p0 + lr) * n_ov + k];
+        if (q0 + lr < n_aux) vb = B[(long)(q0 + lr) * n_ov + k];
+      }
+      As[lk + u][lr] = va * wa;
+      Bs[lk + u][lr] = vb;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  T* o = out + (long)g * n_aux * n_aux;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int p = p0 + ty + 16 * i;
+    if (p >= n_aux) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int q = q0 + tx + 16 * j;
+      if (q >= n_aux || q > p) continue;
+      T v = acc[i][j];
+      if (mode == 1) v = (p == q ? T(1) : T(0)) - v;
+      o[(long)p * n_aux + q] = v;
+      o[(long)q * n_aux + p] = v;
+    }
+  }
+}
+
+// Complex real-axis Pi(x) as A = 1 - Pi, two real halves (dense fallback only).
+__global__ void __launch_bounds__(NT) pi_complex_kernel(const double* __restrict__ B, const double* __restrict__ eps,
+                                                        int n_occ, int n_virt, int n_aux, double x, double eta,
+                                                        double* __restrict__ Ar, double* __restrict__ Ai) {
+  __shared__ double Asr[TK][TM + 4];
+  __shared__ double Asi[TK][TM + 4];
+  __shared__ double Bs[TK][TN + 4];
+  const long n_ov = (long)n_occ * n_virt;
+  const int p0 = blockIdx.y * TM, q0 = blockIdx.x * TN;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  double accr[4][4], acci[4][4];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) accr[i][j] = acci[i][j] = 0.0;
+  const int lr = tid >> 2, lk = (tid & 3) * 4;
+  const double e2 = eta * eta;
+  for (long k0 = 0; k0 < n_ov; k0 += TK) {
+    for (int u = 0; u < 4; ++u) {
+      long k = k0 + lk + u;
+      double cr = 0, ci = 0, va = 0, vb = 0;
+      if (k < n_ov) {
+        double D = pair_energy(eps, n_occ, n_virt, k);
+        double a1 = x - D, a2 = -x - D;
+        double d1 = a1 * a1 + e2, d2 = a2 * a2 + e2;
+        cr = 2.0 * (a1 / d1 + a2 / d2);
+        ci = 2.0 * (-eta / d1 - eta / d2);
+        if (p0 + lr < n_aux) va = B[(long)(p0 + lr) * n_ov + k];
+        if (q0 + lr < n_aux) vb = B[(long)(q0 + lr) * n_ov + k];
+      }
+      Asr[lk + u][lr] = va * cr;
+      Asi[lk + u][lr] = va * ci;
+      Bs[lk + u][lr] = vb;
+    }
+    __syncthreads();
+    for (int kk = 0; kk < TK; ++kk) {
+      double ar[4], ai[4], b[4];
+      for (int i = 0; i < 4; ++i) { ar[i] = Asr[kk][ty + 16 * i]; ai[i] = Asi[kk][ty + 16 * i]; }
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+          accr[i][j] = fma(ar[i], b[j], accr[i][j]);
+          acci[i][j] = fma(ai[i], b[j], acci[i][j]);
+        }
+    }
+    __syncthreads();
+  }
+  for (int i = 0; i < 4; ++i) {
+    int p = p0 + ty + 16 * i;
+    if (p >= n_aux) continue;
+    for (int j = 0; j < 4; ++j) {
+      int q = q0 + tx + 16 * j;
+      if (q >= n_aux) continue;
+      Ar[(long)p * n_aux + q] = (p == q ? 1.0 : 0.0) - accr[i][j];
+      Ai[(long)p * n_aux + q] = -acci[i][j];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ batched Cholesky, one CTA per matrix
+constexpr int CH_NB = 32;
+constexpr int CH_THREADS = 512;
+
+template <typename T>
+__global__ void __launch_bounds__(CH_THREADS) cholesky_kernel(T* base, int n, long stride, int* info) {
+  __shared__ T Ld[CH_NB][CH_NB + 1];
+  __shared__ T Pi_[64][CH_NB + 1];
+  __shared__ T Pj_[64][CH_NB + 1];
+  __shared__ int bad;
+  T* A = base + (long)blockIdx.x * stride;
+  const int tid = threadIdx.x;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int j0 = 0; j0 < n; j0 += CH_NB) {
+    const int nb = min(CH_NB, n - j0);
+    // (1) diagonal block
+    for (int idx = tid; idx < nb * nb; idx += CH_THREADS) {
+      int r = idx / nb, c = idx % nb;
+      Ld[r][c] = A[(long)(j0 + r) * n + j0 + c];
+    }
+    __syncthreads();
+    for (int c = 0; c < nb; ++c) {
+      if (tid == 0) {
+        T d = Ld[c][c];
+        if (!(d > T(0))) { bad = j0 + c + 1; d = T(1); }
+        Ld[c][c] = sqrt(d);
+      }
+      __syncthreads();
+      for (int r = c + 1 + tid; r < nb; r += CH_THREADS) Ld[r][c] /= Ld[c][c];
+      __syncthreads();
+      for (int idx = tid; idx < (nb - c - 1) * (nb - c - 1); idx += CH_THREADS) {
+        int r = c + 1 + idx / (nb - c - 1), s = c + 1 + idx % (nb - c - 1);
+        if (s <= r) Ld[r][s] -= Ld[r][c] * Ld[s][c];
+      }
+      __syncthreads();
+    }
+    for (int idx = tid; idx < nb * nb; idx += CH_THREADS) {
+      int r = idx / nb, c = idx % nb;
+      if (c <= r) A[(long)(j0 + r) * n + j0 + c] = Ld[r][c];
+    }
+    // (2) panel rows below: x L^T = a
+    for (int i = j0 + nb + tid; i < n; i += CH_THREADS) {
+      T xr[CH_NB];
+      for (int c = 0; c < nb; ++c) {
+        T v = A[(long)i * n + j0 + c];
+        for (int s = 0; s < c; ++s) v -= xr[s] * Ld[c][s];
+        xr[c] = v / Ld[c][c];
+      }
+      for (int c = 0; c < nb; ++c) A[(long)i * n + j0 + c] = xr[c];
+    }
+    __threadfence_block();
+    __syncthreads();
+    // (3) trailing lower update A[i][j] -= sum_c P[i][c] P[j][c], i >= j >= j0+nb
+    const int t0 = j0 + nb;
+    const int nt = (n - t0 + 63) / 64;
+    for (int ti = 0; ti < nt; ++ti) {
+      for (int tj = 0; tj <= ti; ++tj) {
+        const int r0 = t0 + ti * 64, c0 = t0 + tj * 64;
+        for (int idx = tid; idx < 64 * CH_NB; idx += CH_THREADS) {
+          int r = idx / CH_NB, c = idx % CH_NB;
+          Pi_[r][c] = (r0 + r < n && c < nb) ? A[(long)(r0 + r) * n + j0 + c] : T(0);
+          Pj_[r][c] = (c0 + r < n && c < nb) ? A[(long)(c0 + r) * n + j0 + c] : T(0);
+        }
+        __syncthreads();
+        const int r = tid >> 3;             // 0..63
+        const int cb = tid & 7;             // cols cb + 8*jj
+        T acc[8];
+        for (int jj = 0; jj < 8; ++jj) acc[jj] = T(0);
+        for (int c = 0; c < nb; ++c) {
+          T a = Pi_[r][c];
+          for (int jj = 0; jj < 8; ++jj) acc[jj] = fma(a, Pj_[cb + 8 * jj][c], acc[jj]);
+        }
+        const int gi = r0 + r;
+        if (gi < n) {
+          for (int jj = 0; jj < 8; ++jj) {
+            int gj = c0 + cb + 8 * jj;
+            if (gj < n && gj <= gi) A[(long)gi * n + gj] -= acc[jj];
+          }
+        }
+        __syncthreads();
+      }
+    }
+    __threadfence_block();
+    __syncthreads();
+  }
+  if (tid == 0) info[blockIdx.x] = bad;
+}
+
+// ------------------------------------------------------------------ TRSM -> W table
+// Work item = (matrix g, tile of 64 right-hand sides).  Y for the tile lives in this CTA's scratch slice.
+template <typename T>
+__global__ void __launch_bounds__(NT) trsm_w_kernel(const T* __restrict__ Lbase, long Lstride, int n, int n_g,
+                                                    const int* __restrict__ g_out, const T* __restrict__ Bn, int R,
+                                                    double* __restrict__ W, int w_ld, T* __restrict__ scratch) {
+  extern __shared__ unsigned char smem_raw[];
+  T* As = reinterpret_cast<T*>(smem_raw);             // [TK][TM+4]
+  T* Bs = As + TK * (TM + 4);                          // [TK][TN+4]
+  T* Ts = Bs + TK * (TN + 4);                          // [64][65]
+  T* Ls = Ts + 64 * 65;                                // [64][65]
+  double* red = reinterpret_cast<double*>(Ls + 64 * 65);  // [2][16][64]
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int n_ct = (R + 63) / 64;
+  const int nJ = (n + 63) / 64;
+  T* Y = scratch + (long)blockIdx.x * n * 64;
+  const long n_items = (long)n_g * n_ct;
+  for (long item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const int g = (int)(item / n_ct);
+    const int r0 = (int)(item % n_ct) * 64;
+    const T* L = Lbase + (long)g * Lstride;
+    double ws[4] = {0, 0, 0, 0}, bs[4] = {0, 0, 0, 0};
+    for (int J = 0; J < nJ; ++J) {
+      const int P0 = J * 64;
+      const int nr = min(64, n - P0);
+      T acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          int P = P0 + ty + 16 * i, c = r0 + tx + 16 * j;
+          T v = (P < n && c < R) ? Bn[(long)c * n + P] : T(0);
+          acc[i][j] = v;
+          bs[j] += (double)v * (double)v;
+        }
+      for (int K = 0; K < J; ++K) {
+        for (int kk0 = 0; kk0 < 64; kk0 += TK) {
+          {
+            // As[kk][r] = L[P0+r][K*64+kk0+kk]; Bs[kk][c] = Y[(K*64+kk0+kk)*64 + c]
+            int r = tid >> 2, k4 = (tid & 3) * 4;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              int kk = k4 + u;
+              int col = K * 64 + kk0 + kk;
+              As[kk * (TM + 4) + r] = (P0 + r < n) ? L[(long)(P0 + r) * n + col] : T(0);
+            }
+            int kr = tid >> 4, c4 = (tid & 15) * 4;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) Bs[kr * (TN + 4) + c4 + u] = Y[(long)(K * 64 + kk0 + kr) * 64 + c4 + u];
+          }
+          __syncthreads();
+#pragma unroll
+          for (int kk = 0; kk < TK; ++kk) {
+            T a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk * (TM + 4) + ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk * (TN + 4) + tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+              for (int j = 0; j < 4; ++j) acc[i][j] = fma(-a[i], b[j], acc[i][j]);
+          }
+          __syncthreads();
+        }
+      }
+      // stage the right-hand side block and the diagonal factor block
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) Ts[(ty + 16 * i) * 65 + tx + 16 * j] = acc[i][j];
+      for (int idx = tid; idx < 64 * 64; idx += NT) {
+        int r = idx >> 6, c = idx & 63;
+        Ls[r * 65 + c] = (r < nr && c <= r) ? L[(long)(P0 + r) * n + P0 + c] : (r == c ? T(1) : T(0));
+      }
+      __syncthreads();
+      if (tid < 64) {
+        const int c = tid;
+        for (int p = 0; p < nr; ++p) {
+          T v = Ts[p * 65 + c];
+          for (int q = 0; q < p; ++q) v = fma(-Ls[p * 65 + q], Ts[q * 65 + c], v);
+          Ts[p * 65 + c] = v / Ls[p * 65 + p];
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          int p = ty + 16 * i, c = tx + 16 * j;
+          T v = (p < nr) ? Ts[p * 65 + c] : T(0);
+          Y[(long)(P0 + p) * 64 + c] = v;   // rows beyond n are never read
+          ws[j] += (double)v * (double)v;
+        }
+      __threadfence_block();
+      __syncthreads();
+    }
+    // reduce per column over ty
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      red[(0 * 16 + ty) * 64 + tx + 16 * j] = ws[j];
+      red[(1 * 16 + ty) * 64 + tx + 16 * j] = bs[j];
+    }
+    __syncthreads();
+    if (tid < 64) {
+      double w = 0, b = 0;
+      for (int y = 0; y < 16; ++y) { w += red[(0 * 16 + y) * 64 + tid]; b += red[(1 * 16 + y) * 64 + tid]; }
+      int r = r0 + tid;
+      if (r < R) W[(long)r * w_ld + g_out[g]] = w - b;
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ residue operator GEMMs
+// gemm1: rows r in [0, 2nr), cols k in [0, n_ov): acc = sum_P V[r][P] B[P][k]  (B is N-contiguous here)
+template <typename T>
+__global__ void __launch_bounds__(NT) op_gemm1_kernel(const T* __restrict__ V, const T* __restrict__ B,
+                                                      const double* __restrict__ eps, int n_occ, int n_virt,
+                                                      int n_aux, const double* __restrict__ xs, double eta, int nr,
+                                                      T* __restrict__ U, int mode) {
+  __shared__ T As[TK][TM + 4];
+  __shared__ T Bs[TK][TN + 4];
+  const long n_ov = (long)n_occ * n_virt;
+  const int M = 2 * nr;
+  const int m0 = blockIdx.y * TM;
+  const long k0c = (long)blockIdx.x * TN;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  for (int p0 = 0; p0 < n_aux; p0 += TK) {
+    {
+      int r = tid >> 2, k4 = (tid & 3) * 4;       // A: V rows, K (=P) contiguous
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        int P = p0 + k4 + u;
+        As[k4 + u][r] = (m0 + r < M && P < n_aux) ? V[(long)(m0 + r) * n_aux + P] : T(0);
+      }
+      int kr = tid >> 4, c4 = (tid & 15) * 4;     // B: rows P, cols k contiguous
+      int P = p0 + kr;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        long k = k0c + c4 + u;
+        Bs[kr][c4 + u] = (P < n_aux && k < n_ov) ? B[(long)P * n_ov + k] : T(0);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][2 * ty + (i & 1) + 32 * (i >> 1)];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  const double e2 = eta * eta;
+#pragma unroll
+  for (int ip = 0; ip < 2; ++ip) {
+    int r = m0 + 2 * ty + 32 * ip;           // even row of the pair
+    if (r >= M) continue;
+    int jr = r >> 1;
+    double x = xs[jr];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      long k = k0c + tx + 16 * j;
+      if (k >= n_ov) continue;
+      double tr = (double)acc[2 * ip][j], ti = -(double)acc[2 * ip + 1][j];
+      double D = pair_energy(eps, n_occ, n_virt, k);
+      double a1 = x - D, a2 = -x - D;
+      double d1 = a1 * a1 + e2, d2 = a2 * a2 + e2;
+      double outr, outi;
+      if (mode == 0) {
+        double cr = 2.0 * (a1 / d1 + a2 / d2);
+        double ci = -2.0 * eta * (1.0 / d1 + 1.0 / d2);
+        outr = cr * tr - ci * ti;
+        outi = cr * ti + ci * tr;
+      } else {
+        // c' = 2[-(a1 - i eta)^2/d1^2 + (a2 - i eta)^2/d2^2]
+        double q1r = (a1 * a1 - e2) / (d1 * d1), q1i = -2.0 * a1 * eta / (d1 * d1);
+        double q2r = (a2 * a2 - e2) / (d2 * d2), q2i = -2.0 * a2 * eta / (d2 * d2);
+        double cr = 2.0 * (-q1r + q2r), ci = 2.0 * (-q1i + q2i);
+        double t2r = tr * tr - ti * ti, t2i = 2.0 * tr * ti;
+        outr = cr * t2r - ci * t2i;
+        outi = cr * t2i + ci * t2r;
+      }
+      U[(long)r * n_ov + k] = (T)outr;
+      U[(long)(r + 1) * n_ov + k] = (T)outi;
+    }
+  }
+}
+
+// gemm2: rows r in [0, 2nr), cols P in [0, n_aux): acc = sum_k U[r][k] B[P][k]  (both K-contiguous)
+template <typename T>
+__global__ void __launch_bounds__(NT) op_gemm2_kernel(const T* __restrict__ U, const T* __restrict__ B, int n_aux,
+                                                      long n_ov, int nr, const T* __restrict__ V,
+                                                      T* __restrict__ out, int mode) {
+  __shared__ T As[TK][TM + 4];
+  __shared__ T Bs[TK][TN + 4];
+  const int M = 2 * nr;
+  const int m0 = blockIdx.y * TM;
+  const int q0 = blockIdx.x * TN;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  const int lr = tid >> 2, lk = (tid & 3) * 4;
+  for (long k0 = 0; k0 < n_ov; k0 += TK) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      long k = k0 + lk + u;
+      As[lk + u][lr] = (m0 + lr < M && k < n_ov) ? U[(long)(m0 + lr) * n_ov + k] : T(0);
+      Bs[lk + u][lr] = (q0 + lr < n_aux && k < n_ov) ? B[(long)(q0 + lr) * n_ov + k] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][2 * ty + (i & 1) + 32 * (i >> 1)];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int r = m0 + 2 * ty + (i & 1) + 32 * (i >> 1);
+    if (r >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int P = q0 + tx + 16 * j;
+      if (P >= n_aux) continue;
+      T v = acc[i][j];
+      if (mode == 1) {
+        T vin = V[(long)r * n_aux + P];
+        v = ((r & 1) ? -vin : vin) - v;
+      }
+      out[(long)r * n_aux + P] = v;
+    }
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+template <typename T>
+void launch_pi_syrk(const T* B, const double* eps, int n_occ, int n_virt, int n_aux, const double* xi, int n_xi,
+                    T* out, int mode, cudaStream_t s) {
+  int nb = (n_aux + TM - 1) / TM;
+  dim3 grid(nb * (nb + 1) / 2, n_xi);
+  pi_syrk_kernel<T><<<grid, NT, 0, s>>>(B, eps, n_occ, n_virt, n_aux, xi, out, mode);
+}
+
+void launch_pi_complex_dense(const double* B, const double* eps, int n_occ, int n_virt, int n_aux, double x,
+                             double eta, double* Ar, double* Ai, cudaStream_t s) {
+  int nb = (n_aux + TM - 1) / TM;
+  dim3 grid(nb, nb);
+  pi_complex_kernel<<<grid, NT, 0, s>>>(B, eps, n_occ, n_virt, n_aux, x, eta, Ar, Ai);
+}
+
+template <typename T>
+void launch_cholesky(T* base, int n, long stride, int batch, int* info, cudaStream_t s) {
+  cholesky_kernel<T><<<batch, CH_THREADS, 0, s>>>(base, n, stride, info);
+}
+
+int trsm_w_default_ctas() {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  return 2 * (nsm > 0 ? nsm : 148);
+}
+
+template <typename T>
+size_t trsm_w_scratch_elems(int n, int n_cta) {
+  return (size_t)n_cta * (size_t)(((n + 63) / 64) * 64) * 64;
+}
+
+template <typename T>
+void launch_trsm_w(const T* Lbase, long Lstride, int n, int n_g, const int* g_out, const T* Bn, int R, double* W,
+                   int w_ld, T* scratch, int n_cta, cudaStream_t s) {
+  size_t smem = sizeof(T) * (2 * TK * (TM + 4) + 2 * 64 * 65) + sizeof(double) * 2 * 16 * 64;
+  cudaFuncSetAttribute(trsm_w_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  long items = (long)n_g * ((R + 63) / 64);
+  int grid = (int)(items < n_cta ? items : n_cta);
+  if (grid <= 0) return;
+  trsm_w_kernel<T><<<grid, NT, smem, s>>>(Lbase, Lstride, n, n_g, g_out, Bn, R, W, w_ld, scratch);
+}
+
+template <typename T>
+void launch_op_gemm1(const T* V, const T* B, const double* eps, int n_occ, int n_virt, int n_aux, const double* x,
+                     double eta, int nr, T* U, int mode, cudaStream_t s) {
+  long n_ov = (long)n_occ * n_virt;
+  dim3 grid((unsigned)((n_ov + TN - 1) / TN), (2 * nr + TM - 1) / TM);
+  op_gemm1_kernel<T><<<grid, NT, 0, s>>>(V, B, eps, n_occ, n_virt, n_aux, x, eta, nr, U, mode);
+}
+
+template <typename T>
+void launch_op_gemm2(const T* U, const T* B, int n_aux, int n_ov, int nr, const T* V, T* out, int mode,
+                     cudaStream_t s) {
+  dim3 grid((n_aux + TN - 1) / TN, (2 * nr + TM - 1) / TM);
+  op_gemm2_kernel<T><<<grid, NT, 0, s>>>(U, B, n_aux, (long)n_ov, nr, V, out, mode);
+}
+
+#define GW_INST(T)                                                                                              \
+  template void launch_pi_syrk<T>(const T*, const double*, int, int, int, const double*, int, T*, int,          \
+                                  cudaStream_t);                                                                \
+  template void launch_cholesky<T>(T*, int, long, int, int*, cudaStream_t);                                     \
+  template size_t trsm_w_scratch_elems<T>(int, int);                                                            \
+  template void launch_trsm_w<T>(const T*, long, int, int, const int*, const T*, int, double*, int, T*, int,    \
+                                 cudaStream_t);                                                                 \
+  template void launch_op_gemm1<T>(const T*, const T*, const double*, int, int, int, const double*, double, int, \
+                                   T*, int, cudaStream_t);                                                      \
+  template void launch_op_gemm2<T>(const T*, const T*, int, int, int, const T*, T*, int, cudaStream_t);
+GW_INST(double)
+GW_INST(float)
+#undef GW_INST
+
+}  // namespace gw

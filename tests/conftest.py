@@ -11,3 +11,12 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+
+
+@pytest.fixture(scope="session")
+def gwlib():
+    """Build (if stale) and load libgw.so."""
+    from paper_2107_10423_gb300 import build
+    build.build_all()
+    from paper_2107_10423_gb300 import gw
+    return gw.load()

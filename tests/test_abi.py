@@ -1,0 +1,98 @@
+"""C ABI: the library builds, loads without a GPU, exports every declared entry point, and rejects bad
+arguments before touching the device."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import gw_oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "gw.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gw_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(gwlib):
+    names = _declared()
+    assert "gw_plan_create" in names and "gw_qp_solve" in names
+    for n in names:
+        assert hasattr(gwlib, n), n
+
+
+def test_binding_lists_every_symbol(gwlib):
+    from paper_2107_10423_gb300 import gw
+    assert sorted(gw.EXPORTED) == _declared()
+
+
+def test_default_config_is_paper_defaults(gwlib):
+    from paper_2107_10423_gb300 import gw
+    c = gw.default_config()
+    # MINRES: at most 25 iterations, 5e-5 on the residual norm, dense fallback above 1e-4 (Sec. 3.3)
+    assert (c.minres_maxit, c.minres_tol, c.minres_fallback_tol) == (25, 5e-5, 1e-4)
+    assert c.n_freq == 128 and c.static_subtraction == 1 and c.precision == gw.GW_PREC_FP64
+
+
+@pytest.mark.parametrize("n,x0", [(16, 0.5), (128, 0.5), (200, 1.3)])
+def test_builtin_grid_matches_oracle(gwlib, n, x0):
+    from paper_2107_10423_gb300 import gw
+    xi, wt = gw.grid(n, x0)
+    rxi, rwt = O.mgl_grid(n, x0)
+    np.testing.assert_allclose(xi, rxi, rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(wt, rwt, rtol=1e-10, atol=1e-15)   # end nodes: 1-t^2 loses digits
+    assert abs(np.sum(wt * x0 / (x0 * x0 + xi ** 2)) - math.pi / 2) < (1e-13 if n >= 64 else 1e-10)
+
+
+def _create(gwlib, cfg, eps, n_t=1, targets=None):
+    from paper_2107_10423_gb300 import gw
+    nb = cfg.n_occ + cfg.n_virt
+    e = np.ascontiguousarray(eps, dtype=np.float64)
+    B = np.zeros((max(cfg.n_aux, 1), max(cfg.n_occ * cfg.n_virt, 1)))
+    Bn = np.zeros((n_t, max(nb, 1), max(cfg.n_aux, 1)))
+    t = np.ascontiguousarray(targets if targets is not None else [0], dtype=np.int32)
+    h = ctypes.c_void_p()
+    st = gwlib.gw_plan_create(ctypes.byref(cfg), e.ctypes.data, B.ctypes.data, Bn.ctypes.data, t.ctypes.data, len(t),
+                              None, None, None, 0, None, ctypes.byref(h))
+    return st, h, gwlib.gw_last_error(None).decode()
+
+
+def test_bad_arguments_rejected_without_gpu(gwlib):
+    from paper_2107_10423_gb300 import gw
+    cfg = gw.default_config(n_occ=0, n_virt=3, n_aux=4)
+    st, h, msg = _create(gwlib, cfg, [0.1, 0.2, 0.3])
+    assert st == gw.GW_ERR_ARG and not h.value and "positive" in msg
+    cfg = gw.default_config(n_occ=2, n_virt=2, n_aux=4)
+    st, h, msg = _create(gwlib, cfg, [-1.0, -2.0, 0.5, 0.7])
+    assert st == gw.GW_ERR_ARG and "ascending" in msg
+    st, h, msg = _create(gwlib, cfg, [-1.0, -0.5, 0.5, 0.7], targets=[7])
+    assert st == gw.GW_ERR_ARG and "out of range" in msg
+    st, h, msg = _create(gwlib, cfg, [-1.0, float("nan"), 0.5, 0.7])
+    assert st == gw.GW_ERR_ARG
+    cfg = gw.default_config(n_occ=2, n_virt=2, n_aux=4, precision=7)
+    st, h, msg = _create(gwlib, cfg, [-1.0, -0.5, 0.5, 0.7])
+    assert st == gw.GW_ERR_ARG and "precision" in msg
+    assert gwlib.gw_grid(0, 0.5, None, None) == gw.GW_ERR_ARG
+    assert gwlib.gw_polarizability(None, None, 0, None) == gw.GW_ERR_ARG
+    gwlib.gw_plan_destroy(None)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_2107_10423_gb300 import gw
+    with pytest.raises(FileNotFoundError):
+        gw.load.__wrapped__(str(tmp_path / "nope.so")) if hasattr(gw.load, "__wrapped__") else \
+            _load_fresh(gw, str(tmp_path / "nope.so"))
+
+
+def _load_fresh(gw, path):
+    saved = gw._lib
+    gw._lib = None
+    try:
+        return gw.load(path)
+    finally:
+        gw._lib = saved

@@ -1,0 +1,116 @@
+"""CUDA path vs the FP64 oracle, element by element on the same seeded inputs (needs a GB300)."""
+import numpy as np
+import pytest
+
+from oracle import gw_oracle as O
+from paper_2107_10423_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TIGHT = dict(minres_tol=1e-12, minres_maxit=600, minres_fallback_tol=1e-9)
+
+
+def _sys(kind):
+    if kind == "water1":
+        return synth.workload(0)
+    if kind == "water2":
+        return synth.water_cluster(2, 21, targets="valence")
+    if kind == "water3_core":
+        return synth.water_cluster(3, 33, targets=[0, 2, 5, 14, 15, 16])
+    raise ValueError(kind)
+
+
+@pytest.fixture(scope="module")
+def gw(gwlib):
+    from paper_2107_10423_gb300 import gw as m
+    return m
+
+
+@pytest.mark.parametrize("kind", ["water1", "water2"])
+def test_pi_fp64(gw, kind):
+    s = _sys(kind)
+    B, Bn = s.b_ia(), s.b_nm()
+    xi = np.array([0.0, 1e-3, 0.37, 2.0, 55.0])
+    with gw.Plan(s.eps, s.n_occ, B, Bn, s.targets) as p:
+        Pi = p.polarizability(xi)
+    for g, x in enumerate(xi):
+        ref = O.pi_imag(s.eps, s.n_occ, B, x)
+        np.testing.assert_allclose(Pi[g], ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+        assert np.array_equal(Pi[g], Pi[g].T)
+
+
+@pytest.mark.parametrize("kind", ["water1", "water2", "water3_core"])
+def test_sigma_cd_fp64(gw, kind):
+    s = _sys(kind)
+    B, Bn = s.b_ia(), s.b_nm()
+    xi, wt = O.mgl_grid(128, 0.5)
+    cd = O.CDSelfEnergy(s.eps, s.n_occ, B, Bn, s.targets, xi, wt, eta=1e-3)
+    rng = np.random.default_rng(5)
+    omega = s.eps[s.targets] + rng.uniform(-0.3, 0.05, len(s.targets))
+    with gw.Plan(s.eps, s.n_occ, B, Bn, s.targets, **TIGHT) as p:
+        sc, dsc, sx = p.sigma_cd(omega)
+    for t in range(len(s.targets)):
+        ref, dref = cd.sigma_c(t, omega[t])
+        assert abs(sc[t] - ref) < 1e-9, (t, sc[t], ref)
+        assert abs(dsc[t] - dref) < 1e-7 * max(1.0, abs(dref)), (t, dsc[t], dref)
+        assert abs(sx[t] - cd.sigma_x(t)) < 1e-13
+
+
+def test_residues_fp64_vs_dense(gw):
+    s = _sys("water2")
+    B, Bn = s.b_ia(), s.b_nm()
+    ti = np.array([0, 1, 3, 5, 7, 9, 2])
+    m = np.array([3, 9, 0, 12, 20, 11, 40])
+    x = np.array([0.05, -0.31, 0.77, 1.4, -0.02, 0.0, 2.3])
+    with gw.Plan(s.eps, s.n_occ, B, Bn, s.targets, **TIGHT) as p:
+        r = p.residues(ti, m, x)
+    for j in range(len(ti)):
+        b = Bn[ti[j], m[j]]
+        w, dw = O.w_corr_and_deriv(O.pi_complex(s.eps, s.n_occ, B, x[j], 1e-3),
+                                   O.dpi_complex(s.eps, s.n_occ, B, x[j], 1e-3), b)
+        assert abs(r["w_re"][j] - w.real) < 1e-10 * max(1, abs(w)), (j, r["w_re"][j], w)
+        assert abs(r["w_im"][j] - w.imag) < 1e-10 * max(1, abs(w))
+        assert abs(r["dw_re"][j] - dw.real) < 1e-8 * max(1, abs(dw)), (j, r["dw_re"][j], dw)
+        assert r["resnorm"][j] <= 1e-12 and r["used_fallback"][j] == 0
+
+
+def test_dense_fallback_matches_oracle(gw):
+    s = _sys("water1")
+    B, Bn = s.b_ia(), s.b_nm()
+    ti, m, x = np.array([0, 1, 1]), np.array([2, 7, 4]), np.array([0.3, -0.9, 1.7])
+    with gw.Plan(s.eps, s.n_occ, B, Bn, s.targets, minres_maxit=2, minres_tol=1e-14,
+                 minres_fallback_tol=1e-13) as p:
+        r = p.residues(ti, m, x)
+    assert np.all(r["used_fallback"] == 1)
+    for j in range(3):
+        w, dw = O.w_corr_and_deriv(O.pi_complex(s.eps, s.n_occ, B, x[j], 1e-3),
+                                   O.dpi_complex(s.eps, s.n_occ, B, x[j], 1e-3), Bn[ti[j], m[j]])
+        assert abs(r["w_re"][j] - w.real) < 1e-10 * max(1, abs(w))
+        assert abs(r["dw_re"][j] - dw.real) < 1e-8 * max(1, abs(dw))
+
+
+@pytest.mark.parametrize("kind,mode", [("water1", "linearised"), ("water1", "steptree"), ("water2", "steptree"),
+                                       ("water3_core", "steptree")])
+def test_qp_fp64_vs_oracle(gw, kind, mode):
+    s = _sys(kind)
+    B, Bn = s.b_ia(), s.b_nm()
+    ref = O.g0w0_cd(s.eps, s.n_occ, B, Bn, s.targets, eta=1e-3, mode=mode)
+    with gw.Plan(s.eps, s.n_occ, B, Bn, s.targets, **TIGHT) as p:
+        e, z, st = p.qp_solve(gw.GW_QP_LINEARISED if mode == "linearised" else gw.GW_QP_STEPTREE)
+    ok = ref["status"] == 0
+    assert np.all(st[ok] == 0)
+    np.testing.assert_allclose(e, ref["e_qp"], rtol=0, atol=1e-5)
+    np.testing.assert_allclose(z, ref["Z"], rtol=0, atol=1e-4)
+
+
+def test_qp_paper_minres_defaults(gw):
+    """Paper defaults (25 iterations, 5e-5, fallback above 1e-4): QP energies stay within 1e-5 Ha of the
+    oracle's exact residues."""
+    s = _sys("water2")
+    B, Bn = s.b_ia(), s.b_nm()
+    ref = O.g0w0_cd(s.eps, s.n_occ, B, Bn, s.targets, eta=1e-3)
+    with gw.Plan(s.eps, s.n_occ, B, Bn, s.targets) as p:
+        e, z, st = p.qp_solve(gw.GW_QP_STEPTREE)
+        stats = p.stats()
+    np.testing.assert_allclose(e, ref["e_qp"], rtol=0, atol=1e-5)
+    assert stats["n_rhs_solved"] > 0
