@@ -129,6 +129,11 @@ gw_status gw_residues_minres(gw_plan_t plan, int n_rhs, const int* target_idx, c
  * Returns GW_ERR_NOT_CONVERGED if any state did not converge. */
 gw_status gw_qp_solve(gw_plan_t plan, gw_qp_mode mode, double* e_qp, double* z_factor, int* state_status);
 
+/* Copy the imaginary-axis table to the host: out [n_targets][n_bas][n_freq + 1] with
+ * out[t][m][g] = W^c_nm(i xi_g) for the grid points g < n_freq and out[t][m][n_freq] = W^c_nm(0)
+ * (Algorithm 1, imaginary-grid loop).  Builds the table first if needed. */
+gw_status gw_w_table(gw_plan_t plan, double* out);
+
 /* Timing and counters of the last calls (host, milliseconds / counts); any pointer may be NULL. */
 typedef struct {
   double ms_screening;         /* Pi + factorisation + W table */

@@ -78,10 +78,20 @@ void launch_minres_finish(const double* B_nm, int n_bas, int n_aux, const int* r
 template <typename T>
 void launch_rowsum_pairs(const T* U, int nr, int n_ov, double* dw_re, double* dw_im, cudaStream_t s);
 
-// Dense fallback: solve (Ar + i Ai) y = b for one right-hand side by complex Gaussian elimination
-// with partial pivoting (single CTA), then W = b^T (y - b), dW = y^T Pi'(x) y.
-void launch_dense_residue(double* Ar, double* Ai, int n, const double* b, double* work, double* result,
-                          int* info, cudaStream_t s);
+// Batched complex LU with partial pivoting (kernels_lu.cu): matrices b at Ar + b*stride, Ai + b*stride.
+template <typename T>
+void launch_zlu(T* Ar, T* Ai, long stride, int n, int batch, int* piv, int* info, cudaStream_t s);
+template <typename T>
+void launch_zlu_solve(const T* Ar, const T* Ai, long stride, int n, int batch, const int* piv, T* yr, T* yi,
+                      long ystride, cudaStream_t s);
+// Fallback bookkeeping: for k < nf with slot index idx[k] (into the MINRES batch), set y planes = (b, 0) before
+// the solve (stage 0), or after it write W = b^T y - b^T b, resnorm 0 and the (u, v) = (y_r, -y_i) rows of V.
+template <typename T>
+void launch_fallback_rhs(const double* B_nm, int n_bas, int n_aux, const int* rt, const int* rm, const int* idx,
+                         int nf, T* y, cudaStream_t s);
+template <typename T>
+void launch_fallback_finish(const double* B_nm, int n_bas, int n_aux, const int* rt, const int* rm, const int* idx,
+                            int nf, const T* y, double* w_re, double* w_im, double* resnorm, T* V, cudaStream_t s);
 
 // R term reduction per target over its right-hand sides [start[t], start[t+1]).
 void launch_residue_reduce(const int* start, int n_t, const double* coef, const double* w_re, const double* dw_re,

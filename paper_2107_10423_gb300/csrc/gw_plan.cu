@@ -46,23 +46,25 @@ struct gw_plan {
   double* d_W = nullptr;      // [n_t][n_bas][n_g + 1]
   float* d_B_ia_f = nullptr;  // mixed: FP32 copy of B_ia
   float* d_B_nm_f = nullptr;  // mixed: FP32 copy of B_nm
+  __nv_bfloat16* d_Bhi = nullptr;   // mixed: BF16 hi/lo split of B_ia, [n_aux][tc_ld(n_ov)]
+  __nv_bfloat16* d_Blo = nullptr;
   bool screening_done = false;
   std::vector<DevBuf*> bufs;
-  DevBuf ws_mat, ws_info, ws_scratch, ws_gout, ws_tc, ws_xi;
+  DevBuf ws_mat, ws_info, ws_scratch, ws_gout, ws_xi, tc_Ahi, tc_Alo, tc_kind, tc_par, tc_err;
   DevBuf mr_V, mr_U, mr_S, mr_vprev, mr_v, mr_d1, mr_d2, mr_x, mr_st, mr_rt, mr_rm, mr_xf, mr_wre, mr_wim,
       mr_dwre, mr_it, mr_res, mr_cnt;
   DevBuf sg_I, sg_dI, sg_R, sg_dR, sg_om, sg_start, sg_coef, sg_act, qp_st;
-  DevBuf fb_Ar, fb_Ai, fb_work, fb_res, fb_info;
+  DevBuf fb_A, fb_y, fb_piv, fb_info, fb_idx;
   int* h_cnt = nullptr;       // pinned
   std::string err;
   gw_stats stats{};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
 
   gw_plan() {
-    DevBuf* all[] = {&ws_mat, &ws_info, &ws_scratch, &ws_gout, &ws_tc, &ws_xi, &mr_V, &mr_U, &mr_S, &mr_vprev,
+    DevBuf* all[] = {&ws_mat, &ws_info, &ws_scratch, &ws_gout, &ws_xi, &tc_Ahi, &tc_Alo, &tc_kind, &tc_par, &tc_err, &mr_V, &mr_U, &mr_S, &mr_vprev,
                      &mr_v, &mr_d1, &mr_d2, &mr_x, &mr_st, &mr_rt, &mr_rm, &mr_xf, &mr_wre, &mr_wim,
                      &mr_dwre, &mr_it, &mr_res, &mr_cnt, &sg_I, &sg_dI, &sg_R, &sg_dR, &sg_om, &sg_start,
-                     &sg_coef, &sg_act, &qp_st, &fb_Ar, &fb_Ai, &fb_work, &fb_res, &fb_info};
+                     &sg_coef, &sg_act, &qp_st, &fb_A, &fb_y, &fb_piv, &fb_info, &fb_idx};
     bufs.assign(all, all + sizeof(all) / sizeof(all[0]));
   }
 };
@@ -125,15 +127,49 @@ double now_ms(gw_plan* P, cudaEvent_t a, cudaEvent_t b) {
   return (double)ms;
 }
 
+// Tensor-core weighted SYRK for `nb` batch entries: out_b = f(B diag(w_b) B^T) with (kind, param) per entry.
+gw_status tc_weighted_syrk(gw_plan* P, const int* kinds, const double* params, int nb, int mode_even, int mode_odd,
+                           float* out) {
+  const int n = P->cfg.n_aux, K = P->n_ov, ld = gw::tc_ld(K);
+  TRY(ensure(P, P->tc_Ahi, sizeof(__nv_bfloat16) * (size_t)nb * n * ld));
+  TRY(ensure(P, P->tc_Alo, sizeof(__nv_bfloat16) * (size_t)nb * n * ld));
+  TRY(ensure(P, P->tc_kind, sizeof(int) * nb));
+  TRY(ensure(P, P->tc_par, sizeof(double) * nb));
+  TRY(ensure(P, P->tc_err, sizeof(int)));
+  CK(cudaMemcpyAsync(P->tc_kind.p, kinds, sizeof(int) * nb, cudaMemcpyHostToDevice, P->stream));
+  CK(cudaMemcpyAsync(P->tc_par.p, params, sizeof(double) * nb, cudaMemcpyHostToDevice, P->stream));
+  CK(cudaMemsetAsync(P->tc_err.p, 0, sizeof(int), P->stream));
+  CK(gw::tc_scale_split(P->d_B_ia_f, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, K, as<int>(P->tc_kind),
+                        as<double>(P->tc_par), P->cfg.eta, nb, as<__nv_bfloat16>(P->tc_Ahi),
+                        as<__nv_bfloat16>(P->tc_Alo), P->stream));
+  CK(gw::tc_gemm(as<__nv_bfloat16>(P->tc_Ahi), as<__nv_bfloat16>(P->tc_Alo), nb, P->d_Bhi, P->d_Blo, n, n, K, 1,
+                 mode_even, mode_odd, out, as<int>(P->tc_err), P->stream));
+  P->stats.n_kernel_launches += 2;
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, P->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+  CK(cudaStreamSynchronize(P->stream));
+  if (herr != 0) return fail(P, GW_ERR_TIMEOUT, "tensor-core GEMM: bounded wait ran out (code %d)", herr);
+  return GW_OK;
+}
+
+// Largest batch of split operands that fits in ~8 GiB.
+int tc_chunk(gw_plan* P, int want) {
+  const size_t per = (size_t)P->cfg.n_aux * gw::tc_ld(P->n_ov) * 4;   // hi + lo
+  size_t c = ((size_t)8 << 30) / (per ? per : 1);
+  return (int)std::max<size_t>(1, std::min<size_t>((size_t)want, c));
+}
+
 // ---------------------------------------------------------------- imaginary-axis screening
 template <typename T>
 gw_status screening_T(gw_plan* P, const T* B, const T* Bn) {
   const int n = P->cfg.n_aux;
   const int n_g1 = P->n_g + 1;
   const int R = P->n_t * P->n_bas;
-  // chunk of frequency matrices held at once: <= 8 GiB and <= n_g1
+  const bool use_tc = (P->cfg.precision == GW_PREC_MIXED);
+  // frequency matrices held at once: <= 8 GiB (and the split-operand budget on the tensor-core path)
   const size_t per = (size_t)n * n * sizeof(T);
   int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_g1, ((size_t)8 << 30) / per));
+  if (use_tc) chunk = tc_chunk(P, chunk);
   TRY(ensure(P, P->ws_mat, per * chunk));
   TRY(ensure(P, P->ws_info, sizeof(int) * chunk));
   TRY(ensure(P, P->ws_gout, sizeof(int) * n_g1));
@@ -142,20 +178,17 @@ gw_status screening_T(gw_plan* P, const T* B, const T* Bn) {
   std::vector<int> gout(n_g1);
   for (int g = 0; g < n_g1; ++g) gout[g] = g;
   CK(cudaMemcpyAsync(P->ws_gout.p, gout.data(), sizeof(int) * n_g1, cudaMemcpyHostToDevice, P->stream));
+  std::vector<double> xi_all(P->h_xi);
+  xi_all.push_back(0.0);
   std::vector<int> info(chunk);
   double ms_pi = 0.0;
   for (int g0 = 0; g0 < n_g1; g0 += chunk) {
     const int nc = std::min(chunk, n_g1 - g0);
     CK(cudaEventRecord(P->ev0, P->stream));
-    bool tc = false;
-    if (P->cfg.precision == GW_PREC_MIXED && sizeof(T) == 4) {
-      gw_status st = gw::pi_tc_build(P->d_B_ia_f, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, P->d_xi + g0, nc,
-                                     reinterpret_cast<float*>(P->ws_mat.p), 1, &P->ws_tc.p, &P->ws_tc.bytes,
-                                     P->stream, &tc);
-      if (st != GW_OK) return fail(P, st, "tensor-core Pi build failed");
-      if (tc) P->stats.n_kernel_launches += 2;
-    }
-    if (!tc) {
+    if (use_tc) {
+      std::vector<int> kinds(nc, 0);
+      TRY(tc_weighted_syrk(P, kinds.data(), xi_all.data() + g0, nc, 1, 1, reinterpret_cast<float*>(P->ws_mat.p)));
+    } else {
       LAUNCH(gw::launch_pi_syrk<T>(B, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, P->d_xi + g0, nc,
                                    as<T>(P->ws_mat), 1, P->stream));
     }
@@ -192,6 +225,75 @@ gw_status ensure_screening(gw_plan* P) {
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   P->screening_done = true;
+  return GW_OK;
+}
+
+// Dense solves for the MINRES batch slots in `need` (Sec. 3.3: build the dielectric matrix and factorise).
+// A_j = 1 - Pi(x_j) is built on the tensor cores (mixed) or by the FP64 SIMT kernel, then factorised by the
+// batched complex LU; W and the derivative-pass vectors are written into the slot.
+template <typename T>
+gw_status dense_fallback(gw_plan* P, const std::vector<int>& need, const int* rt, const int* rm, const double* xf,
+                         double* w_re, double* w_im, double* resnorm) {
+  const int n = P->cfg.n_aux;
+  const size_t mat = (size_t)n * n;
+  const int nneed = (int)need.size();
+  // batch of dense matrices: A planes <= 8 GiB (one LU launch fills the GPU); the tensor-core build runs in
+  // sub-batches sized by the split-operand budget
+  int fb = (int)std::max<size_t>(1, ((size_t)8 << 30) / (2 * mat * sizeof(T)));
+  fb = std::min(fb, nneed);
+  const int sub = (sizeof(T) == 4) ? std::max(1, tc_chunk(P, 2 * fb) / 2) : fb;
+  TRY(ensure(P, P->fb_A, sizeof(T) * 2 * mat * fb));
+  TRY(ensure(P, P->fb_y, sizeof(T) * 2 * (size_t)n * fb));
+  TRY(ensure(P, P->fb_piv, sizeof(int) * (size_t)n * fb));
+  TRY(ensure(P, P->fb_info, sizeof(int) * fb));
+  TRY(ensure(P, P->fb_idx, sizeof(int) * nneed));
+  CK(cudaMemcpyAsync(P->fb_idx.p, need.data(), sizeof(int) * nneed, cudaMemcpyHostToDevice, P->stream));
+  std::vector<double> hx(nneed);
+  {
+    int mx = 0;
+    for (int j : need) mx = std::max(mx, j);
+    std::vector<double> xs(mx + 1);
+    CK(cudaMemcpyAsync(xs.data(), xf, sizeof(double) * (mx + 1), cudaMemcpyDeviceToHost, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+    for (int k = 0; k < nneed; ++k) hx[k] = xs[need[k]];
+  }
+  std::vector<int> info(fb);
+  for (int k0 = 0; k0 < nneed; k0 += fb) {
+    const int nf = std::min(fb, nneed - k0);
+    T* A = as<T>(P->fb_A);
+    if (sizeof(T) == 4) {
+      for (int s0 = 0; s0 < nf; s0 += sub) {
+        const int ns = std::min(sub, nf - s0);
+        std::vector<int> kinds(2 * ns);
+        std::vector<double> par(2 * ns);
+        for (int k = 0; k < ns; ++k) {
+          kinds[2 * k] = 1;
+          kinds[2 * k + 1] = 2;
+          par[2 * k] = par[2 * k + 1] = hx[k0 + s0 + k];
+        }
+        TRY(tc_weighted_syrk(P, kinds.data(), par.data(), 2 * ns, 1, 2,
+                             reinterpret_cast<float*>(A) + 2 * mat * (size_t)s0));
+      }
+    } else {
+      for (int k = 0; k < nf; ++k)
+        LAUNCH(gw::launch_pi_complex_dense(P->d_B_ia, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, hx[k0 + k],
+                                           P->cfg.eta, reinterpret_cast<double*>(A) + 2 * mat * k,
+                                           reinterpret_cast<double*>(A) + 2 * mat * k + mat, P->stream));
+    }
+    LAUNCH(gw::launch_fallback_rhs<T>(P->d_B_nm, P->n_bas, n, rt, rm, as<int>(P->fb_idx) + k0, nf, as<T>(P->fb_y),
+                                      P->stream));
+    LAUNCH(gw::launch_zlu<T>(A, A + mat, (long)(2 * mat), n, nf, as<int>(P->fb_piv), as<int>(P->fb_info),
+                             P->stream));
+    LAUNCH(gw::launch_zlu_solve<T>(A, A + mat, (long)(2 * mat), n, nf, as<int>(P->fb_piv), as<T>(P->fb_y),
+                                   as<T>(P->fb_y) + n, 2L * n, P->stream));
+    LAUNCH(gw::launch_fallback_finish<T>(P->d_B_nm, P->n_bas, n, rt, rm, as<int>(P->fb_idx) + k0, nf,
+                                         as<T>(P->fb_y), w_re, w_im, resnorm, as<T>(P->mr_V), P->stream));
+    CK(cudaMemcpyAsync(info.data(), P->fb_info.p, sizeof(int) * nf, cudaMemcpyDeviceToHost, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+    for (int k = 0; k < nf; ++k)
+      if (info[k] != 0) return fail(P, GW_ERR_NUMERIC, "dense residue solve: zero pivot at column %d", info[k]);
+    P->stats.n_fallback += nf;
+  }
   return GW_OK;
 }
 
@@ -241,9 +343,12 @@ gw_status residues_T(gw_plan* P, int nr_total, const int* d_rt, const int* d_rm,
                                        as<double>(P->mr_v), as<double>(P->mr_d1), as<double>(P->mr_d2),
                                        as<double>(P->mr_x), as<MinresState>(P->mr_st), as<T>(P->mr_V),
                                        as<int>(P->mr_cnt), P->stream));
-      CK(cudaMemcpyAsync(P->h_cnt, P->mr_cnt.p, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
-      CK(cudaStreamSynchronize(P->stream));
-      if (*P->h_cnt == 0) break;
+      // poll the active count every 8 iterations (finished right-hand sides are frozen by the step kernel)
+      if ((it & 7) == 7 || it + 1 == P->cfg.minres_maxit) {
+        CK(cudaMemcpyAsync(P->h_cnt, P->mr_cnt.p, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+        CK(cudaStreamSynchronize(P->stream));
+        if (*P->h_cnt == 0) break;
+      }
     }
     LAUNCH(gw::launch_minres_finish<T>(P->d_B_nm, P->n_bas, n, rt, rm, nr, as<double>(P->mr_x),
                                        as<MinresState>(P->mr_st), w_re + j0, w_im + j0, iters + j0, resnorm + j0,
@@ -258,44 +363,7 @@ gw_status residues_T(gw_plan* P, int nr_total, const int* d_rt, const int* d_rm,
       if (h_fallback) h_fallback[j0 + j] = bad ? 1 : 0;
       if (bad) need.push_back(j);
     }
-    if (!need.empty()) {
-      std::vector<int> ht(nr), hm(nr);
-      std::vector<double> hx(nr);
-      CK(cudaMemcpyAsync(ht.data(), rt, sizeof(int) * nr, cudaMemcpyDeviceToHost, P->stream));
-      CK(cudaMemcpyAsync(hm.data(), rm, sizeof(int) * nr, cudaMemcpyDeviceToHost, P->stream));
-      CK(cudaMemcpyAsync(hx.data(), xf, sizeof(double) * nr, cudaMemcpyDeviceToHost, P->stream));
-      TRY(ensure(P, P->fb_Ar, sizeof(double) * (size_t)n * n));
-      TRY(ensure(P, P->fb_Ai, sizeof(double) * (size_t)n * n));
-      TRY(ensure(P, P->fb_work, sizeof(double) * 2 * (size_t)n));
-      TRY(ensure(P, P->fb_res, sizeof(double) * 2));
-      TRY(ensure(P, P->fb_info, sizeof(int)));
-      CK(cudaStreamSynchronize(P->stream));
-      for (int j : need) {
-        const double* b = P->d_B_nm + ((size_t)ht[j] * P->n_bas + hm[j]) * n;
-        LAUNCH(gw::launch_pi_complex_dense(P->d_B_ia, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, hx[j], eta,
-                                           as<double>(P->fb_Ar), as<double>(P->fb_Ai), P->stream));
-        LAUNCH(gw::launch_dense_residue(as<double>(P->fb_Ar), as<double>(P->fb_Ai), n, b, as<double>(P->fb_work),
-                                        as<double>(P->fb_res), as<int>(P->fb_info), P->stream));
-        double res[2];
-        int info = 0;
-        std::vector<double> y(2 * (size_t)n);
-        CK(cudaMemcpyAsync(res, P->fb_res.p, sizeof(res), cudaMemcpyDeviceToHost, P->stream));
-        CK(cudaMemcpyAsync(&info, P->fb_info.p, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
-        CK(cudaMemcpyAsync(y.data(), P->fb_work.p, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, P->stream));
-        CK(cudaStreamSynchronize(P->stream));
-        if (info != 0) return fail(P, GW_ERR_NUMERIC, "dense residue solve: singular pivot");
-        CK(cudaMemcpyAsync(w_re + j0 + j, &res[0], sizeof(double), cudaMemcpyHostToDevice, P->stream));
-        CK(cudaMemcpyAsync(w_im + j0 + j, &res[1], sizeof(double), cudaMemcpyHostToDevice, P->stream));
-        double zero = 0.0;
-        CK(cudaMemcpyAsync(resnorm + j0 + j, &zero, sizeof(double), cudaMemcpyHostToDevice, P->stream));
-        std::vector<T> yt(2 * (size_t)n);
-        for (size_t i = 0; i < yt.size(); ++i) yt[i] = (T)y[i];
-        CK(cudaMemcpyAsync(as<T>(P->mr_V) + (size_t)2 * j * n, yt.data(), sizeof(T) * 2 * n,
-                           cudaMemcpyHostToDevice, P->stream));
-        CK(cudaStreamSynchronize(P->stream));
-        P->stats.n_fallback++;
-      }
-    }
+    if (!need.empty()) TRY(dense_fallback<T>(P, need, rt, rm, xf, w_re + j0, w_im + j0, resnorm + j0));
     // dW/dx = y^T Pi'(x) y
     LAUNCH(gw::launch_op_gemm1<T>(as<T>(P->mr_V), B, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, xf, eta, nr,
                                   as<T>(P->mr_U), 1, P->stream));
@@ -450,6 +518,8 @@ static void free_plan(gw_plan* P) {
   }
   if (P->d_B_ia_f) cudaFree(P->d_B_ia_f);
   if (P->d_B_nm_f) cudaFree(P->d_B_nm_f);
+  if (P->d_Bhi) cudaFree(P->d_Bhi);
+  if (P->d_Blo) cudaFree(P->d_Blo);
   if (P->h_cnt) cudaFreeHost(P->h_cnt);
   if (P->ev0) cudaEventDestroy(P->ev0);
   if (P->ev1) cudaEventDestroy(P->ev1);
@@ -518,6 +588,22 @@ static gw_status plan_create_impl(gw_plan* P, const gw_config* cfg, const double
     CK(cudaMalloc(&P->d_B_nm_f, sizeof(float) * nBn));
     LAUNCH((convert_f64_f32_kernel<<<1024, 256, 0, P->stream>>>(P->d_B_ia, P->d_B_ia_f, nB)));
     LAUNCH((convert_f64_f32_kernel<<<1024, 256, 0, P->stream>>>(P->d_B_nm, P->d_B_nm_f, nBn)));
+    const size_t nsplit = (size_t)n * gw::tc_ld(P->n_ov);
+    CK(cudaMalloc(&P->d_Bhi, sizeof(__nv_bfloat16) * nsplit));
+    CK(cudaMalloc(&P->d_Blo, sizeof(__nv_bfloat16) * nsplit));
+    int* dk = nullptr;
+    double* dp = nullptr;
+    CK(cudaMalloc(&dk, sizeof(int)));
+    CK(cudaMalloc(&dp, sizeof(double)));
+    const int k3 = 3;
+    const double p0 = 0.0;
+    CK(cudaMemcpyAsync(dk, &k3, sizeof(int), cudaMemcpyHostToDevice, P->stream));
+    CK(cudaMemcpyAsync(dp, &p0, sizeof(double), cudaMemcpyHostToDevice, P->stream));
+    CK(gw::tc_scale_split(P->d_B_ia_f, P->d_eps, cfg->n_occ, cfg->n_virt, n, P->n_ov, dk, dp, 0.0, 1, P->d_Bhi,
+                          P->d_Blo, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+    cudaFree(dk);
+    cudaFree(dp);
   }
   LAUNCH(gw::launch_sigma_x(P->d_B_nm, n_targets, P->n_bas, n, cfg->n_occ, P->d_sx, P->stream));
   P->h_sx.resize(n_targets);
@@ -590,15 +676,12 @@ gw_status gw_polarizability(gw_plan_t P, const double* xi, int n_xi, double* pi_
   CK(cudaEventRecord(P->ev0, P->stream));
   if (P->cfg.precision == GW_PREC_MIXED) {
     TRY(ensure(P, P->ws_mat, sizeof(float) * (size_t)n * n * n_xi));
-    bool tc = false;
-    st = gw::pi_tc_build(P->d_B_ia_f, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, as<double>(dxi), n_xi,
-                         as<float>(P->ws_mat), 0, &P->ws_tc.p, &P->ws_tc.bytes, P->stream, &tc);
-    if (st != GW_OK) return fail(P, st, "tensor-core Pi build failed");
-    if (!tc)
-      LAUNCH(gw::launch_pi_syrk<float>(P->d_B_ia_f, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, as<double>(dxi), n_xi,
-                                       as<float>(P->ws_mat), 0, P->stream));
-    else
-      P->stats.n_kernel_launches += 2;
+    const int chunk = tc_chunk(P, n_xi);
+    for (int g0 = 0; g0 < n_xi; g0 += chunk) {
+      const int nc = std::min(chunk, n_xi - g0);
+      std::vector<int> kinds(nc, 0);
+      TRY(tc_weighted_syrk(P, kinds.data(), xi + g0, nc, 0, 0, as<float>(P->ws_mat) + (size_t)g0 * n * n));
+    }
     CK(cudaEventRecord(P->ev1, P->stream));
     if (pi_out) {
       std::vector<float> h((size_t)n * n * n_xi);
@@ -755,6 +838,13 @@ gw_status gw_grid(int N, double x0, double* xi, double* wt) {
     xi[k] = x0 * (1.0 + t) / (1.0 - t);
     wt[k] = 2.0 * x0 * wgl / ((1.0 - t) * (1.0 - t));
   }
+  return GW_OK;
+}
+
+gw_status gw_w_table(gw_plan_t P, double* out) {
+  if (!P || !out) return P ? fail(P, GW_ERR_ARG, "out is NULL") : GW_ERR_ARG;
+  TRY(ensure_screening(P));
+  CK(cudaMemcpy(out, P->d_W, sizeof(double) * (size_t)P->n_t * P->n_bas * (P->n_g + 1), cudaMemcpyDeviceToHost));
   return GW_OK;
 }
 

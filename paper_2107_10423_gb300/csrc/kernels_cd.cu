@@ -1,6 +1,6 @@
 // Contour-deformation kernels: exchange self-energy, the imaginary-axis quadrature (eq. "inn"),
-// batched MINRES recurrences for the residue systems (eq. "rnn", Sec. 3.3), the dense fallback
-// solve, and the step-tree QP search (Sec. 3.4, Fig. "steptree").  All arithmetic here is FP64.
+// batched MINRES recurrences for the residue systems (eq. "rnn", Sec. 3.3), fallback bookkeeping,
+// and the step-tree QP search (Sec. 3.4, Fig. "steptree").  All arithmetic here is FP64.
 #include "gw_internal.cuh"
 
 #include <cmath>
@@ -229,104 +229,42 @@ __global__ void rowsum_pairs_kernel(const T* __restrict__ U, long n_ov, double* 
   }
 }
 
-// Complex Gaussian elimination with partial pivoting, single CTA.  A = Ar + i Ai (n x n, destroyed),
-// right-hand side b (real).  result[0..1] = W = b^T(y - b); y written to work[0..2n) as (y_r, -y_i).
-__global__ void __launch_bounds__(1024) dense_residue_kernel(double* Ar, double* Ai, int n, const double* __restrict__ b,
-                                                             double* work, double* result, int* info) {
-  __shared__ double bv[32];
-  __shared__ int bi[32];
-  __shared__ int piv_s;
-  double* yr = work;            // rhs / solution, real part
-  double* yi = work + n;        // imaginary part
-  for (int i = threadIdx.x; i < n; i += blockDim.x) { yr[i] = b[i]; yi[i] = 0.0; }
-  if (threadIdx.x == 0) *info = 0;
-  __syncthreads();
-  for (int k = 0; k < n; ++k) {
-    // pivot search on column k
-    double best = -1.0;
-    int bidx = k;
-    for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
-      double m = Ar[(long)i * n + k] * Ar[(long)i * n + k] + Ai[(long)i * n + k] * Ai[(long)i * n + k];
-      if (m > best) { best = m; bidx = i; }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      double ob = __shfl_xor_sync(0xffffffffu, best, o);
-      int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
-      if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
-    }
-    if ((threadIdx.x & 31) == 0) { bv[threadIdx.x >> 5] = best; bi[threadIdx.x >> 5] = bidx; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double bb = -1.0;
-      int ii = k;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-        if (bv[w] > bb || (bv[w] == bb && bi[w] < ii)) { bb = bv[w]; ii = bi[w]; }
-      piv_s = ii;
-      if (!(bb > 0.0)) *info = 1;
-    }
-    __syncthreads();
-    const int p = piv_s;
-    if (p != k) {
-      for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        double t = Ar[(long)k * n + j]; Ar[(long)k * n + j] = Ar[(long)p * n + j]; Ar[(long)p * n + j] = t;
-        t = Ai[(long)k * n + j]; Ai[(long)k * n + j] = Ai[(long)p * n + j]; Ai[(long)p * n + j] = t;
-      }
-      if (threadIdx.x == 0) {
-        double t = yr[k]; yr[k] = yr[p]; yr[p] = t;
-        t = yi[k]; yi[k] = yi[p]; yi[p] = t;
-      }
-    }
-    __syncthreads();
-    const double pr = Ar[(long)k * n + k], pi = Ai[(long)k * n + k];
-    const double pd = pr * pr + pi * pi;
-    const double ipr = pd > 0.0 ? pr / pd : 0.0, ipi = pd > 0.0 ? -pi / pd : 0.0;   // 1/pivot
-    // eliminate rows below: one warp per row
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int i = k + 1 + wid; i < n; i += nw) {
-      const double ar = Ar[(long)i * n + k], ai = Ai[(long)i * n + k];
-      const double lr = ar * ipr - ai * ipi, li = ar * ipi + ai * ipr;
-      for (int j = k + 1 + lane; j < n; j += 32) {
-        const double ur = Ar[(long)k * n + j], ui = Ai[(long)k * n + j];
-        Ar[(long)i * n + j] -= lr * ur - li * ui;
-        Ai[(long)i * n + j] -= lr * ui + li * ur;
-      }
-      if (lane == 0) {
-        const double yrk = yr[k], yik = yi[k];
-        yr[i] -= lr * yrk - li * yik;
-        yi[i] -= lr * yik + li * yrk;
-      }
-    }
-    __syncthreads();
+template <typename T>
+__global__ void fallback_rhs_kernel(const double* __restrict__ B_nm, int n_bas, int n_aux, const int* __restrict__ rt,
+                                    const int* __restrict__ rm, const int* __restrict__ idx, T* __restrict__ y) {
+  const int k = blockIdx.x, j = idx[k];
+  const double* b = B_nm + ((long)rt[j] * n_bas + rm[j]) * n_aux;
+  T* yr = y + (long)k * 2 * n_aux;
+  for (int i = threadIdx.x; i < n_aux; i += blockDim.x) {
+    yr[i] = (T)b[i];
+    yr[n_aux + i] = T(0);
   }
-  // back substitution
-  for (int k = n - 1; k >= 0; --k) {
-    double sr = 0.0, si = 0.0;
-    for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) {
-      const double ar = Ar[(long)k * n + j], ai = Ai[(long)k * n + j];
-      sr += ar * yr[j] - ai * yi[j];
-      si += ar * yi[j] + ai * yr[j];
-    }
-    sr = block_sum(sr, bv);
-    si = block_sum(si, bv);
-    if (threadIdx.x == 0) {
-      const double rr = yr[k] - sr, ri = yi[k] - si;
-      const double pr = Ar[(long)k * n + k], pi = Ai[(long)k * n + k];
-      const double pd = pr * pr + pi * pi;
-      yr[k] = pd > 0.0 ? (rr * pr + ri * pi) / pd : 0.0;
-      yi[k] = pd > 0.0 ? (ri * pr - rr * pi) / pd : 0.0;
-    }
-    __syncthreads();
+}
+
+template <typename T>
+__global__ void fallback_finish_kernel(const double* __restrict__ B_nm, int n_bas, int n_aux,
+                                       const int* __restrict__ rt, const int* __restrict__ rm,
+                                       const int* __restrict__ idx, const T* __restrict__ y, double* w_re,
+                                       double* w_im, double* resnorm, T* V) {
+  __shared__ double buf[32];
+  const int k = blockIdx.x, j = idx[k];
+  const double* b = B_nm + ((long)rt[j] * n_bas + rm[j]) * n_aux;
+  const T* yr = y + (long)k * 2 * n_aux;
+  const T* yi = yr + n_aux;
+  double ar = 0.0, ai = 0.0;
+  for (int i = threadIdx.x; i < n_aux; i += blockDim.x) {
+    ar += b[i] * ((double)yr[i] - b[i]);
+    ai += b[i] * (double)yi[i];
+    V[(long)(2 * j) * n_aux + i] = yr[i];
+    V[(long)(2 * j + 1) * n_aux + i] = -yi[i];
   }
-  // W = b^T y - b^T b; store (u, v) = (y_r, -y_i)
-  double wr = 0.0, wi = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    wr += b[i] * (yr[i] - b[i]);
-    wi += b[i] * yi[i];
+  ar = block_sum(ar, buf);
+  ai = block_sum(ai, buf);
+  if (threadIdx.x == 0) {
+    w_re[j] = ar;
+    w_im[j] = ai;
+    resnorm[j] = 0.0;
   }
-  wr = block_sum(wr, bv);
-  wi = block_sum(wi, bv);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) yi[i] = -yi[i];
-  if (threadIdx.x == 0) { result[0] = wr; result[1] = wi; }
 }
 
 __global__ void residue_reduce_kernel(const int* __restrict__ start, int n_t, const double* __restrict__ coef,
@@ -501,9 +439,17 @@ void launch_rowsum_pairs(const T* U, int nr, int n_ov, double* dw_re, double* dw
   if (nr > 0) rowsum_pairs_kernel<T><<<nr, RT, 0, s>>>(U, (long)n_ov, dw_re, dw_im);
 }
 
-void launch_dense_residue(double* Ar, double* Ai, int n, const double* b, double* work, double* result, int* info,
-                          cudaStream_t s) {
-  dense_residue_kernel<<<1, 1024, 0, s>>>(Ar, Ai, n, b, work, result, info);
+template <typename T>
+void launch_fallback_rhs(const double* B_nm, int n_bas, int n_aux, const int* rt, const int* rm, const int* idx,
+                         int nf, T* y, cudaStream_t s) {
+  if (nf > 0) fallback_rhs_kernel<T><<<nf, RT, 0, s>>>(B_nm, n_bas, n_aux, rt, rm, idx, y);
+}
+
+template <typename T>
+void launch_fallback_finish(const double* B_nm, int n_bas, int n_aux, const int* rt, const int* rm, const int* idx,
+                            int nf, const T* y, double* w_re, double* w_im, double* resnorm, T* V, cudaStream_t s) {
+  if (nf > 0)
+    fallback_finish_kernel<T><<<nf, RT, 0, s>>>(B_nm, n_bas, n_aux, rt, rm, idx, y, w_re, w_im, resnorm, V);
 }
 
 void launch_residue_reduce(const int* start, int n_t, const double* coef, const double* w_re, const double* dw_re,
@@ -529,7 +475,11 @@ void launch_qp_step(QPState* st, const double* R, const double* dR, const double
                                       MinresState*, T*, int*, cudaStream_t);                                      \
   template void launch_minres_finish<T>(const double*, int, int, const int*, const int*, int, const double*,      \
                                         const MinresState*, double*, double*, int*, double*, T*, cudaStream_t);   \
-  template void launch_rowsum_pairs<T>(const T*, int, int, double*, double*, cudaStream_t);
+  template void launch_rowsum_pairs<T>(const T*, int, int, double*, double*, cudaStream_t);                      \
+  template void launch_fallback_rhs<T>(const double*, int, int, const int*, const int*, const int*, int, T*,       \
+                                       cudaStream_t);                                                            \
+  template void launch_fallback_finish<T>(const double*, int, int, const int*, const int*, const int*, int,       \
+                                          const T*, double*, double*, double*, T*, cudaStream_t);
 GW_INST(double)
 GW_INST(float)
 #undef GW_INST

@@ -254,7 +254,8 @@ __global__ void __launch_bounds__(NT) trsm_w_kernel(const T* __restrict__ Lbase,
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int n_ct = (R + 63) / 64;
   const int nJ = (n + 63) / 64;
-  T* Y = scratch + (long)blockIdx.x * n * 64;
+  // per-CTA slice of [nJ*64][64]: the last row block is written in full (zeros past n)
+  T* Y = scratch + (long)blockIdx.x * nJ * 64 * 64;
   const long n_items = (long)n_g * n_ct;
   for (long item = blockIdx.x; item < n_items; item += gridDim.x) {
     const int g = (int)(item / n_ct);

@@ -1,0 +1,296 @@
+// Batched dense solves of the residue systems (1 - Pi(x)) y = b for right-hand sides whose MINRES run
+// stayed above the fallback threshold (Sec. 3.3: "the dielectric matrix is actually built" and factorised;
+// the paper uses Bunch-Kaufman, this library a complex LU with partial pivoting, which gives the same solution).
+// One CTA per matrix; the complex matrix is stored as two real planes (Ar, Ai), row-major n x n.
+#include "gw_internal.cuh"
+
+namespace gw {
+namespace {
+
+constexpr int LU_NB = 32;        // panel width
+constexpr int LU_T = 512;        // threads per CTA
+constexpr int TT = 64;           // trailing-update tile
+
+template <typename T>
+struct cplx {
+  T r, i;
+};
+
+template <typename T>
+__device__ __forceinline__ cplx<T> cdiv(cplx<T> a, cplx<T> b) {
+  const T d = b.r * b.r + b.i * b.i;
+  return {(a.r * b.r + a.i * b.i) / d, (a.i * b.r - a.r * b.i) / d};
+}
+
+// Block-wide argmax of |a|^2 over rows [r0, n) of column c; ties to the lower row.
+template <typename T>
+__device__ int pivot_row(const T* Ar, const T* Ai, int n, int c, int r0, double* sv, int* si) {
+  double best = -1.0;
+  int bidx = r0;
+  for (int i = r0 + threadIdx.x; i < n; i += blockDim.x) {
+    const double m = (double)Ar[(long)i * n + c] * Ar[(long)i * n + c] + (double)Ai[(long)i * n + c] * Ai[(long)i * n + c];
+    if (m > best) { best = m; bidx = i; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+    if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) { sv[threadIdx.x >> 5] = best; si[threadIdx.x >> 5] = bidx; }
+  __syncthreads();
+  double bb = -1.0;
+  int ii = r0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+    if (sv[w] > bb || (sv[w] == bb && si[w] < ii)) { bb = sv[w]; ii = si[w]; }
+  return bb > 0.0 ? ii : -1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(LU_T) zlu_kernel(T* Ar_base, T* Ai_base, long stride, int n, int* piv_base,
+                                                   int* info) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  T* Lr = reinterpret_cast<T*>(sm);               // [TT][LU_NB+1]
+  T* Li = Lr + TT * (LU_NB + 1);
+  T* Ur = Li + TT * (LU_NB + 1);                  // [LU_NB][TT+1]
+  T* Ui = Ur + LU_NB * (TT + 1);
+  __shared__ double sv[32];
+  __shared__ int si[32];
+  T* Ar = Ar_base + (long)blockIdx.x * stride;
+  T* Ai = Ai_base + (long)blockIdx.x * stride;
+  int* piv = piv_base + (long)blockIdx.x * n;
+  int bad = 0;
+  for (int k0 = 0; k0 < n; k0 += LU_NB) {
+    const int nb = min(LU_NB, n - k0), k1 = k0 + nb;
+    // ---- panel factorisation (columns k0..k1-1) with partial pivoting; rows swapped in full
+    for (int c = k0; c < k1; ++c) {
+      int p = pivot_row(Ar, Ai, n, c, c, sv, si);
+      if (p < 0) { bad = c + 1; p = c; }
+      if (threadIdx.x == 0) piv[c] = p;
+      if (p != c) {
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+          T t = Ar[(long)c * n + j]; Ar[(long)c * n + j] = Ar[(long)p * n + j]; Ar[(long)p * n + j] = t;
+          t = Ai[(long)c * n + j]; Ai[(long)c * n + j] = Ai[(long)p * n + j]; Ai[(long)p * n + j] = t;
+        }
+      }
+      __threadfence_block();
+      __syncthreads();
+      const cplx<T> d = {Ar[(long)c * n + c], Ai[(long)c * n + c]};
+      const bool dz = (d.r == T(0) && d.i == T(0));
+      // multipliers and the rank-1 update of the rest of the panel, one warp per row
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+      for (int i = c + 1 + wid; i < n; i += nw) {
+        cplx<T> l = {Ar[(long)i * n + c], Ai[(long)i * n + c]};
+        l = dz ? cplx<T>{T(0), T(0)} : cdiv(l, d);
+        for (int j = c + 1 + lane; j < k1; j += 32) {
+          const T ur = Ar[(long)c * n + j], ui = Ai[(long)c * n + j];
+          Ar[(long)i * n + j] -= l.r * ur - l.i * ui;
+          Ai[(long)i * n + j] -= l.r * ui + l.i * ur;
+        }
+        __syncwarp();
+        if (lane == 0) { Ar[(long)i * n + c] = l.r; Ai[(long)i * n + c] = l.i; }
+      }
+      __threadfence_block();
+      __syncthreads();
+    }
+    if (k1 >= n) break;
+    // ---- U12 = L11^-1 A12 (unit lower), columns j >= k1 in parallel
+    for (int j = k1 + threadIdx.x; j < n; j += blockDim.x) {
+      for (int r = k0 + 1; r < k1; ++r) {
+        T sr = Ar[(long)r * n + j], sI = Ai[(long)r * n + j];
+        for (int q = k0; q < r; ++q) {
+          const T lr = Ar[(long)r * n + q], li = Ai[(long)r * n + q];
+          const T ur = Ar[(long)q * n + j], ui = Ai[(long)q * n + j];
+          sr -= lr * ur - li * ui;
+          sI -= lr * ui + li * ur;
+        }
+        Ar[(long)r * n + j] = sr;
+        Ai[(long)r * n + j] = sI;
+      }
+    }
+    __threadfence_block();
+    __syncthreads();
+    // ---- trailing update A22 -= L21 U12 in TT x TT tiles
+    const int nt = (n - k1 + TT - 1) / TT;
+    for (int t = 0; t < nt * nt; ++t) {
+      const int r0 = k1 + (t / nt) * TT, c0 = k1 + (t % nt) * TT;
+      for (int idx = threadIdx.x; idx < TT * LU_NB; idx += blockDim.x) {
+        const int rr = idx / LU_NB, q = idx % LU_NB;
+        const bool okr = (r0 + rr < n) && (q < nb);
+        Lr[rr * (LU_NB + 1) + q] = okr ? Ar[(long)(r0 + rr) * n + k0 + q] : T(0);
+        Li[rr * (LU_NB + 1) + q] = okr ? Ai[(long)(r0 + rr) * n + k0 + q] : T(0);
+        const int q2 = idx / TT, cc = idx % TT;
+        const bool okc = (c0 + cc < n) && (q2 < nb);
+        Ur[q2 * (TT + 1) + cc] = okc ? Ar[(long)(k0 + q2) * n + c0 + cc] : T(0);
+        Ui[q2 * (TT + 1) + cc] = okc ? Ai[(long)(k0 + q2) * n + c0 + cc] : T(0);
+      }
+      __syncthreads();
+      const int rr = threadIdx.x >> 3, cb = threadIdx.x & 7;    // 64 rows x (8 cols per thread)
+      T accr[8], acci[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) accr[u] = acci[u] = T(0);
+      for (int q = 0; q < nb; ++q) {
+        const T lr = Lr[rr * (LU_NB + 1) + q], li = Li[rr * (LU_NB + 1) + q];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const T ur = Ur[q * (TT + 1) + cb + 8 * u], ui = Ui[q * (TT + 1) + cb + 8 * u];
+          accr[u] += lr * ur - li * ui;
+          acci[u] += lr * ui + li * ur;
+        }
+      }
+      const int gi = r0 + rr;
+      if (gi < n) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int gj = c0 + cb + 8 * u;
+          if (gj < n) {
+            Ar[(long)gi * n + gj] -= accr[u];
+            Ai[(long)gi * n + gj] -= acci[u];
+          }
+        }
+      }
+      __syncthreads();
+    }
+    __threadfence_block();
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) info[blockIdx.x] = bad;
+}
+
+// Solve A y = rhs with the LU factors and pivots of zlu_kernel; rhs/y complex in two planes of length n
+// (yr, yi), overwritten in place.  Forward and back substitution in blocks of 32 rows: the contribution
+// of finished blocks is a parallel mat-vec, the 32 x 32 triangle is solved by one warp.
+template <typename T>
+__global__ void __launch_bounds__(LU_T) zlu_solve_kernel(const T* Ar_base, const T* Ai_base, long stride, int n,
+                                                         const int* piv_base, T* yr_base, T* yi_base, long ystride) {
+  __shared__ T pr[LU_T], pi_[LU_T];
+  __shared__ T br[32], bi[32];
+  const T* Ar = Ar_base + (long)blockIdx.x * stride;
+  const T* Ai = Ai_base + (long)blockIdx.x * stride;
+  const int* piv = piv_base + (long)blockIdx.x * n;
+  T* yr = yr_base + (long)blockIdx.x * ystride;
+  T* yi = yi_base + (long)blockIdx.x * ystride;
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < n; ++c) {
+      const int p = piv[c];
+      if (p != c) {
+        T t = yr[c]; yr[c] = yr[p]; yr[p] = t;
+        t = yi[c]; yi[c] = yi[p]; yi[p] = t;
+      }
+    }
+  }
+  __threadfence_block();
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // forward: L (unit lower)
+  for (int k0 = 0; k0 < n; k0 += 32) {
+    const int nb = min(32, n - k0);
+    // rows k0..k0+nb-1 minus L[row, 0:k0] y[0:k0]; 16 threads per row
+    const int row = k0 + (threadIdx.x >> 4), part = threadIdx.x & 15;
+    T sr = T(0), si = T(0);
+    if ((threadIdx.x >> 4) < nb)
+      for (int q = part; q < k0; q += 16) {
+        const T lr = Ar[(long)row * n + q], li = Ai[(long)row * n + q];
+        sr += lr * yr[q] - li * yi[q];
+        si += lr * yi[q] + li * yr[q];
+      }
+    for (int o = 8; o > 0; o >>= 1) {
+      sr += __shfl_xor_sync(0xffffffffu, sr, o);
+      si += __shfl_xor_sync(0xffffffffu, si, o);
+    }
+    if (part == 0 && (threadIdx.x >> 4) < nb) { br[threadIdx.x >> 4] = yr[row] - sr; bi[threadIdx.x >> 4] = yi[row] - si; }
+    __syncthreads();
+    if (wid == 0) {
+      T vr = lane < nb ? br[lane] : T(0), vi = lane < nb ? bi[lane] : T(0);
+      for (int r = 1; r < nb; ++r) {
+        // y_r -= sum_{q<r} L[k0+r][k0+q] y_q ; lane r accumulates, y_q broadcast by shuffles
+        T ar = T(0), ai = T(0);
+        if (lane < r) {
+          const T lr = Ar[(long)(k0 + r) * n + k0 + lane], li = Ai[(long)(k0 + r) * n + k0 + lane];
+          ar = lr * vr - li * vi;
+          ai = lr * vi + li * vr;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          ar += __shfl_xor_sync(0xffffffffu, ar, o);
+          ai += __shfl_xor_sync(0xffffffffu, ai, o);
+        }
+        if (lane == r) { vr -= ar; vi -= ai; }
+      }
+      if (lane < nb) { yr[k0 + lane] = vr; yi[k0 + lane] = vi; }
+    }
+    __threadfence_block();
+    __syncthreads();
+  }
+  // backward: U (upper, with diagonal)
+  const int nblk = (n + 31) / 32;
+  for (int bk = nblk - 1; bk >= 0; --bk) {
+    const int k0 = bk * 32, nb = min(32, n - k0), k1 = k0 + nb;
+    const int row = k0 + (threadIdx.x >> 4), part = threadIdx.x & 15;
+    T sr = T(0), si = T(0);
+    if ((threadIdx.x >> 4) < nb)
+      for (int q = k1 + part; q < n; q += 16) {
+        const T ur = Ar[(long)row * n + q], ui = Ai[(long)row * n + q];
+        sr += ur * yr[q] - ui * yi[q];
+        si += ur * yi[q] + ui * yr[q];
+      }
+    for (int o = 8; o > 0; o >>= 1) {
+      sr += __shfl_xor_sync(0xffffffffu, sr, o);
+      si += __shfl_xor_sync(0xffffffffu, si, o);
+    }
+    if (part == 0 && (threadIdx.x >> 4) < nb) { br[threadIdx.x >> 4] = yr[row] - sr; bi[threadIdx.x >> 4] = yi[row] - si; }
+    __syncthreads();
+    if (wid == 0) {
+      T vr = lane < nb ? br[lane] : T(0), vi = lane < nb ? bi[lane] : T(0);
+      for (int r = nb - 1; r >= 0; --r) {
+        // y_r = (b_r - sum_{q>r} U[k0+r][k0+q] y_q) / U[k0+r][k0+r]
+        T ar = T(0), ai = T(0);
+        if (lane > r && lane < nb) {
+          const T ur = Ar[(long)(k0 + r) * n + k0 + lane], ui = Ai[(long)(k0 + r) * n + k0 + lane];
+          ar = ur * vr - ui * vi;
+          ai = ur * vi + ui * vr;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          ar += __shfl_xor_sync(0xffffffffu, ar, o);
+          ai += __shfl_xor_sync(0xffffffffu, ai, o);
+        }
+        if (lane == r) {
+          const cplx<T> num = {vr - ar, vi - ai};
+          const cplx<T> dd = {Ar[(long)(k0 + r) * n + k0 + r], Ai[(long)(k0 + r) * n + k0 + r]};
+          const cplx<T> q = (dd.r == T(0) && dd.i == T(0)) ? cplx<T>{T(0), T(0)} : cdiv(num, dd);
+          vr = q.r;
+          vi = q.i;
+        }
+        // broadcast of the solved y_r happens through the next iterations' shuffles (lane r holds it)
+      }
+      if (lane < nb) { yr[k0 + lane] = vr; yi[k0 + lane] = vi; }
+    }
+    __threadfence_block();
+    __syncthreads();
+  }
+  (void)pr;
+  (void)pi_;
+}
+
+}  // namespace
+
+template <typename T>
+void launch_zlu(T* Ar, T* Ai, long stride, int n, int batch, int* piv, int* info, cudaStream_t s) {
+  const size_t smem = sizeof(T) * (2 * TT * (LU_NB + 1) + 2 * LU_NB * (TT + 1));
+  cudaFuncSetAttribute(zlu_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (batch > 0) zlu_kernel<T><<<batch, LU_T, smem, s>>>(Ar, Ai, stride, n, piv, info);
+}
+
+template <typename T>
+void launch_zlu_solve(const T* Ar, const T* Ai, long stride, int n, int batch, const int* piv, T* yr, T* yi,
+                      long ystride, cudaStream_t s) {
+  if (batch > 0) zlu_solve_kernel<T><<<batch, LU_T, 0, s>>>(Ar, Ai, stride, n, piv, yr, yi, ystride);
+}
+
+template void launch_zlu<float>(float*, float*, long, int, int, int*, int*, cudaStream_t);
+template void launch_zlu<double>(double*, double*, long, int, int, int*, int*, cudaStream_t);
+template void launch_zlu_solve<float>(const float*, const float*, long, int, int, const int*, float*, float*, long,
+                                      cudaStream_t);
+template void launch_zlu_solve<double>(const double*, const double*, long, int, int, const int*, double*, double*,
+                                       long, cudaStream_t);
+
+}  // namespace gw

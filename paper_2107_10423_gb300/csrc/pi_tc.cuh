@@ -1,13 +1,21 @@
-// Tensor-core (tcgen05) build of Pi(i xi) with BF16 hi+lo split operands and FP32 accumulation.
+// tcgen05 batched GEMM with BF16 hi+lo split operands (tc_gemm.cu).
 #pragma once
 #include <cuda_runtime.h>
-#include <cstddef>
-#include "gw.h"
+#include <cuda_bf16.h>
 
 namespace gw {
-// Pi_g = -4 sum_k B[P][k] B[Q][k] D_k/(D_k^2 + xi_g^2) for n_xi frequencies, out [n_xi][n][n] FP32
-// (mode 0: Pi, mode 1: 1 - Pi).  B is FP32 [n][n_ov].  Workspace grows through (*ws, *ws_bytes).
-// *used is false when the shapes are not supported by the tensor-core kernel (caller falls back).
-gw_status pi_tc_build(const float* B, const double* eps, int n_occ, int n_virt, int n, const double* xi, int n_xi,
-                      float* out, int mode, void** ws, size_t* ws_bytes, cudaStream_t s, bool* used);
+// Row length (elements) of the split operand arrays for contraction length K (multiple of 8: 16-byte rows).
+int tc_ld(int K);
+// A_b[m][k] = B[m][k] * w(kinds[b], D_k, params[b]) split into BF16 hi/lo, [batch][M][tc_ld(K)].
+// kinds: 0 Pi(i xi) weight -4D/(D^2+xi^2) (param xi); 1 Re c(x); 2 Im c(x) (param x, broadening eta);
+// 3 unit weight.  kinds/params are device arrays of length batch.  B is FP32 [M][K].
+cudaError_t tc_scale_split(const float* B, const double* eps, int n_occ, int n_virt, int M, int K, const int* kinds,
+                           const double* params, double eta, int batch, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                           cudaStream_t s);
+// out_b = f(A_b Bm^T) for b < batch, out [batch][M][N] FP32; lower != 0 computes lower tiles and mirrors.
+// mode_even / mode_odd for even / odd b: 0 v, 1 delta - v, 2 -v.  *err (device) receives a nonzero code if a
+// bounded wait inside the kernel ran out.
+cudaError_t tc_gemm(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int batch, const __nv_bfloat16* Bhi,
+                    const __nv_bfloat16* Blo, int M, int N, int K, int lower, int mode_even, int mode_odd, float* out,
+                    int* err, cudaStream_t s);
 }  // namespace gw

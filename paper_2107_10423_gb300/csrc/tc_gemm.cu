@@ -1,0 +1,401 @@
+// tcgen05 (5th-generation tensor core) batched GEMM with BF16 hi+lo split operands, used for every
+// dense contraction of the mixed-precision path:
+//   out_b[m][n] = f( sum_k A_b[m][k] * Bm[n][k] ),   A_b = Ahi_b + Alo_b,  Bm = Bhi + Blo  (BF16)
+// computed as Ahi*Bhi + Ahi*Blo + Alo*Bhi with FP32 accumulation in tensor memory (TMEM).
+//  * Pi(i xi_b) (Sec. 3.3): A_b = B_ia o w_b with w_b,ia = -4 D_ia/(D_ia^2 + xi_b^2), Bm = B_ia, lower tiles.
+//  * dense real-axis Pi(x_j) for the residue fallback: A = B_ia o Re c(x_j) and B_ia o Im c(x_j).
+// Operands are staged by TMA (cp.async.bulk.tensor, 128-byte swizzle) into a 3-stage shared-memory
+// ring; one elected thread issues tcgen05.mma; the accumulator is read back with tcgen05.ld.
+// Every mbarrier wait is bounded: on timeout the kernel records an error code and unwinds.
+#include "pi_tc.cuh"
+#include "gw_internal.cuh"
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstdio>
+
+namespace gw {
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 3, THREADS = 192, CHUNK = 4;
+constexpr int TILE_BYTES = BM * BK * 2;               // one 128 x 64 BF16 tile = 16 KiB
+constexpr int STAGE_BYTES = 4 * TILE_BYTES;           // Ahi, Alo, Bhi, Blo
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr uint32_t TMEM_COLS = 256;                  // two 128-column accumulators
+constexpr long long WAIT_LIMIT = 1ll << 26;           // bounded spin on every mbarrier
+
+// tcgen05 instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, N = BN, M = BM.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait; returns false (and records `code`) if the phase did not complete in time.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+  for (long long i = 0; i < WAIT_LIMIT; ++i)
+    if (mbar_try(bar, parity)) return true;
+  atomicCAS(err, 0, code);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major tile with 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;                  // leading byte offset (unused with 128-byte swizzle)
+  d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset
+  d |= (uint64_t)1 << 46;                  // descriptor version
+  d |= (uint64_t)2 << 61;                  // SWIZZLE_128B
+  return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(IDESC), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// grid.x: output tile (lower-triangular enumeration when `lower`), grid.y: batch entry.
+// Warp roles: warps 0-3 drain the accumulator (TMEM lane quarter = warp), warp 4 issues TMA, warp 5 issues MMA.
+// The contraction is cut into chunks of CHUNK k-blocks; each chunk accumulates in one of two TMEM buffers and
+// is then added into FP32 registers by the drain warps, so no partial sum runs through more than
+// 3 * 4 * CHUNK tensor-core accumulation steps (the tensor-core accumulator alone drifts over long K).
+// mode_even / mode_odd select the epilogue for even / odd batch entries:
+//   0: v    1: delta_mn - v    2: -v
+__global__ void __launch_bounds__(THREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapAhi, const __grid_constant__ CUtensorMap mapAlo,
+                   const __grid_constant__ CUtensorMap mapBhi, const __grid_constant__ CUtensorMap mapBlo, int M,
+                   int N, int K, int lower, int mode_even, int mode_odd, float* __restrict__ out, long out_batch_stride,
+                   int* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* smem = smem_raw + (base - raw);
+  // barriers: full[S], empty[S], acc_full[2], acc_empty[2]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
+  __shared__ int s_abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int bm, bn;
+  if (lower) {
+    int t = blockIdx.x;
+    bm = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    while ((bm + 1) * (bm + 2) / 2 <= t) ++bm;
+    while (bm * (bm + 1) / 2 > t) --bm;
+    bn = t - bm * (bm + 1) / 2;
+  } else {
+    const int nbn = (N + BN - 1) / BN;
+    bm = blockIdx.x / nbn;
+    bn = blockIdx.x % nbn;
+  }
+  const int m0 = bm * BM, n0 = bn * BN, b = blockIdx.y;
+  const int nk = (K + BK - 1) / BK;
+  const int nchunks = (nk + CHUNK - 1) / CHUNK;
+
+  uint32_t full[STAGES], empty[STAGES];
+  for (int s = 0; s < STAGES; ++s) {
+    full[s] = smem_u32(&bars[s]);
+    empty[s] = smem_u32(&bars[STAGES + s]);
+  }
+  const uint32_t acc_full[2] = {smem_u32(&bars[2 * STAGES]), smem_u32(&bars[2 * STAGES + 1])};
+  const uint32_t acc_empty[2] = {smem_u32(&bars[2 * STAGES + 2]), smem_u32(&bars[2 * STAGES + 3])};
+
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full[s], 1);
+      mbar_init(empty[s], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(acc_full[i], 1);
+      mbar_init(acc_empty[i], 4);      // one arrival per drain warp
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  float acc[BN];                    // drain warps: FP32 sum of the chunk partials for row (warp*32 + lane)
+  bool ok = true;
+  int issued = 0;
+  if (warp == 4) {
+    if (lane == 0) {
+      // ---------------- TMA producer
+      for (int kb = 0; kb < nk; ++kb) {
+        const int s = kb % STAGES, u = kb / STAGES;
+        if (u > 0 && !mbar_wait(empty[s], (u - 1) & 1, err, 1)) { s_abort = 1; break; }
+        if (*(volatile int*)&s_abort) break;
+        const uint32_t st = base + s * STAGE_BYTES;
+        mbar_expect_tx(full[s], STAGE_BYTES);
+        tma_load_3d(st, &mapAhi, kb * BK, m0, b, full[s]);
+        tma_load_3d(st + TILE_BYTES, &mapAlo, kb * BK, m0, b, full[s]);
+        tma_load_2d(st + 2 * TILE_BYTES, &mapBhi, kb * BK, n0, full[s]);
+        tma_load_2d(st + 3 * TILE_BYTES, &mapBlo, kb * BK, n0, full[s]);
+        issued = kb + 1;
+      }
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      for (int kb = 0; kb < nk && !*(volatile int*)&s_abort; ++kb) {
+        const int s = kb % STAGES, u = kb / STAGES;
+        const int c = kb / CHUNK, buf = c & 1, first = (kb % CHUNK) == 0;
+        if (first && c >= 2 && !mbar_wait(acc_empty[buf], ((c >> 1) - 1) & 1, err, 5)) { s_abort = 1; break; }
+        if (!mbar_wait(full[s], u & 1, err, 2)) { s_abort = 1; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t st = base + s * STAGE_BYTES;
+        const uint32_t d = tmem + (uint32_t)(buf * BN);
+#pragma unroll
+        for (int k = 0; k < BK / 16; ++k) {
+          const uint32_t off = k * 32;
+          const uint64_t ahi = sdesc(st + off), alo = sdesc(st + TILE_BYTES + off);
+          const uint64_t bhi = sdesc(st + 2 * TILE_BYTES + off), blo = sdesc(st + 3 * TILE_BYTES + off);
+          mma_bf16(d, ahi, bhi, (!first || k > 0) ? 1u : 0u);
+          mma_bf16(d, ahi, blo, 1u);
+          mma_bf16(d, alo, bhi, 1u);
+        }
+        mma_commit(empty[s]);
+        if ((kb % CHUNK) == CHUNK - 1 || kb == nk - 1) mma_commit(acc_full[buf]);
+      }
+    }
+  } else {
+    // ---------------- drain warps 0-3
+#pragma unroll
+    for (int j = 0; j < BN; ++j) acc[j] = 0.f;
+    for (int c = 0; c < nchunks; ++c) {
+      const int buf = c & 1;
+      ok = mbar_wait(acc_full[buf], (c >> 1) & 1, err, 3);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int q = 0; q < BN / 32; ++q) {
+        uint32_t v[32];
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * BN + q * 32), v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[q * 32 + j] += __uint_as_float(v[j]);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acc_empty[buf]) : "memory");
+    }
+  }
+  __syncwarp();
+  const bool all_ok = __syncthreads_and(ok && !s_abort) != 0;
+  // drain copies still in flight if the pipeline was aborted
+  if (!all_ok && warp == 4 && lane == 0)
+    for (int kb = 0; kb < issued; ++kb) mbar_wait(full[kb % STAGES], (kb / STAGES) & 1, err, 4);
+  __syncthreads();
+  float* stg = reinterpret_cast<float*>(smem);     // [BM][BN + 1], reuses the operand ring
+  if (all_ok && warp < 4) {
+    const int r = warp * 32 + lane;
+#pragma unroll
+    for (int j = 0; j < BN; ++j) stg[r * (BN + 1) + j] = acc[j];
+  }
+  __syncthreads();
+  if (all_ok) {
+    const int mode = (b & 1) ? mode_odd : mode_even;
+    float* o = out + (long)b * out_batch_stride;
+    for (int idx = threadIdx.x; idx < BM * BN; idx += THREADS) {
+      const int rr = idx / BN, cc = idx % BN;
+      const int m = m0 + rr, n = n0 + cc;
+      if (m >= M || n >= N) continue;
+      if (lower && n > m) continue;
+      float v = stg[rr * (BN + 1) + cc];
+      v = mode == 0 ? v : (mode == 1 ? ((m == n ? 1.f : 0.f) - v) : -v);
+      o[(long)m * N + n] = v;
+    }
+    if (lower) {
+      for (int idx = threadIdx.x; idx < BM * BN; idx += THREADS) {
+        const int cc = idx / BM, rr = idx % BM;
+        const int m = m0 + rr, n = n0 + cc;
+        if (m >= M || n >= N || n >= m) continue;
+        const float v = stg[rr * (BN + 1) + cc];
+        o[(long)n * N + m] = mode == 0 ? v : -v;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------- operand preparation (HBM-bound)
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(v);
+  lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+// Weight kinds: 0 Pi(i xi): -4D/(D^2+xi^2);  1: Re c(x);  2: Im c(x);  3: 1 (plain split)
+__device__ __forceinline__ double weight(int kind, double D, double p, double eta) {
+  if (kind == 0) return -4.0 * D / (D * D + p * p);
+  if (kind == 3) return 1.0;
+  const double a1 = p - D, a2 = -p - D, e2 = eta * eta;
+  const double d1 = a1 * a1 + e2, d2 = a2 * a2 + e2;
+  if (kind == 1) return 2.0 * (a1 / d1 + a2 / d2);
+  return -2.0 * eta * (1.0 / d1 + 1.0 / d2);
+}
+
+// A_b[m][k] = B[m][k] * w(kind_b, D_k, param_b), split into BF16 hi/lo; rows padded to ld.
+// grid: (ceil(ld/256), M, batch); block 256.
+__global__ void scale_split_kernel(const float* __restrict__ B, const double* __restrict__ eps, int n_occ, int n_virt,
+                                   int M, int K, int ld, const int* __restrict__ kinds,
+                                   const double* __restrict__ params, double eta, __nv_bfloat16* __restrict__ hi,
+                                   __nv_bfloat16* __restrict__ lo) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = blockIdx.y, b = blockIdx.z;
+  if (k >= ld) return;
+  const long o = ((long)b * M + m) * ld + k;
+  if (k >= K) {
+    hi[o] = __float2bfloat16_rn(0.f);
+    lo[o] = __float2bfloat16_rn(0.f);
+    return;
+  }
+  const int i = k / n_virt, a = k - i * n_virt;
+  const double D = eps[n_occ + a] - eps[i];
+  const float v = (float)((double)B[(long)m * K + k] * weight(kinds[b], D, params[b], eta));
+  __nv_bfloat16 h, l;
+  split_bf16(v, h, l);
+  hi[o] = h;
+  lo[o] = l;
+}
+
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+PFN_encodeTiled get_encode() {
+  static PFN_encodeTiled fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_encodeTiled>(p);
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* map, const void* ptr, int rows, int K, int ld, int batch) {
+  PFN_encodeTiled enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)batch};
+  cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)ld * 2 * rows};
+  cuuint32_t box[3] = {BK, BM, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, batch > 0 ? 3 : 2, const_cast<void*>(ptr), dims, strides,
+                   box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+int tc_ld(int K) { return (K + 7) / 8 * 8; }
+
+cudaError_t tc_scale_split(const float* B, const double* eps, int n_occ, int n_virt, int M, int K, const int* kinds,
+                           const double* params, double eta, int batch, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                           cudaStream_t s) {
+  const int ld = tc_ld(K);
+  dim3 grid((ld + 255) / 256, M, batch);
+  scale_split_kernel<<<grid, 256, 0, s>>>(B, eps, n_occ, n_virt, M, K, ld, kinds, params, eta, hi, lo);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_gemm(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int batch, const __nv_bfloat16* Bhi,
+                    const __nv_bfloat16* Blo, int M, int N, int K, int lower, int mode_even, int mode_odd, float* out,
+                    int* err, cudaStream_t s) {
+  const int ld = tc_ld(K);
+  CUtensorMap mAhi, mAlo, mBhi, mBlo;
+  if (!make_map(&mAhi, Ahi, M, K, ld, batch) || !make_map(&mAlo, Alo, M, K, ld, batch) ||
+      !make_map(&mBhi, Bhi, N, K, ld, 0) || !make_map(&mBlo, Blo, N, K, ld, 0))
+    return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int nbm = (M + BM - 1) / BM, nbn = (N + BN - 1) / BN;
+  const int tiles = lower ? nbm * (nbm + 1) / 2 : nbm * nbn;
+  dim3 grid(tiles, batch);
+  tc_gemm_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(mAhi, mAlo, mBhi, mBlo, M, N, K, lower, mode_even, mode_odd, out,
+                                                   (long)M * N, err);
+  return cudaGetLastError();
+}
+
+}  // namespace gw

@@ -17,7 +17,7 @@ GW_QP_LINEARISED, GW_QP_STEPTREE = 0, 1
 GW_INPUT_ON_DEVICE, GW_BORROW_DEVICE_PTRS = 1, 2
 
 EXPORTED = ["gw_config_default", "gw_plan_create", "gw_polarizability", "gw_sigma_cd", "gw_residues_minres",
-            "gw_qp_solve", "gw_grid", "gw_get_stats", "gw_plan_destroy", "gw_last_error"]
+            "gw_qp_solve", "gw_grid", "gw_w_table", "gw_get_stats", "gw_plan_destroy", "gw_last_error"]
 
 
 class GWError(RuntimeError):
@@ -64,6 +64,8 @@ def load(path: str = LIB_PATH):
     lib.gw_residues_minres.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P, _P, _P]
     lib.gw_qp_solve.argtypes = [_P, ctypes.c_int, _P, _P, _P]
     lib.gw_get_stats.argtypes = [_P, ctypes.POINTER(Stats)]
+    lib.gw_w_table.argtypes = [_P, _P]
+    lib.gw_w_table.restype = ctypes.c_int
     lib.gw_grid.argtypes = [ctypes.c_int, ctypes.c_double, _P, _P]
     lib.gw_grid.restype = ctypes.c_int
     lib.gw_plan_destroy.argtypes = [_P]
@@ -158,6 +160,11 @@ class Plan:
 
     def screening(self):
         self._check(self._lib.gw_polarizability(self._h, None, 0, None))
+
+    def w_table(self):
+        out = np.empty((self.n_t, len(self.eps), self.cfg.n_freq + 1))
+        self._check(self._lib.gw_w_table(self._h, _ptr(out)))
+        return out
 
     def sigma_cd(self, omega):
         om = np.ascontiguousarray(omega, dtype=np.float64)
