@@ -134,18 +134,28 @@ gw_status gw_qp_solve(gw_plan_t plan, gw_qp_mode mode, double* e_qp, double* z_f
  * (Algorithm 1, imaginary-grid loop).  Builds the table first if needed. */
 gw_status gw_w_table(gw_plan_t plan, double* out);
 
-/* Timing and counters of the last calls (host, milliseconds / counts); any pointer may be NULL. */
+/* Timing and counters accumulated since plan creation (host, milliseconds / counts).  ms_kernel and
+ * flops_kernel are per kernel class, timed with CUDA events on the plan's stream:
+ *   0 Pi on tensor cores (tcgen05, incl. operand split)   1 Pi (SIMT)         2 Cholesky of 1 - Pi
+ *   3 triangular solves into the W table                    4 MINRES operator GEMMs
+ *   5 MINRES recurrences                                    6 dense Pi(x) of fallback solves
+ *   7 batched complex LU + solve
+ * flops_kernel counts algorithmic floating-point operations (a multiply-add is 2). */
+#define GW_N_KERNEL_CLASSES 8
 typedef struct {
-  double ms_screening;         /* Pi + factorisation + W table */
-  double ms_pi;                /* Pi build alone (inside ms_screening) */
+  double ms_screening;         /* Pi + factorisation + W table (last build) */
+  double ms_pi;                /* Pi build alone (last build) */
   double ms_sigma_imag;        /* I-term quadrature */
   double ms_residues;          /* batched MINRES + fallback */
-  double ms_qp;                /* whole gw_qp_solve */
+  double ms_qp;                /* last gw_qp_solve */
   long long n_rhs_solved;      /* residue right-hand sides solved */
   long long n_minres_iters;    /* sum over right-hand sides */
   long long n_fallback;        /* dense fallback solves */
   long long n_sigma_evals;     /* Sigma(omega) evaluations (per target) */
   long long n_kernel_launches; /* kernels this plan launched */
+  double ms_kernel[GW_N_KERNEL_CLASSES];
+  double flops_kernel[GW_N_KERNEL_CLASSES];
+  long long launches_kernel[GW_N_KERNEL_CLASSES];
 } gw_stats;
 gw_status gw_get_stats(gw_plan_t plan, gw_stats* out);
 

@@ -59,6 +59,11 @@ struct gw_plan {
   std::string err;
   gw_stats stats{};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+  // per-kernel-class timing: events recorded around launches, resolved after each call's final sync
+  std::vector<cudaEvent_t> tpool;
+  size_t tused = 0;
+  struct Mark { int cls; size_t a, b; double flops; };
+  std::vector<Mark> marks;
 
   gw_plan() {
     DevBuf* all[] = {&ws_mat, &ws_info, &ws_scratch, &ws_gout, &ws_xi, &tc_Ahi, &tc_Alo, &tc_kind, &tc_par, &tc_err, &mr_V, &mr_U, &mr_S, &mr_vprev,
@@ -121,6 +126,36 @@ gw_status ensure(gw_plan* P, DevBuf& b, size_t bytes) {
 template <typename T>
 T* as(DevBuf& b) { return reinterpret_cast<T*>(b.p); }
 
+size_t tick(gw_plan* P) {
+  if (P->tused == P->tpool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return (size_t)-1;
+    P->tpool.push_back(e);
+  }
+  cudaEventRecord(P->tpool[P->tused], P->stream);
+  return P->tused++;
+}
+
+void mark(gw_plan* P, int cls, size_t a, double flops) {
+  size_t b = tick(P);
+  if (a != (size_t)-1 && b != (size_t)-1) P->marks.push_back({cls, a, b, flops});
+  P->stats.launches_kernel[cls]++;
+}
+
+// Accumulate the recorded intervals (the stream must be synchronised).
+void resolve_marks(gw_plan* P) {
+  for (const auto& m : P->marks) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, P->tpool[m.a], P->tpool[m.b]) == cudaSuccess) {
+      P->stats.ms_kernel[m.cls] += ms;
+      P->stats.flops_kernel[m.cls] += m.flops;
+    }
+  }
+  P->marks.clear();
+  P->tused = 0;
+  cudaGetLastError();
+}
+
 double now_ms(gw_plan* P, cudaEvent_t a, cudaEvent_t b) {
   float ms = 0.f;
   cudaEventElapsedTime(&ms, a, b);
@@ -129,7 +164,7 @@ double now_ms(gw_plan* P, cudaEvent_t a, cudaEvent_t b) {
 
 // Tensor-core weighted SYRK for `nb` batch entries: out_b = f(B diag(w_b) B^T) with (kind, param) per entry.
 gw_status tc_weighted_syrk(gw_plan* P, const int* kinds, const double* params, int nb, int mode_even, int mode_odd,
-                           float* out) {
+                           float* out, int cls) {
   const int n = P->cfg.n_aux, K = P->n_ov, ld = gw::tc_ld(K);
   TRY(ensure(P, P->tc_Ahi, sizeof(__nv_bfloat16) * (size_t)nb * n * ld));
   TRY(ensure(P, P->tc_Alo, sizeof(__nv_bfloat16) * (size_t)nb * n * ld));
@@ -139,11 +174,13 @@ gw_status tc_weighted_syrk(gw_plan* P, const int* kinds, const double* params, i
   CK(cudaMemcpyAsync(P->tc_kind.p, kinds, sizeof(int) * nb, cudaMemcpyHostToDevice, P->stream));
   CK(cudaMemcpyAsync(P->tc_par.p, params, sizeof(double) * nb, cudaMemcpyHostToDevice, P->stream));
   CK(cudaMemsetAsync(P->tc_err.p, 0, sizeof(int), P->stream));
+  const size_t t0 = tick(P);
   CK(gw::tc_scale_split(P->d_B_ia_f, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, K, as<int>(P->tc_kind),
                         as<double>(P->tc_par), P->cfg.eta, nb, as<__nv_bfloat16>(P->tc_Ahi),
                         as<__nv_bfloat16>(P->tc_Alo), P->stream));
   CK(gw::tc_gemm(as<__nv_bfloat16>(P->tc_Ahi), as<__nv_bfloat16>(P->tc_Alo), nb, P->d_Bhi, P->d_Blo, n, n, K, 1,
                  mode_even, mode_odd, out, as<int>(P->tc_err), P->stream));
+  mark(P, cls, t0, (double)nb * n * n * K);     // symmetric rank-K update: n^2 K flops per entry
   P->stats.n_kernel_launches += 2;
   int herr = 0;
   CK(cudaMemcpyAsync(&herr, P->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
@@ -187,15 +224,21 @@ gw_status screening_T(gw_plan* P, const T* B, const T* Bn) {
     CK(cudaEventRecord(P->ev0, P->stream));
     if (use_tc) {
       std::vector<int> kinds(nc, 0);
-      TRY(tc_weighted_syrk(P, kinds.data(), xi_all.data() + g0, nc, 1, 1, reinterpret_cast<float*>(P->ws_mat.p)));
+      TRY(tc_weighted_syrk(P, kinds.data(), xi_all.data() + g0, nc, 1, 1, reinterpret_cast<float*>(P->ws_mat.p), 0));
     } else {
+      const size_t t0 = tick(P);
       LAUNCH(gw::launch_pi_syrk<T>(B, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, P->d_xi + g0, nc,
                                    as<T>(P->ws_mat), 1, P->stream));
+      mark(P, 1, t0, (double)nc * n * n * P->n_ov);
     }
     CK(cudaEventRecord(P->ev1, P->stream));
+    size_t t1 = tick(P);
     LAUNCH(gw::launch_cholesky<T>(as<T>(P->ws_mat), n, (long)n * n, nc, as<int>(P->ws_info), P->stream));
+    mark(P, 2, t1, (double)nc * n * n * (double)n / 3.0);
+    t1 = tick(P);
     LAUNCH(gw::launch_trsm_w<T>(as<T>(P->ws_mat), (long)n * n, n, nc, as<int>(P->ws_gout) + g0, Bn, R, P->d_W,
                                 n_g1, as<T>(P->ws_scratch), n_cta, P->stream));
+    mark(P, 3, t1, (double)nc * (double)n * n * R);
     CK(cudaMemcpyAsync(info.data(), P->ws_info.p, sizeof(int) * nc, cudaMemcpyDeviceToHost, P->stream));
     CK(cudaStreamSynchronize(P->stream));
     ms_pi += now_ms(P, P->ev0, P->ev1);
@@ -222,6 +265,7 @@ gw_status ensure_screening(gw_plan* P) {
   CK(cudaEventRecord(b, P->stream));
   CK(cudaEventSynchronize(b));
   P->stats.ms_screening = now_ms(P, a, b);
+  resolve_marks(P);
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   P->screening_done = true;
@@ -272,20 +316,24 @@ gw_status dense_fallback(gw_plan* P, const std::vector<int>& need, const int* rt
           par[2 * k] = par[2 * k + 1] = hx[k0 + s0 + k];
         }
         TRY(tc_weighted_syrk(P, kinds.data(), par.data(), 2 * ns, 1, 2,
-                             reinterpret_cast<float*>(A) + 2 * mat * (size_t)s0));
+                             reinterpret_cast<float*>(A) + 2 * mat * (size_t)s0, 6));
       }
     } else {
+      const size_t t0 = tick(P);
       for (int k = 0; k < nf; ++k)
         LAUNCH(gw::launch_pi_complex_dense(P->d_B_ia, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, hx[k0 + k],
                                            P->cfg.eta, reinterpret_cast<double*>(A) + 2 * mat * k,
                                            reinterpret_cast<double*>(A) + 2 * mat * k + mat, P->stream));
+      mark(P, 6, t0, 4.0 * nf * (double)mat * P->n_ov);
     }
     LAUNCH(gw::launch_fallback_rhs<T>(P->d_B_nm, P->n_bas, n, rt, rm, as<int>(P->fb_idx) + k0, nf, as<T>(P->fb_y),
                                       P->stream));
+    const size_t tl = tick(P);
     LAUNCH(gw::launch_zlu<T>(A, A + mat, (long)(2 * mat), n, nf, as<int>(P->fb_piv), as<int>(P->fb_info),
                              P->stream));
     LAUNCH(gw::launch_zlu_solve<T>(A, A + mat, (long)(2 * mat), n, nf, as<int>(P->fb_piv), as<T>(P->fb_y),
                                    as<T>(P->fb_y) + n, 2L * n, P->stream));
+    mark(P, 7, tl, nf * (8.0 / 3.0 * (double)n * n * n + 8.0 * (double)n * n));
     LAUNCH(gw::launch_fallback_finish<T>(P->d_B_nm, P->n_bas, n, rt, rm, as<int>(P->fb_idx) + k0, nf,
                                          as<T>(P->fb_y), w_re, w_im, resnorm, as<T>(P->mr_V), P->stream));
     CK(cudaMemcpyAsync(info.data(), P->fb_info.p, sizeof(int) * nf, cudaMemcpyDeviceToHost, P->stream));
@@ -333,16 +381,21 @@ gw_status residues_T(gw_plan* P, int nr_total, const int* d_rt, const int* d_rm,
     LAUNCH(gw::launch_minres_init<T>(as<T>(P->mr_S), nr, n, as<double>(P->mr_vprev), as<double>(P->mr_v),
                                      as<double>(P->mr_d1), as<double>(P->mr_d2), as<double>(P->mr_x),
                                      as<MinresState>(P->mr_st), as<T>(P->mr_V), P->stream));
+    const double op_flops = 2.0 * 2.0 * (2.0 * nr) * n * (double)n_ov;   // two GEMMs, 2nr columns each
     for (int it = 0; it < P->cfg.minres_maxit; ++it) {
+      size_t tg = tick(P);
       LAUNCH(gw::launch_op_gemm1<T>(as<T>(P->mr_V), B, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, xf, eta, nr,
                                     as<T>(P->mr_U), 0, P->stream));
       LAUNCH(gw::launch_op_gemm2<T>(as<T>(P->mr_U), B, n, n_ov, nr, as<T>(P->mr_V), as<T>(P->mr_S), 1,
                                     P->stream));
+      mark(P, 4, tg, op_flops);
       CK(cudaMemsetAsync(P->mr_cnt.p, 0, sizeof(int), P->stream));
+      tg = tick(P);
       LAUNCH(gw::launch_minres_step<T>(as<T>(P->mr_S), nr, n, P->cfg.minres_tol, as<double>(P->mr_vprev),
                                        as<double>(P->mr_v), as<double>(P->mr_d1), as<double>(P->mr_d2),
                                        as<double>(P->mr_x), as<MinresState>(P->mr_st), as<T>(P->mr_V),
                                        as<int>(P->mr_cnt), P->stream));
+      mark(P, 5, tg, 0.0);
       // poll the active count every 8 iterations (finished right-hand sides are frozen by the step kernel)
       if ((it & 7) == 7 || it + 1 == P->cfg.minres_maxit) {
         CK(cudaMemcpyAsync(P->h_cnt, P->mr_cnt.p, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
@@ -383,6 +436,7 @@ gw_status residues(gw_plan* P, int nr, const int* d_rt, const int* d_rm, const d
   CK(cudaEventRecord(P->ev1, P->stream));
   CK(cudaEventSynchronize(P->ev1));
   P->stats.ms_residues += now_ms(P, P->ev2, P->ev1);
+  resolve_marks(P);
   P->stats.n_rhs_solved += nr;
   std::vector<int> it(nr);
   CK(cudaMemcpy(it.data(), iters, sizeof(int) * nr, cudaMemcpyDeviceToHost));
@@ -524,6 +578,7 @@ static void free_plan(gw_plan* P) {
   if (P->ev0) cudaEventDestroy(P->ev0);
   if (P->ev1) cudaEventDestroy(P->ev1);
   if (P->ev2) cudaEventDestroy(P->ev2);
+  for (cudaEvent_t e : P->tpool) cudaEventDestroy(e);
   if (P->own_stream && P->stream) cudaStreamDestroy(P->stream);
   delete P;
 }
@@ -665,6 +720,7 @@ gw_status gw_polarizability(gw_plan_t P, const double* xi, int n_xi, double* pi_
   if (!P) return GW_ERR_ARG;
   if (!xi) {
     if (pi_out) return fail(P, GW_ERR_ARG, "pi_out must be NULL when building the plan grid");
+    P->screening_done = false;    // explicit request: rebuild the table
     return ensure_screening(P);
   }
   if (n_xi <= 0) return fail(P, GW_ERR_ARG, "n_xi must be positive");
@@ -680,7 +736,7 @@ gw_status gw_polarizability(gw_plan_t P, const double* xi, int n_xi, double* pi_
     for (int g0 = 0; g0 < n_xi; g0 += chunk) {
       const int nc = std::min(chunk, n_xi - g0);
       std::vector<int> kinds(nc, 0);
-      TRY(tc_weighted_syrk(P, kinds.data(), xi + g0, nc, 0, 0, as<float>(P->ws_mat) + (size_t)g0 * n * n));
+      TRY(tc_weighted_syrk(P, kinds.data(), xi + g0, nc, 0, 0, as<float>(P->ws_mat) + (size_t)g0 * n * n, 0));
     }
     CK(cudaEventRecord(P->ev1, P->stream));
     if (pi_out) {
@@ -700,6 +756,7 @@ gw_status gw_polarizability(gw_plan_t P, const double* xi, int n_xi, double* pi_
   }
   CK(cudaStreamSynchronize(P->stream));
   P->stats.ms_pi = now_ms(P, P->ev0, P->ev1);
+  resolve_marks(P);
   return GW_OK;
 }
 

@@ -38,7 +38,13 @@ class Stats(ctypes.Structure):
     _fields_ = [("ms_screening", ctypes.c_double), ("ms_pi", ctypes.c_double), ("ms_sigma_imag", ctypes.c_double),
                 ("ms_residues", ctypes.c_double), ("ms_qp", ctypes.c_double), ("n_rhs_solved", ctypes.c_longlong),
                 ("n_minres_iters", ctypes.c_longlong), ("n_fallback", ctypes.c_longlong),
-                ("n_sigma_evals", ctypes.c_longlong), ("n_kernel_launches", ctypes.c_longlong)]
+                ("n_sigma_evals", ctypes.c_longlong), ("n_kernel_launches", ctypes.c_longlong),
+                ("ms_kernel", ctypes.c_double * 8), ("flops_kernel", ctypes.c_double * 8),
+                ("launches_kernel", ctypes.c_longlong * 8)]
+
+
+KERNEL_CLASSES = ["pi_tcgen05", "pi_simt", "cholesky", "trsm_w_table", "minres_operator_gemm", "minres_recurrence",
+                  "fallback_pi_dense", "fallback_lu"]
 
 
 _lib = None
@@ -195,7 +201,11 @@ class Plan:
     def stats(self) -> dict:
         st = Stats()
         self._check(self._lib.gw_get_stats(self._h, ctypes.byref(st)))
-        return {f: getattr(st, f) for f, _ in Stats._fields_}
+        out = {}
+        for f, _ in Stats._fields_:
+            v = getattr(st, f)
+            out[f] = list(v) if f.endswith("_kernel") else v
+        return out
 
     def close(self):
         if getattr(self, "_h", None):
