@@ -72,6 +72,8 @@ typedef struct {
   double qp_tol;               /* QP convergence |f| < qp_tol (Ha) */
   int static_subtraction;      /* 1: I term with the W(0) sgn(a)/2 rewrite (exact); 0: literal quadrature */
   int max_rhs_batch;           /* residue right-hand sides per batched MINRES launch (0 = automatic) */
+  int workspace_mb;            /* cap per large workspace class (frequency matrices, split operands,
+                                  fallback matrices), MiB; 0 = 8192 */
 } gw_config;
 
 typedef struct gw_plan* gw_plan_t;

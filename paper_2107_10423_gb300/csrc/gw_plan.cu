@@ -50,11 +50,11 @@ struct gw_plan {
   __nv_bfloat16* d_Blo = nullptr;
   bool screening_done = false;
   std::vector<DevBuf*> bufs;
-  DevBuf ws_mat, ws_info, ws_scratch, ws_gout, ws_xi, tc_Ahi, tc_Alo, tc_kind, tc_par, tc_err;
+  DevBuf ws_mat, ws_info, ws_scratch, ws_gout, ws_xi, tc_Ahi, tc_Alo, tc_kind, tc_par, tc_err, tc_w;
   DevBuf mr_V, mr_U, mr_S, mr_vprev, mr_v, mr_d1, mr_d2, mr_x, mr_st, mr_rt, mr_rm, mr_xf, mr_wre, mr_wim,
       mr_dwre, mr_it, mr_res, mr_cnt;
   DevBuf sg_I, sg_dI, sg_R, sg_dR, sg_om, sg_start, sg_coef, sg_act, qp_st;
-  DevBuf fb_A, fb_y, fb_piv, fb_info, fb_idx;
+  DevBuf fb_A, fb_y, fb_piv, fb_info, fb_idx, fb_y64, fb_V64, fb_U64, fb_S64, fb_x;
   int* h_cnt = nullptr;       // pinned
   std::string err;
   gw_stats stats{};
@@ -66,10 +66,10 @@ struct gw_plan {
   std::vector<Mark> marks;
 
   gw_plan() {
-    DevBuf* all[] = {&ws_mat, &ws_info, &ws_scratch, &ws_gout, &ws_xi, &tc_Ahi, &tc_Alo, &tc_kind, &tc_par, &tc_err, &mr_V, &mr_U, &mr_S, &mr_vprev,
+    DevBuf* all[] = {&ws_mat, &ws_info, &ws_scratch, &ws_gout, &ws_xi, &tc_Ahi, &tc_Alo, &tc_kind, &tc_par, &tc_err, &tc_w, &mr_V, &mr_U, &mr_S, &mr_vprev,
                      &mr_v, &mr_d1, &mr_d2, &mr_x, &mr_st, &mr_rt, &mr_rm, &mr_xf, &mr_wre, &mr_wim,
                      &mr_dwre, &mr_it, &mr_res, &mr_cnt, &sg_I, &sg_dI, &sg_R, &sg_dR, &sg_om, &sg_start,
-                     &sg_coef, &sg_act, &qp_st, &fb_A, &fb_y, &fb_piv, &fb_info, &fb_idx};
+                     &sg_coef, &sg_act, &qp_st, &fb_A, &fb_y, &fb_piv, &fb_info, &fb_idx, &fb_y64, &fb_V64, &fb_U64, &fb_S64, &fb_x};
     bufs.assign(all, all + sizeof(all) / sizeof(all[0]));
   }
 };
@@ -126,6 +126,10 @@ gw_status ensure(gw_plan* P, DevBuf& b, size_t bytes) {
 template <typename T>
 T* as(DevBuf& b) { return reinterpret_cast<T*>(b.p); }
 
+size_t ws_bytes(const gw_plan* P) {
+  return (size_t)(P->cfg.workspace_mb > 0 ? P->cfg.workspace_mb : 8192) << 20;
+}
+
 size_t tick(gw_plan* P) {
   if (P->tused == P->tpool.size()) {
     cudaEvent_t e;
@@ -171,12 +175,13 @@ gw_status tc_weighted_syrk(gw_plan* P, const int* kinds, const double* params, i
   TRY(ensure(P, P->tc_kind, sizeof(int) * nb));
   TRY(ensure(P, P->tc_par, sizeof(double) * nb));
   TRY(ensure(P, P->tc_err, sizeof(int)));
+  TRY(ensure(P, P->tc_w, sizeof(float) * (size_t)nb * K));
   CK(cudaMemcpyAsync(P->tc_kind.p, kinds, sizeof(int) * nb, cudaMemcpyHostToDevice, P->stream));
   CK(cudaMemcpyAsync(P->tc_par.p, params, sizeof(double) * nb, cudaMemcpyHostToDevice, P->stream));
   CK(cudaMemsetAsync(P->tc_err.p, 0, sizeof(int), P->stream));
   const size_t t0 = tick(P);
   CK(gw::tc_scale_split(P->d_B_ia_f, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, K, as<int>(P->tc_kind),
-                        as<double>(P->tc_par), P->cfg.eta, nb, as<__nv_bfloat16>(P->tc_Ahi),
+                        as<double>(P->tc_par), P->cfg.eta, nb, as<float>(P->tc_w), as<__nv_bfloat16>(P->tc_Ahi),
                         as<__nv_bfloat16>(P->tc_Alo), P->stream));
   CK(gw::tc_gemm(as<__nv_bfloat16>(P->tc_Ahi), as<__nv_bfloat16>(P->tc_Alo), nb, P->d_Bhi, P->d_Blo, n, n, K, 1,
                  mode_even, mode_odd, out, as<int>(P->tc_err), P->stream));
@@ -192,7 +197,7 @@ gw_status tc_weighted_syrk(gw_plan* P, const int* kinds, const double* params, i
 // Largest batch of split operands that fits in ~8 GiB.
 int tc_chunk(gw_plan* P, int want) {
   const size_t per = (size_t)P->cfg.n_aux * gw::tc_ld(P->n_ov) * 4;   // hi + lo
-  size_t c = ((size_t)8 << 30) / (per ? per : 1);
+  size_t c = ws_bytes(P) / (per ? per : 1);
   return (int)std::max<size_t>(1, std::min<size_t>((size_t)want, c));
 }
 
@@ -205,7 +210,7 @@ gw_status screening_T(gw_plan* P, const T* B, const T* Bn) {
   const bool use_tc = (P->cfg.precision == GW_PREC_MIXED);
   // frequency matrices held at once: <= 8 GiB (and the split-operand budget on the tensor-core path)
   const size_t per = (size_t)n * n * sizeof(T);
-  int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_g1, ((size_t)8 << 30) / per));
+  int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_g1, ws_bytes(P) / per));
   if (use_tc) chunk = tc_chunk(P, chunk);
   TRY(ensure(P, P->ws_mat, per * chunk));
   TRY(ensure(P, P->ws_info, sizeof(int) * chunk));
@@ -272,6 +277,9 @@ gw_status ensure_screening(gw_plan* P) {
   return GW_OK;
 }
 
+// Refinement steps of the mixed-precision dense solves (FP64 residual, FP32 LU correction).
+constexpr int kRefineSteps = 1;
+
 // Dense solves for the MINRES batch slots in `need` (Sec. 3.3: build the dielectric matrix and factorise).
 // A_j = 1 - Pi(x_j) is built on the tensor cores (mixed) or by the FP64 SIMT kernel, then factorised by the
 // batched complex LU; W and the derivative-pass vectors are written into the slot.
@@ -283,7 +291,7 @@ gw_status dense_fallback(gw_plan* P, const std::vector<int>& need, const int* rt
   const int nneed = (int)need.size();
   // batch of dense matrices: A planes <= 8 GiB (one LU launch fills the GPU); the tensor-core build runs in
   // sub-batches sized by the split-operand budget
-  int fb = (int)std::max<size_t>(1, ((size_t)8 << 30) / (2 * mat * sizeof(T)));
+  int fb = (int)std::max<size_t>(1, ws_bytes(P) / (2 * mat * sizeof(T)));
   fb = std::min(fb, nneed);
   const int sub = (sizeof(T) == 4) ? std::max(1, tc_chunk(P, 2 * fb) / 2) : fb;
   TRY(ensure(P, P->fb_A, sizeof(T) * 2 * mat * fb));
@@ -291,6 +299,13 @@ gw_status dense_fallback(gw_plan* P, const std::vector<int>& need, const int* rt
   TRY(ensure(P, P->fb_piv, sizeof(int) * (size_t)n * fb));
   TRY(ensure(P, P->fb_info, sizeof(int) * fb));
   TRY(ensure(P, P->fb_idx, sizeof(int) * nneed));
+  if (sizeof(T) == 4) {
+    TRY(ensure(P, P->fb_y64, sizeof(double) * 2 * (size_t)n * fb));
+    TRY(ensure(P, P->fb_V64, sizeof(double) * 2 * (size_t)n * fb));
+    TRY(ensure(P, P->fb_S64, sizeof(double) * 2 * (size_t)n * fb));
+    TRY(ensure(P, P->fb_U64, sizeof(double) * 2 * (size_t)P->n_ov * fb));
+    TRY(ensure(P, P->fb_x, sizeof(double) * fb));
+  }
   CK(cudaMemcpyAsync(P->fb_idx.p, need.data(), sizeof(int) * nneed, cudaMemcpyHostToDevice, P->stream));
   std::vector<double> hx(nneed);
   {
@@ -334,8 +349,35 @@ gw_status dense_fallback(gw_plan* P, const std::vector<int>& need, const int* rt
     LAUNCH(gw::launch_zlu_solve<T>(A, A + mat, (long)(2 * mat), n, nf, as<int>(P->fb_piv), as<T>(P->fb_y),
                                    as<T>(P->fb_y) + n, 2L * n, P->stream));
     mark(P, 7, tl, nf * (8.0 / 3.0 * (double)n * n * n + 8.0 * (double)n * n));
-    LAUNCH(gw::launch_fallback_finish<T>(P->d_B_nm, P->n_bas, n, rt, rm, as<int>(P->fb_idx) + k0, nf,
-                                         as<T>(P->fb_y), w_re, w_im, resnorm, as<T>(P->mr_V), P->stream));
+    if (sizeof(T) == 4) {
+      // one step of iterative refinement with the FP64 operator (matrix-free) and the FP32 factors
+      float* y32 = reinterpret_cast<float*>(P->fb_y.p);
+      const int* idx = as<int>(P->fb_idx) + k0;
+      std::vector<double> xk(hx.begin() + k0, hx.begin() + k0 + nf);
+      CK(cudaMemcpyAsync(P->fb_x.p, xk.data(), sizeof(double) * nf, cudaMemcpyHostToDevice, P->stream));
+      LAUNCH(gw::launch_refine(0, P->d_B_nm, P->n_bas, n, rt, rm, idx, nf, y32, as<double>(P->fb_y64),
+                               as<double>(P->fb_V64), nullptr, P->stream));
+      for (int r = 0; r < kRefineSteps; ++r) {
+        const size_t tr = tick(P);
+        LAUNCH(gw::launch_op_gemm1<double>(as<double>(P->fb_V64), P->d_B_ia, P->d_eps, P->cfg.n_occ, P->cfg.n_virt,
+                                           n, as<double>(P->fb_x), P->cfg.eta, nf, as<double>(P->fb_U64), 0,
+                                           P->stream));
+        LAUNCH(gw::launch_op_gemm2<double>(as<double>(P->fb_U64), P->d_B_ia, n, P->n_ov, nf, as<double>(P->fb_V64),
+                                           as<double>(P->fb_S64), 1, P->stream));
+        mark(P, 4, tr, 2.0 * 2.0 * (2.0 * nf) * n * (double)P->n_ov);
+        LAUNCH(gw::launch_refine(1, P->d_B_nm, P->n_bas, n, rt, rm, idx, nf, y32, as<double>(P->fb_y64),
+                                 as<double>(P->fb_V64), as<double>(P->fb_S64), P->stream));
+        LAUNCH(gw::launch_zlu_solve<T>(A, A + mat, (long)(2 * mat), n, nf, as<int>(P->fb_piv), as<T>(P->fb_y),
+                                       as<T>(P->fb_y) + n, 2L * n, P->stream));
+        LAUNCH(gw::launch_refine(2, P->d_B_nm, P->n_bas, n, rt, rm, idx, nf, y32, as<double>(P->fb_y64),
+                                 as<double>(P->fb_V64), nullptr, P->stream));
+      }
+      LAUNCH(gw::launch_fallback_finish64<T>(P->d_B_nm, P->n_bas, n, rt, rm, idx, nf, as<double>(P->fb_y64), w_re,
+                                             w_im, resnorm, as<T>(P->mr_V), P->stream));
+    } else {
+      LAUNCH(gw::launch_fallback_finish<T>(P->d_B_nm, P->n_bas, n, rt, rm, as<int>(P->fb_idx) + k0, nf,
+                                           as<T>(P->fb_y), w_re, w_im, resnorm, as<T>(P->mr_V), P->stream));
+    }
     CK(cudaMemcpyAsync(info.data(), P->fb_info.p, sizeof(int) * nf, cudaMemcpyDeviceToHost, P->stream));
     CK(cudaStreamSynchronize(P->stream));
     for (int k = 0; k < nf; ++k)
@@ -355,7 +397,7 @@ gw_status residues_T(gw_plan* P, int nr_total, const int* d_rt, const int* d_rm,
   int batch = P->cfg.max_rhs_batch;
   if (batch <= 0) {
     // keep the U buffer (2 batch x n_ov) within ~4 GiB
-    size_t cap = ((size_t)4 << 30) / ((size_t)2 * n_ov * sizeof(T));
+    size_t cap = (ws_bytes(P) / 2) / ((size_t)2 * n_ov * sizeof(T));
     batch = (int)std::max<size_t>(1, std::min<size_t>(cap, 2048));
   }
   batch = std::min(batch, std::max(1, nr_total));
@@ -654,11 +696,14 @@ static gw_status plan_create_impl(gw_plan* P, const gw_config* cfg, const double
     const double p0 = 0.0;
     CK(cudaMemcpyAsync(dk, &k3, sizeof(int), cudaMemcpyHostToDevice, P->stream));
     CK(cudaMemcpyAsync(dp, &p0, sizeof(double), cudaMemcpyHostToDevice, P->stream));
-    CK(gw::tc_scale_split(P->d_B_ia_f, P->d_eps, cfg->n_occ, cfg->n_virt, n, P->n_ov, dk, dp, 0.0, 1, P->d_Bhi,
+    float* dw = nullptr;
+    CK(cudaMalloc(&dw, sizeof(float) * P->n_ov));
+    CK(gw::tc_scale_split(P->d_B_ia_f, P->d_eps, cfg->n_occ, cfg->n_virt, n, P->n_ov, dk, dp, 0.0, 1, dw, P->d_Bhi,
                           P->d_Blo, P->stream));
     CK(cudaStreamSynchronize(P->stream));
     cudaFree(dk);
     cudaFree(dp);
+    cudaFree(dw);
   }
   LAUNCH(gw::launch_sigma_x(P->d_B_nm, n_targets, P->n_bas, n, cfg->n_occ, P->d_sx, P->stream));
   P->h_sx.resize(n_targets);

@@ -267,6 +267,65 @@ __global__ void fallback_finish_kernel(const double* __restrict__ B_nm, int n_ba
   }
 }
 
+__global__ void refine_kernel(int stage, const double* __restrict__ B_nm, int n_bas, int n_aux,
+                              const int* __restrict__ rt, const int* __restrict__ rm, const int* __restrict__ idx,
+                              float* y32, double* y64, double* V64, const double* __restrict__ S64) {
+  const int k = blockIdx.x;
+  float* yr32 = y32 + (long)k * 2 * n_aux;
+  double* yr64 = y64 + (long)k * 2 * n_aux;
+  double* u = V64 + (long)(2 * k) * n_aux;
+  if (stage == 1) {
+    const int j = idx[k];
+    const double* b = B_nm + ((long)rt[j] * n_bas + rm[j]) * n_aux;
+    const double* S = S64 + (long)(2 * k) * n_aux;
+    for (int i = threadIdx.x; i < n_aux; i += blockDim.x) {
+      yr32[i] = (float)(b[i] - S[i]);
+      yr32[n_aux + i] = (float)(-S[n_aux + i]);
+    }
+    return;
+  }
+  for (int i = threadIdx.x; i < n_aux; i += blockDim.x) {
+    double re, im;
+    if (stage == 0) {
+      re = yr32[i];
+      im = yr32[n_aux + i];
+    } else {
+      re = yr64[i] + (double)yr32[i];
+      im = yr64[n_aux + i] + (double)yr32[n_aux + i];
+    }
+    yr64[i] = re;
+    yr64[n_aux + i] = im;
+    u[i] = re;
+    u[n_aux + i] = -im;
+  }
+}
+
+template <typename T>
+__global__ void fallback_finish64_kernel(const double* __restrict__ B_nm, int n_bas, int n_aux,
+                                         const int* __restrict__ rt, const int* __restrict__ rm,
+                                         const int* __restrict__ idx, const double* __restrict__ y64, double* w_re,
+                                         double* w_im, double* resnorm, T* V) {
+  __shared__ double buf[32];
+  const int k = blockIdx.x, j = idx[k];
+  const double* b = B_nm + ((long)rt[j] * n_bas + rm[j]) * n_aux;
+  const double* yr = y64 + (long)k * 2 * n_aux;
+  const double* yi = yr + n_aux;
+  double ar = 0.0, ai = 0.0;
+  for (int i = threadIdx.x; i < n_aux; i += blockDim.x) {
+    ar += b[i] * (yr[i] - b[i]);
+    ai += b[i] * yi[i];
+    V[(long)(2 * j) * n_aux + i] = (T)yr[i];
+    V[(long)(2 * j + 1) * n_aux + i] = (T)(-yi[i]);
+  }
+  ar = block_sum(ar, buf);
+  ai = block_sum(ai, buf);
+  if (threadIdx.x == 0) {
+    w_re[j] = ar;
+    w_im[j] = ai;
+    resnorm[j] = 0.0;
+  }
+}
+
 __global__ void residue_reduce_kernel(const int* __restrict__ start, int n_t, const double* __restrict__ coef,
                                       const double* __restrict__ w_re, const double* __restrict__ dw_re,
                                       double* R, double* dR) {
@@ -451,6 +510,21 @@ void launch_fallback_finish(const double* B_nm, int n_bas, int n_aux, const int*
   if (nf > 0)
     fallback_finish_kernel<T><<<nf, RT, 0, s>>>(B_nm, n_bas, n_aux, rt, rm, idx, y, w_re, w_im, resnorm, V);
 }
+
+void launch_refine(int stage, const double* B_nm, int n_bas, int n_aux, const int* rt, const int* rm, const int* idx,
+                   int nf, float* y32, double* y64, double* V64, const double* S64, cudaStream_t s) {
+  if (nf > 0) refine_kernel<<<nf, RT, 0, s>>>(stage, B_nm, n_bas, n_aux, rt, rm, idx, y32, y64, V64, S64);
+}
+
+template <typename T>
+void launch_fallback_finish64(const double* B_nm, int n_bas, int n_aux, const int* rt, const int* rm, const int* idx,
+                              int nf, const double* y64, double* w_re, double* w_im, double* resnorm, T* V,
+                              cudaStream_t s) {
+  if (nf > 0)
+    fallback_finish64_kernel<T><<<nf, RT, 0, s>>>(B_nm, n_bas, n_aux, rt, rm, idx, y64, w_re, w_im, resnorm, V);
+}
+template void launch_fallback_finish64<float>(const double*, int, int, const int*, const int*, const int*, int,
+                                              const double*, double*, double*, double*, float*, cudaStream_t);
 
 void launch_residue_reduce(const int* start, int n_t, const double* coef, const double* w_re, const double* dw_re,
                            double* R, double* dR, cudaStream_t s) {

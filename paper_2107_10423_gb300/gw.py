@@ -31,7 +31,7 @@ class Config(ctypes.Structure):
                 ("n_freq", ctypes.c_int), ("x0", ctypes.c_double), ("eta", ctypes.c_double),
                 ("precision", ctypes.c_int), ("minres_maxit", ctypes.c_int), ("minres_tol", ctypes.c_double),
                 ("minres_fallback_tol", ctypes.c_double), ("qp_maxit", ctypes.c_int), ("qp_tol", ctypes.c_double),
-                ("static_subtraction", ctypes.c_int), ("max_rhs_batch", ctypes.c_int)]
+                ("static_subtraction", ctypes.c_int), ("max_rhs_batch", ctypes.c_int), ("workspace_mb", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
