@@ -232,14 +232,15 @@ def main():
     # per-kernel-class rates over the timed region
     peaks, peak_src = _peaks()
     classes = gw.KERNEL_CLASSES
-    dms = [st1["ms_kernel"][i] - st0["ms_kernel"][i] for i in range(8)]
-    dfl = [st1["flops_kernel"][i] - st0["flops_kernel"][i] for i in range(8)]
-    dln = [st1["launches_kernel"][i] - st0["launches_kernel"][i] for i in range(8)]
+    dms = [st1["ms_kernel"][i] - st0["ms_kernel"][i] for i in range(len(classes))]
+    dfl = [st1["flops_kernel"][i] - st0["flops_kernel"][i] for i in range(len(classes))]
+    dln = [st1["launches_kernel"][i] - st0["launches_kernel"][i] for i in range(len(classes))]
     phases = {classes[i]: {"ms": round(dms[i], 3), "launches": int(dln[i]),
                            "tflops_alg": (round(dfl[i] / dms[i] / 1e9, 3) if dms[i] > 0 and dfl[i] > 0 else None)}
-              for i in range(8) if dln[i] > 0}
-    dom = max(range(8), key=lambda i: dms[i])
+              for i in range(len(classes)) if dln[i] > 0}
+    dom = max(range(len(classes)), key=lambda i: dms[i])
     sm_max = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp64_cls = dom == 8 or prec != gw.GW_PREC_MIXED
     if dom in (0, 6) and prec == gw.GW_PREC_MIXED:
         # BF16 hi+lo: three BF16 products per algorithmic multiply-add -> peak = BF16 peak / 3
         roof = {"bound": "tensor", "peak": peaks["bf16_tflops_sustained"] / 3.0, "unit": "TFLOP/s",
@@ -247,10 +248,10 @@ def main():
     else:
         # SIMT FMA pipe: 152 SMs x 128 FP32 lanes (FP64: 1 TFLOP/s measured class) x 2 flops x SM clock
         fp32 = 152 * 128 * 2 * sm_max * 1e6 / 1e12
-        p = fp32 if prec == gw.GW_PREC_MIXED else 1.0
+        p = 1.0 if fp64_cls else fp32
         roof = {"bound": "alu", "peak": p, "unit": "TFLOP/s",
-                "peak_source": ("152 SM x 128 FP32 lanes x 2 x max SM clock" if prec == gw.GW_PREC_MIXED
-                                else "FP64 FMA rate measured on this GB300 (DFMA microbenchmark, 1.0 TFLOP/s)")}
+                "peak_source": ("FP64 FMA rate measured on this GB300 (DFMA microbenchmark, 1.0 TFLOP/s)" if fp64_cls
+                                else "152 SM x 128 FP32 lanes x 2 x max SM clock")}
     ach = dfl[dom] / dms[dom] / 1e9 if dms[dom] > 0 else 0.0
     roof.update({"kernel": classes[dom], "achieved": round(ach, 3), "frac": round(ach / roof["peak"], 4),
                  "traffic": None, "launches": int(dln[dom]), "ms_per_launch": round(dms[dom] / max(1, dln[dom]), 4)})

@@ -141,9 +141,9 @@ gw_status gw_w_table(gw_plan_t plan, double* out);
  *   0 Pi on tensor cores (tcgen05, incl. operand split)   1 Pi (SIMT)         2 Cholesky of 1 - Pi
  *   3 triangular solves into the W table                    4 MINRES operator GEMMs
  *   5 MINRES recurrences                                    6 dense Pi(x) of fallback solves
- *   7 batched complex LU + solve
+ *   7 batched complex LU + solve                          8 FP64 operator of the mixed-precision refinement
  * flops_kernel counts algorithmic floating-point operations (a multiply-add is 2). */
-#define GW_N_KERNEL_CLASSES 8
+#define GW_N_KERNEL_CLASSES 9
 typedef struct {
   double ms_screening;         /* Pi + factorisation + W table (last build) */
   double ms_pi;                /* Pi build alone (last build) */

@@ -364,7 +364,7 @@ gw_status dense_fallback(gw_plan* P, const std::vector<int>& need, const int* rt
                                            P->stream));
         LAUNCH(gw::launch_op_gemm2<double>(as<double>(P->fb_U64), P->d_B_ia, n, P->n_ov, nf, as<double>(P->fb_V64),
                                            as<double>(P->fb_S64), 1, P->stream));
-        mark(P, 4, tr, 2.0 * 2.0 * (2.0 * nf) * n * (double)P->n_ov);
+        mark(P, 8, tr, 2.0 * 2.0 * (2.0 * nf) * n * (double)P->n_ov);
         LAUNCH(gw::launch_refine(1, P->d_B_nm, P->n_bas, n, rt, rm, idx, nf, y32, as<double>(P->fb_y64),
                                  as<double>(P->fb_V64), as<double>(P->fb_S64), P->stream));
         LAUNCH(gw::launch_zlu_solve<T>(A, A + mat, (long)(2 * mat), n, nf, as<int>(P->fb_piv), as<T>(P->fb_y),

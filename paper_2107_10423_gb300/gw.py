@@ -39,12 +39,12 @@ class Stats(ctypes.Structure):
                 ("ms_residues", ctypes.c_double), ("ms_qp", ctypes.c_double), ("n_rhs_solved", ctypes.c_longlong),
                 ("n_minres_iters", ctypes.c_longlong), ("n_fallback", ctypes.c_longlong),
                 ("n_sigma_evals", ctypes.c_longlong), ("n_kernel_launches", ctypes.c_longlong),
-                ("ms_kernel", ctypes.c_double * 8), ("flops_kernel", ctypes.c_double * 8),
-                ("launches_kernel", ctypes.c_longlong * 8)]
+                ("ms_kernel", ctypes.c_double * 9), ("flops_kernel", ctypes.c_double * 9),
+                ("launches_kernel", ctypes.c_longlong * 9)]
 
 
 KERNEL_CLASSES = ["pi_tcgen05", "pi_simt", "cholesky", "trsm_w_table", "minres_operator_gemm", "minres_recurrence",
-                  "fallback_pi_dense", "fallback_lu"]
+                  "fallback_pi_dense", "fallback_lu", "fallback_refine_fp64"]
 
 
 _lib = None

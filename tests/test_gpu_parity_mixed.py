@@ -8,7 +8,7 @@ from paper_2107_10423_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 MEV = 3.6749322175655e-5      # Ha per meV
-MIXED = dict(minres_tol=1e-7, minres_maxit=200, minres_fallback_tol=1e-6)
+MIXED = dict()     # production settings: paper MINRES defaults (25 / 5e-5 / dense fallback above 1e-4)
 
 
 @pytest.fixture(scope="module")
