@@ -167,6 +167,27 @@ gw_status gw_get_stats(gw_plan_t plan, gw_stats* out);
  * xi, wt: [n] host arrays owned by the caller.  Returns GW_ERR_ARG for n <= 0, x0 <= 0 or NULL. */
 gw_status gw_grid(int n, double x0, double* xi, double* wt);
 
+/* W table from caller-supplied Cholesky factors, for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is the library's imaginary-axis triangular-solve step exposed as a
+ * stand-alone call that allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
+ * Callers that cannot allocate include a serving process that hands all GPU memory to its own pool at
+ * start-up, a host application whose allocator forbids cudaMalloc after initialisation, and latency-
+ * critical paths where an allocation may synchronise the device.
+ *   L   device, [n_mats][n_aux][n_aux] row-major lower Cholesky factors of eps(i xi_g) = 1 - Pi(i xi_g)
+ *       (entries above the diagonal are not read).
+ *   Bn  device, [n_rows][n_aux]: the vectors b_r (for example the B_nm rows of every target n and state m).
+ *   W   device, written at W[r * w_ld + g] = b_r^T (eps_g^-1 - 1) b_r for r < n_rows, g < n_mats.
+ *   stream: cudaStream_t (NULL = default stream).  The call is asynchronous on that stream.
+ * Work space is a fixed 32 MiB device array inside the library; every GPU that loads the library holds it
+ * until the process exits.  Limits: n_aux <= 65536 and n_mats <= 4096; larger sizes return GW_ERR_ARG
+ * before any device work.  Fewer CTAs run when n_aux is large (the array holds one slice per CTA).
+ * The first call on each device looks up the array's device address with cudaGetSymbolAddress and fills a
+ * small index table with a synchronous copy; make that first call before any stream capture.
+ * Every call on a device shares the same array.  Each call writes its slices before reading them, so nothing
+ * has to start at zero, but two calls that overlap on the same GPU (for example on two streams) race. */
+gw_status gw_w_table_noalloc(const double* L, int n_aux, int n_mats, const double* Bn, int n_rows, double* W,
+                             int w_ld, void* stream);
+
 /* Release every device buffer the plan owns.  NULL is ignored. */
 void gw_plan_destroy(gw_plan_t plan);
 

@@ -4,8 +4,10 @@
 //  * triangular solves that turn the factors into the table W^c_nm(i xi) (Algorithm 1, imaginary-grid loop);
 //  * the two skinny GEMMs of the matrix-free residue operator 1 - Pi(x) (Sec. 3.3, MINRES paragraph).
 #include "gw_internal.cuh"
+#include "gw.h"
 
 #include <cstdio>
+#include <mutex>
 
 namespace gw {
 
@@ -573,3 +575,62 @@ GW_INST(float)
 #undef GW_INST
 
 }  // namespace gw
+
+// =====================================================================================================
+// W table from caller-supplied Cholesky factors without any device allocation.
+//
+// Some callers cannot allocate device memory when they call into this library: a serving process that
+// reserves all GPU memory for its own pool at start-up, a host application whose allocator forbids
+// cudaMalloc after initialisation, or code on a latency-critical path where an allocation (which may
+// synchronise the device) is not acceptable.  gw_w_table_noalloc gives them the W-table triangular solves
+// with the per-CTA work space taken from the fixed array below instead of cudaMalloc.
+// =====================================================================================================
+#define GW_NOALLOC_SCRATCH_BYTES (32u << 20)   // 32 MiB, held by every GPU that loads the library
+#define GW_NOALLOC_MAX_MATS 4096
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[GW_NOALLOC_SCRATCH_BYTES];
+static __device__ __align__(256) int g_noalloc_index[GW_NOALLOC_MAX_MATS];
+
+namespace {
+struct NoallocDevice {
+  void* scratch = nullptr;
+  int* index = nullptr;
+  bool ready = false;
+};
+std::mutex g_noalloc_mu;
+NoallocDevice g_noalloc_dev[128];
+int g_noalloc_host_index[GW_NOALLOC_MAX_MATS];
+}  // namespace
+
+extern "C" gw_status gw_w_table_noalloc(const double* L, int n_aux, int n_mats, const double* Bn, int n_rows,
+                                        double* W, int w_ld, void* stream) {
+  if (!L || !Bn || !W || n_aux <= 0 || n_mats <= 0 || n_rows <= 0 || w_ld < n_mats) return GW_ERR_ARG;
+  if (n_mats > GW_NOALLOC_MAX_MATS) return GW_ERR_ARG;
+  const size_t slice = (size_t)((n_aux + 63) / 64) * 64 * 64 * sizeof(double);
+  if (slice > GW_NOALLOC_SCRATCH_BYTES) return GW_ERR_ARG;   // n_aux beyond 65536
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return GW_ERR_CUDA;
+  NoallocDevice& d = g_noalloc_dev[dev];
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!d.ready) {
+      // once per device, with that device current: device addresses of the fixed arrays and the
+      // frequency index table 0, 1, 2, ... (a synchronous copy, before any stream capture)
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return GW_ERR_CUDA;
+      d.scratch = p;
+      if (cudaGetSymbolAddress(&p, g_noalloc_index) != cudaSuccess) return GW_ERR_CUDA;
+      d.index = static_cast<int*>(p);
+      for (int i = 0; i < GW_NOALLOC_MAX_MATS; ++i) g_noalloc_host_index[i] = i;
+      if (cudaMemcpyToSymbol(g_noalloc_index, g_noalloc_host_index, sizeof(g_noalloc_host_index)) != cudaSuccess)
+        return GW_ERR_CUDA;
+      d.ready = true;
+    }
+  }
+  int n_cta = (int)(GW_NOALLOC_SCRATCH_BYTES / slice);
+  const int full = gw::trsm_w_default_ctas();
+  n_cta = n_cta < full ? n_cta : full;
+  gw::launch_trsm_w<double>(L, (long)n_aux * n_aux, n_aux, n_mats, d.index, Bn, n_rows, W, w_ld,
+                            static_cast<double*>(d.scratch), n_cta, static_cast<cudaStream_t>(stream));
+  return cudaGetLastError() == cudaSuccess ? GW_OK : GW_ERR_CUDA;
+}

@@ -17,7 +17,7 @@ GW_QP_LINEARISED, GW_QP_STEPTREE = 0, 1
 GW_INPUT_ON_DEVICE, GW_BORROW_DEVICE_PTRS = 1, 2
 
 EXPORTED = ["gw_config_default", "gw_plan_create", "gw_polarizability", "gw_sigma_cd", "gw_residues_minres",
-            "gw_qp_solve", "gw_grid", "gw_w_table", "gw_get_stats", "gw_plan_destroy", "gw_last_error"]
+            "gw_qp_solve", "gw_grid", "gw_w_table", "gw_w_table_noalloc", "gw_get_stats", "gw_plan_destroy", "gw_last_error"]
 
 
 class GWError(RuntimeError):
@@ -70,6 +70,8 @@ def load(path: str = LIB_PATH):
     lib.gw_residues_minres.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P, _P, _P]
     lib.gw_qp_solve.argtypes = [_P, ctypes.c_int, _P, _P, _P]
     lib.gw_get_stats.argtypes = [_P, ctypes.POINTER(Stats)]
+    lib.gw_w_table_noalloc.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, ctypes.c_int, _P]
+    lib.gw_w_table_noalloc.restype = ctypes.c_int
     lib.gw_w_table.argtypes = [_P, _P]
     lib.gw_w_table.restype = ctypes.c_int
     lib.gw_grid.argtypes = [ctypes.c_int, ctypes.c_double, _P, _P]

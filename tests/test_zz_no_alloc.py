@@ -1,0 +1,47 @@
+"""gw_w_table_noalloc: the W-table triangular solves for callers that cannot allocate device memory
+(a process that gives all GPU memory to its own pool, an allocator that forbids cudaMalloc after start-up).
+Its output must equal the plan-based W table of gw_w_table, on two calls in a row.  This file is collected
+last so that a stop at the first failure has already run every other test."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import gw_oracle as O
+from paper_2107_10423_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def test_noalloc_w_table_matches_plan(gwlib):
+    import torch
+    from paper_2107_10423_gb300 import gw
+    s = synth.water_cluster(2, 21, targets="valence")
+    B, Bn = s.b_ia(), s.b_nm()
+    with gw.Plan(s.eps, s.n_occ, B, Bn, s.targets) as p:
+        ref = p.w_table()                                  # [n_t][n_bas][n_freq + 1], FP64 path
+    xi, _ = gw.grid(128, 0.5)
+    xis = np.concatenate([xi, [0.0]])
+    n = s.n_aux
+    L = np.stack([np.linalg.cholesky(np.eye(n) - O.pi_imag(s.eps, s.n_occ, B, x)) for x in xis])
+    dev = torch.device("cuda", 0)
+    L_d = torch.from_numpy(np.ascontiguousarray(L)).to(dev)
+    rows = np.ascontiguousarray(Bn.reshape(-1, n))
+    Bn_d = torch.from_numpy(rows).to(dev)
+    R, G = rows.shape[0], len(xis)
+    for call in range(2):
+        W_d = torch.full((R, G), float("nan"), dtype=torch.float64, device=dev)
+        st = gwlib.gw_w_table_noalloc(ctypes.c_void_p(L_d.data_ptr()), n, G, ctypes.c_void_p(Bn_d.data_ptr()), R,
+                                      ctypes.c_void_p(W_d.data_ptr()), G, None)
+        assert st == gw.GW_OK
+        torch.cuda.synchronize()
+        W = W_d.cpu().numpy().reshape(ref.shape)
+        np.testing.assert_allclose(W, ref, rtol=0, atol=1e-12 * max(1.0, np.abs(ref).max()), err_msg=f"call {call}")
+
+
+def test_noalloc_rejects_oversize(gwlib):
+    from paper_2107_10423_gb300 import gw
+    one = ctypes.c_void_p(16)     # never dereferenced: the size checks come first
+    assert gwlib.gw_w_table_noalloc(one, 70000, 3, one, 5, one, 3, None) == gw.GW_ERR_ARG
+    assert gwlib.gw_w_table_noalloc(one, 64, 5000, one, 5, one, 5000, None) == gw.GW_ERR_ARG
+    assert gwlib.gw_w_table_noalloc(one, 64, 3, one, 5, one, 2, None) == gw.GW_ERR_ARG
