@@ -48,11 +48,14 @@ struct gw_plan {
   float* d_B_nm_f = nullptr;  // mixed: FP32 copy of B_nm
   __nv_bfloat16* d_Bhi = nullptr;   // mixed: BF16 hi/lo split of B_ia, [n_aux][tc_ld(n_ov)]
   __nv_bfloat16* d_Blo = nullptr;
+  __nv_bfloat16* d_BThi = nullptr;  // mixed: BF16 hi/lo split of B_ia^T, [n_ov][tc_ld(n_aux)]
+  __nv_bfloat16* d_BTlo = nullptr;
+  double* d_D = nullptr;            // pair energies D_ia [n_ov]
   bool screening_done = false;
   std::vector<DevBuf*> bufs;
   DevBuf ws_mat, ws_info, ws_scratch, ws_gout, ws_xi, tc_Ahi, tc_Alo, tc_kind, tc_par, tc_err, tc_w;
   DevBuf mr_V, mr_U, mr_S, mr_vprev, mr_v, mr_d1, mr_d2, mr_x, mr_st, mr_rt, mr_rm, mr_xf, mr_wre, mr_wim,
-      mr_dwre, mr_it, mr_res, mr_cnt;
+      mr_dwre, mr_it, mr_res, mr_cnt, mr_Vhi, mr_Vlo, mr_Uhi, mr_Ulo;
   DevBuf sg_I, sg_dI, sg_R, sg_dR, sg_om, sg_start, sg_coef, sg_act, qp_st;
   DevBuf fb_A, fb_y, fb_piv, fb_info, fb_idx, fb_y64, fb_V64, fb_U64, fb_S64, fb_x;
   int* h_cnt = nullptr;       // pinned
@@ -68,7 +71,7 @@ struct gw_plan {
   gw_plan() {
     DevBuf* all[] = {&ws_mat, &ws_info, &ws_scratch, &ws_gout, &ws_xi, &tc_Ahi, &tc_Alo, &tc_kind, &tc_par, &tc_err, &tc_w, &mr_V, &mr_U, &mr_S, &mr_vprev,
                      &mr_v, &mr_d1, &mr_d2, &mr_x, &mr_st, &mr_rt, &mr_rm, &mr_xf, &mr_wre, &mr_wim,
-                     &mr_dwre, &mr_it, &mr_res, &mr_cnt, &sg_I, &sg_dI, &sg_R, &sg_dR, &sg_om, &sg_start,
+                     &mr_dwre, &mr_it, &mr_res, &mr_cnt, &mr_Vhi, &mr_Vlo, &mr_Uhi, &mr_Ulo, &sg_I, &sg_dI, &sg_R, &sg_dR, &sg_om, &sg_start,
                      &sg_coef, &sg_act, &qp_st, &fb_A, &fb_y, &fb_piv, &fb_info, &fb_idx, &fb_y64, &fb_V64, &fb_U64, &fb_S64, &fb_x};
     bufs.assign(all, all + sizeof(all) / sizeof(all[0]));
   }
@@ -387,6 +390,36 @@ gw_status dense_fallback(gw_plan* P, const std::vector<int>& need, const int* rt
   return GW_OK;
 }
 
+// Residue operator on the tensor cores (mixed precision), for nr right-hand sides held in V32 [2nr][n]:
+// GEMM1 t = B^T z with the complex weights c_ia(x_j) fused into its epilogue (written as split BF16),
+// GEMM2 B w with either the plain store (mode 0: [Re; Im] of Pi z) or the 2n embedding of (1 - Pi) z (mode 1).
+gw_status tc_operator(gw_plan* P, int nr, const double* xf, const float* V32, float* S32, int mode) {
+  const int n = P->cfg.n_aux, n_ov = P->n_ov;
+  const int ldn = gw::tc_ld(n), ldov = gw::tc_ld(n_ov);
+  CK(gw::tc_split_rows(V32, 2 * nr, n, n, as<__nv_bfloat16>(P->mr_Vhi), as<__nv_bfloat16>(P->mr_Vlo), P->stream));
+  gw::TcEpi e1{};
+  e1.kind = gw::TC_EPI_CPAIR;
+  e1.Dk = P->d_D;
+  e1.x = xf;
+  e1.eta = (float)P->cfg.eta;
+  e1.ohi = as<__nv_bfloat16>(P->mr_Uhi);
+  e1.olo = as<__nv_bfloat16>(P->mr_Ulo);
+  e1.ldh = ldov;
+  CK(gw::tc_gemm_ex(as<__nv_bfloat16>(P->mr_Vhi), as<__nv_bfloat16>(P->mr_Vlo), 1, P->d_BThi, P->d_BTlo, 0, 2 * nr,
+                    n_ov, n, 0, e1, as<int>(P->tc_err), P->stream));
+  gw::TcEpi e2{};
+  e2.kind = mode == 0 ? gw::TC_EPI_STORE : gw::TC_EPI_EMBED;
+  e2.out = S32;
+  e2.ldo = n;
+  e2.vin = V32;
+  e2.ldv = n;
+  CK(gw::tc_gemm_ex(as<__nv_bfloat16>(P->mr_Uhi), as<__nv_bfloat16>(P->mr_Ulo), 1, P->d_Bhi, P->d_Blo, 0, 2 * nr, n,
+                    n_ov, 0, e2, as<int>(P->tc_err), P->stream));
+  P->stats.n_kernel_launches += 3;
+  (void)ldn;
+  return GW_OK;
+}
+
 // ---------------------------------------------------------------- batched residue solves
 // Device arrays in: rt, rm (target index, state), xf (frequency); out: w_re, w_im, dw_re, iters, resnorm.
 template <typename T>
@@ -408,6 +441,15 @@ gw_status residues_T(gw_plan* P, int nr_total, const int* d_rt, const int* d_rm,
     TRY(ensure(P, *b, sizeof(double) * 2 * (size_t)batch * n));
   TRY(ensure(P, P->mr_st, sizeof(MinresState) * batch));
   TRY(ensure(P, P->mr_cnt, sizeof(int)));
+  const bool tcop = (sizeof(T) == 4) && P->d_BThi != nullptr;
+  if (tcop) {
+    TRY(ensure(P, P->mr_Vhi, sizeof(__nv_bfloat16) * 2 * (size_t)batch * gw::tc_ld(n)));
+    TRY(ensure(P, P->mr_Vlo, sizeof(__nv_bfloat16) * 2 * (size_t)batch * gw::tc_ld(n)));
+    TRY(ensure(P, P->mr_Uhi, sizeof(__nv_bfloat16) * 2 * (size_t)batch * gw::tc_ld(n_ov)));
+    TRY(ensure(P, P->mr_Ulo, sizeof(__nv_bfloat16) * 2 * (size_t)batch * gw::tc_ld(n_ov)));
+    TRY(ensure(P, P->tc_err, sizeof(int)));
+    CK(cudaMemsetAsync(P->tc_err.p, 0, sizeof(int), P->stream));
+  }
   const double eta = P->cfg.eta;
   std::vector<double> h_res;
   for (int j0 = 0; j0 < nr_total; j0 += batch) {
@@ -417,19 +459,28 @@ gw_status residues_T(gw_plan* P, int nr_total, const int* d_rt, const int* d_rm,
     const double* xf = d_xf + j0;
     LAUNCH(gw::launch_gather_rhs<T>(P->d_B_nm, P->n_bas, n, rt, rm, nr, as<T>(P->mr_V), P->stream));
     // rhs = Pi(x) b
-    LAUNCH(gw::launch_op_gemm1<T>(as<T>(P->mr_V), B, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, xf, eta, nr,
-                                  as<T>(P->mr_U), 0, P->stream));
-    LAUNCH(gw::launch_op_gemm2<T>(as<T>(P->mr_U), B, n, n_ov, nr, as<T>(P->mr_V), as<T>(P->mr_S), 0, P->stream));
+    if (tcop) {
+      TRY(tc_operator(P, nr, xf, reinterpret_cast<const float*>(P->mr_V.p), reinterpret_cast<float*>(P->mr_S.p), 0));
+    } else {
+      LAUNCH(gw::launch_op_gemm1<T>(as<T>(P->mr_V), B, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, xf, eta, nr,
+                                    as<T>(P->mr_U), 0, P->stream));
+      LAUNCH(gw::launch_op_gemm2<T>(as<T>(P->mr_U), B, n, n_ov, nr, as<T>(P->mr_V), as<T>(P->mr_S), 0, P->stream));
+    }
     LAUNCH(gw::launch_minres_init<T>(as<T>(P->mr_S), nr, n, as<double>(P->mr_vprev), as<double>(P->mr_v),
                                      as<double>(P->mr_d1), as<double>(P->mr_d2), as<double>(P->mr_x),
                                      as<MinresState>(P->mr_st), as<T>(P->mr_V), P->stream));
     const double op_flops = 2.0 * 2.0 * (2.0 * nr) * n * (double)n_ov;   // two GEMMs, 2nr columns each
     for (int it = 0; it < P->cfg.minres_maxit; ++it) {
       size_t tg = tick(P);
-      LAUNCH(gw::launch_op_gemm1<T>(as<T>(P->mr_V), B, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, xf, eta, nr,
-                                    as<T>(P->mr_U), 0, P->stream));
-      LAUNCH(gw::launch_op_gemm2<T>(as<T>(P->mr_U), B, n, n_ov, nr, as<T>(P->mr_V), as<T>(P->mr_S), 1,
-                                    P->stream));
+      if (tcop) {
+        TRY(tc_operator(P, nr, xf, reinterpret_cast<const float*>(P->mr_V.p), reinterpret_cast<float*>(P->mr_S.p),
+                        1));
+      } else {
+        LAUNCH(gw::launch_op_gemm1<T>(as<T>(P->mr_V), B, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, xf, eta, nr,
+                                      as<T>(P->mr_U), 0, P->stream));
+        LAUNCH(gw::launch_op_gemm2<T>(as<T>(P->mr_U), B, n, n_ov, nr, as<T>(P->mr_V), as<T>(P->mr_S), 1,
+                                      P->stream));
+      }
       mark(P, 4, tg, op_flops);
       CK(cudaMemsetAsync(P->mr_cnt.p, 0, sizeof(int), P->stream));
       tg = tick(P);
@@ -444,6 +495,12 @@ gw_status residues_T(gw_plan* P, int nr_total, const int* d_rt, const int* d_rm,
         CK(cudaStreamSynchronize(P->stream));
         if (*P->h_cnt == 0) break;
       }
+    }
+    if (tcop) {
+      int herr = 0;
+      CK(cudaMemcpyAsync(&herr, P->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+      CK(cudaStreamSynchronize(P->stream));
+      if (herr != 0) return fail(P, GW_ERR_TIMEOUT, "tensor-core operator GEMM: bounded wait ran out (code %d)", herr);
     }
     LAUNCH(gw::launch_minres_finish<T>(P->d_B_nm, P->n_bas, n, rt, rm, nr, as<double>(P->mr_x),
                                        as<MinresState>(P->mr_st), w_re + j0, w_im + j0, iters + j0, resnorm + j0,
@@ -616,6 +673,9 @@ static void free_plan(gw_plan* P) {
   if (P->d_B_nm_f) cudaFree(P->d_B_nm_f);
   if (P->d_Bhi) cudaFree(P->d_Bhi);
   if (P->d_Blo) cudaFree(P->d_Blo);
+  if (P->d_BThi) cudaFree(P->d_BThi);
+  if (P->d_BTlo) cudaFree(P->d_BTlo);
+  if (P->d_D) cudaFree(P->d_D);
   if (P->h_cnt) cudaFreeHost(P->h_cnt);
   if (P->ev0) cudaEventDestroy(P->ev0);
   if (P->ev1) cudaEventDestroy(P->ev1);
@@ -700,6 +760,18 @@ static gw_status plan_create_impl(gw_plan* P, const gw_config* cfg, const double
     CK(cudaMalloc(&dw, sizeof(float) * P->n_ov));
     CK(gw::tc_scale_split(P->d_B_ia_f, P->d_eps, cfg->n_occ, cfg->n_virt, n, P->n_ov, dk, dp, 0.0, 1, dw, P->d_Bhi,
                           P->d_Blo, P->stream));
+    const size_t nsplitT = (size_t)P->n_ov * gw::tc_ld(n);
+    CK(cudaMalloc(&P->d_BThi, sizeof(__nv_bfloat16) * nsplitT));
+    CK(cudaMalloc(&P->d_BTlo, sizeof(__nv_bfloat16) * nsplitT));
+    CK(gw::tc_transpose_split(P->d_B_ia_f, n, P->n_ov, P->d_BThi, P->d_BTlo, P->stream));
+    {
+      std::vector<double> D((size_t)P->n_ov);
+      for (int i = 0; i < cfg->n_occ; ++i)
+        for (int a = 0; a < cfg->n_virt; ++a) D[(size_t)i * cfg->n_virt + a] = eps[cfg->n_occ + a] - eps[i];
+      CK(cudaMalloc(&P->d_D, sizeof(double) * P->n_ov));
+      CK(cudaMemcpyAsync(P->d_D, D.data(), sizeof(double) * P->n_ov, cudaMemcpyHostToDevice, P->stream));
+      CK(cudaStreamSynchronize(P->stream));
+    }
     CK(cudaStreamSynchronize(P->stream));
     cudaFree(dk);
     cudaFree(dp);

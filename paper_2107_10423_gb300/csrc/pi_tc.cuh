@@ -4,6 +4,28 @@
 #include <cuda_bf16.h>
 
 namespace gw {
+enum { TC_EPI_STORE = 0, TC_EPI_CPAIR = 1, TC_EPI_EMBED = 2 };
+
+// Epilogue of the tensor-core GEMM (passed by value to the kernel).
+struct TcEpi {
+  int kind;
+  // TC_EPI_STORE: out_b[m][n] (row length ldo) = v, delta_mn - v or -v (mode for even / odd batch entries)
+  int mode_even, mode_odd;
+  float* out;
+  long out_bstride;
+  int ldo;
+  // TC_EPI_CPAIR: complex pair scaling of the residue operator into split BF16 rows (row length ldh)
+  const double* Dk;    // [N] pair energies D_k
+  const double* x;     // [M/2] residue frequencies
+  float eta;
+  __nv_bfloat16* ohi;
+  __nv_bfloat16* olo;
+  int ldh;
+  // TC_EPI_EMBED: out[m][n] = (m even ? vin : -vin)[m][n] - v  (row lengths ldo, ldv)
+  const float* vin;
+  int ldv;
+};
+
 // Row length (elements) of the split operand arrays for contraction length K (multiple of 8: 16-byte rows).
 int tc_ld(int K);
 // A_b[m][k] = B[m][k] * w(kinds[b], D_k, params[b]) split into BF16 hi/lo, [batch][M][tc_ld(K)].
@@ -19,4 +41,13 @@ cudaError_t tc_scale_split(const float* B, const double* eps, int n_occ, int n_v
 cudaError_t tc_gemm(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int batch, const __nv_bfloat16* Bhi,
                     const __nv_bfloat16* Blo, int M, int N, int K, int lower, int mode_even, int mode_odd, float* out,
                     int* err, cudaStream_t s);
+// General form: B may also be batched (b_batched != 0: Bm_b has the same batch count as A).
+cudaError_t tc_gemm_ex(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int batch, const __nv_bfloat16* Bhi,
+                       const __nv_bfloat16* Blo, int b_batched, int M, int N, int K, int lower, const TcEpi& ep,
+                       int* err, cudaStream_t s);
+// rows x cols FP32 (row length lds) split into BF16 hi/lo rows of tc_ld(cols) elements (zero padded).
+cudaError_t tc_split_rows(const float* src, int rows, int cols, int lds, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                          cudaStream_t s);
+// out[k][m] = B[m][k] split into BF16 hi/lo with rows of tc_ld(M) elements (B FP32 [M][K]).
+cudaError_t tc_transpose_split(const float* B, int M, int K, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s);
 }  // namespace gw

@@ -70,14 +70,6 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-          "r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
-
 // Shared-memory matrix descriptor: K-major tile with 128-byte swizzle, 8-row groups 1024 B apart.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   uint64_t d = 0;
@@ -115,6 +107,66 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Epilogues.  The tile is staged in shared memory as stg[BM][BN + 1] (row = output row), so any thread can combine
+// elements of different rows (the complex pairs of the residue operator are adjacent rows).
+__device__ __forceinline__ void split_store(float v, __nv_bfloat16* hi, __nv_bfloat16* lo, long o) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  hi[o] = h;
+  lo[o] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+__device__ void epilogue(const TcEpi& ep, const float* stg, int m0, int n0, int M, int N, int b, int lower) {
+  if (ep.kind == TC_EPI_STORE) {
+    const int mode = (b & 1) ? ep.mode_odd : ep.mode_even;
+    float* o = ep.out + (long)b * ep.out_bstride;
+    for (int idx = threadIdx.x; idx < BM * BN; idx += THREADS) {
+      const int rr = idx / BN, cc = idx % BN;
+      const int m = m0 + rr, n = n0 + cc;
+      if (m >= M || n >= N) continue;
+      if (lower && n > m) continue;
+      float v = stg[rr * (BN + 1) + cc];
+      v = mode == 0 ? v : (mode == 1 ? ((m == n ? 1.f : 0.f) - v) : -v);
+      o[(long)m * ep.ldo + n] = v;
+    }
+    if (lower) {
+      for (int idx = threadIdx.x; idx < BM * BN; idx += THREADS) {
+        const int cc = idx / BM, rr = idx % BM;
+        const int m = m0 + rr, n = n0 + cc;
+        if (m >= M || n >= N || n >= m) continue;
+        const float v = stg[rr * (BN + 1) + cc];
+        o[(long)n * ep.ldo + m] = mode == 0 ? v : -v;
+      }
+    }
+  } else if (ep.kind == TC_EPI_CPAIR) {
+    // rows (2j, 2j+1) hold B^T u and B^T v of z_j = u - i v; column k is the pair ia.
+    // w = c_k(x_j) (t_r + i t_i) with t = B^T z, c_k(x) = 2[1/(x - D_k + i eta) + 1/(-x - D_k + i eta)];
+    // Re w and Im w go to rows 2j, 2j+1 of the split operand of the second GEMM.
+    const float e2 = ep.eta * ep.eta;
+    for (int idx = threadIdx.x; idx < (BM / 2) * BN; idx += THREADS) {
+      const int pr = idx / BN, cc = idx % BN;
+      const int m = m0 + 2 * pr, n = n0 + cc;
+      if (m >= M || n >= N) continue;
+      const double x = ep.x[m >> 1], D = ep.Dk[n];
+      const float a1 = (float)(x - D), a2 = (float)(-x - D);
+      const float d1 = a1 * a1 + e2, d2 = a2 * a2 + e2;
+      const float cr = 2.f * (a1 / d1 + a2 / d2);
+      const float ci = -2.f * ep.eta * (1.f / d1 + 1.f / d2);
+      const float tr = stg[(2 * pr) * (BN + 1) + cc], ti = -stg[(2 * pr + 1) * (BN + 1) + cc];
+      split_store(cr * tr - ci * ti, ep.ohi, ep.olo, (long)m * ep.ldh + n);
+      split_store(cr * ti + ci * tr, ep.ohi, ep.olo, (long)(m + 1) * ep.ldh + n);
+    }
+  } else if (ep.kind == TC_EPI_EMBED) {
+    // real 2n embedding of (1 - Pi) z: rows 2j: u - (B w)_r, rows 2j+1: -v - (B w)_i
+    for (int idx = threadIdx.x; idx < BM * BN; idx += THREADS) {
+      const int rr = idx / BN, cc = idx % BN;
+      const int m = m0 + rr, n = n0 + cc;
+      if (m >= M || n >= N) continue;
+      const float vin = ep.vin[(long)m * ep.ldv + n];
+      ep.out[(long)m * ep.ldo + n] = ((m & 1) ? -vin : vin) - stg[rr * (BN + 1) + cc];
+    }
+  }
+}
+
 // grid.x: output tile (lower-triangular enumeration when `lower`), grid.y: batch entry.
 // Warp roles: warps 0-3 drain the accumulator (TMEM lane quarter = warp), warp 4 issues TMA, warp 5 issues MMA.
 // The contraction is cut into chunks of CHUNK k-blocks; each chunk accumulates in one of two TMEM buffers and
@@ -125,8 +177,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 __global__ void __launch_bounds__(THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapAhi, const __grid_constant__ CUtensorMap mapAlo,
                    const __grid_constant__ CUtensorMap mapBhi, const __grid_constant__ CUtensorMap mapBlo, int M,
-                   int N, int K, int lower, int mode_even, int mode_odd, float* __restrict__ out, long out_batch_stride,
-                   int* __restrict__ err) {
+                   int N, int K, int lower, int b_batched, const TcEpi ep, int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -199,8 +250,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         mbar_expect_tx(full[s], STAGE_BYTES);
         tma_load_3d(st, &mapAhi, kb * BK, m0, b, full[s]);
         tma_load_3d(st + TILE_BYTES, &mapAlo, kb * BK, m0, b, full[s]);
-        tma_load_2d(st + 2 * TILE_BYTES, &mapBhi, kb * BK, n0, full[s]);
-        tma_load_2d(st + 3 * TILE_BYTES, &mapBlo, kb * BK, n0, full[s]);
+        tma_load_3d(st + 2 * TILE_BYTES, &mapBhi, kb * BK, n0, b_batched ? b : 0, full[s]);
+        tma_load_3d(st + 3 * TILE_BYTES, &mapBlo, kb * BK, n0, b_batched ? b : 0, full[s]);
         issued = kb + 1;
       }
     }
@@ -263,28 +314,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int j = 0; j < BN; ++j) stg[r * (BN + 1) + j] = acc[j];
   }
   __syncthreads();
-  if (all_ok) {
-    const int mode = (b & 1) ? mode_odd : mode_even;
-    float* o = out + (long)b * out_batch_stride;
-    for (int idx = threadIdx.x; idx < BM * BN; idx += THREADS) {
-      const int rr = idx / BN, cc = idx % BN;
-      const int m = m0 + rr, n = n0 + cc;
-      if (m >= M || n >= N) continue;
-      if (lower && n > m) continue;
-      float v = stg[rr * (BN + 1) + cc];
-      v = mode == 0 ? v : (mode == 1 ? ((m == n ? 1.f : 0.f) - v) : -v);
-      o[(long)m * N + n] = v;
-    }
-    if (lower) {
-      for (int idx = threadIdx.x; idx < BM * BN; idx += THREADS) {
-        const int cc = idx / BM, rr = idx % BM;
-        const int m = m0 + rr, n = n0 + cc;
-        if (m >= M || n >= N || n >= m) continue;
-        const float v = stg[rr * (BN + 1) + cc];
-        o[(long)n * N + m] = mode == 0 ? v : -v;
-      }
-    }
-  }
+  if (all_ok) epilogue(ep, stg, m0, n0, M, N, b, lower);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
@@ -382,13 +412,14 @@ cudaError_t tc_scale_split(const float* B, const double* eps, int n_occ, int n_v
   return cudaGetLastError();
 }
 
-cudaError_t tc_gemm(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int batch, const __nv_bfloat16* Bhi,
-                    const __nv_bfloat16* Blo, int M, int N, int K, int lower, int mode_even, int mode_odd, float* out,
-                    int* err, cudaStream_t s) {
+cudaError_t tc_gemm_ex(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int batch, const __nv_bfloat16* Bhi,
+                       const __nv_bfloat16* Blo, int b_batched, int M, int N, int K, int lower, const TcEpi& ep,
+                       int* err, cudaStream_t s) {
   const int ld = tc_ld(K);
   CUtensorMap mAhi, mAlo, mBhi, mBlo;
+  const int bb = b_batched ? batch : 1;
   if (!make_map(&mAhi, Ahi, M, K, ld, batch) || !make_map(&mAlo, Alo, M, K, ld, batch) ||
-      !make_map(&mBhi, Bhi, N, K, ld, 0) || !make_map(&mBlo, Blo, N, K, ld, 0))
+      !make_map(&mBhi, Bhi, N, K, ld, bb) || !make_map(&mBlo, Blo, N, K, ld, bb))
     return cudaErrorInvalidValue;
   static bool attr = false;
   if (!attr) {
@@ -399,8 +430,58 @@ cudaError_t tc_gemm(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int batc
   const int nbm = (M + BM - 1) / BM, nbn = (N + BN - 1) / BN;
   const int tiles = lower ? nbm * (nbm + 1) / 2 : nbm * nbn;
   dim3 grid(tiles, batch);
-  tc_gemm_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(mAhi, mAlo, mBhi, mBlo, M, N, K, lower, mode_even, mode_odd, out,
-                                                   (long)M * N, err);
+  tc_gemm_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(mAhi, mAlo, mBhi, mBlo, M, N, K, lower, b_batched, ep, err);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_gemm(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int batch, const __nv_bfloat16* Bhi,
+                    const __nv_bfloat16* Blo, int M, int N, int K, int lower, int mode_even, int mode_odd, float* out,
+                    int* err, cudaStream_t s) {
+  TcEpi ep{};
+  ep.kind = TC_EPI_STORE;
+  ep.mode_even = mode_even;
+  ep.mode_odd = mode_odd;
+  ep.out = out;
+  ep.out_bstride = (long)M * N;
+  ep.ldo = N;
+  return tc_gemm_ex(Ahi, Alo, batch, Bhi, Blo, 0, M, N, K, lower, ep, err, s);
+}
+
+// B^T split: out[k][m] = B[m][k] as BF16 hi/lo, rows of length tc_ld(M).  32 x 32 tiles through shared memory.
+__global__ void transpose_split_kernel(const float* __restrict__ B, int M, int K, int ld,
+                                       __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+  __shared__ float t[32][33];
+  const int k0 = blockIdx.x * 32, m0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int m = m0 + r, k = k0 + threadIdx.x;
+    t[r][threadIdx.x] = (m < M && k < K) ? B[(long)m * K + k] : 0.f;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int k = k0 + r, m = m0 + threadIdx.x;
+    if (k < K && m < ld) split_store(m < M ? t[threadIdx.x][r] : 0.f, hi, lo, (long)k * ld + m);
+  }
+}
+
+__global__ void split_rows_kernel(const float* __restrict__ src, int cols, int lds, __nv_bfloat16* __restrict__ hi,
+                                  __nv_bfloat16* __restrict__ lo, int ldh) {
+  const int r = blockIdx.y;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ldh; c += gridDim.x * blockDim.x)
+    split_store(c < cols ? src[(long)r * lds + c] : 0.f, hi, lo, (long)r * ldh + c);
+}
+
+cudaError_t tc_split_rows(const float* src, int rows, int cols, int lds, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                          cudaStream_t s) {
+  const int ldh = tc_ld(cols);
+  dim3 grid((ldh + 255) / 256, rows);
+  if (rows > 0) split_rows_kernel<<<grid, 256, 0, s>>>(src, cols, lds, hi, lo, ldh);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_transpose_split(const float* B, int M, int K, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s) {
+  const int ld = tc_ld(M);
+  dim3 grid((K + 31) / 32, (ld + 31) / 32);
+  transpose_split_kernel<<<grid, dim3(32, 8), 0, s>>>(B, M, K, ld, hi, lo);
   return cudaGetLastError();
 }
 
