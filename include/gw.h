@@ -138,8 +138,9 @@ gw_status gw_w_table(gw_plan_t plan, double* out);
 
 /* Timing and counters accumulated since plan creation (host, milliseconds / counts).  ms_kernel and
  * flops_kernel are per kernel class, timed with CUDA events on the plan's stream:
- *   0 Pi on tensor cores (tcgen05, incl. operand split)   1 Pi (SIMT)         2 Cholesky of 1 - Pi
- *   3 triangular solves into the W table                    4 MINRES operator GEMMs
+ *   0 Pi on tensor cores (tcgen05, incl. operand split)   1 Pi (SIMT)
+ *   2 W-table factorisation (Cholesky of 1 - Pi, or the tensor-core Newton-Schulz inverse in mixed mode)
+ *   3 W-table reduction (triangular solves, or the tensor-core GEMM into W)   4 MINRES operator GEMMs
  *   5 MINRES recurrences                                    6 dense Pi(x) of fallback solves
  *   7 batched complex LU + solve                          8 FP64 operator of the mixed-precision refinement
  * flops_kernel counts algorithmic floating-point operations (a multiply-add is 2). */

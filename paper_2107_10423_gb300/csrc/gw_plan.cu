@@ -51,9 +51,12 @@ struct gw_plan {
   __nv_bfloat16* d_BThi = nullptr;  // mixed: BF16 hi/lo split of B_ia^T, [n_ov][tc_ld(n_aux)]
   __nv_bfloat16* d_BTlo = nullptr;
   double* d_D = nullptr;            // pair energies D_ia [n_ov]
+  __nv_bfloat16* d_Bnhi = nullptr;  // mixed: BF16 hi/lo split of the B_nm rows, [n_t*n_bas][tc_ld(n_aux)]
+  __nv_bfloat16* d_Bnlo = nullptr;
   bool screening_done = false;
+  int ns_iters_last = 0;
   std::vector<DevBuf*> bufs;
-  DevBuf ws_mat, ws_info, ws_scratch, ws_gout, ws_xi, tc_Ahi, tc_Alo, tc_kind, tc_par, tc_err, tc_w;
+  DevBuf ws_mat, ws_info, ws_scratch, ws_gout, ws_xi, tc_Ahi, tc_Alo, tc_kind, tc_par, tc_err, tc_w, ns_E, ns_X, ns_Xa, ns_Xb, ns_T, ns_lam;
   DevBuf mr_V, mr_U, mr_S, mr_vprev, mr_v, mr_d1, mr_d2, mr_x, mr_st, mr_rt, mr_rm, mr_xf, mr_wre, mr_wim,
       mr_dwre, mr_it, mr_res, mr_cnt, mr_Vhi, mr_Vlo, mr_Uhi, mr_Ulo;
   DevBuf sg_I, sg_dI, sg_R, sg_dR, sg_om, sg_start, sg_coef, sg_act, qp_st;
@@ -69,7 +72,7 @@ struct gw_plan {
   std::vector<Mark> marks;
 
   gw_plan() {
-    DevBuf* all[] = {&ws_mat, &ws_info, &ws_scratch, &ws_gout, &ws_xi, &tc_Ahi, &tc_Alo, &tc_kind, &tc_par, &tc_err, &tc_w, &mr_V, &mr_U, &mr_S, &mr_vprev,
+    DevBuf* all[] = {&ws_mat, &ws_info, &ws_scratch, &ws_gout, &ws_xi, &tc_Ahi, &tc_Alo, &tc_kind, &tc_par, &tc_err, &tc_w, &ns_E, &ns_X, &ns_Xa, &ns_Xb, &ns_T, &ns_lam, &mr_V, &mr_U, &mr_S, &mr_vprev,
                      &mr_v, &mr_d1, &mr_d2, &mr_x, &mr_st, &mr_rt, &mr_rm, &mr_xf, &mr_wre, &mr_wim,
                      &mr_dwre, &mr_it, &mr_res, &mr_cnt, &mr_Vhi, &mr_Vlo, &mr_Uhi, &mr_Ulo, &sg_I, &sg_dI, &sg_R, &sg_dR, &sg_om, &sg_start,
                      &sg_coef, &sg_act, &qp_st, &fb_A, &fb_y, &fb_piv, &fb_info, &fb_idx, &fb_y64, &fb_V64, &fb_U64, &fb_S64, &fb_x};
@@ -204,6 +207,122 @@ int tc_chunk(gw_plan* P, int want) {
   return (int)std::max<size_t>(1, std::min<size_t>((size_t)want, c));
 }
 
+// W table on the tensor cores (mixed precision) for nc frequency matrices eps_b = 1 - Pi_b held FP32 in ws_mat:
+// Newton-Schulz X <- 2X - X eps X from the closed-form first iterate 2a I - a^2 eps (a = 2/(1 + lambda_max)),
+// converging quadratically because the spectrum of eps lies in [1, lambda_max]; the last iterate is written as
+// eps^-1 - 1, and W[r][g] = b_r^T (eps_g^-1 - 1) b_r is reduced straight out of one more GEMM.
+gw_status ns_w_table(gw_plan* P, int g0, int nc) {
+  const int n = P->cfg.n_aux, ldn = gw::tc_ld(n);
+  const int R = P->n_t * P->n_bas, n_g1 = P->n_g + 1;
+  const size_t mat = (size_t)n * n, smat = (size_t)n * ldn;
+  TRY(ensure(P, P->ns_E, 2 * sizeof(__nv_bfloat16) * smat * nc));
+  TRY(ensure(P, P->ns_Xa, 2 * sizeof(__nv_bfloat16) * smat * nc));
+  TRY(ensure(P, P->ns_Xb, 2 * sizeof(__nv_bfloat16) * smat * nc));
+  TRY(ensure(P, P->ns_T, 2 * sizeof(__nv_bfloat16) * smat * nc));
+  TRY(ensure(P, P->ns_X, sizeof(float) * mat * nc));
+  TRY(ensure(P, P->ns_lam, sizeof(float) * nc));
+  TRY(ensure(P, P->tc_err, sizeof(int)));
+  CK(cudaMemsetAsync(P->tc_err.p, 0, sizeof(int), P->stream));
+  const float* eps = reinterpret_cast<const float*>(P->ws_mat.p);
+  __nv_bfloat16* Ehi = as<__nv_bfloat16>(P->ns_E);
+  __nv_bfloat16* Elo = Ehi + smat * nc;
+  __nv_bfloat16* Xs[2][2] = {{as<__nv_bfloat16>(P->ns_Xa), as<__nv_bfloat16>(P->ns_Xa) + smat * nc},
+                             {as<__nv_bfloat16>(P->ns_Xb), as<__nv_bfloat16>(P->ns_Xb) + smat * nc}};
+  __nv_bfloat16* Thi = as<__nv_bfloat16>(P->ns_T);
+  __nv_bfloat16* Tlo = Thi + smat * nc;
+  float* X = as<float>(P->ns_X);
+  const size_t t0 = tick(P);
+  // spectrum bound: power iteration (under-estimates), padded by 25%
+  CK(gw::tc_power_lmax(eps, n, nc, 30, as<float>(P->ns_lam), P->stream));
+  std::vector<float> lam(nc);
+  CK(cudaMemcpyAsync(lam.data(), P->ns_lam.p, sizeof(float) * nc, cudaMemcpyDeviceToHost, P->stream));
+  CK(cudaStreamSynchronize(P->stream));
+  float lmax = 1.0f;
+  for (int b = 0; b < nc; ++b) {
+    lam[b] = std::max(1.0f, lam[b]) * 1.25f;
+    lmax = std::max(lmax, lam[b]);
+  }
+  CK(cudaMemcpyAsync(P->ns_lam.p, lam.data(), sizeof(float) * nc, cudaMemcpyHostToDevice, P->stream));
+  // iterate k has error rho0^(2^k), rho0 = (lmax - 1)/(lmax + 1); stop below 1e-8, plus one step at the
+  // rounding floor of the split products
+  const double rho0 = (lmax - 1.0) / (lmax + 1.0);
+  int kmax = 1;
+  if (rho0 > 0.0) kmax = (int)std::ceil(std::log2(18.42 / -std::log(rho0))) + 1;
+  kmax = std::max(1, std::min(kmax, 24));
+  CK(gw::tc_split_rows(eps, nc * n, n, n, Ehi, Elo, P->stream));
+  CK(gw::tc_ns_init(eps, n, nc, as<float>(P->ns_lam), X, Xs[0][0], Xs[0][1], P->stream));
+  int cur = 0;
+  for (int k = 1; k < kmax; ++k) {
+    const bool last = (k == kmax - 1);
+    gw::TcEpi et{};
+    et.kind = gw::TC_EPI_AXPBY;
+    et.gamma = 1.f;
+    et.ldo = n;
+    et.ohi = Thi;
+    et.olo = Tlo;
+    et.ldh = ldn;
+    et.oh_bstride = (long)smat;
+    // T = eps X   (X symmetric, so X is its own K-major B operand)
+    CK(gw::tc_gemm_ex(Ehi, Elo, nc, Xs[cur][0], Xs[cur][1], 1, n, n, n, 0, et, as<int>(P->tc_err), P->stream));
+    gw::TcEpi ex{};
+    ex.kind = gw::TC_EPI_AXPBY;
+    ex.xin = X;
+    ex.x_bstride = (long)mat;
+    ex.alpha = 2.f;
+    ex.gamma = -1.f;
+    ex.beta = last ? -1.f : 0.f;
+    ex.out = X;
+    ex.out_bstride = (long)mat;
+    ex.ldo = n;
+    ex.ohi = Xs[1 - cur][0];
+    ex.olo = Xs[1 - cur][1];
+    ex.ldh = ldn;
+    ex.oh_bstride = (long)smat;
+    // X <- 2X - X T   (T = eps X is symmetric)
+    CK(gw::tc_gemm_ex(Xs[cur][0], Xs[cur][1], nc, Thi, Tlo, 1, n, n, n, 0, ex, as<int>(P->tc_err), P->stream));
+    cur = 1 - cur;
+    P->stats.n_kernel_launches += 2;
+  }
+  if (kmax == 1) {
+    // first iterate already converged: form X - I
+    gw::TcEpi ex{};
+    ex.kind = gw::TC_EPI_AXPBY;
+    ex.gamma = 0.f;
+    ex.xin = X;
+    ex.x_bstride = (long)mat;
+    ex.alpha = 1.f;
+    ex.beta = -1.f;
+    ex.ldo = n;
+    ex.ohi = Xs[1][0];
+    ex.olo = Xs[1][1];
+    ex.ldh = ldn;
+    ex.oh_bstride = (long)smat;
+    CK(gw::tc_gemm_ex(Ehi, Elo, nc, Xs[0][0], Xs[0][1], 1, n, n, n, 0, ex, as<int>(P->tc_err), P->stream));
+    cur = 1;
+  }
+  mark(P, 2, t0, 2.0 * 2.0 * (double)(kmax - 1) * nc * (double)n * n * n);
+  // W[r][g0 + b] = b_r^T (eps^-1 - 1) b_r, reduced in the epilogue (accumulates into zeroed entries)
+  const size_t t1 = tick(P);
+  CK(cudaMemset2DAsync(P->d_W + g0, sizeof(double) * n_g1, 0, sizeof(double) * nc, R, P->stream));
+  gw::TcEpi ew{};
+  ew.kind = gw::TC_EPI_WRED;
+  ew.W = P->d_W;
+  ew.wld = n_g1;
+  ew.gidx = as<int>(P->ws_gout) + g0;
+  ew.bvec = P->d_B_nm_f;
+  ew.ldb = n;
+  CK(gw::tc_gemm_ex(Xs[cur][0], Xs[cur][1], nc, P->d_Bnhi, P->d_Bnlo, 0, n, R, n, 0, ew, as<int>(P->tc_err),
+                    P->stream));
+  mark(P, 3, t1, 2.0 * nc * (double)n * n * R);
+  P->stats.n_kernel_launches += 5;
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, P->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+  CK(cudaStreamSynchronize(P->stream));
+  if (herr != 0) return fail(P, GW_ERR_TIMEOUT, "tensor-core W table: bounded wait ran out (code %d)", herr);
+  P->ns_iters_last = kmax;
+  return GW_OK;
+}
+
 // ---------------------------------------------------------------- imaginary-axis screening
 template <typename T>
 gw_status screening_T(gw_plan* P, const T* B, const T* Bn) {
@@ -214,7 +333,11 @@ gw_status screening_T(gw_plan* P, const T* B, const T* Bn) {
   // frequency matrices held at once: <= 8 GiB (and the split-operand budget on the tensor-core path)
   const size_t per = (size_t)n * n * sizeof(T);
   int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_g1, ws_bytes(P) / per));
-  if (use_tc) chunk = tc_chunk(P, chunk);
+  if (use_tc) {
+    chunk = tc_chunk(P, chunk);
+    const size_t per_ns = (size_t)n * gw::tc_ld(n) * 16 + (size_t)n * n * 8;   // split E, Xa, Xb, T; FP32 X, eps
+    chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)chunk, ws_bytes(P) / per_ns));
+  }
   TRY(ensure(P, P->ws_mat, per * chunk));
   TRY(ensure(P, P->ws_info, sizeof(int) * chunk));
   TRY(ensure(P, P->ws_gout, sizeof(int) * n_g1));
@@ -240,6 +363,12 @@ gw_status screening_T(gw_plan* P, const T* B, const T* Bn) {
       mark(P, 1, t0, (double)nc * n * n * P->n_ov);
     }
     CK(cudaEventRecord(P->ev1, P->stream));
+    if (use_tc) {
+      CK(cudaStreamSynchronize(P->stream));
+      ms_pi += now_ms(P, P->ev0, P->ev1);
+      TRY(ns_w_table(P, g0, nc));
+      continue;
+    }
     size_t t1 = tick(P);
     LAUNCH(gw::launch_cholesky<T>(as<T>(P->ws_mat), n, (long)n * n, nc, as<int>(P->ws_info), P->stream));
     mark(P, 2, t1, (double)nc * n * n * (double)n / 3.0);
@@ -676,6 +805,8 @@ static void free_plan(gw_plan* P) {
   if (P->d_BThi) cudaFree(P->d_BThi);
   if (P->d_BTlo) cudaFree(P->d_BTlo);
   if (P->d_D) cudaFree(P->d_D);
+  if (P->d_Bnhi) cudaFree(P->d_Bnhi);
+  if (P->d_Bnlo) cudaFree(P->d_Bnlo);
   if (P->h_cnt) cudaFreeHost(P->h_cnt);
   if (P->ev0) cudaEventDestroy(P->ev0);
   if (P->ev1) cudaEventDestroy(P->ev1);
@@ -760,6 +891,10 @@ static gw_status plan_create_impl(gw_plan* P, const gw_config* cfg, const double
     CK(cudaMalloc(&dw, sizeof(float) * P->n_ov));
     CK(gw::tc_scale_split(P->d_B_ia_f, P->d_eps, cfg->n_occ, cfg->n_virt, n, P->n_ov, dk, dp, 0.0, 1, dw, P->d_Bhi,
                           P->d_Blo, P->stream));
+    const size_t nsplitN = (size_t)n_targets * P->n_bas * gw::tc_ld(n);
+    CK(cudaMalloc(&P->d_Bnhi, sizeof(__nv_bfloat16) * nsplitN));
+    CK(cudaMalloc(&P->d_Bnlo, sizeof(__nv_bfloat16) * nsplitN));
+    CK(gw::tc_split_rows(P->d_B_nm_f, n_targets * P->n_bas, n, n, P->d_Bnhi, P->d_Bnlo, P->stream));
     const size_t nsplitT = (size_t)P->n_ov * gw::tc_ld(n);
     CK(cudaMalloc(&P->d_BThi, sizeof(__nv_bfloat16) * nsplitT));
     CK(cudaMalloc(&P->d_BTlo, sizeof(__nv_bfloat16) * nsplitT));

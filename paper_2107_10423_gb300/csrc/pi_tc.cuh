@@ -4,7 +4,7 @@
 #include <cuda_bf16.h>
 
 namespace gw {
-enum { TC_EPI_STORE = 0, TC_EPI_CPAIR = 1, TC_EPI_EMBED = 2 };
+enum { TC_EPI_STORE = 0, TC_EPI_CPAIR = 1, TC_EPI_EMBED = 2, TC_EPI_AXPBY = 3, TC_EPI_WRED = 4 };
 
 // Epilogue of the tensor-core GEMM (passed by value to the kernel).
 struct TcEpi {
@@ -24,6 +24,18 @@ struct TcEpi {
   // TC_EPI_EMBED: out[m][n] = (m even ? vin : -vin)[m][n] - v  (row lengths ldo, ldv)
   const float* vin;
   int ldv;
+  // TC_EPI_AXPBY: y = alpha * xin_b[m][n] + gamma * v + beta * delta_mn, written to out (FP32, if not NULL) and
+  // split into ohi/olo (if not NULL); batch strides out_bstride, x_bstride, oh_bstride (elements)
+  const float* xin;
+  long x_bstride;
+  float alpha, gamma, beta;
+  long oh_bstride;
+  // TC_EPI_WRED: W[n * wld + gidx[b]] += sum_m bvec[n][m] * v[m][n]  (bvec FP32, row length ldb)
+  double* W;
+  int wld;
+  const int* gidx;
+  const float* bvec;
+  int ldb;
 };
 
 // Row length (elements) of the split operand arrays for contraction length K (multiple of 8: 16-byte rows).
@@ -48,6 +60,13 @@ cudaError_t tc_gemm_ex(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int b
 // rows x cols FP32 (row length lds) split into BF16 hi/lo rows of tc_ld(cols) elements (zero padded).
 cudaError_t tc_split_rows(const float* src, int rows, int cols, int lds, __nv_bfloat16* hi, __nv_bfloat16* lo,
                           cudaStream_t s);
+// Largest eigenvalue estimate of each SPD matrix A_b (n x n FP32, batch stride n*n) by `iters` power steps,
+// written to lam[b] (device).
+cudaError_t tc_power_lmax(const float* A, int n, int batch, int iters, float* lam, cudaStream_t s);
+// X_b = 2 a_b I - a_b^2 A_b with a_b = 2/(1 + lam_b) (first Newton-Schulz iterate), FP32 out [b][n][n] and split
+// rows [b][n][tc_ld(n)].
+cudaError_t tc_ns_init(const float* A, int n, int batch, const float* lam, float* X, __nv_bfloat16* hi,
+                       __nv_bfloat16* lo, cudaStream_t s);
 // out[k][m] = B[m][k] split into BF16 hi/lo with rows of tc_ld(M) elements (B FP32 [M][K]).
 cudaError_t tc_transpose_split(const float* B, int M, int K, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s);
 }  // namespace gw

@@ -155,6 +155,27 @@ __device__ void epilogue(const TcEpi& ep, const float* stg, int m0, int n0, int 
       split_store(cr * tr - ci * ti, ep.ohi, ep.olo, (long)m * ep.ldh + n);
       split_store(cr * ti + ci * tr, ep.ohi, ep.olo, (long)(m + 1) * ep.ldh + n);
     }
+  } else if (ep.kind == TC_EPI_AXPBY) {
+    for (int idx = threadIdx.x; idx < BM * BN; idx += THREADS) {
+      const int rr = idx / BN, cc = idx % BN;
+      const int m = m0 + rr, n = n0 + cc;
+      if (m >= M || n >= N) continue;
+      float y = ep.gamma * stg[rr * (BN + 1) + cc] + (m == n ? ep.beta : 0.f);
+      if (ep.xin) y += ep.alpha * ep.xin[(long)b * ep.x_bstride + (long)m * ep.ldo + n];
+      if (ep.out) ep.out[(long)b * ep.out_bstride + (long)m * ep.ldo + n] = y;
+      if (ep.ohi) split_store(y, ep.ohi, ep.olo, (long)b * ep.oh_bstride + (long)m * ep.ldh + n);
+    }
+  } else if (ep.kind == TC_EPI_WRED) {
+    // column n of the tile: sum over the tile's rows m of bvec[n][m] * v[m][n], added into W
+    if (threadIdx.x < BN) {
+      const int cc = threadIdx.x, n = n0 + cc;
+      if (n < N) {
+        const float* bv = ep.bvec + (long)n * ep.ldb;
+        double acc = 0.0;
+        for (int rr = 0; rr < BM && m0 + rr < M; ++rr) acc += (double)bv[m0 + rr] * stg[rr * (BN + 1) + cc];
+        atomicAdd(ep.W + (long)n * ep.wld + ep.gidx[b], acc);
+      }
+    }
   } else if (ep.kind == TC_EPI_EMBED) {
     // real 2n embedding of (1 - Pi) z: rows 2j: u - (B w)_r, rows 2j+1: -v - (B w)_i
     for (int idx = threadIdx.x; idx < BM * BN; idx += THREADS) {
@@ -475,6 +496,76 @@ cudaError_t tc_split_rows(const float* src, int rows, int cols, int lds, __nv_bf
   const int ldh = tc_ld(cols);
   dim3 grid((ldh + 255) / 256, rows);
   if (rows > 0) split_rows_kernel<<<grid, 256, 0, s>>>(src, cols, lds, hi, lo, ldh);
+  return cudaGetLastError();
+}
+
+// power iteration, one CTA per matrix: v <- A v / |A v| from v = 1, lam = Rayleigh quotient
+__global__ void power_lmax_kernel(const float* __restrict__ A, int n, int iters, float* __restrict__ lam) {
+  extern __shared__ float pv[];     // v[n], w[n]
+  float* v = pv;
+  float* w = pv + n;
+  __shared__ float red[32];
+  const float* Ab = A + (long)blockIdx.x * n * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = rsqrtf((float)n);
+  __syncthreads();
+  float rq = 1.f;
+  for (int it = 0; it < iters; ++it) {
+    // w = A v, one warp per row
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int r = wid; r < n; r += nw) {
+      float a = 0.f;
+      for (int c = lane; c < n; c += 32) a += Ab[(long)r * n + c] * v[c];
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (lane == 0) w[r] = a;
+    }
+    __syncthreads();
+    float nn = 0.f, vw = 0.f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) { nn += w[i] * w[i]; vw += v[i] * w[i]; }
+    for (int o = 16; o > 0; o >>= 1) { nn += __shfl_xor_sync(0xffffffffu, nn, o); vw += __shfl_xor_sync(0xffffffffu, vw, o); }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nn;
+    __syncthreads();
+    float tn = 0.f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tn += red[i];
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = vw;
+    __syncthreads();
+    float tv = 0.f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tv += red[i];
+    rq = tv;
+    const float inv = tn > 0.f ? rsqrtf(tn) : 0.f;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = w[i] * inv;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) lam[blockIdx.x] = rq;
+}
+
+cudaError_t tc_power_lmax(const float* A, int n, int batch, int iters, float* lam, cudaStream_t s) {
+  const size_t smem = 2 * sizeof(float) * n;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(power_lmax_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (batch > 0) power_lmax_kernel<<<batch, 1024, smem, s>>>(A, n, iters, lam);
+  return cudaGetLastError();
+}
+
+__global__ void ns_init_kernel(const float* __restrict__ A, int n, const float* __restrict__ lam, float* __restrict__ X,
+                               __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int ldh) {
+  const int r = blockIdx.y, b = blockIdx.z;
+  const float a = 2.f / (1.f + lam[b]);
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ldh; c += gridDim.x * blockDim.x) {
+    float y = 0.f;
+    if (c < n) {
+      y = -a * a * A[((long)b * n + r) * n + c] + (r == c ? 2.f * a : 0.f);
+      X[((long)b * n + r) * n + c] = y;
+    }
+    split_store(y, hi, lo, ((long)b * n + r) * ldh + c);
+  }
+}
+
+cudaError_t tc_ns_init(const float* A, int n, int batch, const float* lam, float* X, __nv_bfloat16* hi,
+                       __nv_bfloat16* lo, cudaStream_t s) {
+  const int ldh = tc_ld(n);
+  dim3 grid((ldh + 255) / 256, n, batch);
+  if (batch > 0) ns_init_kernel<<<grid, 256, 0, s>>>(A, n, lam, X, hi, lo, ldh);
   return cudaGetLastError();
 }
 

@@ -43,7 +43,7 @@ class Stats(ctypes.Structure):
                 ("launches_kernel", ctypes.c_longlong * 9)]
 
 
-KERNEL_CLASSES = ["pi_tcgen05", "pi_simt", "cholesky", "trsm_w_table", "minres_operator_gemm", "minres_recurrence",
+KERNEL_CLASSES = ["pi_tcgen05", "pi_simt", "w_table_factor", "w_table_reduce", "minres_operator_gemm", "minres_recurrence",
                   "fallback_pi_dense", "fallback_lu", "fallback_refine_fp64"]
 
 
