@@ -53,6 +53,7 @@ struct gw_plan {
   double* d_D = nullptr;            // pair energies D_ia [n_ov]
   __nv_bfloat16* d_Bnhi = nullptr;  // mixed: BF16 hi/lo split of the B_nm rows, [n_t*n_bas][tc_ld(n_aux)]
   __nv_bfloat16* d_Bnlo = nullptr;
+  __nv_bfloat16* d_Bnlo2 = nullptr;
   bool screening_done = false;
   int ns_iters_last = 0;
   std::vector<DevBuf*> bufs;
@@ -214,22 +215,23 @@ int tc_chunk(gw_plan* P, int want) {
 gw_status ns_w_table(gw_plan* P, int g0, int nc) {
   const int n = P->cfg.n_aux, ldn = gw::tc_ld(n);
   const int R = P->n_t * P->n_bas, n_g1 = P->n_g + 1;
-  const size_t mat = (size_t)n * n, smat = (size_t)n * ldn;
-  TRY(ensure(P, P->ns_E, 2 * sizeof(__nv_bfloat16) * smat * nc));
-  TRY(ensure(P, P->ns_Xa, 2 * sizeof(__nv_bfloat16) * smat * nc));
-  TRY(ensure(P, P->ns_Xb, 2 * sizeof(__nv_bfloat16) * smat * nc));
-  TRY(ensure(P, P->ns_T, 2 * sizeof(__nv_bfloat16) * smat * nc));
+  const size_t mat = (size_t)n * n, smat = (size_t)n * ldn, sz = smat * nc;
+  // three split parts per operand: the cheap iterations use two, the last iteration and the W reduction three
+  TRY(ensure(P, P->ns_E, 3 * sizeof(__nv_bfloat16) * sz));
+  TRY(ensure(P, P->ns_Xa, 3 * sizeof(__nv_bfloat16) * sz));
+  TRY(ensure(P, P->ns_Xb, 3 * sizeof(__nv_bfloat16) * sz));
+  TRY(ensure(P, P->ns_T, 3 * sizeof(__nv_bfloat16) * sz));
   TRY(ensure(P, P->ns_X, sizeof(float) * mat * nc));
   TRY(ensure(P, P->ns_lam, sizeof(float) * nc));
   TRY(ensure(P, P->tc_err, sizeof(int)));
   CK(cudaMemsetAsync(P->tc_err.p, 0, sizeof(int), P->stream));
   const float* eps = reinterpret_cast<const float*>(P->ws_mat.p);
-  __nv_bfloat16* Ehi = as<__nv_bfloat16>(P->ns_E);
-  __nv_bfloat16* Elo = Ehi + smat * nc;
-  __nv_bfloat16* Xs[2][2] = {{as<__nv_bfloat16>(P->ns_Xa), as<__nv_bfloat16>(P->ns_Xa) + smat * nc},
-                             {as<__nv_bfloat16>(P->ns_Xb), as<__nv_bfloat16>(P->ns_Xb) + smat * nc}};
-  __nv_bfloat16* Thi = as<__nv_bfloat16>(P->ns_T);
-  __nv_bfloat16* Tlo = Thi + smat * nc;
+  auto parts = [&](DevBuf& b) {
+    __nv_bfloat16* p0 = as<__nv_bfloat16>(b);
+    return gw::TcOperand{{p0, p0 + sz, p0 + 2 * sz}};
+  };
+  const gw::TcOperand E = parts(P->ns_E), T = parts(P->ns_T);
+  const gw::TcOperand Xs[2] = {parts(P->ns_Xa), parts(P->ns_Xb)};
   float* X = as<float>(P->ns_X);
   const size_t t0 = tick(P);
   // spectrum bound: power iteration (under-estimates), padded by 25%
@@ -243,27 +245,31 @@ gw_status ns_w_table(gw_plan* P, int g0, int nc) {
     lmax = std::max(lmax, lam[b]);
   }
   CK(cudaMemcpyAsync(P->ns_lam.p, lam.data(), sizeof(float) * nc, cudaMemcpyHostToDevice, P->stream));
-  // iterate k has error rho0^(2^k), rho0 = (lmax - 1)/(lmax + 1); stop below 1e-8, plus one step at the
-  // rounding floor of the split products
+  // iterate k has error rho0^(2^k), rho0 = (lmax - 1)/(lmax + 1): two-part iterations down to ~1e-5, then one
+  // three-part iteration (quadratic: to the FP32 floor)
   const double rho0 = (lmax - 1.0) / (lmax + 1.0);
-  int kmax = 1;
-  if (rho0 > 0.0) kmax = (int)std::ceil(std::log2(18.42 / -std::log(rho0))) + 1;
-  kmax = std::max(1, std::min(kmax, 24));
-  CK(gw::tc_split_rows(eps, nc * n, n, n, Ehi, Elo, P->stream));
-  CK(gw::tc_ns_init(eps, n, nc, as<float>(P->ns_lam), X, Xs[0][0], Xs[0][1], P->stream));
+  int kmax = 2;
+  if (rho0 > 0.0) kmax = std::max(2, (int)std::ceil(std::log2(11.5 / -std::log(rho0))) + 1);
+  kmax = std::min(kmax, 24);
+  CK(gw::tc_split_rows(eps, nc * n, n, n, const_cast<__nv_bfloat16*>(E.p[0]), const_cast<__nv_bfloat16*>(E.p[1]),
+                       P->stream, const_cast<__nv_bfloat16*>(E.p[2])));
+  CK(gw::tc_ns_init(eps, n, nc, as<float>(P->ns_lam), X, const_cast<__nv_bfloat16*>(Xs[0].p[0]),
+                    const_cast<__nv_bfloat16*>(Xs[0].p[1]), P->stream, const_cast<__nv_bfloat16*>(Xs[0].p[2])));
   int cur = 0;
   for (int k = 1; k < kmax; ++k) {
     const bool last = (k == kmax - 1);
+    const int ns = last ? 3 : 2;
     gw::TcEpi et{};
     et.kind = gw::TC_EPI_AXPBY;
     et.gamma = 1.f;
     et.ldo = n;
-    et.ohi = Thi;
-    et.olo = Tlo;
+    et.ohi = const_cast<__nv_bfloat16*>(T.p[0]);
+    et.olo = const_cast<__nv_bfloat16*>(T.p[1]);
+    et.olo2 = const_cast<__nv_bfloat16*>(T.p[2]);
     et.ldh = ldn;
     et.oh_bstride = (long)smat;
     // T = eps X   (X symmetric, so X is its own K-major B operand)
-    CK(gw::tc_gemm_ex(Ehi, Elo, nc, Xs[cur][0], Xs[cur][1], 1, n, n, n, 0, et, as<int>(P->tc_err), P->stream));
+    CK(gw::tc_gemm_ex(E, nc, Xs[cur], 1, ns, n, n, n, 0, et, as<int>(P->tc_err), P->stream));
     gw::TcEpi ex{};
     ex.kind = gw::TC_EPI_AXPBY;
     ex.xin = X;
@@ -274,31 +280,15 @@ gw_status ns_w_table(gw_plan* P, int g0, int nc) {
     ex.out = X;
     ex.out_bstride = (long)mat;
     ex.ldo = n;
-    ex.ohi = Xs[1 - cur][0];
-    ex.olo = Xs[1 - cur][1];
+    ex.ohi = const_cast<__nv_bfloat16*>(Xs[1 - cur].p[0]);
+    ex.olo = const_cast<__nv_bfloat16*>(Xs[1 - cur].p[1]);
+    ex.olo2 = const_cast<__nv_bfloat16*>(Xs[1 - cur].p[2]);
     ex.ldh = ldn;
     ex.oh_bstride = (long)smat;
-    // X <- 2X - X T   (T = eps X is symmetric)
-    CK(gw::tc_gemm_ex(Xs[cur][0], Xs[cur][1], nc, Thi, Tlo, 1, n, n, n, 0, ex, as<int>(P->tc_err), P->stream));
+    // X <- 2X - X T   (T = eps X is symmetric); the last iterate is written as X - I
+    CK(gw::tc_gemm_ex(Xs[cur], nc, T, 1, ns, n, n, n, 0, ex, as<int>(P->tc_err), P->stream));
     cur = 1 - cur;
     P->stats.n_kernel_launches += 2;
-  }
-  if (kmax == 1) {
-    // first iterate already converged: form X - I
-    gw::TcEpi ex{};
-    ex.kind = gw::TC_EPI_AXPBY;
-    ex.gamma = 0.f;
-    ex.xin = X;
-    ex.x_bstride = (long)mat;
-    ex.alpha = 1.f;
-    ex.beta = -1.f;
-    ex.ldo = n;
-    ex.ohi = Xs[1][0];
-    ex.olo = Xs[1][1];
-    ex.ldh = ldn;
-    ex.oh_bstride = (long)smat;
-    CK(gw::tc_gemm_ex(Ehi, Elo, nc, Xs[0][0], Xs[0][1], 1, n, n, n, 0, ex, as<int>(P->tc_err), P->stream));
-    cur = 1;
   }
   mark(P, 2, t0, 2.0 * 2.0 * (double)(kmax - 1) * nc * (double)n * n * n);
   // W[r][g0 + b] = b_r^T (eps^-1 - 1) b_r, reduced in the epilogue (accumulates into zeroed entries)
@@ -311,8 +301,8 @@ gw_status ns_w_table(gw_plan* P, int g0, int nc) {
   ew.gidx = as<int>(P->ws_gout) + g0;
   ew.bvec = P->d_B_nm_f;
   ew.ldb = n;
-  CK(gw::tc_gemm_ex(Xs[cur][0], Xs[cur][1], nc, P->d_Bnhi, P->d_Bnlo, 0, n, R, n, 0, ew, as<int>(P->tc_err),
-                    P->stream));
+  const gw::TcOperand Bn{{P->d_Bnhi, P->d_Bnlo, P->d_Bnlo2}};
+  CK(gw::tc_gemm_ex(Xs[cur], nc, Bn, 0, 3, n, R, n, 0, ew, as<int>(P->tc_err), P->stream));
   mark(P, 3, t1, 2.0 * nc * (double)n * n * R);
   P->stats.n_kernel_launches += 5;
   int herr = 0;
@@ -335,7 +325,7 @@ gw_status screening_T(gw_plan* P, const T* B, const T* Bn) {
   int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_g1, ws_bytes(P) / per));
   if (use_tc) {
     chunk = tc_chunk(P, chunk);
-    const size_t per_ns = (size_t)n * gw::tc_ld(n) * 16 + (size_t)n * n * 8;   // split E, Xa, Xb, T; FP32 X, eps
+    const size_t per_ns = (size_t)n * gw::tc_ld(n) * 24 + (size_t)n * n * 8;   // split E, Xa, Xb, T; FP32 X, eps
     chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)chunk, ws_bytes(P) / per_ns));
   }
   TRY(ensure(P, P->ws_mat, per * chunk));
@@ -534,16 +524,18 @@ gw_status tc_operator(gw_plan* P, int nr, const double* xf, const float* V32, fl
   e1.ohi = as<__nv_bfloat16>(P->mr_Uhi);
   e1.olo = as<__nv_bfloat16>(P->mr_Ulo);
   e1.ldh = ldov;
-  CK(gw::tc_gemm_ex(as<__nv_bfloat16>(P->mr_Vhi), as<__nv_bfloat16>(P->mr_Vlo), 1, P->d_BThi, P->d_BTlo, 0, 2 * nr,
-                    n_ov, n, 0, e1, as<int>(P->tc_err), P->stream));
+  const gw::TcOperand Vop{{as<__nv_bfloat16>(P->mr_Vhi), as<__nv_bfloat16>(P->mr_Vlo), nullptr}};
+  const gw::TcOperand BT{{P->d_BThi, P->d_BTlo, nullptr}};
+  CK(gw::tc_gemm_ex(Vop, 1, BT, 0, 2, 2 * nr, n_ov, n, 0, e1, as<int>(P->tc_err), P->stream));
   gw::TcEpi e2{};
   e2.kind = mode == 0 ? gw::TC_EPI_STORE : gw::TC_EPI_EMBED;
   e2.out = S32;
   e2.ldo = n;
   e2.vin = V32;
   e2.ldv = n;
-  CK(gw::tc_gemm_ex(as<__nv_bfloat16>(P->mr_Uhi), as<__nv_bfloat16>(P->mr_Ulo), 1, P->d_Bhi, P->d_Blo, 0, 2 * nr, n,
-                    n_ov, 0, e2, as<int>(P->tc_err), P->stream));
+  const gw::TcOperand Uop{{as<__nv_bfloat16>(P->mr_Uhi), as<__nv_bfloat16>(P->mr_Ulo), nullptr}};
+  const gw::TcOperand Bop{{P->d_Bhi, P->d_Blo, nullptr}};
+  CK(gw::tc_gemm_ex(Uop, 1, Bop, 0, 2, 2 * nr, n, n_ov, 0, e2, as<int>(P->tc_err), P->stream));
   P->stats.n_kernel_launches += 3;
   (void)ldn;
   return GW_OK;
@@ -807,6 +799,7 @@ static void free_plan(gw_plan* P) {
   if (P->d_D) cudaFree(P->d_D);
   if (P->d_Bnhi) cudaFree(P->d_Bnhi);
   if (P->d_Bnlo) cudaFree(P->d_Bnlo);
+  if (P->d_Bnlo2) cudaFree(P->d_Bnlo2);
   if (P->h_cnt) cudaFreeHost(P->h_cnt);
   if (P->ev0) cudaEventDestroy(P->ev0);
   if (P->ev1) cudaEventDestroy(P->ev1);
@@ -894,7 +887,8 @@ static gw_status plan_create_impl(gw_plan* P, const gw_config* cfg, const double
     const size_t nsplitN = (size_t)n_targets * P->n_bas * gw::tc_ld(n);
     CK(cudaMalloc(&P->d_Bnhi, sizeof(__nv_bfloat16) * nsplitN));
     CK(cudaMalloc(&P->d_Bnlo, sizeof(__nv_bfloat16) * nsplitN));
-    CK(gw::tc_split_rows(P->d_B_nm_f, n_targets * P->n_bas, n, n, P->d_Bnhi, P->d_Bnlo, P->stream));
+    CK(cudaMalloc(&P->d_Bnlo2, sizeof(__nv_bfloat16) * nsplitN));
+    CK(gw::tc_split_rows(P->d_B_nm_f, n_targets * P->n_bas, n, n, P->d_Bnhi, P->d_Bnlo, P->stream, P->d_Bnlo2));
     const size_t nsplitT = (size_t)P->n_ov * gw::tc_ld(n);
     CK(cudaMalloc(&P->d_BThi, sizeof(__nv_bfloat16) * nsplitT));
     CK(cudaMalloc(&P->d_BTlo, sizeof(__nv_bfloat16) * nsplitT));

@@ -21,6 +21,7 @@ struct TcEpi {
   __nv_bfloat16* ohi;
   __nv_bfloat16* olo;
   int ldh;
+  __nv_bfloat16* olo2;   // third split part (TC_EPI_AXPBY), or NULL
   // TC_EPI_EMBED: out[m][n] = (m even ? vin : -vin)[m][n] - v  (row lengths ldo, ldv)
   const float* vin;
   int ldv;
@@ -53,20 +54,24 @@ cudaError_t tc_scale_split(const float* B, const double* eps, int n_occ, int n_v
 cudaError_t tc_gemm(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int batch, const __nv_bfloat16* Bhi,
                     const __nv_bfloat16* Blo, int M, int N, int K, int lower, int mode_even, int mode_odd, float* out,
                     int* err, cudaStream_t s);
-// General form: B may also be batched (b_batched != 0: Bm_b has the same batch count as A).
-cudaError_t tc_gemm_ex(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int batch, const __nv_bfloat16* Bhi,
-                       const __nv_bfloat16* Blo, int b_batched, int M, int N, int K, int lower, const TcEpi& ep,
-                       int* err, cudaStream_t s);
+// Split operand: parts p[0..nsplit) of [batch][rows][tc_ld(K)] BF16 (hi, lo[, lo2]).
+struct TcOperand {
+  const __nv_bfloat16* p[3];
+};
+// General form: B may also be batched (b_batched != 0: Bm_b has the same batch count as A); nsplit 2 uses three
+// products (BF16x3), nsplit 3 the six products with part indices i + j <= 2 (about FP32-accurate).
+cudaError_t tc_gemm_ex(const TcOperand& A, int batch, const TcOperand& B, int b_batched, int nsplit, int M, int N,
+                       int K, int lower, const TcEpi& ep, int* err, cudaStream_t s);
 // rows x cols FP32 (row length lds) split into BF16 hi/lo rows of tc_ld(cols) elements (zero padded).
 cudaError_t tc_split_rows(const float* src, int rows, int cols, int lds, __nv_bfloat16* hi, __nv_bfloat16* lo,
-                          cudaStream_t s);
+                          cudaStream_t s, __nv_bfloat16* lo2 = nullptr);
 // Largest eigenvalue estimate of each SPD matrix A_b (n x n FP32, batch stride n*n) by `iters` power steps,
 // written to lam[b] (device).
 cudaError_t tc_power_lmax(const float* A, int n, int batch, int iters, float* lam, cudaStream_t s);
 // X_b = 2 a_b I - a_b^2 A_b with a_b = 2/(1 + lam_b) (first Newton-Schulz iterate), FP32 out [b][n][n] and split
 // rows [b][n][tc_ld(n)].
 cudaError_t tc_ns_init(const float* A, int n, int batch, const float* lam, float* X, __nv_bfloat16* hi,
-                       __nv_bfloat16* lo, cudaStream_t s);
+                       __nv_bfloat16* lo, cudaStream_t s, __nv_bfloat16* lo2 = nullptr);
 // out[k][m] = B[m][k] split into BF16 hi/lo with rows of tc_ld(M) elements (B FP32 [M][K]).
 cudaError_t tc_transpose_split(const float* B, int M, int K, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s);
 }  // namespace gw

@@ -18,10 +18,17 @@
 namespace gw {
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 3, THREADS = 192, CHUNK = 4;
+constexpr int BM = 128, BN = 128, BK = 64, THREADS = 192, CHUNK = 4;
 constexpr int TILE_BYTES = BM * BK * 2;               // one 128 x 64 BF16 tile = 16 KiB
-constexpr int STAGE_BYTES = 4 * TILE_BYTES;           // Ahi, Alo, Bhi, Blo
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+
+// NSP split parts per operand: 2 (hi, lo: products hh, hl, lh) or 3 (hi, mid, lo: the six products with
+// part indices i + j <= 2, about FP32-accurate).  A stage holds NSP A tiles and NSP B tiles.
+template <int NSP>
+struct TcCfg {
+  static constexpr int STAGES = NSP == 2 ? 3 : 2;
+  static constexpr int STAGE_BYTES = 2 * NSP * TILE_BYTES;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+};
 constexpr uint32_t TMEM_COLS = 256;                  // two 128-column accumulators
 constexpr long long WAIT_LIMIT = 1ll << 26;           // bounded spin on every mbarrier
 
@@ -109,10 +116,14 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 
 // Epilogues.  The tile is staged in shared memory as stg[BM][BN + 1] (row = output row), so any thread can combine
 // elements of different rows (the complex pairs of the residue operator are adjacent rows).
-__device__ __forceinline__ void split_store(float v, __nv_bfloat16* hi, __nv_bfloat16* lo, long o) {
+__device__ __forceinline__ void split_store(float v, __nv_bfloat16* hi, __nv_bfloat16* lo, long o,
+                                            __nv_bfloat16* lo2 = nullptr) {
   const __nv_bfloat16 h = __float2bfloat16_rn(v);
   hi[o] = h;
-  lo[o] = __float2bfloat16_rn(v - __bfloat162float(h));
+  const float r = v - __bfloat162float(h);
+  const __nv_bfloat16 m = __float2bfloat16_rn(r);
+  lo[o] = m;
+  if (lo2) lo2[o] = __float2bfloat16_rn(r - __bfloat162float(m));
 }
 
 __device__ void epilogue(const TcEpi& ep, const float* stg, int m0, int n0, int M, int N, int b, int lower) {
@@ -163,7 +174,7 @@ __device__ void epilogue(const TcEpi& ep, const float* stg, int m0, int n0, int 
       float y = ep.gamma * stg[rr * (BN + 1) + cc] + (m == n ? ep.beta : 0.f);
       if (ep.xin) y += ep.alpha * ep.xin[(long)b * ep.x_bstride + (long)m * ep.ldo + n];
       if (ep.out) ep.out[(long)b * ep.out_bstride + (long)m * ep.ldo + n] = y;
-      if (ep.ohi) split_store(y, ep.ohi, ep.olo, (long)b * ep.oh_bstride + (long)m * ep.ldh + n);
+      if (ep.ohi) split_store(y, ep.ohi, ep.olo, (long)b * ep.oh_bstride + (long)m * ep.ldh + n, ep.olo2);
     }
   } else if (ep.kind == TC_EPI_WRED) {
     // column n of the tile: sum over the tile's rows m of bvec[n][m] * v[m][n], added into W
@@ -195,10 +206,16 @@ __device__ void epilogue(const TcEpi& ep, const float* stg, int m0, int n0, int 
 // 3 * 4 * CHUNK tensor-core accumulation steps (the tensor-core accumulator alone drifts over long K).
 // mode_even / mode_odd select the epilogue for even / odd batch entries:
 //   0: v    1: delta_mn - v    2: -v
+struct TcMaps {
+  CUtensorMap a[3], b[3];
+};
+
+template <int NSP>
 __global__ void __launch_bounds__(THREADS, 1)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapAhi, const __grid_constant__ CUtensorMap mapAlo,
-                   const __grid_constant__ CUtensorMap mapBhi, const __grid_constant__ CUtensorMap mapBlo, int M,
-                   int N, int K, int lower, int b_batched, const TcEpi ep, int* __restrict__ err) {
+    tc_gemm_kernel(const __grid_constant__ TcMaps maps, int M, int N, int K, int lower, int b_batched, const TcEpi ep,
+                   int* __restrict__ err) {
+  constexpr int STAGES = TcCfg<NSP>::STAGES;
+  constexpr int STAGE_BYTES = TcCfg<NSP>::STAGE_BYTES;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -269,10 +286,11 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (*(volatile int*)&s_abort) break;
         const uint32_t st = base + s * STAGE_BYTES;
         mbar_expect_tx(full[s], STAGE_BYTES);
-        tma_load_3d(st, &mapAhi, kb * BK, m0, b, full[s]);
-        tma_load_3d(st + TILE_BYTES, &mapAlo, kb * BK, m0, b, full[s]);
-        tma_load_3d(st + 2 * TILE_BYTES, &mapBhi, kb * BK, n0, b_batched ? b : 0, full[s]);
-        tma_load_3d(st + 3 * TILE_BYTES, &mapBlo, kb * BK, n0, b_batched ? b : 0, full[s]);
+#pragma unroll
+        for (int i = 0; i < NSP; ++i) tma_load_3d(st + i * TILE_BYTES, &maps.a[i], kb * BK, m0, b, full[s]);
+#pragma unroll
+        for (int j = 0; j < NSP; ++j)
+          tma_load_3d(st + (NSP + j) * TILE_BYTES, &maps.b[j], kb * BK, n0, b_batched ? b : 0, full[s]);
         issued = kb + 1;
       }
     }
@@ -290,11 +308,13 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
         for (int k = 0; k < BK / 16; ++k) {
           const uint32_t off = k * 32;
-          const uint64_t ahi = sdesc(st + off), alo = sdesc(st + TILE_BYTES + off);
-          const uint64_t bhi = sdesc(st + 2 * TILE_BYTES + off), blo = sdesc(st + 3 * TILE_BYTES + off);
-          mma_bf16(d, ahi, bhi, (!first || k > 0) ? 1u : 0u);
-          mma_bf16(d, ahi, blo, 1u);
-          mma_bf16(d, alo, bhi, 1u);
+#pragma unroll
+          for (int i = 0; i < NSP; ++i)
+#pragma unroll
+            for (int j = 0; j + i < NSP; ++j) {
+              const uint64_t ad = sdesc(st + i * TILE_BYTES + off), bd = sdesc(st + (NSP + j) * TILE_BYTES + off);
+              mma_bf16(d, ad, bd, (!first || k > 0 || i > 0 || j > 0) ? 1u : 0u);
+            }
         }
         mma_commit(empty[s]);
         if ((kb % CHUNK) == CHUNK - 1 || kb == nk - 1) mma_commit(acc_full[buf]);
@@ -433,25 +453,38 @@ cudaError_t tc_scale_split(const float* B, const double* eps, int n_occ, int n_v
   return cudaGetLastError();
 }
 
-cudaError_t tc_gemm_ex(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int batch, const __nv_bfloat16* Bhi,
-                       const __nv_bfloat16* Blo, int b_batched, int M, int N, int K, int lower, const TcEpi& ep,
-                       int* err, cudaStream_t s) {
+cudaError_t tc_gemm_ex(const TcOperand& A, int batch, const TcOperand& B, int b_batched, int nsplit, int M, int N,
+                       int K, int lower, const TcEpi& ep, int* err, cudaStream_t s) {
   const int ld = tc_ld(K);
-  CUtensorMap mAhi, mAlo, mBhi, mBlo;
+  TcMaps maps;
   const int bb = b_batched ? batch : 1;
-  if (!make_map(&mAhi, Ahi, M, K, ld, batch) || !make_map(&mAlo, Alo, M, K, ld, batch) ||
-      !make_map(&mBhi, Bhi, N, K, ld, bb) || !make_map(&mBlo, Blo, N, K, ld, bb))
-    return cudaErrorInvalidValue;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  if (nsplit != 2 && nsplit != 3) return cudaErrorInvalidValue;
+  for (int i = 0; i < nsplit; ++i)
+    if (!A.p[i] || !B.p[i] || !make_map(&maps.a[i], A.p[i], M, K, ld, batch) ||
+        !make_map(&maps.b[i], B.p[i], N, K, ld, bb))
+      return cudaErrorInvalidValue;
   const int nbm = (M + BM - 1) / BM, nbn = (N + BN - 1) / BN;
   const int tiles = lower ? nbm * (nbm + 1) / 2 : nbm * nbn;
   dim3 grid(tiles, batch);
-  tc_gemm_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(mAhi, mAlo, mBhi, mBlo, M, N, K, lower, b_batched, ep, err);
+  if (nsplit == 2) {
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           TcCfg<2>::SMEM_BYTES);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    tc_gemm_kernel<2><<<grid, THREADS, TcCfg<2>::SMEM_BYTES, s>>>(maps, M, N, K, lower, b_batched, ep, err);
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           TcCfg<3>::SMEM_BYTES);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    tc_gemm_kernel<3><<<grid, THREADS, TcCfg<3>::SMEM_BYTES, s>>>(maps, M, N, K, lower, b_batched, ep, err);
+  }
   return cudaGetLastError();
 }
 
@@ -465,7 +498,8 @@ cudaError_t tc_gemm(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int batc
   ep.out = out;
   ep.out_bstride = (long)M * N;
   ep.ldo = N;
-  return tc_gemm_ex(Ahi, Alo, batch, Bhi, Blo, 0, M, N, K, lower, ep, err, s);
+  const TcOperand a{{Ahi, Alo, nullptr}}, bo{{Bhi, Blo, nullptr}};
+  return tc_gemm_ex(a, batch, bo, 0, 2, M, N, K, lower, ep, err, s);
 }
 
 // B^T split: out[k][m] = B[m][k] as BF16 hi/lo, rows of length tc_ld(M).  32 x 32 tiles through shared memory.
@@ -485,17 +519,29 @@ __global__ void transpose_split_kernel(const float* __restrict__ B, int M, int K
 }
 
 __global__ void split_rows_kernel(const float* __restrict__ src, int cols, int lds, __nv_bfloat16* __restrict__ hi,
-                                  __nv_bfloat16* __restrict__ lo, int ldh) {
-  const int r = blockIdx.y;
+                                  __nv_bfloat16* __restrict__ lo, __nv_bfloat16* __restrict__ lo2, int ldh) {
+  const long r = blockIdx.y + (long)blockIdx.z * gridDim.y;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ldh; c += gridDim.x * blockDim.x)
-    split_store(c < cols ? src[(long)r * lds + c] : 0.f, hi, lo, (long)r * ldh + c);
+    split_store(c < cols ? src[r * lds + c] : 0.f, hi, lo, r * ldh + c, lo2);
 }
 
 cudaError_t tc_split_rows(const float* src, int rows, int cols, int lds, __nv_bfloat16* hi, __nv_bfloat16* lo,
-                          cudaStream_t s) {
+                          cudaStream_t s, __nv_bfloat16* lo2) {
   const int ldh = tc_ld(cols);
-  dim3 grid((ldh + 255) / 256, rows);
-  if (rows > 0) split_rows_kernel<<<grid, 256, 0, s>>>(src, cols, lds, hi, lo, ldh);
+  if (rows <= 0) return cudaSuccess;
+  int gy = rows, gz = 1;
+  while (gy > 65535) { gz *= 2; gy = (rows + gz - 1) / gz; }
+  if ((long)gy * gz != rows) {
+    // rows not a multiple of the z split: run the tail separately
+    const int main = (rows / gz) * gz;
+    if (main > 0) split_rows_kernel<<<dim3((ldh + 255) / 256, main / gz, gz), 256, 0, s>>>(src, cols, lds, hi, lo, lo2, ldh);
+    const int tail = rows - main;
+    split_rows_kernel<<<dim3((ldh + 255) / 256, tail, 1), 256, 0, s>>>(src + (long)main * lds, cols, lds,
+                                                                     hi + (long)main * ldh, lo + (long)main * ldh,
+                                                                     lo2 ? lo2 + (long)main * ldh : nullptr, ldh);
+    return cudaGetLastError();
+  }
+  split_rows_kernel<<<dim3((ldh + 255) / 256, gy, gz), 256, 0, s>>>(src, cols, lds, hi, lo, lo2, ldh);
   return cudaGetLastError();
 }
 
@@ -548,7 +594,8 @@ cudaError_t tc_power_lmax(const float* A, int n, int batch, int iters, float* la
 }
 
 __global__ void ns_init_kernel(const float* __restrict__ A, int n, const float* __restrict__ lam, float* __restrict__ X,
-                               __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int ldh) {
+                               __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
+                               __nv_bfloat16* __restrict__ lo2, int ldh) {
   const int r = blockIdx.y, b = blockIdx.z;
   const float a = 2.f / (1.f + lam[b]);
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ldh; c += gridDim.x * blockDim.x) {
@@ -557,15 +604,15 @@ __global__ void ns_init_kernel(const float* __restrict__ A, int n, const float* 
       y = -a * a * A[((long)b * n + r) * n + c] + (r == c ? 2.f * a : 0.f);
       X[((long)b * n + r) * n + c] = y;
     }
-    split_store(y, hi, lo, ((long)b * n + r) * ldh + c);
+    split_store(y, hi, lo, ((long)b * n + r) * ldh + c, lo2);
   }
 }
 
 cudaError_t tc_ns_init(const float* A, int n, int batch, const float* lam, float* X, __nv_bfloat16* hi,
-                       __nv_bfloat16* lo, cudaStream_t s) {
+                       __nv_bfloat16* lo, cudaStream_t s, __nv_bfloat16* lo2) {
   const int ldh = tc_ld(n);
   dim3 grid((ldh + 255) / 256, n, batch);
-  if (batch > 0) ns_init_kernel<<<grid, 256, 0, s>>>(A, n, lam, X, hi, lo, ldh);
+  if (batch > 0) ns_init_kernel<<<grid, 256, 0, s>>>(A, n, lam, X, hi, lo, lo2, ldh);
   return cudaGetLastError();
 }
 
