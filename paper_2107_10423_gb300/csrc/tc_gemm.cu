@@ -18,18 +18,22 @@
 namespace gw {
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64, THREADS = 192, CHUNK = 4;
+constexpr int BM = 128, BN = 128, BK = 64, THREADS = 192;
 constexpr int TILE_BYTES = BM * BK * 2;               // one 128 x 64 BF16 tile = 16 KiB
 
 // NSP split parts per operand: 2 (hi, lo: products hh, hl, lh) or 3 (hi, mid, lo: the six products with
 // part indices i + j <= 2, about FP32-accurate).  A stage holds NSP A tiles and NSP B tiles.
 template <int NSP>
 struct TcCfg {
+  static constexpr int CHUNK = NSP == 2 ? 4 : 1;     // k-blocks per TMEM chunk before the drain
   static constexpr int STAGES = NSP == 2 ? 3 : 2;
   static constexpr int STAGE_BYTES = 2 * NSP * TILE_BYTES;
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 };
-constexpr uint32_t TMEM_COLS = 256;                  // two 128-column accumulators
+// Two chunk buffers x two accumulators (hi*hi alone; every cross product together) x 128 columns.  Keeping the
+// dominant hi*hi product apart leaves its accumulator one accumulate per k-step; the cross terms are 2^8
+// smaller, so their accumulator's rounding is negligible.
+constexpr uint32_t TMEM_COLS = 512;
 constexpr long long WAIT_LIMIT = 1ll << 26;           // bounded spin on every mbarrier
 
 // tcgen05 instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, N = BN, M = BM.
@@ -202,8 +206,9 @@ __device__ void epilogue(const TcEpi& ep, const float* stg, int m0, int n0, int 
 // grid.x: output tile (lower-triangular enumeration when `lower`), grid.y: batch entry.
 // Warp roles: warps 0-3 drain the accumulator (TMEM lane quarter = warp), warp 4 issues TMA, warp 5 issues MMA.
 // The contraction is cut into chunks of CHUNK k-blocks; each chunk accumulates in one of two TMEM buffers and
-// is then added into FP32 registers by the drain warps, so no partial sum runs through more than
-// 3 * 4 * CHUNK tensor-core accumulation steps (the tensor-core accumulator alone drifts over long K).
+// is then added into FP32 registers by the drain warps (round to nearest), so no partial sum runs through more
+// than 4 * CHUNK tensor-core accumulates of the dominant hi*hi product (the tensor-core accumulator loses about
+// one ulp per accumulate, which over long K leaves a systematic relative error).
 // mode_even / mode_odd select the epilogue for even / odd batch entries:
 //   0: v    1: delta_mn - v    2: -v
 struct TcMaps {
@@ -216,6 +221,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                    int* __restrict__ err) {
   constexpr int STAGES = TcCfg<NSP>::STAGES;
   constexpr int STAGE_BYTES = TcCfg<NSP>::STAGE_BYTES;
+  constexpr int CHUNK = TcCfg<NSP>::CHUNK;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -304,7 +310,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (!mbar_wait(full[s], u & 1, err, 2)) { s_abort = 1; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t st = base + s * STAGE_BYTES;
-        const uint32_t d = tmem + (uint32_t)(buf * BN);
+        const uint32_t dbig = tmem + (uint32_t)(buf * 2 * BN), dsmall = dbig + BN;
 #pragma unroll
         for (int k = 0; k < BK / 16; ++k) {
           const uint32_t off = k * 32;
@@ -313,7 +319,9 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
             for (int j = 0; j + i < NSP; ++j) {
               const uint64_t ad = sdesc(st + i * TILE_BYTES + off), bd = sdesc(st + (NSP + j) * TILE_BYTES + off);
-              mma_bf16(d, ad, bd, (!first || k > 0 || i > 0 || j > 0) ? 1u : 0u);
+              const bool is_big = (i == 0 && j == 0);
+              const bool first_in_acc = first && k == 0 && (is_big || (i == 0 && j == 1));
+              mma_bf16(is_big ? dbig : dsmall, ad, bd, first_in_acc ? 0u : 1u);
             }
         }
         mma_commit(empty[s]);
@@ -332,10 +340,12 @@ __global__ void __launch_bounds__(THREADS, 1)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
       for (int q = 0; q < BN / 32; ++q) {
-        uint32_t v[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * BN + q * 32), v);
+        uint32_t v[32], w[32];
+        const uint32_t col = (uint32_t)(buf * 2 * BN + q * 32);
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + col, v);
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + col + BN, w);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) acc[q * 32 + j] += __uint_as_float(v[j]);
+        for (int j = 0; j < 32; ++j) acc[q * 32 + j] += __uint_as_float(v[j]) + __uint_as_float(w[j]);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
