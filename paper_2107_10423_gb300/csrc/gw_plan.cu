@@ -56,6 +56,8 @@ struct gw_plan {
   __nv_bfloat16* d_Bnlo2 = nullptr;
   bool screening_done = false;
   int ns_iters_last = 0;
+  float ns_lam_global = 0.f;   // spectrum bound of eps(i xi) for every xi: lambda_max(eps(0)), padded
+  int ns_kmax = 0;
   std::vector<DevBuf*> bufs;
   DevBuf ws_mat, ws_info, ws_scratch, ws_gout, ws_xi, tc_Ahi, tc_Alo, tc_kind, tc_par, tc_err, tc_w, ns_E, ns_X, ns_Xa, ns_Xb, ns_T, ns_lam;
   DevBuf mr_V, mr_U, mr_S, mr_vprev, mr_v, mr_d1, mr_d2, mr_x, mr_st, mr_rt, mr_rm, mr_xf, mr_wre, mr_wim,
@@ -234,23 +236,30 @@ gw_status ns_w_table(gw_plan* P, int g0, int nc) {
   const gw::TcOperand Xs[2] = {parts(P->ns_Xa), parts(P->ns_Xb)};
   float* X = as<float>(P->ns_X);
   const size_t t0 = tick(P);
-  // spectrum bound: power iteration (under-estimates), padded by 25%
-  CK(gw::tc_power_lmax(eps, n, nc, 30, as<float>(P->ns_lam), P->stream));
-  std::vector<float> lam(nc);
-  CK(cudaMemcpyAsync(lam.data(), P->ns_lam.p, sizeof(float) * nc, cudaMemcpyDeviceToHost, P->stream));
-  CK(cudaStreamSynchronize(P->stream));
-  float lmax = 1.0f;
-  for (int b = 0; b < nc; ++b) {
-    lam[b] = std::max(1.0f, lam[b]) * 1.25f;
-    lmax = std::max(lmax, lam[b]);
+  // One spectrum bound and one iteration count for every frequency, so that every matrix goes through the
+  // same sequence of operations (errors then vary smoothly with xi, which the I-term derivative needs near
+  // xi = 0).  eps(i xi) <= eps(0) in the Loewner order, so lambda_max(eps(0)) bounds all of them; the first
+  // chunk holds xi = 0.  Power iteration under-estimates: pad by 25%.
+  if (g0 == 0 || P->ns_kmax == 0) {
+    CK(gw::tc_power_lmax(eps, n, nc, 30, as<float>(P->ns_lam), P->stream));
+    std::vector<float> lam(nc);
+    CK(cudaMemcpyAsync(lam.data(), P->ns_lam.p, sizeof(float) * nc, cudaMemcpyDeviceToHost, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+    float lmax = 1.0f;
+    for (int b = 0; b < nc; ++b) lmax = std::max(lmax, lam[b]);
+    P->ns_lam_global = lmax * 1.25f;
+    // iterate k has error rho0^(2^k), rho0 = (lmax - 1)/(lmax + 1): two-part iterations down to ~1e-5, then
+    // one three-part iteration (quadratic: to the FP32 floor)
+    const double rho0 = (P->ns_lam_global - 1.0) / (P->ns_lam_global + 1.0);
+    int k = 2;
+    if (rho0 > 0.0) k = std::max(2, (int)std::ceil(std::log2(11.5 / -std::log(rho0))) + 1);
+    P->ns_kmax = std::min(k, 24);
   }
-  CK(cudaMemcpyAsync(P->ns_lam.p, lam.data(), sizeof(float) * nc, cudaMemcpyHostToDevice, P->stream));
-  // iterate k has error rho0^(2^k), rho0 = (lmax - 1)/(lmax + 1): two-part iterations down to ~1e-5, then one
-  // three-part iteration (quadratic: to the FP32 floor)
-  const double rho0 = (lmax - 1.0) / (lmax + 1.0);
-  int kmax = 2;
-  if (rho0 > 0.0) kmax = std::max(2, (int)std::ceil(std::log2(11.5 / -std::log(rho0))) + 1);
-  kmax = std::min(kmax, 24);
+  const int kmax = P->ns_kmax;
+  {
+    std::vector<float> lam(nc, P->ns_lam_global);
+    CK(cudaMemcpyAsync(P->ns_lam.p, lam.data(), sizeof(float) * nc, cudaMemcpyHostToDevice, P->stream));
+  }
   CK(gw::tc_split_rows(eps, nc * n, n, n, const_cast<__nv_bfloat16*>(E.p[0]), const_cast<__nv_bfloat16*>(E.p[1]),
                        P->stream, const_cast<__nv_bfloat16*>(E.p[2])));
   CK(gw::tc_ns_init(eps, n, nc, as<float>(P->ns_lam), X, const_cast<__nv_bfloat16*>(Xs[0].p[0]),
@@ -333,11 +342,16 @@ gw_status screening_T(gw_plan* P, const T* B, const T* Bn) {
   TRY(ensure(P, P->ws_gout, sizeof(int) * n_g1));
   const int n_cta = gw::trsm_w_default_ctas();
   TRY(ensure(P, P->ws_scratch, sizeof(T) * gw::trsm_w_scratch_elems<T>(n, n_cta)));
+  // processing order: the static point xi = 0 first, then the grid ascending; gout maps position -> W column
   std::vector<int> gout(n_g1);
-  for (int g = 0; g < n_g1; ++g) gout[g] = g;
+  gout[0] = P->n_g;
+  for (int g = 0; g < P->n_g; ++g) gout[g + 1] = g;
   CK(cudaMemcpyAsync(P->ws_gout.p, gout.data(), sizeof(int) * n_g1, cudaMemcpyHostToDevice, P->stream));
-  std::vector<double> xi_all(P->h_xi);
-  xi_all.push_back(0.0);
+  std::vector<double> xi_all(n_g1);
+  for (int i = 0; i < n_g1; ++i) xi_all[i] = gout[i] < P->n_g ? P->h_xi[gout[i]] : 0.0;
+  TRY(ensure(P, P->ws_xi, sizeof(double) * n_g1));
+  CK(cudaMemcpyAsync(P->ws_xi.p, xi_all.data(), sizeof(double) * n_g1, cudaMemcpyHostToDevice, P->stream));
+  P->ns_kmax = 0;
   std::vector<int> info(chunk);
   double ms_pi = 0.0;
   for (int g0 = 0; g0 < n_g1; g0 += chunk) {
@@ -348,7 +362,7 @@ gw_status screening_T(gw_plan* P, const T* B, const T* Bn) {
       TRY(tc_weighted_syrk(P, kinds.data(), xi_all.data() + g0, nc, 1, 1, reinterpret_cast<float*>(P->ws_mat.p), 0));
     } else {
       const size_t t0 = tick(P);
-      LAUNCH(gw::launch_pi_syrk<T>(B, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, P->d_xi + g0, nc,
+      LAUNCH(gw::launch_pi_syrk<T>(B, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, as<double>(P->ws_xi) + g0, nc,
                                    as<T>(P->ws_mat), 1, P->stream));
       mark(P, 1, t0, (double)nc * n * n * P->n_ov);
     }
