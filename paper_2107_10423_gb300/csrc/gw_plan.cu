@@ -59,7 +59,7 @@ struct gw_plan {
   float ns_lam_global = 0.f;   // spectrum bound of eps(i xi) for every xi: lambda_max(eps(0)), padded
   int ns_kmax = 0;
   std::vector<DevBuf*> bufs;
-  DevBuf ws_mat, ws_info, ws_scratch, ws_gout, ws_xi, tc_Ahi, tc_Alo, tc_kind, tc_par, tc_err, tc_w, ns_E, ns_X, ns_Xa, ns_Xb, ns_T, ns_lam;
+  DevBuf ws_mat, ws_info, ws_scratch, ws_gout, ws_xi, tc_Ahi, tc_Alo, tc_kind, tc_par, tc_err, tc_w, ns_E, ns_X, ns_X2, ns_Xa, ns_Xb, ns_T, ns_lam;
   DevBuf mr_V, mr_U, mr_S, mr_vprev, mr_v, mr_d1, mr_d2, mr_x, mr_st, mr_rt, mr_rm, mr_xf, mr_wre, mr_wim,
       mr_dwre, mr_it, mr_res, mr_cnt, mr_Vhi, mr_Vlo, mr_Uhi, mr_Ulo;
   DevBuf sg_I, sg_dI, sg_R, sg_dR, sg_om, sg_start, sg_coef, sg_act, qp_st;
@@ -75,7 +75,7 @@ struct gw_plan {
   std::vector<Mark> marks;
 
   gw_plan() {
-    DevBuf* all[] = {&ws_mat, &ws_info, &ws_scratch, &ws_gout, &ws_xi, &tc_Ahi, &tc_Alo, &tc_kind, &tc_par, &tc_err, &tc_w, &ns_E, &ns_X, &ns_Xa, &ns_Xb, &ns_T, &ns_lam, &mr_V, &mr_U, &mr_S, &mr_vprev,
+    DevBuf* all[] = {&ws_mat, &ws_info, &ws_scratch, &ws_gout, &ws_xi, &tc_Ahi, &tc_Alo, &tc_kind, &tc_par, &tc_err, &tc_w, &ns_E, &ns_X, &ns_X2, &ns_Xa, &ns_Xb, &ns_T, &ns_lam, &mr_V, &mr_U, &mr_S, &mr_vprev,
                      &mr_v, &mr_d1, &mr_d2, &mr_x, &mr_st, &mr_rt, &mr_rm, &mr_xf, &mr_wre, &mr_wim,
                      &mr_dwre, &mr_it, &mr_res, &mr_cnt, &mr_Vhi, &mr_Vlo, &mr_Uhi, &mr_Ulo, &sg_I, &sg_dI, &sg_R, &sg_dR, &sg_om, &sg_start,
                      &sg_coef, &sg_act, &qp_st, &fb_A, &fb_y, &fb_piv, &fb_info, &fb_idx, &fb_y64, &fb_V64, &fb_U64, &fb_S64, &fb_x};
@@ -211,7 +211,7 @@ int tc_chunk(gw_plan* P, int want) {
 }
 
 // W table on the tensor cores (mixed precision) for nc frequency matrices eps_b = 1 - Pi_b held FP32 in ws_mat:
-// Newton-Schulz X <- 2X - X eps X from the closed-form first iterate 2a I - a^2 eps (a = 2/(1 + lambda_max)),
+// Newton-Schulz X <- 2X - (X eps) X from the closed-form first iterate 2a I - a^2 eps (a = 2/(1 + lambda_max)),
 // converging quadratically because the spectrum of eps lies in [1, lambda_max]; the last iterate is written as
 // eps^-1 - 1, and W[r][g] = b_r^T (eps_g^-1 - 1) b_r is reduced straight out of one more GEMM.
 gw_status ns_w_table(gw_plan* P, int g0, int nc) {
@@ -224,6 +224,7 @@ gw_status ns_w_table(gw_plan* P, int g0, int nc) {
   TRY(ensure(P, P->ns_Xb, 3 * sizeof(__nv_bfloat16) * sz));
   TRY(ensure(P, P->ns_T, 3 * sizeof(__nv_bfloat16) * sz));
   TRY(ensure(P, P->ns_X, sizeof(float) * mat * nc));
+  TRY(ensure(P, P->ns_X2, sizeof(float) * mat * nc));
   TRY(ensure(P, P->ns_lam, sizeof(float) * nc));
   TRY(ensure(P, P->tc_err, sizeof(int)));
   CK(cudaMemsetAsync(P->tc_err.p, 0, sizeof(int), P->stream));
@@ -265,9 +266,19 @@ gw_status ns_w_table(gw_plan* P, int g0, int nc) {
   CK(gw::tc_ns_init(eps, n, nc, as<float>(P->ns_lam), X, const_cast<__nv_bfloat16*>(Xs[0].p[0]),
                     const_cast<__nv_bfloat16*>(Xs[0].p[1]), P->stream, const_cast<__nv_bfloat16*>(Xs[0].p[2])));
   int cur = 0;
+  float* Xf[2] = {X, as<float>(P->ns_X2)};
+  int xf = 0;
   for (int k = 1; k < kmax; ++k) {
     const bool last = (k == kmax - 1);
     const int ns = last ? 3 : 2;
+    if (last) {
+      // the products below take X as its own transpose: make the iterate exactly symmetric before the
+      // high-precision step, so that its error F maps to -F eps F (quadratic) for any F
+      CK(gw::tc_sym_split(Xf[xf], n, nc, Xf[1 - xf], const_cast<__nv_bfloat16*>(Xs[cur].p[0]),
+                          const_cast<__nv_bfloat16*>(Xs[cur].p[1]), const_cast<__nv_bfloat16*>(Xs[cur].p[2]),
+                          P->stream));
+      xf = 1 - xf;
+    }
     gw::TcEpi et{};
     et.kind = gw::TC_EPI_AXPBY;
     et.gamma = 1.f;
@@ -277,16 +288,16 @@ gw_status ns_w_table(gw_plan* P, int g0, int nc) {
     et.olo2 = const_cast<__nv_bfloat16*>(T.p[2]);
     et.ldh = ldn;
     et.oh_bstride = (long)smat;
-    // T = eps X   (X symmetric, so X is its own K-major B operand)
-    CK(gw::tc_gemm_ex(E, nc, Xs[cur], 1, ns, n, n, n, 0, et, as<int>(P->tc_err), P->stream));
+    // S = X eps   (eps is symmetric, so it is its own K-major B operand)
+    CK(gw::tc_gemm_ex(Xs[cur], nc, E, 1, ns, n, n, n, 0, et, as<int>(P->tc_err), P->stream));
     gw::TcEpi ex{};
     ex.kind = gw::TC_EPI_AXPBY;
-    ex.xin = X;
+    ex.xin = Xf[xf];
     ex.x_bstride = (long)mat;
     ex.alpha = 2.f;
     ex.gamma = -1.f;
     ex.beta = last ? -1.f : 0.f;
-    ex.out = X;
+    ex.out = Xf[xf];
     ex.out_bstride = (long)mat;
     ex.ldo = n;
     ex.ohi = const_cast<__nv_bfloat16*>(Xs[1 - cur].p[0]);
@@ -294,15 +305,15 @@ gw_status ns_w_table(gw_plan* P, int g0, int nc) {
     ex.olo2 = const_cast<__nv_bfloat16*>(Xs[1 - cur].p[2]);
     ex.ldh = ldn;
     ex.oh_bstride = (long)smat;
-    // X <- 2X - X T   (T = eps X is symmetric); the last iterate is written as X - I
-    CK(gw::tc_gemm_ex(Xs[cur], nc, T, 1, ns, n, n, n, 0, ex, as<int>(P->tc_err), P->stream));
+    // X <- 2X - S X = 2X - X eps X  (X symmetric: X is its own transpose as the B operand); the last iterate is
+    // written as X - I
+    CK(gw::tc_gemm_ex(T, nc, Xs[cur], 1, ns, n, n, n, 0, ex, as<int>(P->tc_err), P->stream));
     cur = 1 - cur;
     P->stats.n_kernel_launches += 2;
   }
   mark(P, 2, t0, 2.0 * 2.0 * (double)(kmax - 1) * nc * (double)n * n * n);
-  // W[r][g0 + b] = b_r^T (eps^-1 - 1) b_r, reduced in the epilogue (accumulates into zeroed entries)
+  // W[r][gout[g0 + b]] = b_r^T (eps^-1 - 1) b_r, reduced in the epilogue into the table zeroed before the chunks
   const size_t t1 = tick(P);
-  CK(cudaMemset2DAsync(P->d_W + g0, sizeof(double) * n_g1, 0, sizeof(double) * nc, R, P->stream));
   gw::TcEpi ew{};
   ew.kind = gw::TC_EPI_WRED;
   ew.W = P->d_W;
@@ -352,6 +363,7 @@ gw_status screening_T(gw_plan* P, const T* B, const T* Bn) {
   TRY(ensure(P, P->ws_xi, sizeof(double) * n_g1));
   CK(cudaMemcpyAsync(P->ws_xi.p, xi_all.data(), sizeof(double) * n_g1, cudaMemcpyHostToDevice, P->stream));
   P->ns_kmax = 0;
+  if (use_tc) CK(cudaMemsetAsync(P->d_W, 0, sizeof(double) * (size_t)R * n_g1, P->stream));   // W is accumulated
   std::vector<int> info(chunk);
   double ms_pi = 0.0;
   for (int g0 = 0; g0 < n_g1; g0 += chunk) {

@@ -72,6 +72,9 @@ cudaError_t tc_power_lmax(const float* A, int n, int batch, int iters, float* la
 // rows [b][n][tc_ld(n)].
 cudaError_t tc_ns_init(const float* A, int n, int batch, const float* lam, float* X, __nv_bfloat16* hi,
                        __nv_bfloat16* lo, cudaStream_t s, __nv_bfloat16* lo2 = nullptr);
+// Y_b = (X_b + X_b^T)/2 for n x n FP32 matrices (out of place), with its split parts (rows of tc_ld(n)).
+cudaError_t tc_sym_split(const float* X, int n, int batch, float* Y, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                         __nv_bfloat16* lo2, cudaStream_t s);
 // out[k][m] = B[m][k] split into BF16 hi/lo with rows of tc_ld(M) elements (B FP32 [M][K]).
 cudaError_t tc_transpose_split(const float* B, int M, int K, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s);
 }  // namespace gw

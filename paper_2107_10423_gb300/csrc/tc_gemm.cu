@@ -626,6 +626,29 @@ cudaError_t tc_ns_init(const float* A, int n, int batch, const float* lam, float
   return cudaGetLastError();
 }
 
+// Y_b = (X_b + X_b^T)/2 (FP32, out of place) and its split parts; one thread per element.
+__global__ void sym_split_kernel(const float* __restrict__ X, int n, float* __restrict__ Y, __nv_bfloat16* __restrict__ hi,
+                                 __nv_bfloat16* __restrict__ lo, __nv_bfloat16* __restrict__ lo2, int ldh) {
+  const int r = blockIdx.y, b = blockIdx.z;
+  const float* Xb = X + (long)b * n * n;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ldh; c += gridDim.x * blockDim.x) {
+    float v = 0.f;
+    if (c < n) {
+      v = 0.5f * (Xb[(long)r * n + c] + Xb[(long)c * n + r]);
+      Y[((long)b * n + r) * n + c] = v;
+    }
+    split_store(v, hi, lo, ((long)b * n + r) * ldh + c, lo2);
+  }
+}
+
+cudaError_t tc_sym_split(const float* X, int n, int batch, float* Y, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                         __nv_bfloat16* lo2, cudaStream_t s) {
+  const int ldh = tc_ld(n);
+  dim3 grid((ldh + 255) / 256, n, batch);
+  if (batch > 0) sym_split_kernel<<<grid, 256, 0, s>>>(X, n, Y, hi, lo, lo2, ldh);
+  return cudaGetLastError();
+}
+
 cudaError_t tc_transpose_split(const float* B, int M, int K, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s) {
   const int ld = tc_ld(M);
   dim3 grid((K + 31) / 32, (ld + 31) / 32);
