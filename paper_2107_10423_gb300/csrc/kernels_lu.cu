@@ -9,7 +9,8 @@ namespace {
 
 constexpr int LU_NB = 32;        // panel width
 constexpr int LU_T = 512;        // threads per CTA
-constexpr int TT = 64;           // trailing-update tile
+constexpr int TTM = 64;          // trailing-update tile rows (16 thread rows x 4)
+constexpr int TTN = 128;         // trailing-update tile columns (32 thread columns x 4)
 
 template <typename T>
 struct cplx {
@@ -50,10 +51,10 @@ template <typename T>
 __global__ void __launch_bounds__(LU_T) zlu_kernel(T* Ar_base, T* Ai_base, long stride, int n, int* piv_base,
                                                    int* info) {
   extern __shared__ __align__(16) unsigned char sm[];
-  T* Lr = reinterpret_cast<T*>(sm);               // [TT][LU_NB+1]
-  T* Li = Lr + TT * (LU_NB + 1);
-  T* Ur = Li + TT * (LU_NB + 1);                  // [LU_NB][TT+1]
-  T* Ui = Ur + LU_NB * (TT + 1);
+  T* Lr = reinterpret_cast<T*>(sm);               // [TTM][LU_NB+1]
+  T* Li = Lr + TTM * (LU_NB + 1);
+  T* Ur = Li + TTM * (LU_NB + 1);                 // [LU_NB][TTN+1]
+  T* Ui = Ur + LU_NB * (TTN + 1);
   __shared__ double sv[32];
   __shared__ int si[32];
   T* Ar = Ar_base + (long)blockIdx.x * stride;
@@ -110,42 +111,61 @@ __global__ void __launch_bounds__(LU_T) zlu_kernel(T* Ar_base, T* Ai_base, long 
     }
     __threadfence_block();
     __syncthreads();
-    // ---- trailing update A22 -= L21 U12 in TT x TT tiles
-    const int nt = (n - k1 + TT - 1) / TT;
-    for (int t = 0; t < nt * nt; ++t) {
-      const int r0 = k1 + (t / nt) * TT, c0 = k1 + (t % nt) * TT;
-      for (int idx = threadIdx.x; idx < TT * LU_NB; idx += blockDim.x) {
+    // ---- trailing update A22 -= L21 U12 in TTM x TTN tiles, 4 x 4 complex outputs per thread
+    const int ntm = (n - k1 + TTM - 1) / TTM, ntn = (n - k1 + TTN - 1) / TTN;
+    const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
+    for (int t = 0; t < ntm * ntn; ++t) {
+      const int r0 = k1 + (t / ntn) * TTM, c0 = k1 + (t % ntn) * TTN;
+      for (int idx = threadIdx.x; idx < TTM * LU_NB; idx += blockDim.x) {
         const int rr = idx / LU_NB, q = idx % LU_NB;
         const bool okr = (r0 + rr < n) && (q < nb);
         Lr[rr * (LU_NB + 1) + q] = okr ? Ar[(long)(r0 + rr) * n + k0 + q] : T(0);
         Li[rr * (LU_NB + 1) + q] = okr ? Ai[(long)(r0 + rr) * n + k0 + q] : T(0);
-        const int q2 = idx / TT, cc = idx % TT;
-        const bool okc = (c0 + cc < n) && (q2 < nb);
-        Ur[q2 * (TT + 1) + cc] = okc ? Ar[(long)(k0 + q2) * n + c0 + cc] : T(0);
-        Ui[q2 * (TT + 1) + cc] = okc ? Ai[(long)(k0 + q2) * n + c0 + cc] : T(0);
+      }
+      for (int idx = threadIdx.x; idx < LU_NB * TTN; idx += blockDim.x) {
+        const int q = idx / TTN, cc = idx % TTN;
+        const bool okc = (c0 + cc < n) && (q < nb);
+        Ur[q * (TTN + 1) + cc] = okc ? Ar[(long)(k0 + q) * n + c0 + cc] : T(0);
+        Ui[q * (TTN + 1) + cc] = okc ? Ai[(long)(k0 + q) * n + c0 + cc] : T(0);
       }
       __syncthreads();
-      const int rr = threadIdx.x >> 3, cb = threadIdx.x & 7;    // 64 rows x (8 cols per thread)
-      T accr[8], acci[8];
+      T accr[4][4], acci[4][4];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) accr[u] = acci[u] = T(0);
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) accr[i][j] = acci[i][j] = T(0);
       for (int q = 0; q < nb; ++q) {
-        const T lr = Lr[rr * (LU_NB + 1) + q], li = Li[rr * (LU_NB + 1) + q];
+        T lr[4], li[4], ur[4], ui[4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const T ur = Ur[q * (TT + 1) + cb + 8 * u], ui = Ui[q * (TT + 1) + cb + 8 * u];
-          accr[u] += lr * ur - li * ui;
-          acci[u] += lr * ui + li * ur;
+        for (int i = 0; i < 4; ++i) {
+          lr[i] = Lr[(ty + 16 * i) * (LU_NB + 1) + q];
+          li[i] = Li[(ty + 16 * i) * (LU_NB + 1) + q];
         }
-      }
-      const int gi = r0 + rr;
-      if (gi < n) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int gj = c0 + cb + 8 * u;
+        for (int j = 0; j < 4; ++j) {
+          ur[j] = Ur[q * (TTN + 1) + tx + 32 * j];
+          ui[j] = Ui[q * (TTN + 1) + tx + 32 * j];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            accr[i][j] = fma(lr[i], ur[j], accr[i][j]);
+            accr[i][j] = fma(-li[i], ui[j], accr[i][j]);
+            acci[i][j] = fma(lr[i], ui[j], acci[i][j]);
+            acci[i][j] = fma(li[i], ur[j], acci[i][j]);
+          }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int gi = r0 + ty + 16 * i;
+        if (gi >= n) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int gj = c0 + tx + 32 * j;
           if (gj < n) {
-            Ar[(long)gi * n + gj] -= accr[u];
-            Ai[(long)gi * n + gj] -= acci[u];
+            Ar[(long)gi * n + gj] -= accr[i][j];
+            Ai[(long)gi * n + gj] -= acci[i][j];
           }
         }
       }
@@ -275,7 +295,7 @@ __global__ void __launch_bounds__(LU_T) zlu_solve_kernel(const T* Ar_base, const
 
 template <typename T>
 void launch_zlu(T* Ar, T* Ai, long stride, int n, int batch, int* piv, int* info, cudaStream_t s) {
-  const size_t smem = sizeof(T) * (2 * TT * (LU_NB + 1) + 2 * LU_NB * (TT + 1));
+  const size_t smem = sizeof(T) * (2 * TTM * (LU_NB + 1) + 2 * LU_NB * (TTN + 1));
   cudaFuncSetAttribute(zlu_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (batch > 0) zlu_kernel<T><<<batch, LU_T, smem, s>>>(Ar, Ai, stride, n, piv, info);
 }
