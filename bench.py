@@ -164,6 +164,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-jobs", type=int, default=32)
+    ap.add_argument("--serve-nmax", type=int, default=16)
     ap.add_argument("--workload", default="water16", choices=["water16", "water8"],
                     help="water16: the (H2O)_16-shaped job (default); water8: a smaller case for profiler captures")
     args = ap.parse_args()
@@ -306,6 +309,29 @@ def main():
                            "states": [int(v) for v in sub.targets], "abs_err_meV": [round(float(v) / MEV, 4) for v in err],
                            "max_abs_err_meV": round(float(err.max()) / MEV, 4), "within_5meV": bool(err.max() < 5 * MEV),
                            "fp64_seconds": round(time.perf_counter() - t0, 2)}
+
+    if rank == 0 and not args.no_serving:
+        # continuous batching on a bounded prefix of the serving stream (Poisson arrivals at 4 jobs/s,
+        # (H2O)_n with n log-uniform in [1, 64]; 30% O1s core jobs), same arrival times, versus the same jobs
+        # run one after another on the same GPU
+        from paper_2107_10423_gb300 import serve
+        stream = synth.serving_stream()
+        jobs = serve.make_jobs(stream, n_max=args.serve_nmax, limit=args.serve_jobs)
+        srv = serve.Server(max_slots=4, hbm_budget=120 << 30)
+        t0 = time.perf_counter()
+        done = srv.run(jobs)
+        span = time.perf_counter() - t0
+        sv = serve.summarize(done, makespan=span)
+        serial_jobs = serve.make_jobs(stream, n_max=args.serve_nmax, limit=args.serve_jobs)
+        t0 = time.perf_counter()
+        for j in serial_jobs:
+            j.result = serve.run_job(j)
+        serial_s = time.perf_counter() - t0
+        out["serving"] = {"sample": f"first {len(jobs)} jobs with n <= {args.serve_nmax} of the 256-job stream "
+                                    f"(arrivals over {jobs[-1].arrival:.1f} s), mixed precision, linearised QP",
+                          "slots": 4, **{k: (round(v, 4) if isinstance(v, float) else v) for k, v in sv.items()},
+                          "serial_jobs_per_s": round(len(serial_jobs) / serial_s, 4),
+                          "serial_seconds": round(serial_s, 2)}
 
     if rank == 0 and not args.no_cpu_baseline:
         job, desc = oracle_sample(s, B_h, Bn_h, count_residues(s))
