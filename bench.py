@@ -223,14 +223,9 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    from paper_2107_10423_gb300 import replicas
+    ms, n_states, value = replicas.aggregate(e0.elapsed_time(e1), len(s.targets) * args.steps, device=dev)
     st1 = plan.stats()
-    n_states = len(s.targets) * args.steps * world
-    value = n_states / (ms / 1e3)
 
     # per-kernel-class rates over the timed region
     peaks, peak_src = _peaks()

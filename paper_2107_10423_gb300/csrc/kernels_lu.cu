@@ -57,6 +57,7 @@ __global__ void __launch_bounds__(LU_T) zlu_kernel(T* Ar_base, T* Ai_base, long 
   T* Ui = Ur + LU_NB * (TTN + 1);
   __shared__ double sv[32];
   __shared__ int si[32];
+  __shared__ T prow_r[LU_NB], prow_i[LU_NB];
   T* Ar = Ar_base + (long)blockIdx.x * stride;
   T* Ai = Ai_base + (long)blockIdx.x * stride;
   int* piv = piv_base + (long)blockIdx.x * n;
@@ -78,18 +79,25 @@ __global__ void __launch_bounds__(LU_T) zlu_kernel(T* Ar_base, T* Ai_base, long 
       __syncthreads();
       const cplx<T> d = {Ar[(long)c * n + c], Ai[(long)c * n + c]};
       const bool dz = (d.r == T(0) && d.i == T(0));
-      // multipliers and the rank-1 update of the rest of the panel, one warp per row
-      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-      for (int i = c + 1 + wid; i < n; i += nw) {
+      // pivot-row segment of the panel in shared memory, then one thread per row below: multiplier and the
+      // rank-1 update of the rest of the panel (independent rows, so the loads overlap)
+      for (int j = c + 1 + threadIdx.x; j < k1; j += blockDim.x) {
+        prow_r[j - k0] = Ar[(long)c * n + j];
+        prow_i[j - k0] = Ai[(long)c * n + j];
+      }
+      __syncthreads();
+      for (int i = c + 1 + threadIdx.x; i < n; i += blockDim.x) {
         cplx<T> l = {Ar[(long)i * n + c], Ai[(long)i * n + c]};
         l = dz ? cplx<T>{T(0), T(0)} : cdiv(l, d);
-        for (int j = c + 1 + lane; j < k1; j += 32) {
-          const T ur = Ar[(long)c * n + j], ui = Ai[(long)c * n + j];
-          Ar[(long)i * n + j] -= l.r * ur - l.i * ui;
-          Ai[(long)i * n + j] -= l.r * ui + l.i * ur;
+        T* ri = Ar + (long)i * n;
+        T* ii = Ai + (long)i * n;
+        for (int j = c + 1; j < k1; ++j) {
+          const T ur = prow_r[j - k0], ui = prow_i[j - k0];
+          ri[j] -= l.r * ur - l.i * ui;
+          ii[j] -= l.r * ui + l.i * ur;
         }
-        __syncwarp();
-        if (lane == 0) { Ar[(long)i * n + c] = l.r; Ai[(long)i * n + c] = l.i; }
+        ri[c] = l.r;
+        ii[c] = l.i;
       }
       __threadfence_block();
       __syncthreads();
