@@ -312,21 +312,24 @@ def main():
         from paper_2107_10423_gb300 import serve
         stream = synth.serving_stream()
         jobs = serve.make_jobs(stream, n_max=args.serve_nmax, limit=args.serve_jobs)
-        srv = serve.Server(max_slots=4, hbm_budget=120 << 30)
-        t0 = time.perf_counter()
-        done = srv.run(jobs)
-        span = time.perf_counter() - t0
-        sv = serve.summarize(done, makespan=span)
-        serial_jobs = serve.make_jobs(stream, n_max=args.serve_nmax, limit=args.serve_jobs)
-        t0 = time.perf_counter()
-        for j in serial_jobs:
-            j.result = serve.run_job(j)
-        serial_s = time.perf_counter() - t0
+        def served(slots, at_zero):
+            js = serve.make_jobs(stream, n_max=args.serve_nmax, limit=args.serve_jobs)
+            if at_zero:
+                for j in js:
+                    j.arrival = 0.0
+            t0 = time.perf_counter()
+            done = serve.Server(max_slots=slots, hbm_budget=120 << 30).run(js)
+            return serve.summarize(done, makespan=time.perf_counter() - t0)
+
+        rnd = lambda d: {k: (round(v, 4) if isinstance(v, float) else v) for k, v in d.items()}
+        live4, live1 = served(4, False), served(1, False)
+        cap4, cap1 = served(4, True), served(1, True)
         out["serving"] = {"sample": f"first {len(jobs)} jobs with n <= {args.serve_nmax} of the 256-job stream "
-                                    f"(arrivals over {jobs[-1].arrival:.1f} s), mixed precision, linearised QP",
-                          "slots": 4, **{k: (round(v, 4) if isinstance(v, float) else v) for k, v in sv.items()},
-                          "serial_jobs_per_s": round(len(serial_jobs) / serial_s, 4),
-                          "serial_seconds": round(serial_s, 2)}
+                                    f"(Poisson arrivals over {jobs[-1].arrival:.1f} s), mixed precision, linearised QP",
+                          "arrivals_4_slots": rnd(live4), "arrivals_1_slot": rnd(live1),
+                          "capacity_jobs_per_s_4_slots": round(cap4["jobs_per_s"], 3),
+                          "capacity_jobs_per_s_1_slot": round(cap1["jobs_per_s"], 3),
+                          "capacity_p99_latency_s_4_slots": round(cap4["p99_latency_s"], 3)}
 
     if rank == 0 and not args.no_cpu_baseline:
         job, desc = oracle_sample(s, B_h, Bn_h, count_residues(s))
