@@ -7,7 +7,7 @@
 namespace gw {
 namespace {
 
-constexpr int LU_NB = 32;        // panel width
+constexpr int LU_NB = 64;        // panel width (the trailing matrix is read and written once per panel)
 constexpr int LU_T = 512;        // threads per CTA
 constexpr int TTM = 64;          // trailing-update tile rows (16 thread rows x 4)
 constexpr int TTN = 128;         // trailing-update tile columns (32 thread columns x 4)
@@ -137,11 +137,19 @@ __global__ void __launch_bounds__(LU_T) zlu_kernel(T* Ar_base, T* Ai_base, long 
         Ui[q * (TTN + 1) + cc] = okc ? Ai[(long)(k0 + q) * n + c0 + cc] : T(0);
       }
       __syncthreads();
+      // this thread's 4 x 4 outputs are loaded before the K loop so that their latency overlaps the FMAs
       T accr[4][4], acci[4][4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < 4; ++i) {
+        const int gi = r0 + ty + 16 * i;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) accr[i][j] = acci[i][j] = T(0);
+        for (int j = 0; j < 4; ++j) {
+          const int gj = c0 + tx + 32 * j;
+          const bool in = gi < n && gj < n;
+          accr[i][j] = in ? Ar[(long)gi * n + gj] : T(0);
+          acci[i][j] = in ? Ai[(long)gi * n + gj] : T(0);
+        }
+      }
       for (int q = 0; q < nb; ++q) {
         T lr[4], li[4], ur[4], ui[4];
 #pragma unroll
@@ -158,10 +166,10 @@ __global__ void __launch_bounds__(LU_T) zlu_kernel(T* Ar_base, T* Ai_base, long 
         for (int i = 0; i < 4; ++i)
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            accr[i][j] = fma(lr[i], ur[j], accr[i][j]);
-            accr[i][j] = fma(-li[i], ui[j], accr[i][j]);
-            acci[i][j] = fma(lr[i], ui[j], acci[i][j]);
-            acci[i][j] = fma(li[i], ur[j], acci[i][j]);
+            accr[i][j] = fma(-lr[i], ur[j], accr[i][j]);
+            accr[i][j] = fma(li[i], ui[j], accr[i][j]);
+            acci[i][j] = fma(-lr[i], ui[j], acci[i][j]);
+            acci[i][j] = fma(-li[i], ur[j], acci[i][j]);
           }
       }
 #pragma unroll
@@ -172,8 +180,8 @@ __global__ void __launch_bounds__(LU_T) zlu_kernel(T* Ar_base, T* Ai_base, long 
         for (int j = 0; j < 4; ++j) {
           const int gj = c0 + tx + 32 * j;
           if (gj < n) {
-            Ar[(long)gi * n + gj] -= accr[i][j];
-            Ai[(long)gi * n + gj] -= acci[i][j];
+            Ar[(long)gi * n + gj] = accr[i][j];
+            Ai[(long)gi * n + gj] = acci[i][j];
           }
         }
       }
