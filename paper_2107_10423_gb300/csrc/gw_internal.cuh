@@ -93,12 +93,12 @@ template <typename T>
 void launch_fallback_finish(const double* B_nm, int n_bas, int n_aux, const int* rt, const int* rm, const int* idx,
                             int nf, const T* y, double* w_re, double* w_im, double* resnorm, T* V, cudaStream_t s);
 
-// FP64 iterative refinement of fallback solves (k < nf; y32 planes [nf][2][n], y64 the same in FP64):
-//   stage 0: y64 = y32;            V64 rows (2k, 2k+1) = (Re y, -Im y)
-//   stage 1: y32 = [b; 0] - S64    (residual of the FP64 operator, next right-hand side)
-//   stage 2: y64 += y32;           V64 rows = (Re y, -Im y)
+// Iterative refinement of fallback solves (k < nf; y32 planes [nf][2][n], y64 the same in FP64):
+//   stage 0: y64 = y32;            V32 rows (2k, 2k+1) = (Re y, -Im y)
+//   stage 1: y32 = [b; 0] - S32    (residual of the three-part operator, next right-hand side)
+//   stage 2: y64 += y32;           V32 rows = (Re y, -Im y)
 void launch_refine(int stage, const double* B_nm, int n_bas, int n_aux, const int* rt, const int* rm, const int* idx,
-                   int nf, float* y32, double* y64, double* V64, const double* S64, cudaStream_t s);
+                   int nf, float* y32, double* y64, float* V32, const float* S32, cudaStream_t s);
 // W = b^T y - b^T b from FP64 solutions; V (operator precision) rows of slot idx[k] = (Re y, -Im y); resnorm 0.
 template <typename T>
 void launch_fallback_finish64(const double* B_nm, int n_bas, int n_aux, const int* rt, const int* rm, const int* idx,

@@ -50,6 +50,8 @@ struct gw_plan {
   __nv_bfloat16* d_Blo = nullptr;
   __nv_bfloat16* d_BThi = nullptr;  // mixed: BF16 hi/lo split of B_ia^T, [n_ov][tc_ld(n_aux)]
   __nv_bfloat16* d_BTlo = nullptr;
+  __nv_bfloat16* d_Blo2 = nullptr;  // mixed: third split parts of B_ia and B_ia^T (refinement operator)
+  __nv_bfloat16* d_BTlo2 = nullptr;
   double* d_D = nullptr;            // pair energies D_ia [n_ov]
   __nv_bfloat16* d_Bnhi = nullptr;  // mixed: BF16 hi/lo split of the B_nm rows, [n_t*n_bas][tc_ld(n_aux)]
   __nv_bfloat16* d_Bnlo = nullptr;
@@ -63,7 +65,7 @@ struct gw_plan {
   DevBuf mr_V, mr_U, mr_S, mr_vprev, mr_v, mr_d1, mr_d2, mr_x, mr_st, mr_rt, mr_rm, mr_xf, mr_wre, mr_wim,
       mr_dwre, mr_it, mr_res, mr_cnt, mr_Vhi, mr_Vlo, mr_Uhi, mr_Ulo;
   DevBuf sg_I, sg_dI, sg_R, sg_dR, sg_om, sg_start, sg_coef, sg_act, qp_st;
-  DevBuf fb_A, fb_y, fb_piv, fb_info, fb_idx, fb_y64, fb_V64, fb_U64, fb_S64, fb_x;
+  DevBuf fb_A, fb_y, fb_piv, fb_info, fb_idx, fb_y64, fb_V32, fb_S32, fb_Vp, fb_Up, fb_x;
   int* h_cnt = nullptr;       // pinned
   std::string err;
   gw_stats stats{};
@@ -78,7 +80,7 @@ struct gw_plan {
     DevBuf* all[] = {&ws_mat, &ws_info, &ws_scratch, &ws_gout, &ws_xi, &tc_Ahi, &tc_Alo, &tc_kind, &tc_par, &tc_err, &tc_w, &ns_E, &ns_X, &ns_X2, &ns_Xa, &ns_Xb, &ns_T, &ns_lam, &mr_V, &mr_U, &mr_S, &mr_vprev,
                      &mr_v, &mr_d1, &mr_d2, &mr_x, &mr_st, &mr_rt, &mr_rm, &mr_xf, &mr_wre, &mr_wim,
                      &mr_dwre, &mr_it, &mr_res, &mr_cnt, &mr_Vhi, &mr_Vlo, &mr_Uhi, &mr_Ulo, &sg_I, &sg_dI, &sg_R, &sg_dR, &sg_om, &sg_start,
-                     &sg_coef, &sg_act, &qp_st, &fb_A, &fb_y, &fb_piv, &fb_info, &fb_idx, &fb_y64, &fb_V64, &fb_U64, &fb_S64, &fb_x};
+                     &sg_coef, &sg_act, &qp_st, &fb_A, &fb_y, &fb_piv, &fb_info, &fb_idx, &fb_y64, &fb_V32, &fb_S32, &fb_Vp, &fb_Up, &fb_x};
     bufs.assign(all, all + sizeof(all) / sizeof(all[0]));
   }
 };
@@ -425,7 +427,10 @@ gw_status ensure_screening(gw_plan* P) {
   return GW_OK;
 }
 
-// Refinement steps of the mixed-precision dense solves (FP64 residual, FP32 LU correction).
+gw_status tc_operator3(gw_plan* P, int nf, const double* xf, const float* V32, float* S32);
+
+// Refinement steps of the mixed-precision dense solves (three-part tensor-core residual, FP32 LU correction,
+// solution accumulated in FP64).
 constexpr int kRefineSteps = 1;
 
 // Dense solves for the MINRES batch slots in `need` (Sec. 3.3: build the dielectric matrix and factorise).
@@ -449,9 +454,11 @@ gw_status dense_fallback(gw_plan* P, const std::vector<int>& need, const int* rt
   TRY(ensure(P, P->fb_idx, sizeof(int) * nneed));
   if (sizeof(T) == 4) {
     TRY(ensure(P, P->fb_y64, sizeof(double) * 2 * (size_t)n * fb));
-    TRY(ensure(P, P->fb_V64, sizeof(double) * 2 * (size_t)n * fb));
-    TRY(ensure(P, P->fb_S64, sizeof(double) * 2 * (size_t)n * fb));
-    TRY(ensure(P, P->fb_U64, sizeof(double) * 2 * (size_t)P->n_ov * fb));
+    TRY(ensure(P, P->fb_V32, sizeof(float) * 2 * (size_t)n * fb));
+    TRY(ensure(P, P->fb_S32, sizeof(float) * 2 * (size_t)n * fb));
+    TRY(ensure(P, P->fb_Vp, 3 * sizeof(__nv_bfloat16) * 2 * (size_t)gw::tc_ld(n) * fb));
+    TRY(ensure(P, P->fb_Up, 3 * sizeof(__nv_bfloat16) * 2 * (size_t)gw::tc_ld(P->n_ov) * fb));
+    TRY(ensure(P, P->tc_err, sizeof(int)));
     TRY(ensure(P, P->fb_x, sizeof(double) * fb));
   }
   CK(cudaMemcpyAsync(P->fb_idx.p, need.data(), sizeof(int) * nneed, cudaMemcpyHostToDevice, P->stream));
@@ -504,21 +511,17 @@ gw_status dense_fallback(gw_plan* P, const std::vector<int>& need, const int* rt
       std::vector<double> xk(hx.begin() + k0, hx.begin() + k0 + nf);
       CK(cudaMemcpyAsync(P->fb_x.p, xk.data(), sizeof(double) * nf, cudaMemcpyHostToDevice, P->stream));
       LAUNCH(gw::launch_refine(0, P->d_B_nm, P->n_bas, n, rt, rm, idx, nf, y32, as<double>(P->fb_y64),
-                               as<double>(P->fb_V64), nullptr, P->stream));
+                               as<float>(P->fb_V32), nullptr, P->stream));
       for (int r = 0; r < kRefineSteps; ++r) {
         const size_t tr = tick(P);
-        LAUNCH(gw::launch_op_gemm1<double>(as<double>(P->fb_V64), P->d_B_ia, P->d_eps, P->cfg.n_occ, P->cfg.n_virt,
-                                           n, as<double>(P->fb_x), P->cfg.eta, nf, as<double>(P->fb_U64), 0,
-                                           P->stream));
-        LAUNCH(gw::launch_op_gemm2<double>(as<double>(P->fb_U64), P->d_B_ia, n, P->n_ov, nf, as<double>(P->fb_V64),
-                                           as<double>(P->fb_S64), 1, P->stream));
+        TRY(tc_operator3(P, nf, as<double>(P->fb_x), as<float>(P->fb_V32), as<float>(P->fb_S32)));
         mark(P, 8, tr, 2.0 * 2.0 * (2.0 * nf) * n * (double)P->n_ov);
         LAUNCH(gw::launch_refine(1, P->d_B_nm, P->n_bas, n, rt, rm, idx, nf, y32, as<double>(P->fb_y64),
-                                 as<double>(P->fb_V64), as<double>(P->fb_S64), P->stream));
+                                 as<float>(P->fb_V32), as<float>(P->fb_S32), P->stream));
         LAUNCH(gw::launch_zlu_solve<T>(A, A + mat, (long)(2 * mat), n, nf, as<int>(P->fb_piv), as<T>(P->fb_y),
                                        as<T>(P->fb_y) + n, 2L * n, P->stream));
         LAUNCH(gw::launch_refine(2, P->d_B_nm, P->n_bas, n, rt, rm, idx, nf, y32, as<double>(P->fb_y64),
-                                 as<double>(P->fb_V64), nullptr, P->stream));
+                                 as<float>(P->fb_V32), nullptr, P->stream));
       }
       LAUNCH(gw::launch_fallback_finish64<T>(P->d_B_nm, P->n_bas, n, rt, rm, idx, nf, as<double>(P->fb_y64), w_re,
                                              w_im, resnorm, as<T>(P->mr_V), P->stream));
@@ -564,6 +567,44 @@ gw_status tc_operator(gw_plan* P, int nr, const double* xf, const float* V32, fl
   CK(gw::tc_gemm_ex(Uop, 1, Bop, 0, 2, 2 * nr, n, n_ov, 0, e2, as<int>(P->tc_err), P->stream));
   P->stats.n_kernel_launches += 3;
   (void)ldn;
+  return GW_OK;
+}
+
+// Three-part (about FP32-accurate) residue operator for the refinement of dense fallback solves: the embedding
+// output S32 = [Re; Im]((1 - Pi(x)) z) for nf right-hand sides z held as (u, v) rows in V32.
+gw_status tc_operator3(gw_plan* P, int nf, const double* xf, const float* V32, float* S32) {
+  const int n = P->cfg.n_aux, n_ov = P->n_ov;
+  const size_t sv = 2 * (size_t)nf * gw::tc_ld(n), su = 2 * (size_t)nf * gw::tc_ld(n_ov);
+  __nv_bfloat16* vp = as<__nv_bfloat16>(P->fb_Vp);
+  __nv_bfloat16* up = as<__nv_bfloat16>(P->fb_Up);
+  CK(cudaMemsetAsync(P->tc_err.p, 0, sizeof(int), P->stream));
+  CK(gw::tc_split_rows(V32, 2 * nf, n, n, vp, vp + sv, P->stream, vp + 2 * sv));
+  gw::TcEpi e1{};
+  e1.kind = gw::TC_EPI_CPAIR;
+  e1.Dk = P->d_D;
+  e1.x = xf;
+  e1.eta = (float)P->cfg.eta;
+  e1.ohi = up;
+  e1.olo = up + su;
+  e1.olo2 = up + 2 * su;
+  e1.ldh = gw::tc_ld(n_ov);
+  const gw::TcOperand Vop{{vp, vp + sv, vp + 2 * sv}};
+  const gw::TcOperand BT{{P->d_BThi, P->d_BTlo, P->d_BTlo2}};
+  CK(gw::tc_gemm_ex(Vop, 1, BT, 0, 3, 2 * nf, n_ov, n, 0, e1, as<int>(P->tc_err), P->stream));
+  gw::TcEpi e2{};
+  e2.kind = gw::TC_EPI_EMBED;
+  e2.out = S32;
+  e2.ldo = n;
+  e2.vin = V32;
+  e2.ldv = n;
+  const gw::TcOperand Uop{{up, up + su, up + 2 * su}};
+  const gw::TcOperand Bop{{P->d_Bhi, P->d_Blo, P->d_Blo2}};
+  CK(gw::tc_gemm_ex(Uop, 1, Bop, 0, 3, 2 * nf, n, n_ov, 0, e2, as<int>(P->tc_err), P->stream));
+  P->stats.n_kernel_launches += 3;
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, P->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+  CK(cudaStreamSynchronize(P->stream));
+  if (herr != 0) return fail(P, GW_ERR_TIMEOUT, "tensor-core refinement operator: bounded wait ran out (code %d)", herr);
   return GW_OK;
 }
 
@@ -822,6 +863,8 @@ static void free_plan(gw_plan* P) {
   if (P->d_Blo) cudaFree(P->d_Blo);
   if (P->d_BThi) cudaFree(P->d_BThi);
   if (P->d_BTlo) cudaFree(P->d_BTlo);
+  if (P->d_Blo2) cudaFree(P->d_Blo2);
+  if (P->d_BTlo2) cudaFree(P->d_BTlo2);
   if (P->d_D) cudaFree(P->d_D);
   if (P->d_Bnhi) cudaFree(P->d_Bnhi);
   if (P->d_Bnlo) cudaFree(P->d_Bnlo);
@@ -898,18 +941,8 @@ static gw_status plan_create_impl(gw_plan* P, const gw_config* cfg, const double
     const size_t nsplit = (size_t)n * gw::tc_ld(P->n_ov);
     CK(cudaMalloc(&P->d_Bhi, sizeof(__nv_bfloat16) * nsplit));
     CK(cudaMalloc(&P->d_Blo, sizeof(__nv_bfloat16) * nsplit));
-    int* dk = nullptr;
-    double* dp = nullptr;
-    CK(cudaMalloc(&dk, sizeof(int)));
-    CK(cudaMalloc(&dp, sizeof(double)));
-    const int k3 = 3;
-    const double p0 = 0.0;
-    CK(cudaMemcpyAsync(dk, &k3, sizeof(int), cudaMemcpyHostToDevice, P->stream));
-    CK(cudaMemcpyAsync(dp, &p0, sizeof(double), cudaMemcpyHostToDevice, P->stream));
-    float* dw = nullptr;
-    CK(cudaMalloc(&dw, sizeof(float) * P->n_ov));
-    CK(gw::tc_scale_split(P->d_B_ia_f, P->d_eps, cfg->n_occ, cfg->n_virt, n, P->n_ov, dk, dp, 0.0, 1, dw, P->d_Bhi,
-                          P->d_Blo, P->stream));
+    CK(cudaMalloc(&P->d_Blo2, sizeof(__nv_bfloat16) * nsplit));
+    CK(gw::tc_split_rows(P->d_B_ia_f, n, P->n_ov, P->n_ov, P->d_Bhi, P->d_Blo, P->stream, P->d_Blo2));
     const size_t nsplitN = (size_t)n_targets * P->n_bas * gw::tc_ld(n);
     CK(cudaMalloc(&P->d_Bnhi, sizeof(__nv_bfloat16) * nsplitN));
     CK(cudaMalloc(&P->d_Bnlo, sizeof(__nv_bfloat16) * nsplitN));
@@ -918,7 +951,8 @@ static gw_status plan_create_impl(gw_plan* P, const gw_config* cfg, const double
     const size_t nsplitT = (size_t)P->n_ov * gw::tc_ld(n);
     CK(cudaMalloc(&P->d_BThi, sizeof(__nv_bfloat16) * nsplitT));
     CK(cudaMalloc(&P->d_BTlo, sizeof(__nv_bfloat16) * nsplitT));
-    CK(gw::tc_transpose_split(P->d_B_ia_f, n, P->n_ov, P->d_BThi, P->d_BTlo, P->stream));
+    CK(cudaMalloc(&P->d_BTlo2, sizeof(__nv_bfloat16) * nsplitT));
+    CK(gw::tc_transpose_split(P->d_B_ia_f, n, P->n_ov, P->d_BThi, P->d_BTlo, P->stream, P->d_BTlo2));
     {
       std::vector<double> D((size_t)P->n_ov);
       for (int i = 0; i < cfg->n_occ; ++i)
@@ -928,9 +962,6 @@ static gw_status plan_create_impl(gw_plan* P, const gw_config* cfg, const double
       CK(cudaStreamSynchronize(P->stream));
     }
     CK(cudaStreamSynchronize(P->stream));
-    cudaFree(dk);
-    cudaFree(dp);
-    cudaFree(dw);
   }
   LAUNCH(gw::launch_sigma_x(P->d_B_nm, n_targets, P->n_bas, n, cfg->n_occ, P->d_sx, P->stream));
   P->h_sx.resize(n_targets);

@@ -269,15 +269,15 @@ __global__ void fallback_finish_kernel(const double* __restrict__ B_nm, int n_ba
 
 __global__ void refine_kernel(int stage, const double* __restrict__ B_nm, int n_bas, int n_aux,
                               const int* __restrict__ rt, const int* __restrict__ rm, const int* __restrict__ idx,
-                              float* y32, double* y64, double* V64, const double* __restrict__ S64) {
+                              float* y32, double* y64, float* V32, const float* __restrict__ S32) {
   const int k = blockIdx.x;
   float* yr32 = y32 + (long)k * 2 * n_aux;
   double* yr64 = y64 + (long)k * 2 * n_aux;
-  double* u = V64 + (long)(2 * k) * n_aux;
+  float* u = V32 + (long)(2 * k) * n_aux;
   if (stage == 1) {
     const int j = idx[k];
     const double* b = B_nm + ((long)rt[j] * n_bas + rm[j]) * n_aux;
-    const double* S = S64 + (long)(2 * k) * n_aux;
+    const float* S = S32 + (long)(2 * k) * n_aux;
     for (int i = threadIdx.x; i < n_aux; i += blockDim.x) {
       yr32[i] = (float)(b[i] - S[i]);
       yr32[n_aux + i] = (float)(-S[n_aux + i]);
@@ -295,8 +295,8 @@ __global__ void refine_kernel(int stage, const double* __restrict__ B_nm, int n_
     }
     yr64[i] = re;
     yr64[n_aux + i] = im;
-    u[i] = re;
-    u[n_aux + i] = -im;
+    u[i] = (float)re;
+    u[n_aux + i] = (float)(-im);
   }
 }
 
@@ -512,8 +512,8 @@ void launch_fallback_finish(const double* B_nm, int n_bas, int n_aux, const int*
 }
 
 void launch_refine(int stage, const double* B_nm, int n_bas, int n_aux, const int* rt, const int* rm, const int* idx,
-                   int nf, float* y32, double* y64, double* V64, const double* S64, cudaStream_t s) {
-  if (nf > 0) refine_kernel<<<nf, RT, 0, s>>>(stage, B_nm, n_bas, n_aux, rt, rm, idx, y32, y64, V64, S64);
+                   int nf, float* y32, double* y64, float* V32, const float* S32, cudaStream_t s) {
+  if (nf > 0) refine_kernel<<<nf, RT, 0, s>>>(stage, B_nm, n_bas, n_aux, rt, rm, idx, y32, y64, V32, S32);
 }
 
 template <typename T>

@@ -7,7 +7,7 @@
 namespace gw {
 namespace {
 
-constexpr int LU_NB = 64;        // panel width (the trailing matrix is read and written once per panel)
+constexpr int LU_NB = 32;        // panel width
 constexpr int LU_T = 512;        // threads per CTA
 constexpr int TTM = 64;          // trailing-update tile rows (16 thread rows x 4)
 constexpr int TTN = 128;         // trailing-update tile columns (32 thread columns x 4)
@@ -57,15 +57,62 @@ __global__ void __launch_bounds__(LU_T) zlu_kernel(T* Ar_base, T* Ai_base, long 
   T* Ui = Ur + LU_NB * (TTN + 1);
   __shared__ double sv[32];
   __shared__ int si[32];
-  __shared__ T prow_r[LU_NB], prow_i[LU_NB];
+  __shared__ T L11r[LU_NB * (LU_NB + 1)], L11i[LU_NB * (LU_NB + 1)];   // strictly lower part of the panel's top block
+  __shared__ T ucol_r[LU_NB], ucol_i[LU_NB];
   T* Ar = Ar_base + (long)blockIdx.x * stride;
   T* Ai = Ai_base + (long)blockIdx.x * stride;
   int* piv = piv_base + (long)blockIdx.x * n;
   int bad = 0;
   for (int k0 = 0; k0 < n; k0 += LU_NB) {
     const int nb = min(LU_NB, n - k0), k1 = k0 + nb;
-    // ---- panel factorisation (columns k0..k1-1) with partial pivoting; rows swapped in full
+    // ---- panel factorisation (columns k0..k1-1), left-looking with partial pivoting; rows swapped in full.
+    // Column c is brought up to date only when it becomes the pivot column: its U part (rows k0..c-1) by a
+    // triangular solve with L11 (kept in shared memory), its rows below by one matrix-vector pass (thread per
+    // row, contiguous reads), so every panel element is written once.
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int c = k0; c < k1; ++c) {
+      const int cc = c - k0;
+      if (wid == 0) {
+        // U part of column c: u_r = a_rc - sum_{q<r} L11[r][q] u_q, r = k0..c-1 (lane r holds u_r)
+        T vr = lane < cc ? Ar[(long)(k0 + lane) * n + c] : T(0);
+        T vi = lane < cc ? Ai[(long)(k0 + lane) * n + c] : T(0);
+        for (int r = 1; r < cc; ++r) {
+          T ar = T(0), ai = T(0);
+          if (lane < r) {
+            const T lr = L11r[r * (LU_NB + 1) + lane], li = L11i[r * (LU_NB + 1) + lane];
+            ar = lr * vr - li * vi;
+            ai = lr * vi + li * vr;
+          }
+          for (int o = 16; o > 0; o >>= 1) {
+            ar += __shfl_xor_sync(0xffffffffu, ar, o);
+            ai += __shfl_xor_sync(0xffffffffu, ai, o);
+          }
+          if (lane == r) { vr -= ar; vi -= ai; }
+        }
+        if (lane < cc) {
+          ucol_r[lane] = vr;
+          ucol_i[lane] = vi;
+          Ar[(long)(k0 + lane) * n + c] = vr;
+          Ai[(long)(k0 + lane) * n + c] = vi;
+        }
+      }
+      __syncthreads();
+      // rows c..n-1: a_ic -= sum_{q<c} L_iq u_q
+      if (cc > 0) {
+        for (int i = c + threadIdx.x; i < n; i += blockDim.x) {
+          const T* lr = Ar + (long)i * n + k0;
+          const T* li = Ai + (long)i * n + k0;
+          T sr = T(0), si2 = T(0);
+          for (int q = 0; q < cc; ++q) {
+            sr += lr[q] * ucol_r[q] - li[q] * ucol_i[q];
+            si2 += lr[q] * ucol_i[q] + li[q] * ucol_r[q];
+          }
+          Ar[(long)i * n + c] -= sr;
+          Ai[(long)i * n + c] -= si2;
+        }
+      }
+      __threadfence_block();
+      __syncthreads();
       int p = pivot_row(Ar, Ai, n, c, c, sv, si);
       if (p < 0) { bad = c + 1; p = c; }
       if (threadIdx.x == 0) piv[c] = p;
@@ -77,44 +124,37 @@ __global__ void __launch_bounds__(LU_T) zlu_kernel(T* Ar_base, T* Ai_base, long 
       }
       __threadfence_block();
       __syncthreads();
+      // L11 row cc (multipliers of columns k0..c-1 of the new pivot row)
+      if (threadIdx.x < cc) {
+        L11r[cc * (LU_NB + 1) + threadIdx.x] = Ar[(long)c * n + k0 + threadIdx.x];
+        L11i[cc * (LU_NB + 1) + threadIdx.x] = Ai[(long)c * n + k0 + threadIdx.x];
+      }
       const cplx<T> d = {Ar[(long)c * n + c], Ai[(long)c * n + c]};
       const bool dz = (d.r == T(0) && d.i == T(0));
-      // pivot-row segment of the panel in shared memory, then one thread per row below: multiplier and the
-      // rank-1 update of the rest of the panel (independent rows, so the loads overlap)
-      for (int j = c + 1 + threadIdx.x; j < k1; j += blockDim.x) {
-        prow_r[j - k0] = Ar[(long)c * n + j];
-        prow_i[j - k0] = Ai[(long)c * n + j];
-      }
-      __syncthreads();
       for (int i = c + 1 + threadIdx.x; i < n; i += blockDim.x) {
         cplx<T> l = {Ar[(long)i * n + c], Ai[(long)i * n + c]};
         l = dz ? cplx<T>{T(0), T(0)} : cdiv(l, d);
-        T* ri = Ar + (long)i * n;
-        T* ii = Ai + (long)i * n;
-        for (int j = c + 1; j < k1; ++j) {
-          const T ur = prow_r[j - k0], ui = prow_i[j - k0];
-          ri[j] -= l.r * ur - l.i * ui;
-          ii[j] -= l.r * ui + l.i * ur;
-        }
-        ri[c] = l.r;
-        ii[c] = l.i;
+        Ar[(long)i * n + c] = l.r;
+        Ai[(long)i * n + c] = l.i;
       }
       __threadfence_block();
       __syncthreads();
     }
     if (k1 >= n) break;
-    // ---- U12 = L11^-1 A12 (unit lower), columns j >= k1 in parallel
+    // ---- U12 = L11^-1 A12 (unit lower), one column per thread, L11 from shared memory
     for (int j = k1 + threadIdx.x; j < n; j += blockDim.x) {
-      for (int r = k0 + 1; r < k1; ++r) {
-        T sr = Ar[(long)r * n + j], sI = Ai[(long)r * n + j];
-        for (int q = k0; q < r; ++q) {
-          const T lr = Ar[(long)r * n + q], li = Ai[(long)r * n + q];
-          const T ur = Ar[(long)q * n + j], ui = Ai[(long)q * n + j];
+      T* cr = Ar + (long)k0 * n + j;      // column j of the panel rows; solved entries are read back from cache
+      T* ci = Ai + (long)k0 * n + j;
+      for (int r = 1; r < nb; ++r) {
+        T sr = cr[(long)r * n], sI = ci[(long)r * n];
+        for (int q = 0; q < r; ++q) {
+          const T lr = L11r[r * (LU_NB + 1) + q], li = L11i[r * (LU_NB + 1) + q];
+          const T ur = cr[(long)q * n], ui = ci[(long)q * n];
           sr -= lr * ur - li * ui;
           sI -= lr * ui + li * ur;
         }
-        Ar[(long)r * n + j] = sr;
-        Ai[(long)r * n + j] = sI;
+        cr[(long)r * n] = sr;
+        ci[(long)r * n] = sI;
       }
     }
     __threadfence_block();

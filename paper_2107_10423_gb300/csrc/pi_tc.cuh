@@ -21,7 +21,7 @@ struct TcEpi {
   __nv_bfloat16* ohi;
   __nv_bfloat16* olo;
   int ldh;
-  __nv_bfloat16* olo2;   // third split part (TC_EPI_AXPBY), or NULL
+  __nv_bfloat16* olo2;   // third split part (TC_EPI_AXPBY, TC_EPI_CPAIR), or NULL
   // TC_EPI_EMBED: out[m][n] = (m even ? vin : -vin)[m][n] - v  (row lengths ldo, ldv)
   const float* vin;
   int ldv;
@@ -76,5 +76,6 @@ cudaError_t tc_ns_init(const float* A, int n, int batch, const float* lam, float
 cudaError_t tc_sym_split(const float* X, int n, int batch, float* Y, __nv_bfloat16* hi, __nv_bfloat16* lo,
                          __nv_bfloat16* lo2, cudaStream_t s);
 // out[k][m] = B[m][k] split into BF16 hi/lo with rows of tc_ld(M) elements (B FP32 [M][K]).
-cudaError_t tc_transpose_split(const float* B, int M, int K, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s);
+cudaError_t tc_transpose_split(const float* B, int M, int K, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s,
+                               __nv_bfloat16* lo2 = nullptr);
 }  // namespace gw

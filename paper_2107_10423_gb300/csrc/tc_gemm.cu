@@ -167,8 +167,8 @@ __device__ void epilogue(const TcEpi& ep, const float* stg, int m0, int n0, int 
       const float cr = 2.f * (a1 / d1 + a2 / d2);
       const float ci = -2.f * ep.eta * (1.f / d1 + 1.f / d2);
       const float tr = stg[(2 * pr) * (BN + 1) + cc], ti = -stg[(2 * pr + 1) * (BN + 1) + cc];
-      split_store(cr * tr - ci * ti, ep.ohi, ep.olo, (long)m * ep.ldh + n);
-      split_store(cr * ti + ci * tr, ep.ohi, ep.olo, (long)(m + 1) * ep.ldh + n);
+      split_store(cr * tr - ci * ti, ep.ohi, ep.olo, (long)m * ep.ldh + n, ep.olo2);
+      split_store(cr * ti + ci * tr, ep.ohi, ep.olo, (long)(m + 1) * ep.ldh + n, ep.olo2);
     }
   } else if (ep.kind == TC_EPI_AXPBY) {
     for (int idx = threadIdx.x; idx < BM * BN; idx += THREADS) {
@@ -514,7 +514,8 @@ cudaError_t tc_gemm(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int batc
 
 // B^T split: out[k][m] = B[m][k] as BF16 hi/lo, rows of length tc_ld(M).  32 x 32 tiles through shared memory.
 __global__ void transpose_split_kernel(const float* __restrict__ B, int M, int K, int ld,
-                                       __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+                                       __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
+                                       __nv_bfloat16* __restrict__ lo2) {
   __shared__ float t[32][33];
   const int k0 = blockIdx.x * 32, m0 = blockIdx.y * 32;
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
@@ -524,7 +525,7 @@ __global__ void transpose_split_kernel(const float* __restrict__ B, int M, int K
   __syncthreads();
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int k = k0 + r, m = m0 + threadIdx.x;
-    if (k < K && m < ld) split_store(m < M ? t[threadIdx.x][r] : 0.f, hi, lo, (long)k * ld + m);
+    if (k < K && m < ld) split_store(m < M ? t[threadIdx.x][r] : 0.f, hi, lo, (long)k * ld + m, lo2);
   }
 }
 
@@ -649,10 +650,11 @@ cudaError_t tc_sym_split(const float* X, int n, int batch, float* Y, __nv_bfloat
   return cudaGetLastError();
 }
 
-cudaError_t tc_transpose_split(const float* B, int M, int K, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s) {
+cudaError_t tc_transpose_split(const float* B, int M, int K, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s,
+                               __nv_bfloat16* lo2) {
   const int ld = tc_ld(M);
   dim3 grid((K + 31) / 32, (ld + 31) / 32);
-  transpose_split_kernel<<<grid, dim3(32, 8), 0, s>>>(B, M, K, ld, hi, lo);
+  transpose_split_kernel<<<grid, dim3(32, 8), 0, s>>>(B, M, K, ld, hi, lo, lo2);
   return cudaGetLastError();
 }
 
