@@ -74,6 +74,11 @@ typedef struct {
   int max_rhs_batch;           /* residue right-hand sides per batched MINRES launch (0 = automatic) */
   int workspace_mb;            /* cap per large workspace class (frequency matrices, split operands,
                                   fallback matrices), MiB; 0 = 8192 */
+  double refine_tol;           /* mixed: a dense-fallback solve whose first refinement correction (residual from the
+                                  three-part tensor-core operator), relative to the solution in the 2-norm, exceeds
+                                  refine_tol takes one more step with the residual from the FP64 operator
+                                  (near-resonant, ill-conditioned residues); 0 = every solve, < 0 = none;
+                                  default 1e-6 */
 } gw_config;
 
 typedef struct gw_plan* gw_plan_t;
@@ -142,7 +147,8 @@ gw_status gw_w_table(gw_plan_t plan, double* out);
  *   2 W-table factorisation (Cholesky of 1 - Pi, or the tensor-core Newton-Schulz inverse in mixed mode)
  *   3 W-table reduction (triangular solves, or the tensor-core GEMM into W)   4 MINRES operator GEMMs
  *   5 MINRES recurrences                                    6 dense Pi(x) of fallback solves
- *   7 batched complex LU + solve                          8 FP64 operator of the mixed-precision refinement
+ *   7 batched complex LU + solve                          8 residual operators of the mixed-precision refinement
+ *                                                           (three-part tensor-core, and FP64 where selected)
  * flops_kernel counts algorithmic floating-point operations (a multiply-add is 2). */
 #define GW_N_KERNEL_CLASSES 9
 typedef struct {
@@ -159,6 +165,7 @@ typedef struct {
   double ms_kernel[GW_N_KERNEL_CLASSES];
   double flops_kernel[GW_N_KERNEL_CLASSES];
   long long launches_kernel[GW_N_KERNEL_CLASSES];
+  long long n_refine_fp64;     /* dense-fallback solves that took the FP64-operator refinement step */
 } gw_stats;
 gw_status gw_get_stats(gw_plan_t plan, gw_stats* out);
 

@@ -95,10 +95,14 @@ void launch_fallback_finish(const double* B_nm, int n_bas, int n_aux, const int*
 
 // Iterative refinement of fallback solves (k < nf; y32 planes [nf][2][n], y64 the same in FP64):
 //   stage 0: y64 = y32;            V32 rows (2k, 2k+1) = (Re y, -Im y)
-//   stage 1: y32 = [b; 0] - S32    (residual of the three-part operator, next right-hand side)
-//   stage 2: y64 += y32;           V32 rows = (Re y, -Im y)
+//   stage 1: y32 = [b; 0] - S      (residual, next right-hand side; S = S32 rows (2k, 2k+1), or, if S64 is given,
+//                                   S64 rows (2q, 2q+1) with q = pos[k] (q = k without pos; q < 0: y32 = 0))
+//   stage 2: y64 += y32;           V32 rows = (Re y, -Im y); rho[k] = |y32| / |y64| if rho is given
 void launch_refine(int stage, const double* B_nm, int n_bas, int n_aux, const int* rt, const int* rm, const int* idx,
-                   int nf, float* y32, double* y64, float* V32, const float* S32, cudaStream_t s);
+                   int nf, float* y32, double* y64, float* V32, const float* S32, cudaStream_t s,
+                   const double* S64 = nullptr, const int* pos = nullptr, double* rho = nullptr);
+// V64 rows (2q, 2q+1) = (Re y, -Im y) of the FP64 solution sel[q] (q without sel) of y64 [.][2][n], q < m.
+void launch_refine_v64(int m, int n_aux, const int* sel, const double* y64, double* V64, cudaStream_t s);
 // W = b^T y - b^T b from FP64 solutions; V (operator precision) rows of slot idx[k] = (Re y, -Im y); resnorm 0.
 template <typename T>
 void launch_fallback_finish64(const double* B_nm, int n_bas, int n_aux, const int* rt, const int* rm, const int* idx,

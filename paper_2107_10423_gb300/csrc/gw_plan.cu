@@ -65,7 +65,8 @@ struct gw_plan {
   DevBuf mr_V, mr_U, mr_S, mr_vprev, mr_v, mr_d1, mr_d2, mr_x, mr_st, mr_rt, mr_rm, mr_xf, mr_wre, mr_wim,
       mr_dwre, mr_it, mr_res, mr_cnt, mr_Vhi, mr_Vlo, mr_Uhi, mr_Ulo;
   DevBuf sg_I, sg_dI, sg_R, sg_dR, sg_om, sg_start, sg_coef, sg_act, qp_st;
-  DevBuf fb_A, fb_y, fb_piv, fb_info, fb_idx, fb_y64, fb_V32, fb_S32, fb_Vp, fb_Up, fb_x;
+  DevBuf fb_A, fb_y, fb_piv, fb_info, fb_idx, fb_y64, fb_V32, fb_S32, fb_Vp, fb_Up, fb_x, fb_V64, fb_U64, fb_S64, fb_sel,
+      fb_pos, fb_rho, fb_xs;
   int* h_cnt = nullptr;       // pinned
   std::string err;
   gw_stats stats{};
@@ -80,7 +81,7 @@ struct gw_plan {
     DevBuf* all[] = {&ws_mat, &ws_info, &ws_scratch, &ws_gout, &ws_xi, &tc_Ahi, &tc_Alo, &tc_kind, &tc_par, &tc_err, &tc_w, &ns_E, &ns_X, &ns_X2, &ns_Xa, &ns_Xb, &ns_T, &ns_lam, &mr_V, &mr_U, &mr_S, &mr_vprev,
                      &mr_v, &mr_d1, &mr_d2, &mr_x, &mr_st, &mr_rt, &mr_rm, &mr_xf, &mr_wre, &mr_wim,
                      &mr_dwre, &mr_it, &mr_res, &mr_cnt, &mr_Vhi, &mr_Vlo, &mr_Uhi, &mr_Ulo, &sg_I, &sg_dI, &sg_R, &sg_dR, &sg_om, &sg_start,
-                     &sg_coef, &sg_act, &qp_st, &fb_A, &fb_y, &fb_piv, &fb_info, &fb_idx, &fb_y64, &fb_V32, &fb_S32, &fb_Vp, &fb_Up, &fb_x};
+                     &sg_coef, &sg_act, &qp_st, &fb_A, &fb_y, &fb_piv, &fb_info, &fb_idx, &fb_y64, &fb_V32, &fb_S32, &fb_Vp, &fb_Up, &fb_x, &fb_V64, &fb_U64, &fb_S64, &fb_sel, &fb_pos, &fb_rho, &fb_xs};
     bufs.assign(all, all + sizeof(all) / sizeof(all[0]));
   }
 };
@@ -429,10 +430,6 @@ gw_status ensure_screening(gw_plan* P) {
 
 gw_status tc_operator3(gw_plan* P, int nf, const double* xf, const float* V32, float* S32);
 
-// Refinement steps of the mixed-precision dense solves (three-part tensor-core residual, FP32 LU correction,
-// solution accumulated in FP64).
-constexpr int kRefineSteps = 1;
-
 // Dense solves for the MINRES batch slots in `need` (Sec. 3.3: build the dielectric matrix and factorise).
 // A_j = 1 - Pi(x_j) is built on the tensor cores (mixed) or by the FP64 SIMT kernel, then factorised by the
 // batched complex LU; W and the derivative-pass vectors are written into the slot.
@@ -460,6 +457,10 @@ gw_status dense_fallback(gw_plan* P, const std::vector<int>& need, const int* rt
     TRY(ensure(P, P->fb_Up, 3 * sizeof(__nv_bfloat16) * 2 * (size_t)gw::tc_ld(P->n_ov) * fb));
     TRY(ensure(P, P->tc_err, sizeof(int)));
     TRY(ensure(P, P->fb_x, sizeof(double) * fb));
+    TRY(ensure(P, P->fb_xs, sizeof(double) * fb));
+    TRY(ensure(P, P->fb_rho, sizeof(double) * fb));
+    TRY(ensure(P, P->fb_sel, sizeof(int) * fb));
+    TRY(ensure(P, P->fb_pos, sizeof(int) * fb));
   }
   CK(cudaMemcpyAsync(P->fb_idx.p, need.data(), sizeof(int) * nneed, cudaMemcpyHostToDevice, P->stream));
   std::vector<double> hx(nneed);
@@ -505,14 +506,15 @@ gw_status dense_fallback(gw_plan* P, const std::vector<int>& need, const int* rt
                                    as<T>(P->fb_y) + n, 2L * n, P->stream));
     mark(P, 7, tl, nf * (8.0 / 3.0 * (double)n * n * n + 8.0 * (double)n * n));
     if (sizeof(T) == 4) {
-      // one step of iterative refinement with the FP64 operator (matrix-free) and the FP32 factors
+      // iterative refinement with the FP32 factors (matrix-free residuals), solution accumulated in FP64
       float* y32 = reinterpret_cast<float*>(P->fb_y.p);
       const int* idx = as<int>(P->fb_idx) + k0;
       std::vector<double> xk(hx.begin() + k0, hx.begin() + k0 + nf);
       CK(cudaMemcpyAsync(P->fb_x.p, xk.data(), sizeof(double) * nf, cudaMemcpyHostToDevice, P->stream));
       LAUNCH(gw::launch_refine(0, P->d_B_nm, P->n_bas, n, rt, rm, idx, nf, y32, as<double>(P->fb_y64),
                                as<float>(P->fb_V32), nullptr, P->stream));
-      for (int r = 0; r < kRefineSteps; ++r) {
+      // step 1: residual from the three-part tensor-core operator (about FP32-accurate), FP32 LU correction
+      {
         const size_t tr = tick(P);
         TRY(tc_operator3(P, nf, as<double>(P->fb_x), as<float>(P->fb_V32), as<float>(P->fb_S32)));
         mark(P, 8, tr, 2.0 * 2.0 * (2.0 * nf) * n * (double)P->n_ov);
@@ -521,7 +523,53 @@ gw_status dense_fallback(gw_plan* P, const std::vector<int>& need, const int* rt
         LAUNCH(gw::launch_zlu_solve<T>(A, A + mat, (long)(2 * mat), n, nf, as<int>(P->fb_piv), as<T>(P->fb_y),
                                        as<T>(P->fb_y) + n, 2L * n, P->stream));
         LAUNCH(gw::launch_refine(2, P->d_B_nm, P->n_bas, n, rt, rm, idx, nf, y32, as<double>(P->fb_y64),
-                                 as<float>(P->fb_V32), nullptr, P->stream));
+                                 as<float>(P->fb_V32), nullptr, P->stream, nullptr, nullptr,
+                                 P->cfg.refine_tol > 0.0 ? as<double>(P->fb_rho) : nullptr));
+      }
+      // step 2, for the solves the first correction shows to be ill-conditioned (|dy|/|y| > refine_tol: a
+      // near-resonant x_j, where the operator's FP32-level error limits step 1): residual from the FP64 operator
+      if (P->cfg.refine_tol >= 0.0) {
+        std::vector<int> sel, pos(nf, -1);
+        std::vector<double> xs;
+        if (P->cfg.refine_tol > 0.0) {
+          std::vector<double> rho(nf);
+          CK(cudaMemcpyAsync(rho.data(), P->fb_rho.p, sizeof(double) * nf, cudaMemcpyDeviceToHost, P->stream));
+          CK(cudaStreamSynchronize(P->stream));
+          for (int k = 0; k < nf; ++k)
+            if (!(rho[k] <= P->cfg.refine_tol)) sel.push_back(k);   // NaN selects too
+        } else {
+          for (int k = 0; k < nf; ++k) sel.push_back(k);
+        }
+        const int m = (int)sel.size();
+        if (m > 0) {
+          for (int q = 0; q < m; ++q) {
+            pos[sel[q]] = q;
+            xs.push_back(hx[k0 + sel[q]]);
+          }
+          TRY(ensure(P, P->fb_V64, sizeof(double) * 2 * (size_t)n * m));
+          TRY(ensure(P, P->fb_S64, sizeof(double) * 2 * (size_t)n * m));
+          TRY(ensure(P, P->fb_U64, sizeof(double) * 2 * (size_t)P->n_ov * m));
+          CK(cudaMemcpyAsync(P->fb_sel.p, sel.data(), sizeof(int) * m, cudaMemcpyHostToDevice, P->stream));
+          CK(cudaMemcpyAsync(P->fb_pos.p, pos.data(), sizeof(int) * nf, cudaMemcpyHostToDevice, P->stream));
+          CK(cudaMemcpyAsync(P->fb_xs.p, xs.data(), sizeof(double) * m, cudaMemcpyHostToDevice, P->stream));
+          const size_t tr = tick(P);
+          LAUNCH(gw::launch_refine_v64(m, n, as<int>(P->fb_sel), as<double>(P->fb_y64), as<double>(P->fb_V64),
+                                       P->stream));
+          LAUNCH(gw::launch_op_gemm1<double>(as<double>(P->fb_V64), P->d_B_ia, P->d_eps, P->cfg.n_occ,
+                                             P->cfg.n_virt, n, as<double>(P->fb_xs), P->cfg.eta, m,
+                                             as<double>(P->fb_U64), 0, P->stream));
+          LAUNCH(gw::launch_op_gemm2<double>(as<double>(P->fb_U64), P->d_B_ia, n, P->n_ov, m,
+                                             as<double>(P->fb_V64), as<double>(P->fb_S64), 1, P->stream));
+          mark(P, 8, tr, 2.0 * 2.0 * (2.0 * m) * n * (double)P->n_ov);
+          LAUNCH(gw::launch_refine(1, P->d_B_nm, P->n_bas, n, rt, rm, idx, nf, y32, as<double>(P->fb_y64),
+                                   as<float>(P->fb_V32), nullptr, P->stream, as<double>(P->fb_S64),
+                                   as<int>(P->fb_pos)));
+          LAUNCH(gw::launch_zlu_solve<T>(A, A + mat, (long)(2 * mat), n, nf, as<int>(P->fb_piv), as<T>(P->fb_y),
+                                         as<T>(P->fb_y) + n, 2L * n, P->stream));
+          LAUNCH(gw::launch_refine(2, P->d_B_nm, P->n_bas, n, rt, rm, idx, nf, y32, as<double>(P->fb_y64),
+                                   as<float>(P->fb_V32), nullptr, P->stream));
+          P->stats.n_refine_fp64 += m;
+        }
       }
       LAUNCH(gw::launch_fallback_finish64<T>(P->d_B_nm, P->n_bas, n, rt, rm, idx, nf, as<double>(P->fb_y64), w_re,
                                              w_im, resnorm, as<T>(P->mr_V), P->stream));
@@ -843,6 +891,7 @@ void gw_config_default(gw_config* c) {
   c->qp_tol = 1e-8;
   c->static_subtraction = 1;
   c->max_rhs_batch = 0;
+  c->refine_tol = 1e-6;
 }
 
 static void free_plan(gw_plan* P) {

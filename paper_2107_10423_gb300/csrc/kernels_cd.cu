@@ -269,7 +269,9 @@ __global__ void fallback_finish_kernel(const double* __restrict__ B_nm, int n_ba
 
 __global__ void refine_kernel(int stage, const double* __restrict__ B_nm, int n_bas, int n_aux,
                               const int* __restrict__ rt, const int* __restrict__ rm, const int* __restrict__ idx,
-                              float* y32, double* y64, float* V32, const float* __restrict__ S32) {
+                              float* y32, double* y64, float* V32, const float* __restrict__ S32,
+                              const double* __restrict__ S64, const int* __restrict__ pos, double* rho) {
+  __shared__ double buf[32];
   const int k = blockIdx.x;
   float* yr32 = y32 + (long)k * 2 * n_aux;
   double* yr64 = y64 + (long)k * 2 * n_aux;
@@ -277,26 +279,48 @@ __global__ void refine_kernel(int stage, const double* __restrict__ B_nm, int n_
   if (stage == 1) {
     const int j = idx[k];
     const double* b = B_nm + ((long)rt[j] * n_bas + rm[j]) * n_aux;
-    const float* S = S32 + (long)(2 * k) * n_aux;
-    for (int i = threadIdx.x; i < n_aux; i += blockDim.x) {
-      yr32[i] = (float)(b[i] - S[i]);
-      yr32[n_aux + i] = (float)(-S[n_aux + i]);
+    if (S64) {
+      const int q = pos ? pos[k] : k;
+      if (q < 0) {   // solve not selected: zero right-hand side, zero correction
+        for (int i = threadIdx.x; i < 2 * n_aux; i += blockDim.x) yr32[i] = 0.0f;
+        return;
+      }
+      const double* S = S64 + (long)(2 * q) * n_aux;
+      for (int i = threadIdx.x; i < n_aux; i += blockDim.x) {
+        yr32[i] = (float)(b[i] - S[i]);
+        yr32[n_aux + i] = (float)(-S[n_aux + i]);
+      }
+    } else {
+      const float* S = S32 + (long)(2 * k) * n_aux;
+      for (int i = threadIdx.x; i < n_aux; i += blockDim.x) {
+        yr32[i] = (float)(b[i] - (double)S[i]);
+        yr32[n_aux + i] = (float)(-(double)S[n_aux + i]);
+      }
     }
     return;
   }
+  double cn = 0.0, yn = 0.0;
   for (int i = threadIdx.x; i < n_aux; i += blockDim.x) {
     double re, im;
     if (stage == 0) {
       re = yr32[i];
       im = yr32[n_aux + i];
     } else {
-      re = yr64[i] + (double)yr32[i];
-      im = yr64[n_aux + i] + (double)yr32[n_aux + i];
+      const double cr = yr32[i], ci = yr32[n_aux + i];
+      re = yr64[i] + cr;
+      im = yr64[n_aux + i] + ci;
+      cn += cr * cr + ci * ci;
     }
+    yn += re * re + im * im;
     yr64[i] = re;
     yr64[n_aux + i] = im;
     u[i] = (float)re;
     u[n_aux + i] = (float)(-im);
+  }
+  if (rho) {
+    cn = block_sum(cn, buf);
+    yn = block_sum(yn, buf);
+    if (threadIdx.x == 0) rho[k] = yn > 0.0 ? sqrt(cn / yn) : 0.0;
   }
 }
 
@@ -323,6 +347,17 @@ __global__ void fallback_finish64_kernel(const double* __restrict__ B_nm, int n_
     w_re[j] = ar;
     w_im[j] = ai;
     resnorm[j] = 0.0;
+  }
+}
+
+__global__ void refine_v64_kernel(int n_aux, const int* __restrict__ sel, const double* __restrict__ y64,
+                                  double* __restrict__ V64) {
+  const int q = blockIdx.x;
+  const double* y = y64 + (long)(sel ? sel[q] : q) * 2 * n_aux;
+  double* u = V64 + (long)(2 * q) * n_aux;
+  for (int i = threadIdx.x; i < n_aux; i += blockDim.x) {
+    u[i] = y[i];
+    u[n_aux + i] = -y[n_aux + i];
   }
 }
 
@@ -512,8 +547,10 @@ void launch_fallback_finish(const double* B_nm, int n_bas, int n_aux, const int*
 }
 
 void launch_refine(int stage, const double* B_nm, int n_bas, int n_aux, const int* rt, const int* rm, const int* idx,
-                   int nf, float* y32, double* y64, float* V32, const float* S32, cudaStream_t s) {
-  if (nf > 0) refine_kernel<<<nf, RT, 0, s>>>(stage, B_nm, n_bas, n_aux, rt, rm, idx, y32, y64, V32, S32);
+                   int nf, float* y32, double* y64, float* V32, const float* S32, cudaStream_t s,
+                   const double* S64, const int* pos, double* rho) {
+  if (nf > 0)
+    refine_kernel<<<nf, RT, 0, s>>>(stage, B_nm, n_bas, n_aux, rt, rm, idx, y32, y64, V32, S32, S64, pos, rho);
 }
 
 template <typename T>
@@ -525,6 +562,10 @@ void launch_fallback_finish64(const double* B_nm, int n_bas, int n_aux, const in
 }
 template void launch_fallback_finish64<float>(const double*, int, int, const int*, const int*, const int*, int,
                                               const double*, double*, double*, double*, float*, cudaStream_t);
+
+void launch_refine_v64(int m, int n_aux, const int* sel, const double* y64, double* V64, cudaStream_t s) {
+  if (m > 0) refine_v64_kernel<<<m, RT, 0, s>>>(n_aux, sel, y64, V64);
+}
 
 void launch_residue_reduce(const int* start, int n_t, const double* coef, const double* w_re, const double* dw_re,
                            double* R, double* dR, cudaStream_t s) {

@@ -31,7 +31,8 @@ class Config(ctypes.Structure):
                 ("n_freq", ctypes.c_int), ("x0", ctypes.c_double), ("eta", ctypes.c_double),
                 ("precision", ctypes.c_int), ("minres_maxit", ctypes.c_int), ("minres_tol", ctypes.c_double),
                 ("minres_fallback_tol", ctypes.c_double), ("qp_maxit", ctypes.c_int), ("qp_tol", ctypes.c_double),
-                ("static_subtraction", ctypes.c_int), ("max_rhs_batch", ctypes.c_int), ("workspace_mb", ctypes.c_int)]
+                ("static_subtraction", ctypes.c_int), ("max_rhs_batch", ctypes.c_int), ("workspace_mb", ctypes.c_int),
+                ("refine_tol", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -40,11 +41,11 @@ class Stats(ctypes.Structure):
                 ("n_minres_iters", ctypes.c_longlong), ("n_fallback", ctypes.c_longlong),
                 ("n_sigma_evals", ctypes.c_longlong), ("n_kernel_launches", ctypes.c_longlong),
                 ("ms_kernel", ctypes.c_double * 9), ("flops_kernel", ctypes.c_double * 9),
-                ("launches_kernel", ctypes.c_longlong * 9)]
+                ("launches_kernel", ctypes.c_longlong * 9), ("n_refine_fp64", ctypes.c_longlong)]
 
 
 KERNEL_CLASSES = ["pi_tcgen05", "pi_simt", "w_table_factor", "w_table_reduce", "minres_operator_gemm", "minres_recurrence",
-                  "fallback_pi_dense", "fallback_lu", "fallback_refine_fp64"]
+                  "fallback_pi_dense", "fallback_lu", "fallback_refine"]
 
 
 _lib = None
