@@ -79,6 +79,9 @@ typedef struct {
                                   refine_tol takes one more step with the residual from the FP64 operator
                                   (near-resonant, ill-conditioned residues); 0 = every solve, < 0 = none;
                                   default 1e-6 */
+  int op_parts;                /* mixed: BF16 parts per operand of the MINRES operator: 2 (hi, lo: three products,
+                                  about 2^-16 relative; default) or 3 (hi, mid, lo: six products, about
+                                  FP32-accurate) */
 } gw_config;
 
 typedef struct gw_plan* gw_plan_t;

@@ -63,7 +63,7 @@ struct gw_plan {
   std::vector<DevBuf*> bufs;
   DevBuf ws_mat, ws_info, ws_scratch, ws_gout, ws_xi, tc_Ahi, tc_Alo, tc_kind, tc_par, tc_err, tc_w, ns_E, ns_X, ns_X2, ns_Xa, ns_Xb, ns_T, ns_lam;
   DevBuf mr_V, mr_U, mr_S, mr_vprev, mr_v, mr_d1, mr_d2, mr_x, mr_st, mr_rt, mr_rm, mr_xf, mr_wre, mr_wim,
-      mr_dwre, mr_it, mr_res, mr_cnt, mr_Vhi, mr_Vlo, mr_Uhi, mr_Ulo;
+      mr_dwre, mr_it, mr_res, mr_cnt, mr_Vhi, mr_Vlo, mr_Uhi, mr_Ulo, mr_Vlo2, mr_Ulo2;
   DevBuf sg_I, sg_dI, sg_R, sg_dR, sg_om, sg_start, sg_coef, sg_act, qp_st;
   DevBuf fb_A, fb_y, fb_piv, fb_info, fb_idx, fb_y64, fb_V32, fb_S32, fb_Vp, fb_Up, fb_x, fb_V64, fb_U64, fb_S64, fb_sel,
       fb_pos, fb_rho, fb_xs;
@@ -80,7 +80,7 @@ struct gw_plan {
   gw_plan() {
     DevBuf* all[] = {&ws_mat, &ws_info, &ws_scratch, &ws_gout, &ws_xi, &tc_Ahi, &tc_Alo, &tc_kind, &tc_par, &tc_err, &tc_w, &ns_E, &ns_X, &ns_X2, &ns_Xa, &ns_Xb, &ns_T, &ns_lam, &mr_V, &mr_U, &mr_S, &mr_vprev,
                      &mr_v, &mr_d1, &mr_d2, &mr_x, &mr_st, &mr_rt, &mr_rm, &mr_xf, &mr_wre, &mr_wim,
-                     &mr_dwre, &mr_it, &mr_res, &mr_cnt, &mr_Vhi, &mr_Vlo, &mr_Uhi, &mr_Ulo, &sg_I, &sg_dI, &sg_R, &sg_dR, &sg_om, &sg_start,
+                     &mr_dwre, &mr_it, &mr_res, &mr_cnt, &mr_Vhi, &mr_Vlo, &mr_Uhi, &mr_Ulo, &mr_Vlo2, &mr_Ulo2, &sg_I, &sg_dI, &sg_R, &sg_dR, &sg_om, &sg_start,
                      &sg_coef, &sg_act, &qp_st, &fb_A, &fb_y, &fb_piv, &fb_info, &fb_idx, &fb_y64, &fb_V32, &fb_S32, &fb_Vp, &fb_Up, &fb_x, &fb_V64, &fb_U64, &fb_S64, &fb_sel, &fb_pos, &fb_rho, &fb_xs};
     bufs.assign(all, all + sizeof(all) / sizeof(all[0]));
   }
@@ -591,8 +591,12 @@ gw_status dense_fallback(gw_plan* P, const std::vector<int>& need, const int* rt
 // GEMM2 B w with either the plain store (mode 0: [Re; Im] of Pi z) or the 2n embedding of (1 - Pi) z (mode 1).
 gw_status tc_operator(gw_plan* P, int nr, const double* xf, const float* V32, float* S32, int mode) {
   const int n = P->cfg.n_aux, n_ov = P->n_ov;
-  const int ldn = gw::tc_ld(n), ldov = gw::tc_ld(n_ov);
-  CK(gw::tc_split_rows(V32, 2 * nr, n, n, as<__nv_bfloat16>(P->mr_Vhi), as<__nv_bfloat16>(P->mr_Vlo), P->stream));
+  const int ldov = gw::tc_ld(n_ov);
+  const bool three = P->cfg.op_parts >= 3;
+  __nv_bfloat16* vlo2 = three ? as<__nv_bfloat16>(P->mr_Vlo2) : nullptr;
+  __nv_bfloat16* ulo2 = three ? as<__nv_bfloat16>(P->mr_Ulo2) : nullptr;
+  CK(gw::tc_split_rows(V32, 2 * nr, n, n, as<__nv_bfloat16>(P->mr_Vhi), as<__nv_bfloat16>(P->mr_Vlo), P->stream,
+                       vlo2));
   gw::TcEpi e1{};
   e1.kind = gw::TC_EPI_CPAIR;
   e1.Dk = P->d_D;
@@ -600,21 +604,22 @@ gw_status tc_operator(gw_plan* P, int nr, const double* xf, const float* V32, fl
   e1.eta = (float)P->cfg.eta;
   e1.ohi = as<__nv_bfloat16>(P->mr_Uhi);
   e1.olo = as<__nv_bfloat16>(P->mr_Ulo);
+  e1.olo2 = ulo2;
   e1.ldh = ldov;
-  const gw::TcOperand Vop{{as<__nv_bfloat16>(P->mr_Vhi), as<__nv_bfloat16>(P->mr_Vlo), nullptr}};
-  const gw::TcOperand BT{{P->d_BThi, P->d_BTlo, nullptr}};
-  CK(gw::tc_gemm_ex(Vop, 1, BT, 0, 2, 2 * nr, n_ov, n, 0, e1, as<int>(P->tc_err), P->stream));
+  const gw::TcOperand Vop{{as<__nv_bfloat16>(P->mr_Vhi), as<__nv_bfloat16>(P->mr_Vlo), vlo2}};
+  const gw::TcOperand BT{{P->d_BThi, P->d_BTlo, three ? P->d_BTlo2 : nullptr}};
+  const int ns = three ? 3 : 2;
+  CK(gw::tc_gemm_ex(Vop, 1, BT, 0, ns, 2 * nr, n_ov, n, 0, e1, as<int>(P->tc_err), P->stream));
   gw::TcEpi e2{};
   e2.kind = mode == 0 ? gw::TC_EPI_STORE : gw::TC_EPI_EMBED;
   e2.out = S32;
   e2.ldo = n;
   e2.vin = V32;
   e2.ldv = n;
-  const gw::TcOperand Uop{{as<__nv_bfloat16>(P->mr_Uhi), as<__nv_bfloat16>(P->mr_Ulo), nullptr}};
-  const gw::TcOperand Bop{{P->d_Bhi, P->d_Blo, nullptr}};
-  CK(gw::tc_gemm_ex(Uop, 1, Bop, 0, 2, 2 * nr, n, n_ov, 0, e2, as<int>(P->tc_err), P->stream));
+  const gw::TcOperand Uop{{as<__nv_bfloat16>(P->mr_Uhi), as<__nv_bfloat16>(P->mr_Ulo), ulo2}};
+  const gw::TcOperand Bop{{P->d_Bhi, P->d_Blo, three ? P->d_Blo2 : nullptr}};
+  CK(gw::tc_gemm_ex(Uop, 1, Bop, 0, ns, 2 * nr, n, n_ov, 0, e2, as<int>(P->tc_err), P->stream));
   P->stats.n_kernel_launches += 3;
-  (void)ldn;
   return GW_OK;
 }
 
@@ -683,6 +688,10 @@ gw_status residues_T(gw_plan* P, int nr_total, const int* d_rt, const int* d_rm,
     TRY(ensure(P, P->mr_Vlo, sizeof(__nv_bfloat16) * 2 * (size_t)batch * gw::tc_ld(n)));
     TRY(ensure(P, P->mr_Uhi, sizeof(__nv_bfloat16) * 2 * (size_t)batch * gw::tc_ld(n_ov)));
     TRY(ensure(P, P->mr_Ulo, sizeof(__nv_bfloat16) * 2 * (size_t)batch * gw::tc_ld(n_ov)));
+    if (P->cfg.op_parts >= 3) {
+      TRY(ensure(P, P->mr_Vlo2, sizeof(__nv_bfloat16) * 2 * (size_t)batch * gw::tc_ld(n)));
+      TRY(ensure(P, P->mr_Ulo2, sizeof(__nv_bfloat16) * 2 * (size_t)batch * gw::tc_ld(n_ov)));
+    }
     TRY(ensure(P, P->tc_err, sizeof(int)));
     CK(cudaMemsetAsync(P->tc_err.p, 0, sizeof(int), P->stream));
   }
@@ -892,6 +901,7 @@ void gw_config_default(gw_config* c) {
   c->static_subtraction = 1;
   c->max_rhs_batch = 0;
   c->refine_tol = 1e-6;
+  c->op_parts = 2;
 }
 
 static void free_plan(gw_plan* P) {
@@ -1045,6 +1055,8 @@ gw_status gw_plan_create(const gw_config* cfg, const double* eps, const double* 
   if (!(cfg->x0 > 0.0) && !xi) return fail(nullptr, GW_ERR_ARG, "x0 must be positive");
   if (!(cfg->eta >= 0.0)) return fail(nullptr, GW_ERR_ARG, "eta must be >= 0");
   if (cfg->minres_maxit < 0 || cfg->qp_maxit <= 0) return fail(nullptr, GW_ERR_ARG, "bad iteration caps");
+  if (cfg->op_parts != 2 && cfg->op_parts != 3)
+    return fail(nullptr, GW_ERR_ARG, "op_parts must be 2 or 3 (got %d)", cfg->op_parts);
   const int n_bas = cfg->n_occ + cfg->n_virt;
   for (int i = 0; i < n_bas; ++i) {
     if (!std::isfinite(eps[i])) return fail(nullptr, GW_ERR_ARG, "eps[%d] is not finite", i);

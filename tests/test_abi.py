@@ -77,6 +77,9 @@ def test_bad_arguments_rejected_without_gpu(gwlib):
     cfg = gw.default_config(n_occ=2, n_virt=2, n_aux=4, precision=7)
     st, h, msg = _create(gwlib, cfg, [-1.0, -0.5, 0.5, 0.7])
     assert st == gw.GW_ERR_ARG and "precision" in msg
+    cfg = gw.default_config(n_occ=2, n_virt=2, n_aux=4, op_parts=4)
+    st, h, msg = _create(gwlib, cfg, [-1.0, -0.5, 0.5, 0.7])
+    assert st == gw.GW_ERR_ARG and "op_parts" in msg
     assert gwlib.gw_grid(0, 0.5, None, None) == gw.GW_ERR_ARG
     assert gwlib.gw_polarizability(None, None, 0, None) == gw.GW_ERR_ARG
     gwlib.gw_plan_destroy(None)
