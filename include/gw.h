@@ -82,6 +82,8 @@ typedef struct {
   int op_parts;                /* mixed: BF16 parts per operand of the MINRES operator: 2 (hi, lo: three products,
                                   about 2^-16 relative; default) or 3 (hi, mid, lo: six products, about
                                   FP32-accurate) */
+  int deriv_fp64;              /* mixed: residue derivative pass y^T Pi'(x) y in FP64 (1) or FP32 with FP64
+                                  reduction (0, default) */
 } gw_config;
 
 typedef struct gw_plan* gw_plan_t;

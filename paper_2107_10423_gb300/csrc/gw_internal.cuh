@@ -34,12 +34,20 @@ int trsm_w_default_ctas();
 // Matrix-free operator of the residue systems (MINRES), for a batch of nr right-hand sides.
 // V: [2nr][n_aux] pairs (u, v) encoding z = u - i v.
 // gemm1: U[2j..2j+1][k] = c_k(x_j) * t_k (mode 0) or c'_k(x_j) * t_k^2 (mode 1), t = B^T z
-//   with c_k(x) = 2[1/(x-D_k+i eta) + 1/(-x-D_k+i eta)], c' its x-derivative.
+//   with c_k(x) = 2[1/(x-D_k+i eta) + 1/(-x-D_k+i eta)], c' its x-derivative;
+//   mode 2: dw[j] += sum_k Re(c'_k(x_j) t_k^2) in FP64 (dw zeroed by the caller, U unused), skipping the pairs
+//   with |x_j - D_k| < cut or |-x_j - D_k| < cut (added by launch_deriv_resonant).
 // gemm2: S[r][P] = sum_k U[r][k] B[P][k]; mode 0 writes S (= [Re; Im] of Pi z),
 //   mode 1 writes the real embedding [u - S_re; -v - S_im] of (1 - Pi) z.
 template <typename T>
 void launch_op_gemm1(const T* V, const T* B, const double* eps, int n_occ, int n_virt, int n_aux, const double* x,
-                     double eta, int nr, T* U, int mode, cudaStream_t s);
+                     double eta, int nr, T* U, int mode, cudaStream_t s, double* dw = nullptr,
+                     double cut = 0.0);
+// The pairs that mode 2 skips, in FP64: dw[j] += Re(c'_k(x_j) t_k^2) with t from the FP64 rows of V64 and the FP64
+// B_ia [n_aux][n_ov]; Dsort ascending pair energies with their pair indices kidx.
+void launch_deriv_resonant(const double* V64, const double* B, long n_ov, int n_aux, const double* Dsort,
+                           const int* kidx, const double* xs, int nr, double eta, double cut, double* dw,
+                           cudaStream_t s);
 template <typename T>
 void launch_op_gemm2(const T* U, const T* B, int n_aux, int n_ov, int nr, const T* V, T* out, int mode,
                      cudaStream_t s);
@@ -69,11 +77,12 @@ void launch_minres_init(const T* S, int nr, int n_aux, double* vprev, double* v,
 template <typename T>
 void launch_minres_step(const T* P, int nr, int n_aux, double tol, double* vprev, double* v, double* d1, double* d2,
                         double* x, MinresState* st, T* V, int* n_active, cudaStream_t s);
-// After MINRES: W = b^T delta; y = b + delta written into V as (u, v) = (y_r, -y_i) for the derivative pass.
+// After MINRES: W = b^T delta; y = b + delta written into V as (u, v) = (y_r, -y_i) for the derivative pass
+// (and into V64 in FP64 when given).
 template <typename T>
 void launch_minres_finish(const double* B_nm, int n_bas, int n_aux, const int* rhs_t, const int* rhs_m, int nr,
                           const double* x, const MinresState* st, double* w_re, double* w_im, int* iters,
-                          double* resnorm, T* V, cudaStream_t s);
+                          double* resnorm, T* V, cudaStream_t s, double* V64 = nullptr);
 // dW_j = sum_k U[2j][k] + i U[2j+1][k] (derivative pass output); writes Re into dw_re.
 template <typename T>
 void launch_rowsum_pairs(const T* U, int nr, int n_ov, double* dw_re, double* dw_im, cudaStream_t s);
@@ -107,9 +116,11 @@ void launch_refine_v64(int m, int n_aux, const int* sel, const double* y64, doub
 template <typename T>
 void launch_fallback_finish64(const double* B_nm, int n_bas, int n_aux, const int* rt, const int* rm, const int* idx,
                               int nf, const double* y64, double* w_re, double* w_im, double* resnorm, T* V,
-                              cudaStream_t s);
+                              cudaStream_t s, double* V64 = nullptr);
 
 // R term reduction per target over its right-hand sides [start[t], start[t+1]).
+// W[r][g] += W[r][n_g] for g < n_cols (table [R][n_g + 1]): columns held as differences from the static one.
+void launch_w_add_static(double* W, long R, int n_g, int n_cols, cudaStream_t s);
 void launch_residue_reduce(const int* start, int n_t, const double* coef, const double* w_re, const double* dw_re,
                            double* R, double* dR, cudaStream_t s);
 

@@ -53,6 +53,9 @@ struct gw_plan {
   __nv_bfloat16* d_Blo2 = nullptr;  // mixed: third split parts of B_ia and B_ia^T (refinement operator)
   __nv_bfloat16* d_BTlo2 = nullptr;
   double* d_D = nullptr;            // pair energies D_ia [n_ov]
+  double* d_Dsort = nullptr;        // mixed: D_ia ascending, with the pair index of each entry in d_Dkidx
+  int* d_Dkidx = nullptr;
+  double D_min = 0.0;               // smallest pair energy
   __nv_bfloat16* d_Bnhi = nullptr;  // mixed: BF16 hi/lo split of the B_nm rows, [n_t*n_bas][tc_ld(n_aux)]
   __nv_bfloat16* d_Bnlo = nullptr;
   __nv_bfloat16* d_Bnlo2 = nullptr;
@@ -60,10 +63,12 @@ struct gw_plan {
   int ns_iters_last = 0;
   float ns_lam_global = 0.f;   // spectrum bound of eps(i xi) for every xi: lambda_max(eps(0)), padded
   int ns_kmax = 0;
+  int ns_ndiff = 0;           // lowest grid points whose W column is built in the difference form
   std::vector<DevBuf*> bufs;
-  DevBuf ws_mat, ws_info, ws_scratch, ws_gout, ws_xi, tc_Ahi, tc_Alo, tc_kind, tc_par, tc_err, tc_w, ns_E, ns_X, ns_X2, ns_Xa, ns_Xb, ns_T, ns_lam;
+  DevBuf ws_mat, ws_info, ws_scratch, ws_gout, ws_xi, tc_Ahi, tc_Alo, tc_kind, tc_par, tc_err, tc_w, ns_E, ns_X, ns_X2, ns_Xa, ns_Xb, ns_T, ns_lam,
+      ns_E0;
   DevBuf mr_V, mr_U, mr_S, mr_vprev, mr_v, mr_d1, mr_d2, mr_x, mr_st, mr_rt, mr_rm, mr_xf, mr_wre, mr_wim,
-      mr_dwre, mr_it, mr_res, mr_cnt, mr_Vhi, mr_Vlo, mr_Uhi, mr_Ulo, mr_Vlo2, mr_Ulo2;
+      mr_dwre, mr_it, mr_res, mr_cnt, mr_Vhi, mr_Vlo, mr_Uhi, mr_Ulo, mr_Vlo2, mr_Ulo2, mr_V64;
   DevBuf sg_I, sg_dI, sg_R, sg_dR, sg_om, sg_start, sg_coef, sg_act, qp_st;
   DevBuf fb_A, fb_y, fb_piv, fb_info, fb_idx, fb_y64, fb_V32, fb_S32, fb_Vp, fb_Up, fb_x, fb_V64, fb_U64, fb_S64, fb_sel,
       fb_pos, fb_rho, fb_xs;
@@ -78,9 +83,9 @@ struct gw_plan {
   std::vector<Mark> marks;
 
   gw_plan() {
-    DevBuf* all[] = {&ws_mat, &ws_info, &ws_scratch, &ws_gout, &ws_xi, &tc_Ahi, &tc_Alo, &tc_kind, &tc_par, &tc_err, &tc_w, &ns_E, &ns_X, &ns_X2, &ns_Xa, &ns_Xb, &ns_T, &ns_lam, &mr_V, &mr_U, &mr_S, &mr_vprev,
+    DevBuf* all[] = {&ws_mat, &ws_info, &ws_scratch, &ws_gout, &ws_xi, &tc_Ahi, &tc_Alo, &tc_kind, &tc_par, &tc_err, &tc_w, &ns_E, &ns_X, &ns_X2, &ns_Xa, &ns_Xb, &ns_T, &ns_lam, &ns_E0, &mr_V, &mr_U, &mr_S, &mr_vprev,
                      &mr_v, &mr_d1, &mr_d2, &mr_x, &mr_st, &mr_rt, &mr_rm, &mr_xf, &mr_wre, &mr_wim,
-                     &mr_dwre, &mr_it, &mr_res, &mr_cnt, &mr_Vhi, &mr_Vlo, &mr_Uhi, &mr_Ulo, &mr_Vlo2, &mr_Ulo2, &sg_I, &sg_dI, &sg_R, &sg_dR, &sg_om, &sg_start,
+                     &mr_dwre, &mr_it, &mr_res, &mr_cnt, &mr_Vhi, &mr_Vlo, &mr_Uhi, &mr_Ulo, &mr_Vlo2, &mr_Ulo2, &mr_V64, &sg_I, &sg_dI, &sg_R, &sg_dR, &sg_om, &sg_start,
                      &sg_coef, &sg_act, &qp_st, &fb_A, &fb_y, &fb_piv, &fb_info, &fb_idx, &fb_y64, &fb_V32, &fb_S32, &fb_Vp, &fb_Up, &fb_x, &fb_V64, &fb_U64, &fb_S64, &fb_sel, &fb_pos, &fb_rho, &fb_xs};
     bufs.assign(all, all + sizeof(all) / sizeof(all[0]));
   }
@@ -315,18 +320,95 @@ gw_status ns_w_table(gw_plan* P, int g0, int nc) {
     P->stats.n_kernel_launches += 2;
   }
   mark(P, 2, t0, 2.0 * 2.0 * (double)(kmax - 1) * nc * (double)n * n * n);
-  // W[r][gout[g0 + b]] = b_r^T (eps^-1 - 1) b_r, reduced in the epilogue into the table zeroed before the chunks
-  const size_t t1 = tick(P);
-  gw::TcEpi ew{};
-  ew.kind = gw::TC_EPI_WRED;
-  ew.W = P->d_W;
-  ew.wld = n_g1;
-  ew.gidx = as<int>(P->ws_gout) + g0;
-  ew.bvec = P->d_B_nm_f;
-  ew.ldb = n;
+  // W table, reduced in the epilogue of one more GEMM into the table zeroed before the chunks:
+  //   static point and grid points g >= ns_ndiff:  W[r][g] = b_r^T (eps_g^-1 - 1) b_r
+  //   grid points g < ns_ndiff (xi_g well below every D_ia):
+  //     W[r][g] - W[r][n_g] = b_r^T eps_g^-1 M_g eps_0^-1 b_r,  M_g = Pi(i xi_g) - Pi(0)
+  //                         = 4 xi_g^2 sum_ia B_ia B_ia^T / (D_ia (D_ia^2 + xi_g^2))   (eps_g = eps_0 - M_g).
+  // The I term's omega-derivative weighs W_g - W_0 of the diagonal state by w_g/xi_g^2 at the first nodes; there
+  // the difference is O(xi^2) and, formed from two separately computed columns, it would carry their rounding
+  // error; in this form its error is relative to itself.  W[r][n_g] is added to those columns after the chunks.
   const gw::TcOperand Bn{{P->d_Bnhi, P->d_Bnlo, P->d_Bnlo2}};
-  CK(gw::tc_gemm_ex(Xs[cur], nc, Bn, 0, 3, n, R, n, 0, ew, as<int>(P->tc_err), P->stream));
-  mark(P, 3, t1, 2.0 * nc * (double)n * n * R);
+  auto wred = [&](const gw::TcOperand& A, int nb, int pos) {
+    gw::TcEpi ew{};
+    ew.kind = gw::TC_EPI_WRED;
+    ew.W = P->d_W;
+    ew.wld = n_g1;
+    ew.gidx = as<int>(P->ws_gout) + pos;
+    ew.bvec = P->d_B_nm_f;
+    ew.ldb = n;
+    return gw::tc_gemm_ex(A, nb, Bn, 0, 3, n, R, n, 0, ew, as<int>(P->tc_err), P->stream);
+  };
+  auto shift = [&](const gw::TcOperand& op, int b) {
+    return gw::TcOperand{{op.p[0] + b * smat, op.p[1] + b * smat, op.p[2] + b * smat}};
+  };
+  int b0 = 0;
+  if (g0 == 0) {
+    if (P->ns_ndiff > 0) {   // keep eps_0^-1 - 1 (split) for the difference columns of later chunks
+      TRY(ensure(P, P->ns_E0, 3 * sizeof(__nv_bfloat16) * smat));
+      __nv_bfloat16* e0 = as<__nv_bfloat16>(P->ns_E0);
+      for (int i = 0; i < 3; ++i)
+        CK(cudaMemcpyAsync(e0 + i * smat, Xs[cur].p[i], sizeof(__nv_bfloat16) * smat, cudaMemcpyDeviceToDevice,
+                           P->stream));
+    }
+    b0 = 1;
+  }
+  // positions [b0, b1) of this chunk are difference columns (position p > 0 holds grid point p - 1)
+  const int b1 = std::max(b0, std::min(nc, P->ns_ndiff + 1 - g0));
+  const size_t t1 = tick(P);
+  if (b0 > 0) CK(wred(Xs[cur], 1, g0));
+  if (nc > b1) CK(wred(shift(Xs[cur], b1), nc - b1, g0 + b1));
+  mark(P, 3, t1, 2.0 * (b0 + nc - b1) * (double)n * n * R);
+  const int nb = b1 - b0;
+  if (nb > 0) {
+    __nv_bfloat16* e0 = as<__nv_bfloat16>(P->ns_E0);
+    const gw::TcOperand E0{{e0, e0 + smat, e0 + 2 * smat}};
+    std::vector<int> kinds(nb, 4);
+    std::vector<double> xis(nb);
+    for (int b = 0; b < nb; ++b) xis[b] = P->h_xi[g0 + b0 + b - 1];
+    // M_b in FP32 (ws_mat: eps is no longer needed) and split (ns_E)
+    float* Mf = as<float>(P->ws_mat);
+    TRY(tc_weighted_syrk(P, kinds.data(), xis.data(), nb, 0, 0, Mf, 0));
+    const size_t t2 = tick(P);
+    CK(gw::tc_split_rows(Mf, nb * n, n, n, const_cast<__nv_bfloat16*>(E.p[0]), const_cast<__nv_bfloat16*>(E.p[1]),
+                         P->stream, const_cast<__nv_bfloat16*>(E.p[2])));
+    // C_b = M_b eps_0^-1 = M_b E_0 + M_b   (E_0 = eps_0^-1 - 1 is symmetric: its own K-major operand)
+    float* C = Xf[1 - xf];
+    gw::TcEpi e1{};
+    e1.kind = gw::TC_EPI_AXPBY;
+    e1.gamma = 1.f;
+    e1.alpha = 1.f;
+    e1.xin = Mf;
+    e1.x_bstride = (long)mat;
+    e1.out = C;
+    e1.out_bstride = (long)mat;
+    e1.ldo = n;
+    CK(gw::tc_gemm_ex(E, nb, E0, 0, 3, n, n, n, 0, e1, as<int>(P->tc_err), P->stream));
+    // C_b^T = eps_0^-1 M_b, split, as the K-major operand of the next product
+    for (int b = 0; b < nb; ++b)
+      CK(gw::tc_transpose_split(C + b * mat, n, n, const_cast<__nv_bfloat16*>(T.p[0]) + b * smat,
+                                const_cast<__nv_bfloat16*>(T.p[1]) + b * smat, P->stream,
+                                const_cast<__nv_bfloat16*>(T.p[2]) + b * smat));
+    // K_b = eps_b^-1 M_b eps_0^-1 = E_b C_b + C_b, written split for the reduction
+    gw::TcEpi e2{};
+    e2.kind = gw::TC_EPI_AXPBY;
+    e2.gamma = 1.f;
+    e2.alpha = 1.f;
+    e2.xin = C;
+    e2.x_bstride = (long)mat;
+    e2.ldo = n;
+    e2.ohi = const_cast<__nv_bfloat16*>(Xs[1 - cur].p[0]);
+    e2.olo = const_cast<__nv_bfloat16*>(Xs[1 - cur].p[1]);
+    e2.olo2 = const_cast<__nv_bfloat16*>(Xs[1 - cur].p[2]);
+    e2.ldh = ldn;
+    e2.oh_bstride = (long)smat;
+    CK(gw::tc_gemm_ex(shift(Xs[cur], b0), nb, T, 1, 3, n, n, n, 0, e2, as<int>(P->tc_err), P->stream));
+    mark(P, 2, t2, 2.0 * 2.0 * nb * (double)n * n * n);
+    const size_t t3 = tick(P);
+    CK(wred(Xs[1 - cur], nb, g0 + b0));
+    mark(P, 3, t3, 2.0 * nb * (double)n * n * R);
+    P->stats.n_kernel_launches += 4 + nb;
+  }
   P->stats.n_kernel_launches += 5;
   int herr = 0;
   CK(cudaMemcpyAsync(&herr, P->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
@@ -366,6 +448,11 @@ gw_status screening_T(gw_plan* P, const T* B, const T* Bn) {
   TRY(ensure(P, P->ws_xi, sizeof(double) * n_g1));
   CK(cudaMemcpyAsync(P->ws_xi.p, xi_all.data(), sizeof(double) * n_g1, cudaMemcpyHostToDevice, P->stream));
   P->ns_kmax = 0;
+  // difference-form columns: grid points with xi_g below a tenth of the smallest pair energy (there
+  // |Pi(i xi_g) - Pi(0)| <= 1% of |Pi(0)|)
+  P->ns_ndiff = 0;
+  if (use_tc)
+    while (P->ns_ndiff < P->n_g && P->h_xi[P->ns_ndiff] < 0.1 * P->D_min) ++P->ns_ndiff;
   if (use_tc) CK(cudaMemsetAsync(P->d_W, 0, sizeof(double) * (size_t)R * n_g1, P->stream));   // W is accumulated
   std::vector<int> info(chunk);
   double ms_pi = 0.0;
@@ -402,6 +489,7 @@ gw_status screening_T(gw_plan* P, const T* B, const T* Bn) {
       if (info[i] != 0)
         return fail(P, GW_ERR_NUMERIC, "Cholesky of eps(i xi) failed at frequency %d, pivot %d", g0 + i, info[i]);
   }
+  if (use_tc && P->ns_ndiff > 0) LAUNCH(gw::launch_w_add_static(P->d_W, R, P->n_g, P->ns_ndiff, P->stream));
   P->stats.ms_pi = ms_pi;
   return GW_OK;
 }
@@ -429,6 +517,9 @@ gw_status ensure_screening(gw_plan* P) {
 }
 
 gw_status tc_operator3(gw_plan* P, int nf, const double* xf, const float* V32, float* S32);
+
+// Half-width (Ha) of the window around each resonance x = +-D_ia whose derivative terms are computed in FP64.
+constexpr double kResonantCut = 0.1;
 
 // Dense solves for the MINRES batch slots in `need` (Sec. 3.3: build the dielectric matrix and factorise).
 // A_j = 1 - Pi(x_j) is built on the tensor cores (mixed) or by the FP64 SIMT kernel, then factorised by the
@@ -572,7 +663,7 @@ gw_status dense_fallback(gw_plan* P, const std::vector<int>& need, const int* rt
         }
       }
       LAUNCH(gw::launch_fallback_finish64<T>(P->d_B_nm, P->n_bas, n, rt, rm, idx, nf, as<double>(P->fb_y64), w_re,
-                                             w_im, resnorm, as<T>(P->mr_V), P->stream));
+                                             w_im, resnorm, as<T>(P->mr_V), P->stream, as<double>(P->mr_V64)));
     } else {
       LAUNCH(gw::launch_fallback_finish<T>(P->d_B_nm, P->n_bas, n, rt, rm, as<int>(P->fb_idx) + k0, nf,
                                            as<T>(P->fb_y), w_re, w_im, resnorm, as<T>(P->mr_V), P->stream));
@@ -678,6 +769,9 @@ gw_status residues_T(gw_plan* P, int nr_total, const int* d_rt, const int* d_rm,
   TRY(ensure(P, P->mr_V, sizeof(T) * 2 * (size_t)batch * n));
   TRY(ensure(P, P->mr_S, sizeof(T) * 2 * (size_t)batch * n));
   TRY(ensure(P, P->mr_U, sizeof(T) * 2 * (size_t)batch * n_ov));
+  const bool d64 = (sizeof(T) == 4) && P->cfg.deriv_fp64;
+  if (sizeof(T) == 4) TRY(ensure(P, P->mr_V64, sizeof(double) * 2 * (size_t)batch * n));
+  double* V64 = (sizeof(T) == 4) ? as<double>(P->mr_V64) : nullptr;
   for (DevBuf* b : {&P->mr_vprev, &P->mr_v, &P->mr_d1, &P->mr_d2, &P->mr_x})
     TRY(ensure(P, *b, sizeof(double) * 2 * (size_t)batch * n));
   TRY(ensure(P, P->mr_st, sizeof(MinresState) * batch));
@@ -749,7 +843,7 @@ gw_status residues_T(gw_plan* P, int nr_total, const int* d_rt, const int* d_rm,
     }
     LAUNCH(gw::launch_minres_finish<T>(P->d_B_nm, P->n_bas, n, rt, rm, nr, as<double>(P->mr_x),
                                        as<MinresState>(P->mr_st), w_re + j0, w_im + j0, iters + j0, resnorm + j0,
-                                       as<T>(P->mr_V), P->stream));
+                                       as<T>(P->mr_V), P->stream, V64));
     // dense fallback for right-hand sides above the fallback threshold (Sec. 3.3, MINRES defaults paragraph)
     h_res.resize(nr);
     CK(cudaMemcpyAsync(h_res.data(), resnorm + j0, sizeof(double) * nr, cudaMemcpyDeviceToHost, P->stream));
@@ -761,10 +855,24 @@ gw_status residues_T(gw_plan* P, int nr_total, const int* d_rt, const int* d_rm,
       if (bad) need.push_back(j);
     }
     if (!need.empty()) TRY(dense_fallback<T>(P, need, rt, rm, xf, w_re + j0, w_im + j0, resnorm + j0));
-    // dW/dx = y^T Pi'(x) y
-    LAUNCH(gw::launch_op_gemm1<T>(as<T>(P->mr_V), B, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, xf, eta, nr,
-                                  as<T>(P->mr_U), 1, P->stream));
-    LAUNCH(gw::launch_rowsum_pairs<T>(as<T>(P->mr_U), nr, n_ov, dw_re + j0, nullptr, P->stream));
+    // dW/dx = y^T Pi'(x) y, reduced in FP64 inside the GEMM.  Mixed: the FP32 pass leaves out the pairs within
+    // kResonantCut of resonance, where c'(x) reaches 2/eta^2 and FP32 rounding of t = B^T y would dominate dW;
+    // those are added in FP64.
+    CK(cudaMemsetAsync(dw_re + j0, 0, sizeof(double) * nr, P->stream));
+    const size_t td = tick(P);
+    if (d64) {
+      LAUNCH(gw::launch_op_gemm1<double>(V64, P->d_B_ia, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, xf, eta, nr,
+                                         nullptr, 2, P->stream, dw_re + j0));
+    } else if (sizeof(T) == 4) {
+      LAUNCH(gw::launch_op_gemm1<T>(as<T>(P->mr_V), B, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, xf, eta, nr,
+                                    nullptr, 2, P->stream, dw_re + j0, kResonantCut));
+      LAUNCH(gw::launch_deriv_resonant(V64, P->d_B_ia, n_ov, n, P->d_Dsort, P->d_Dkidx, xf, nr, eta, kResonantCut,
+                                       dw_re + j0, P->stream));
+    } else {
+      LAUNCH(gw::launch_op_gemm1<T>(as<T>(P->mr_V), B, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, xf, eta, nr,
+                                    nullptr, 2, P->stream, dw_re + j0));
+    }
+    mark(P, 4, td, 2.0 * (2.0 * nr) * n * (double)n_ov);
   }
   return GW_OK;
 }
@@ -925,6 +1033,8 @@ static void free_plan(gw_plan* P) {
   if (P->d_Blo2) cudaFree(P->d_Blo2);
   if (P->d_BTlo2) cudaFree(P->d_BTlo2);
   if (P->d_D) cudaFree(P->d_D);
+  if (P->d_Dsort) cudaFree(P->d_Dsort);
+  if (P->d_Dkidx) cudaFree(P->d_Dkidx);
   if (P->d_Bnhi) cudaFree(P->d_Bnhi);
   if (P->d_Bnlo) cudaFree(P->d_Bnlo);
   if (P->d_Bnlo2) cudaFree(P->d_Bnlo2);
@@ -1018,6 +1128,16 @@ static gw_status plan_create_impl(gw_plan* P, const gw_config* cfg, const double
         for (int a = 0; a < cfg->n_virt; ++a) D[(size_t)i * cfg->n_virt + a] = eps[cfg->n_occ + a] - eps[i];
       CK(cudaMalloc(&P->d_D, sizeof(double) * P->n_ov));
       CK(cudaMemcpyAsync(P->d_D, D.data(), sizeof(double) * P->n_ov, cudaMemcpyHostToDevice, P->stream));
+      std::vector<int> order((size_t)P->n_ov);
+      for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
+      std::sort(order.begin(), order.end(), [&](int a, int b) { return D[a] < D[b]; });
+      std::vector<double> Ds(order.size());
+      for (size_t k = 0; k < order.size(); ++k) Ds[k] = D[order[k]];
+      P->D_min = Ds.empty() ? 0.0 : Ds[0];
+      CK(cudaMalloc(&P->d_Dsort, sizeof(double) * P->n_ov));
+      CK(cudaMalloc(&P->d_Dkidx, sizeof(int) * P->n_ov));
+      CK(cudaMemcpyAsync(P->d_Dsort, Ds.data(), sizeof(double) * P->n_ov, cudaMemcpyHostToDevice, P->stream));
+      CK(cudaMemcpyAsync(P->d_Dkidx, order.data(), sizeof(int) * P->n_ov, cudaMemcpyHostToDevice, P->stream));
       CK(cudaStreamSynchronize(P->stream));
     }
     CK(cudaStreamSynchronize(P->stream));

@@ -186,7 +186,8 @@ template <typename T>
 __global__ void minres_finish_kernel(const double* __restrict__ B_nm, int n_bas, int n_aux,
                                      const int* __restrict__ rt, const int* __restrict__ rm,
                                      const double* __restrict__ x, const MinresState* __restrict__ st,
-                                     double* w_re, double* w_im, int* iters, double* resnorm, T* V) {
+                                     double* w_re, double* w_im, int* iters, double* resnorm, T* V,
+                                     double* V64) {
   __shared__ double buf[32];
   const int j = blockIdx.x;
   const double* b = B_nm + ((long)rt[j] * n_bas + rm[j]) * n_aux;
@@ -198,6 +199,10 @@ __global__ void minres_finish_kernel(const double* __restrict__ B_nm, int n_bas,
     ai += b[i] * x2;
     V[off + i] = (T)(b[i] + x1);     // u = Re y = b + x1
     V[off + n_aux + i] = (T)x2;      // v = -Im y = x2   (delta = x1 - i x2)
+    if (V64) {
+      V64[off + i] = b[i] + x1;
+      V64[off + n_aux + i] = x2;
+    }
   }
   ar = block_sum(ar, buf);
   ai = block_sum(ai, buf);
@@ -328,7 +333,7 @@ template <typename T>
 __global__ void fallback_finish64_kernel(const double* __restrict__ B_nm, int n_bas, int n_aux,
                                          const int* __restrict__ rt, const int* __restrict__ rm,
                                          const int* __restrict__ idx, const double* __restrict__ y64, double* w_re,
-                                         double* w_im, double* resnorm, T* V) {
+                                         double* w_im, double* resnorm, T* V, double* V64) {
   __shared__ double buf[32];
   const int k = blockIdx.x, j = idx[k];
   const double* b = B_nm + ((long)rt[j] * n_bas + rm[j]) * n_aux;
@@ -340,6 +345,10 @@ __global__ void fallback_finish64_kernel(const double* __restrict__ B_nm, int n_
     ai += b[i] * yi[i];
     V[(long)(2 * j) * n_aux + i] = (T)yr[i];
     V[(long)(2 * j + 1) * n_aux + i] = (T)(-yi[i]);
+    if (V64) {
+      V64[(long)(2 * j) * n_aux + i] = yr[i];
+      V64[(long)(2 * j + 1) * n_aux + i] = -yi[i];
+    }
   }
   ar = block_sum(ar, buf);
   ai = block_sum(ai, buf);
@@ -359,6 +368,14 @@ __global__ void refine_v64_kernel(int n_aux, const int* __restrict__ sel, const 
     u[i] = y[i];
     u[n_aux + i] = -y[n_aux + i];
   }
+}
+
+__global__ void w_add_static_kernel(double* W, long R, int n_g, int n_cols) {
+  const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= R * n_cols) return;
+  const long r = i / n_cols;
+  const int g = (int)(i - r * n_cols);
+  W[r * (n_g + 1) + g] += W[r * (n_g + 1) + n_g];
 }
 
 __global__ void residue_reduce_kernel(const int* __restrict__ start, int n_t, const double* __restrict__ coef,
@@ -523,9 +540,10 @@ void launch_minres_step(const T* P, int nr, int n_aux, double tol, double* vprev
 template <typename T>
 void launch_minres_finish(const double* B_nm, int n_bas, int n_aux, const int* rhs_t, const int* rhs_m, int nr,
                           const double* x, const MinresState* st, double* w_re, double* w_im, int* iters,
-                          double* resnorm, T* V, cudaStream_t s) {
+                          double* resnorm, T* V, cudaStream_t s, double* V64) {
   if (nr > 0)
-    minres_finish_kernel<T><<<nr, RT, 0, s>>>(B_nm, n_bas, n_aux, rhs_t, rhs_m, x, st, w_re, w_im, iters, resnorm, V);
+    minres_finish_kernel<T><<<nr, RT, 0, s>>>(B_nm, n_bas, n_aux, rhs_t, rhs_m, x, st, w_re, w_im, iters, resnorm, V,
+                                              V64);
 }
 
 template <typename T>
@@ -556,15 +574,22 @@ void launch_refine(int stage, const double* B_nm, int n_bas, int n_aux, const in
 template <typename T>
 void launch_fallback_finish64(const double* B_nm, int n_bas, int n_aux, const int* rt, const int* rm, const int* idx,
                               int nf, const double* y64, double* w_re, double* w_im, double* resnorm, T* V,
-                              cudaStream_t s) {
+                              cudaStream_t s, double* V64) {
   if (nf > 0)
-    fallback_finish64_kernel<T><<<nf, RT, 0, s>>>(B_nm, n_bas, n_aux, rt, rm, idx, y64, w_re, w_im, resnorm, V);
+    fallback_finish64_kernel<T><<<nf, RT, 0, s>>>(B_nm, n_bas, n_aux, rt, rm, idx, y64, w_re, w_im, resnorm, V,
+                                                  V64);
 }
 template void launch_fallback_finish64<float>(const double*, int, int, const int*, const int*, const int*, int,
-                                              const double*, double*, double*, double*, float*, cudaStream_t);
+                                              const double*, double*, double*, double*, float*, cudaStream_t,
+                                              double*);
 
 void launch_refine_v64(int m, int n_aux, const int* sel, const double* y64, double* V64, cudaStream_t s) {
   if (m > 0) refine_v64_kernel<<<m, RT, 0, s>>>(n_aux, sel, y64, V64);
+}
+
+void launch_w_add_static(double* W, long R, int n_g, int n_cols, cudaStream_t s) {
+  const long nt = R * n_cols;
+  if (nt > 0) w_add_static_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(W, R, n_g, n_cols);
 }
 
 void launch_residue_reduce(const int* start, int n_t, const double* coef, const double* w_re, const double* dw_re,
@@ -589,7 +614,8 @@ void launch_qp_step(QPState* st, const double* R, const double* dR, const double
   template void launch_minres_step<T>(const T*, int, int, double, double*, double*, double*, double*, double*,    \
                                       MinresState*, T*, int*, cudaStream_t);                                      \
   template void launch_minres_finish<T>(const double*, int, int, const int*, const int*, int, const double*,      \
-                                        const MinresState*, double*, double*, int*, double*, T*, cudaStream_t);   \
+                                        const MinresState*, double*, double*, int*, double*, T*, cudaStream_t,    \
+                                        double*);                                                                 \
   template void launch_rowsum_pairs<T>(const T*, int, int, double*, double*, cudaStream_t);                      \
   template void launch_fallback_rhs<T>(const double*, int, int, const int*, const int*, const int*, int, T*,       \
                                        cudaStream_t);                                                            \

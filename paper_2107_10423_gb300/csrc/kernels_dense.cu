@@ -362,7 +362,8 @@ template <typename T>
 __global__ void __launch_bounds__(NT) op_gemm1_kernel(const T* __restrict__ V, const T* __restrict__ B,
                                                       const double* __restrict__ eps, int n_occ, int n_virt,
                                                       int n_aux, const double* __restrict__ xs, double eta, int nr,
-                                                      T* __restrict__ U, int mode) {
+                                                      T* __restrict__ U, int mode, double* __restrict__ dw,
+                                                      double cut) {
   __shared__ T As[TK][TM + 4];
   __shared__ T Bs[TK][TN + 4];
   const long n_ov = (long)n_occ * n_virt;
@@ -407,6 +408,36 @@ __global__ void __launch_bounds__(NT) op_gemm1_kernel(const T* __restrict__ V, c
     __syncthreads();
   }
   const double e2 = eta * eta;
+  if (mode == 2) {
+    // derivative pass fused with its reduction: dw[j] += sum_k Re(c'_k(x_j) t_k^2) in FP64 (no U round trip)
+#pragma unroll
+    for (int ip = 0; ip < 2; ++ip) {
+      const int r = m0 + 2 * ty + 32 * ip;
+      double sum = 0.0;
+      if (r < M) {
+        const double x = xs[r >> 1];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const long k = k0c + tx + 16 * j;
+          if (k >= n_ov) continue;
+          const double tr = (double)acc[2 * ip][j], ti = -(double)acc[2 * ip + 1][j];
+          const double D = pair_energy(eps, n_occ, n_virt, k);
+          const double a1 = x - D, a2 = -x - D;
+          if (fabs(a1) < cut || fabs(a2) < cut) continue;   // near resonance: FP64 pass (deriv_resonant)
+          const double d1 = a1 * a1 + e2, d2 = a2 * a2 + e2;
+          const double q1r = (a1 * a1 - e2) / (d1 * d1), q1i = -2.0 * a1 * eta / (d1 * d1);
+          const double q2r = (a2 * a2 - e2) / (d2 * d2), q2i = -2.0 * a2 * eta / (d2 * d2);
+          const double cr = 2.0 * (-q1r + q2r), ci = 2.0 * (-q1i + q2i);
+          sum += cr * (tr * tr - ti * ti) - ci * (2.0 * tr * ti);
+        }
+      }
+      // the 16 lanes tx of one ty hold the same row: reduce within each half warp
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      if (tx == 0 && r < M) atomicAdd(dw + (r >> 1), sum);
+    }
+    return;
+  }
 #pragma unroll
   for (int ip = 0; ip < 2; ++ip) {
     int r = m0 + 2 * ty + 32 * ip;           // even row of the pair
@@ -439,6 +470,80 @@ __global__ void __launch_bounds__(NT) op_gemm1_kernel(const T* __restrict__ V, c
       U[(long)r * n_ov + k] = (T)outr;
       U[(long)(r + 1) * n_ov + k] = (T)outi;
     }
+  }
+}
+
+// First index q of the ascending array with a[q] >= v.
+__device__ __forceinline__ long lower_index(const double* a, long n, double v) {
+  long lo = 0, hi = n;
+  while (lo < hi) {
+    const long mid = (lo + hi) >> 1;
+    if (a[mid] < v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// FP64 part of the fused derivative pass: the pairs k near resonance with x_j (|x_j - D_k| < cut or
+// |-x_j - D_k| < cut, the same test in the same arithmetic as the FP32 pass, which skips them).  One CTA per right-hand
+// side; candidate windows come from the ascending pair energies Dsort (pair index kidx), widened by cut on each side
+// and then filtered by the exact test, so every pair is counted once.  One warp per pair:
+// t_k = sum_P B[P][k] (u_P - i v_P) from the FP64 rows (u, v) = V64 rows (2j, 2j+1); dw[j] += Re(c'_k(x_j) t_k^2).
+__global__ void __launch_bounds__(256) deriv_resonant_kernel(const double* __restrict__ V64,
+                                                             const double* __restrict__ B, long n_ov, int n_aux,
+                                                             const double* __restrict__ Dsort,
+                                                             const int* __restrict__ kidx,
+                                                             const double* __restrict__ xs, double eta, double cut,
+                                                             double* __restrict__ dw) {
+  __shared__ long rng[4];
+  __shared__ double red[8];
+  const int j = blockIdx.x;
+  const double x = xs[j], e2 = eta * eta;
+  if (threadIdx.x == 0) {
+    long l1 = lower_index(Dsort, n_ov, x - 2.0 * cut), h1 = lower_index(Dsort, n_ov, x + 2.0 * cut);
+    long l2 = lower_index(Dsort, n_ov, -x - 2.0 * cut), h2 = lower_index(Dsort, n_ov, -x + 2.0 * cut);
+    if (l2 < h1 && l1 < h2) {   // overlapping windows: one merged window
+      l1 = l1 < l2 ? l1 : l2;
+      h1 = h1 > h2 ? h1 : h2;
+      l2 = h2 = 0;
+    }
+    rng[0] = l1; rng[1] = h1; rng[2] = l2; rng[3] = h2;
+  }
+  __syncthreads();
+  const double* u = V64 + (long)(2 * j) * n_aux;
+  const double* v = u + n_aux;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double sum = 0.0;
+  for (int w = 0; w < 2; ++w) {
+    for (long q = rng[2 * w] + warp; q < rng[2 * w + 1]; q += nw) {
+      const double D = Dsort[q];
+      const double a1 = x - D, a2 = -x - D;
+      if (!(fabs(a1) < cut || fabs(a2) < cut)) continue;   // warp-uniform
+      const long k = kidx[q];
+      double tr = 0.0, tv = 0.0;
+      for (int P = lane; P < n_aux; P += 32) {
+        const double b = B[(long)P * n_ov + k];
+        tr += b * u[P];
+        tv += b * v[P];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        tr += __shfl_xor_sync(0xffffffffu, tr, o);
+        tv += __shfl_xor_sync(0xffffffffu, tv, o);
+      }
+      const double ti = -tv;
+      const double d1 = a1 * a1 + e2, d2 = a2 * a2 + e2;
+      const double q1r = (a1 * a1 - e2) / (d1 * d1), q1i = -2.0 * a1 * eta / (d1 * d1);
+      const double q2r = (a2 * a2 - e2) / (d2 * d2), q2i = -2.0 * a2 * eta / (d2 * d2);
+      const double cr = 2.0 * (-q1r + q2r), ci = 2.0 * (-q1i + q2i);
+      if (lane == 0) sum += cr * (tr * tr - ti * ti) - ci * (2.0 * tr * ti);
+    }
+  }
+  if (lane == 0) red[warp] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += red[w];
+    atomicAdd(dw + j, t);
   }
 }
 
@@ -501,6 +606,12 @@ __global__ void __launch_bounds__(NT) op_gemm2_kernel(const T* __restrict__ U, c
 
 }  // namespace
 
+void launch_deriv_resonant(const double* V64, const double* B, long n_ov, int n_aux, const double* Dsort,
+                           const int* kidx, const double* xs, int nr, double eta, double cut, double* dw,
+                           cudaStream_t s) {
+  if (nr > 0) deriv_resonant_kernel<<<nr, 256, 0, s>>>(V64, B, n_ov, n_aux, Dsort, kidx, xs, eta, cut, dw);
+}
+
 // ------------------------------------------------------------------ launchers
 template <typename T>
 void launch_pi_syrk(const T* B, const double* eps, int n_occ, int n_virt, int n_aux, const double* xi, int n_xi,
@@ -547,10 +658,10 @@ void launch_trsm_w(const T* Lbase, long Lstride, int n, int n_g, const int* g_ou
 
 template <typename T>
 void launch_op_gemm1(const T* V, const T* B, const double* eps, int n_occ, int n_virt, int n_aux, const double* x,
-                     double eta, int nr, T* U, int mode, cudaStream_t s) {
+                     double eta, int nr, T* U, int mode, cudaStream_t s, double* dw, double cut) {
   long n_ov = (long)n_occ * n_virt;
   dim3 grid((unsigned)((n_ov + TN - 1) / TN), (2 * nr + TM - 1) / TM);
-  op_gemm1_kernel<T><<<grid, NT, 0, s>>>(V, B, eps, n_occ, n_virt, n_aux, x, eta, nr, U, mode);
+  op_gemm1_kernel<T><<<grid, NT, 0, s>>>(V, B, eps, n_occ, n_virt, n_aux, x, eta, nr, U, mode, dw, cut);
 }
 
 template <typename T>
@@ -568,7 +679,7 @@ void launch_op_gemm2(const T* U, const T* B, int n_aux, int n_ov, int nr, const 
   template void launch_trsm_w<T>(const T*, long, int, int, const int*, const T*, int, double*, int, T*, int,    \
                                  cudaStream_t);                                                                 \
   template void launch_op_gemm1<T>(const T*, const T*, const double*, int, int, int, const double*, double, int, \
-                                   T*, int, cudaStream_t);                                                      \
+                                   T*, int, cudaStream_t, double*, double);                                     \
   template void launch_op_gemm2<T>(const T*, const T*, int, int, int, const T*, T*, int, cudaStream_t);
 GW_INST(double)
 GW_INST(float)

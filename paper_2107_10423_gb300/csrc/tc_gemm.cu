@@ -380,10 +380,12 @@ __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bflo
   lo = __float2bfloat16_rn(v - __bfloat162float(hi));
 }
 
-// Weight kinds: 0 Pi(i xi): -4D/(D^2+xi^2);  1: Re c(x);  2: Im c(x);  3: 1 (plain split)
+// Weight kinds: 0 Pi(i xi): -4D/(D^2+xi^2);  1: Re c(x);  2: Im c(x);  3: 1 (plain split);
+// 4 Pi(i xi) - Pi(0): 4 xi^2/(D (D^2+xi^2))
 __device__ __forceinline__ double weight(int kind, double D, double p, double eta) {
   if (kind == 0) return -4.0 * D / (D * D + p * p);
   if (kind == 3) return 1.0;
+  if (kind == 4) return 4.0 * p * p / (D * (D * D + p * p));
   const double a1 = p - D, a2 = -p - D, e2 = eta * eta;
   const double d1 = a1 * a1 + e2, d2 = a2 * a2 + e2;
   if (kind == 1) return 2.0 * (a1 / d1 + a2 / d2);
