@@ -82,14 +82,16 @@ typedef struct {
   int op_parts;                /* mixed: BF16 parts per operand of the MINRES operator: 2 (hi, lo: three products,
                                   about 2^-16 relative; default) or 3 (hi, mid, lo: six products, about
                                   FP32-accurate) */
-  int deriv_fp64;              /* mixed: residue derivative pass y^T Pi'(x) y in FP64 (1) or FP32 with FP64
-                                  reduction (0, default) */
+  int deriv_fp64;              /* mixed: residue derivative pass y^T Pi'(x) y all in FP64 (1), or (0, default) FP32
+                                  products with an FP64 reduction and FP64 terms for the pairs within 0.1 Ha of
+                                  resonance (x = +-D_ia) */
 } gw_config;
 
 typedef struct gw_plan* gw_plan_t;
 
 /* Fill *cfg with defaults: n_freq 128, x0 0.5, eta 1e-3, FP64, MINRES 25 / 5e-5 / 1e-4,
- * qp_maxit 50, qp_tol 1e-8, static_subtraction 1.  Sizes are set to 0. */
+ * qp_maxit 50, qp_tol 1e-8, static_subtraction 1, refine_tol 1e-6, op_parts 2, deriv_fp64 0.
+ * Sizes are set to 0. */
 void gw_config_default(gw_config* cfg);
 
 /* Create a plan (Algorithm 1, Init).

@@ -81,3 +81,21 @@ def test_mixed_pi_accuracy(gw):
     for g, x in enumerate(xi):
         ref = O.pi_imag(s.eps, s.n_occ, B, x)
         assert np.abs(Pi[g] - ref).max() < 2e-5 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("deriv_fp64", [0, 1])
+def test_mixed_dsigma_at_the_ks_energy(gw, deriv_fp64):
+    """dSigma_c/domega at omega = e_n, the input of the linearised QP equation, against the oracle's exact CD.
+    At omega = e_n the I term weighs W(i xi) - W(0) of the diagonal state by w/xi^2 at the first grid nodes, and
+    residues sit near the poles of Pi(x); both are where FP32 rounding would show."""
+    s = synth.water_cluster(3, 43, targets="valence")
+    B, Bn = s.b_ia(), s.b_nm()
+    xi, wt = O.mgl_grid(128, 0.5)
+    cd = O.CDSelfEnergy(s.eps, s.n_occ, B, Bn, s.targets, xi, wt, eta=1e-3)
+    om = s.eps[s.targets]
+    with gw.Plan(s.eps, s.n_occ, B, Bn, s.targets, precision=gw.GW_PREC_MIXED, deriv_fp64=deriv_fp64) as p:
+        sc, dsc, _ = p.sigma_cd(om)
+    ref = np.array([cd.sigma_c(t, om[t]) for t in range(len(s.targets))])
+    print("dSigma_c error:", np.abs(dsc - ref[:, 1]).max(), " Sigma_c error meV:", np.abs(sc - ref[:, 0]).max() / MEV)
+    assert np.all(np.abs(sc - ref[:, 0]) < 1 * MEV), np.abs(sc - ref[:, 0]) / MEV
+    assert np.all(np.abs(dsc - ref[:, 1]) < 2e-5), np.abs(dsc - ref[:, 1])
