@@ -85,12 +85,14 @@ typedef struct {
   int deriv_fp64;              /* mixed: residue derivative pass y^T Pi'(x) y all in FP64 (1), or (0, default) FP32
                                   products with an FP64 reduction and FP64 terms for the pairs within 0.1 Ha of
                                   resonance (x = +-D_ia) */
+  int refine_df;               /* mixed: the FP64-accurate refinement residual in double-float arithmetic (FP32
+                                  pairs, 48-bit, on the FP32 pipes: 1, default) or in FP64 (0) */
 } gw_config;
 
 typedef struct gw_plan* gw_plan_t;
 
 /* Fill *cfg with defaults: n_freq 128, x0 0.5, eta 1e-3, FP64, MINRES 25 / 5e-5 / 1e-4,
- * qp_maxit 50, qp_tol 1e-8, static_subtraction 1, refine_tol 1e-6, op_parts 2, deriv_fp64 0.
+ * qp_maxit 50, qp_tol 1e-8, static_subtraction 1, refine_tol 1e-6, op_parts 2, deriv_fp64 0, refine_df 1.
  * Sizes are set to 0. */
 void gw_config_default(gw_config* cfg);
 

@@ -71,7 +71,7 @@ struct gw_plan {
       mr_dwre, mr_it, mr_res, mr_cnt, mr_Vhi, mr_Vlo, mr_Uhi, mr_Ulo, mr_Vlo2, mr_Ulo2, mr_V64;
   DevBuf sg_I, sg_dI, sg_R, sg_dR, sg_om, sg_start, sg_coef, sg_act, qp_st;
   DevBuf fb_A, fb_y, fb_piv, fb_info, fb_idx, fb_y64, fb_V32, fb_S32, fb_Vp, fb_Up, fb_x, fb_V64, fb_U64, fb_S64, fb_sel,
-      fb_pos, fb_rho, fb_xs;
+      fb_pos, fb_rho, fb_xs, fb_Bh, fb_Bl;
   int* h_cnt = nullptr;       // pinned
   std::string err;
   gw_stats stats{};
@@ -86,7 +86,7 @@ struct gw_plan {
     DevBuf* all[] = {&ws_mat, &ws_info, &ws_scratch, &ws_gout, &ws_xi, &tc_Ahi, &tc_Alo, &tc_kind, &tc_par, &tc_err, &tc_w, &ns_E, &ns_X, &ns_X2, &ns_Xa, &ns_Xb, &ns_T, &ns_lam, &ns_E0, &mr_V, &mr_U, &mr_S, &mr_vprev,
                      &mr_v, &mr_d1, &mr_d2, &mr_x, &mr_st, &mr_rt, &mr_rm, &mr_xf, &mr_wre, &mr_wim,
                      &mr_dwre, &mr_it, &mr_res, &mr_cnt, &mr_Vhi, &mr_Vlo, &mr_Uhi, &mr_Ulo, &mr_Vlo2, &mr_Ulo2, &mr_V64, &sg_I, &sg_dI, &sg_R, &sg_dR, &sg_om, &sg_start,
-                     &sg_coef, &sg_act, &qp_st, &fb_A, &fb_y, &fb_piv, &fb_info, &fb_idx, &fb_y64, &fb_V32, &fb_S32, &fb_Vp, &fb_Up, &fb_x, &fb_V64, &fb_U64, &fb_S64, &fb_sel, &fb_pos, &fb_rho, &fb_xs};
+                     &sg_coef, &sg_act, &qp_st, &fb_A, &fb_y, &fb_piv, &fb_info, &fb_idx, &fb_y64, &fb_V32, &fb_S32, &fb_Vp, &fb_Up, &fb_x, &fb_V64, &fb_U64, &fb_S64, &fb_sel, &fb_pos, &fb_rho, &fb_xs, &fb_Bh, &fb_Bl};
     bufs.assign(all, all + sizeof(all) / sizeof(all[0]));
   }
 };
@@ -646,11 +646,26 @@ gw_status dense_fallback(gw_plan* P, const std::vector<int>& need, const int* rt
           const size_t tr = tick(P);
           LAUNCH(gw::launch_refine_v64(m, n, as<int>(P->fb_sel), as<double>(P->fb_y64), as<double>(P->fb_V64),
                                        P->stream));
-          LAUNCH(gw::launch_op_gemm1<double>(as<double>(P->fb_V64), P->d_B_ia, P->d_eps, P->cfg.n_occ,
-                                             P->cfg.n_virt, n, as<double>(P->fb_xs), P->cfg.eta, m,
-                                             as<double>(P->fb_U64), 0, P->stream));
-          LAUNCH(gw::launch_op_gemm2<double>(as<double>(P->fb_U64), P->d_B_ia, n, P->n_ov, m,
-                                             as<double>(P->fb_V64), as<double>(P->fb_S64), 1, P->stream));
+          if (P->cfg.refine_df) {
+            // double-float (FP32 pair) residual: 48-bit products and sums on the FP32 pipes
+            if (!P->fb_Bh.p) {
+              const size_t nb = (size_t)n * P->n_ov;
+              TRY(ensure(P, P->fb_Bh, sizeof(float) * nb));
+              TRY(ensure(P, P->fb_Bl, sizeof(float) * nb));
+              LAUNCH(gw::launch_df_split(P->d_B_ia, (long)nb, as<float>(P->fb_Bh), as<float>(P->fb_Bl), P->stream));
+            }
+            LAUNCH(gw::launch_op_gemm1_df(as<double>(P->fb_V64), as<float>(P->fb_Bh), as<float>(P->fb_Bl), P->d_eps,
+                                          P->cfg.n_occ, P->cfg.n_virt, n, as<double>(P->fb_xs), P->cfg.eta, m,
+                                          as<double>(P->fb_U64), P->stream));
+            LAUNCH(gw::launch_op_gemm2_df(as<double>(P->fb_U64), as<float>(P->fb_Bh), as<float>(P->fb_Bl), n,
+                                          P->n_ov, m, as<double>(P->fb_V64), as<double>(P->fb_S64), P->stream));
+          } else {
+            LAUNCH(gw::launch_op_gemm1<double>(as<double>(P->fb_V64), P->d_B_ia, P->d_eps, P->cfg.n_occ,
+                                               P->cfg.n_virt, n, as<double>(P->fb_xs), P->cfg.eta, m,
+                                               as<double>(P->fb_U64), 0, P->stream));
+            LAUNCH(gw::launch_op_gemm2<double>(as<double>(P->fb_U64), P->d_B_ia, n, P->n_ov, m,
+                                               as<double>(P->fb_V64), as<double>(P->fb_S64), 1, P->stream));
+          }
           mark(P, 8, tr, 2.0 * 2.0 * (2.0 * m) * n * (double)P->n_ov);
           LAUNCH(gw::launch_refine(1, P->d_B_nm, P->n_bas, n, rt, rm, idx, nf, y32, as<double>(P->fb_y64),
                                    as<float>(P->fb_V32), nullptr, P->stream, as<double>(P->fb_S64),
@@ -1010,6 +1025,7 @@ void gw_config_default(gw_config* c) {
   c->max_rhs_batch = 0;
   c->refine_tol = 1e-6;
   c->op_parts = 2;
+  c->refine_df = 1;
 }
 
 static void free_plan(gw_plan* P) {

@@ -604,7 +604,201 @@ __global__ void __launch_bounds__(NT) op_gemm2_kernel(const T* __restrict__ U, c
   }
 }
 
+// ------------------------------------------------------------------ double-float GEMMs (refinement residual)
+// A double x is carried as the FP32 pair (h, l), h = fl(x), l = fl(x - h): 48 significant bits.  A multiply-add
+// s += a b takes the product exactly to FP32 pair precision (h*h by an FMA error term, plus the two cross terms)
+// and adds it with Knuth's TwoSum; the low word collects every rounding error and is folded in once at the end.
+// The _rn intrinsics keep the compiler from contracting the error-free steps into FMAs.
+__device__ __forceinline__ void df_split(double x, float& h, float& l) {
+  h = __double2float_rn(x);
+  l = __double2float_rn(x - (double)h);
+}
+
+__device__ __forceinline__ void df_mac(float ah, float al, float bh, float bl, float& sh, float& sl) {
+  const float ph = __fmul_rn(ah, bh);
+  float pe = __fmaf_rn(ah, bh, -ph);
+  pe = __fmaf_rn(ah, bl, pe);
+  pe = __fmaf_rn(al, bh, pe);
+  const float t = __fadd_rn(sh, ph);
+  const float v = __fsub_rn(t, sh);
+  const float e = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, v)), __fsub_rn(ph, v));
+  sl = __fadd_rn(sl, __fadd_rn(e, pe));
+  sh = t;
+}
+
+// df gemm1: U[r][k] for rows r of V [2nr][n_aux] (FP64) against B = Bh + Bl [n_aux][n_ov], then the complex
+// weights c_k(x_j) of the pair (2j, 2j+1) as in op_gemm1 mode 0; U in FP64.
+__global__ void __launch_bounds__(NT) op_gemm1_df_kernel(const double* __restrict__ V, const float* __restrict__ Bh,
+                                                         const float* __restrict__ Bl, const double* __restrict__ eps,
+                                                         int n_occ, int n_virt, int n_aux,
+                                                         const double* __restrict__ xs, double eta, int nr,
+                                                         double* __restrict__ U) {
+  __shared__ float Ah_s[TK][TM + 4], Al_s[TK][TM + 4];
+  __shared__ float Bh_s[TK][TN + 4], Bl_s[TK][TN + 4];
+  const long n_ov = (long)n_occ * n_virt;
+  const int M = 2 * nr;
+  const int m0 = blockIdx.y * TM;
+  const long k0c = (long)blockIdx.x * TN;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float ah_[4][4], al_[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) ah_[i][j] = al_[i][j] = 0.f;
+  for (int p0 = 0; p0 < n_aux; p0 += TK) {
+    {
+      const int r = tid >> 2, k4 = (tid & 3) * 4;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int P = p0 + k4 + u;
+        float h = 0.f, l = 0.f;
+        if (m0 + r < M && P < n_aux) df_split(V[(long)(m0 + r) * n_aux + P], h, l);
+        Ah_s[k4 + u][r] = h;
+        Al_s[k4 + u][r] = l;
+      }
+      const int kr = tid >> 4, c4 = (tid & 15) * 4;
+      const int P = p0 + kr;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const long k = k0c + c4 + u;
+        const bool in = P < n_aux && k < n_ov;
+        Bh_s[kr][c4 + u] = in ? Bh[(long)P * n_ov + k] : 0.f;
+        Bl_s[kr][c4 + u] = in ? Bl[(long)P * n_ov + k] : 0.f;
+      }
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < TK; ++kk) {
+      float a_h[4], a_l[4], b_h[4], b_l[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int c = 2 * ty + (i & 1) + 32 * (i >> 1);
+        a_h[i] = Ah_s[kk][c];
+        a_l[i] = Al_s[kk][c];
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        b_h[j] = Bh_s[kk][tx + 16 * j];
+        b_l[j] = Bl_s[kk][tx + 16 * j];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) df_mac(a_h[i], a_l[i], b_h[j], b_l[j], ah_[i][j], al_[i][j]);
+    }
+    __syncthreads();
+  }
+  const double e2 = eta * eta;
+#pragma unroll
+  for (int ip = 0; ip < 2; ++ip) {
+    const int r = m0 + 2 * ty + 32 * ip;
+    if (r >= M) continue;
+    const double x = xs[r >> 1];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const long k = k0c + tx + 16 * j;
+      if (k >= n_ov) continue;
+      const double tr = (double)ah_[2 * ip][j] + (double)al_[2 * ip][j];
+      const double ti = -((double)ah_[2 * ip + 1][j] + (double)al_[2 * ip + 1][j]);
+      const double D = pair_energy(eps, n_occ, n_virt, k);
+      const double a1 = x - D, a2 = -x - D;
+      const double d1 = a1 * a1 + e2, d2 = a2 * a2 + e2;
+      const double cr = 2.0 * (a1 / d1 + a2 / d2);
+      const double ci = -2.0 * eta * (1.0 / d1 + 1.0 / d2);
+      U[(long)r * n_ov + k] = cr * tr - ci * ti;
+      U[(long)(r + 1) * n_ov + k] = cr * ti + ci * tr;
+    }
+  }
+}
+
+// df gemm2: acc[r][P] = sum_k U[r][k] B[P][k]; out = the real embedding [u - acc_re; -v - acc_im] (op_gemm2 mode 1).
+__global__ void __launch_bounds__(NT) op_gemm2_df_kernel(const double* __restrict__ U, const float* __restrict__ Bh,
+                                                         const float* __restrict__ Bl, int n_aux, long n_ov, int nr,
+                                                         const double* __restrict__ V, double* __restrict__ out) {
+  __shared__ float Ah_s[TK][TM + 4], Al_s[TK][TM + 4];
+  __shared__ float Bh_s[TK][TN + 4], Bl_s[TK][TN + 4];
+  const int M = 2 * nr;
+  const int m0 = blockIdx.y * TM;
+  const int q0 = blockIdx.x * TN;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float ah_[4][4], al_[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) ah_[i][j] = al_[i][j] = 0.f;
+  const int lr = tid >> 2, lk = (tid & 3) * 4;
+  for (long k0 = 0; k0 < n_ov; k0 += TK) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long k = k0 + lk + u;
+      float h = 0.f, l = 0.f;
+      if (m0 + lr < M && k < n_ov) df_split(U[(long)(m0 + lr) * n_ov + k], h, l);
+      Ah_s[lk + u][lr] = h;
+      Al_s[lk + u][lr] = l;
+      const bool in = q0 + lr < n_aux && k < n_ov;
+      Bh_s[lk + u][lr] = in ? Bh[(long)(q0 + lr) * n_ov + k] : 0.f;
+      Bl_s[lk + u][lr] = in ? Bl[(long)(q0 + lr) * n_ov + k] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < TK; ++kk) {
+      float a_h[4], a_l[4], b_h[4], b_l[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int c = 2 * ty + (i & 1) + 32 * (i >> 1);
+        a_h[i] = Ah_s[kk][c];
+        a_l[i] = Al_s[kk][c];
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        b_h[j] = Bh_s[kk][tx + 16 * j];
+        b_l[j] = Bl_s[kk][tx + 16 * j];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) df_mac(a_h[i], a_l[i], b_h[j], b_l[j], ah_[i][j], al_[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = m0 + 2 * ty + (i & 1) + 32 * (i >> 1);
+    if (r >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int P = q0 + tx + 16 * j;
+      if (P >= n_aux) continue;
+      const double v = (double)ah_[i][j] + (double)al_[i][j];
+      const double vin = V[(long)r * n_aux + P];
+      out[(long)r * n_aux + P] = ((r & 1) ? -vin : vin) - v;
+    }
+  }
+}
+
+__global__ void df_split_kernel(const double* __restrict__ x, long n, float* __restrict__ h, float* __restrict__ l) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    df_split(x[i], h[i], l[i]);
+}
+
 }  // namespace
+
+void launch_df_split(const double* x, long n, float* h, float* l, cudaStream_t s) {
+  if (n > 0) df_split_kernel<<<1216, 256, 0, s>>>(x, n, h, l);
+}
+
+void launch_op_gemm1_df(const double* V, const float* Bh, const float* Bl, const double* eps, int n_occ, int n_virt,
+                        int n_aux, const double* x, double eta, int nr, double* U, cudaStream_t s) {
+  const long n_ov = (long)n_occ * n_virt;
+  const dim3 grid((unsigned)((n_ov + TN - 1) / TN), (2 * nr + TM - 1) / TM);
+  if (nr > 0) op_gemm1_df_kernel<<<grid, NT, 0, s>>>(V, Bh, Bl, eps, n_occ, n_virt, n_aux, x, eta, nr, U);
+}
+
+void launch_op_gemm2_df(const double* U, const float* Bh, const float* Bl, int n_aux, int n_ov, int nr,
+                        const double* V, double* out, cudaStream_t s) {
+  const dim3 grid((n_aux + TN - 1) / TN, (2 * nr + TM - 1) / TM);
+  if (nr > 0) op_gemm2_df_kernel<<<grid, NT, 0, s>>>(U, Bh, Bl, n_aux, (long)n_ov, nr, V, out);
+}
 
 void launch_deriv_resonant(const double* V64, const double* B, long n_ov, int n_aux, const double* Dsort,
                            const int* kidx, const double* xs, int nr, double eta, double cut, double* dw,

@@ -99,3 +99,18 @@ def test_mixed_dsigma_at_the_ks_energy(gw, deriv_fp64):
     print("dSigma_c error:", np.abs(dsc - ref[:, 1]).max(), " Sigma_c error meV:", np.abs(sc - ref[:, 0]).max() / MEV)
     assert np.all(np.abs(sc - ref[:, 0]) < 1 * MEV), np.abs(sc - ref[:, 0]) / MEV
     assert np.all(np.abs(dsc - ref[:, 1]) < 2e-5), np.abs(dsc - ref[:, 1])
+
+
+def test_double_float_refinement_residual_matches_fp64(gw):
+    """The refinement residual of the dense fallback solves in double-float arithmetic (FP32 pairs) against the
+    same residual in FP64: the QP energies agree far below the accuracy bar, and both match the oracle."""
+    s = synth.water_cluster(3, 43, targets="valence")
+    B, Bn = s.b_ia(), s.b_nm()
+    ref = O.g0w0_cd(s.eps, s.n_occ, B, Bn, s.targets, eta=1e-3, mode="linearised")
+    out = {}
+    for df in (0, 1):
+        with gw.Plan(s.eps, s.n_occ, B, Bn, s.targets, precision=gw.GW_PREC_MIXED, refine_df=df) as p:
+            out[df] = p.qp_solve(gw.GW_QP_LINEARISED)[0]
+            assert p.stats()["n_refine_fp64"] > 0
+    assert np.abs(out[1] - out[0]).max() < 0.01 * MEV, np.abs(out[1] - out[0]).max() / MEV
+    assert np.abs(out[1] - ref["e_qp"]).max() < 1 * MEV, np.abs(out[1] - ref["e_qp"]).max() / MEV
