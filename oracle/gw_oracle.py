@@ -14,7 +14,7 @@ Notation (Sec. 3.1-3.3): closed shell, orthonormal Coulomb-metric auxiliary
 basis, B[P, ia] = (P|ia) with pair index ia = i*n_virt + a, D_ia = e_a - e_i,
 b_nm = B[:, nm] for a target state n and any state m.
 
-Readings where the paper is silent or garbled (each one listed in the design doc):
+Readings where the paper is silent or garbled:
   * Pi on the imaginary axis uses eta = 0; on the real axis Pi(x) keeps the
     paper's +i*eta inside both pole terms and the residue frequency is the
     real x = e_m - omega (no second i*eta);
