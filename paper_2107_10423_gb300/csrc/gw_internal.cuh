@@ -33,9 +33,8 @@ int trsm_w_default_ctas();
 
 // Matrix-free operator of the residue systems (MINRES), for a batch of nr right-hand sides.
 // V: [2nr][n_aux] pairs (u, v) encoding z = u - i v.
-// gemm1: U[2j..2j+1][k] = c_k(x_j) * t_k (mode 0) or c'_k(x_j) * t_k^2 (mode 1), t = B^T z
-//   with c_k(x) = 2[1/(x-D_k+i eta) + 1/(-x-D_k+i eta)], c' its x-derivative;
-//   mode 2: dw[j] += sum_k Re(c'_k(x_j) t_k^2) in FP64 (dw zeroed by the caller, U unused), skipping the pairs
+// gemm1: mode 0: U[2j..2j+1][k] = c_k(x_j) * t_k, t = B^T z, with c_k(x) = 2[1/(x-D_k+i eta) + 1/(-x-D_k+i eta)];
+//   mode 2: dw[j] += sum_k Re(c'_k(x_j) t_k^2) in FP64, c' the x-derivative (dw zeroed by the caller, U unused), skipping the pairs
 //   with |x_j - D_k| < cut or |-x_j - D_k| < cut (added by launch_deriv_resonant).
 // gemm2: S[r][P] = sum_k U[r][k] B[P][k]; mode 0 writes S (= [Re; Im] of Pi z),
 //   mode 1 writes the real embedding [u - S_re; -v - S_im] of (1 - Pi) z.
@@ -90,9 +89,6 @@ template <typename T>
 void launch_minres_finish(const double* B_nm, int n_bas, int n_aux, const int* rhs_t, const int* rhs_m, int nr,
                           const double* x, const MinresState* st, double* w_re, double* w_im, int* iters,
                           double* resnorm, T* V, cudaStream_t s, double* V64 = nullptr);
-// dW_j = sum_k U[2j][k] + i U[2j+1][k] (derivative pass output); writes Re into dw_re.
-template <typename T>
-void launch_rowsum_pairs(const T* U, int nr, int n_ov, double* dw_re, double* dw_im, cudaStream_t s);
 
 // Batched complex LU with partial pivoting (kernels_lu.cu): matrices b at Ar + b*stride, Ai + b*stride.
 template <typename T>

@@ -216,25 +216,6 @@ __global__ void minres_finish_kernel(const double* __restrict__ B_nm, int n_bas,
 }
 
 template <typename T>
-__global__ void rowsum_pairs_kernel(const T* __restrict__ U, long n_ov, double* dw_re, double* dw_im) {
-  __shared__ double buf[32];
-  const int j = blockIdx.x;
-  const T* ur = U + (long)(2 * j) * n_ov;
-  const T* ui = ur + n_ov;
-  double sr = 0.0, si = 0.0;
-  for (long k = threadIdx.x; k < n_ov; k += blockDim.x) {
-    sr += (double)ur[k];
-    si += (double)ui[k];
-  }
-  sr = block_sum(sr, buf);
-  si = block_sum(si, buf);
-  if (threadIdx.x == 0) {
-    dw_re[j] = sr;
-    if (dw_im) dw_im[j] = si;
-  }
-}
-
-template <typename T>
 __global__ void fallback_rhs_kernel(const double* __restrict__ B_nm, int n_bas, int n_aux, const int* __restrict__ rt,
                                     const int* __restrict__ rm, const int* __restrict__ idx, T* __restrict__ y) {
   const int k = blockIdx.x, j = idx[k];
@@ -547,11 +528,6 @@ void launch_minres_finish(const double* B_nm, int n_bas, int n_aux, const int* r
 }
 
 template <typename T>
-void launch_rowsum_pairs(const T* U, int nr, int n_ov, double* dw_re, double* dw_im, cudaStream_t s) {
-  if (nr > 0) rowsum_pairs_kernel<T><<<nr, RT, 0, s>>>(U, (long)n_ov, dw_re, dw_im);
-}
-
-template <typename T>
 void launch_fallback_rhs(const double* B_nm, int n_bas, int n_aux, const int* rt, const int* rm, const int* idx,
                          int nf, T* y, cudaStream_t s) {
   if (nf > 0) fallback_rhs_kernel<T><<<nf, RT, 0, s>>>(B_nm, n_bas, n_aux, rt, rm, idx, y);
@@ -616,7 +592,6 @@ void launch_qp_step(QPState* st, const double* R, const double* dR, const double
   template void launch_minres_finish<T>(const double*, int, int, const int*, const int*, int, const double*,      \
                                         const MinresState*, double*, double*, int*, double*, T*, cudaStream_t,    \
                                         double*);                                                                 \
-  template void launch_rowsum_pairs<T>(const T*, int, int, double*, double*, cudaStream_t);                      \
   template void launch_fallback_rhs<T>(const double*, int, int, const int*, const int*, const int*, int, T*,       \
                                        cudaStream_t);                                                            \
   template void launch_fallback_finish<T>(const double*, int, int, const int*, const int*, const int*, int,       \

@@ -409,7 +409,8 @@ __global__ void __launch_bounds__(NT) op_gemm1_kernel(const T* __restrict__ V, c
   }
   const double e2 = eta * eta;
   if (mode == 2) {
-    // derivative pass fused with its reduction: dw[j] += sum_k Re(c'_k(x_j) t_k^2) in FP64 (no U round trip)
+    // derivative pass fused with its reduction: dw[j] += sum_k Re(c'_k(x_j) t_k^2) in FP64 (no U round trip),
+    // c' = 2[-(a1 - i eta)^2/d1^2 + (a2 - i eta)^2/d2^2]
 #pragma unroll
     for (int ip = 0; ip < 2; ++ip) {
       const int r = m0 + 2 * ty + 32 * ip;
@@ -452,21 +453,10 @@ __global__ void __launch_bounds__(NT) op_gemm1_kernel(const T* __restrict__ V, c
       double D = pair_energy(eps, n_occ, n_virt, k);
       double a1 = x - D, a2 = -x - D;
       double d1 = a1 * a1 + e2, d2 = a2 * a2 + e2;
-      double outr, outi;
-      if (mode == 0) {
-        double cr = 2.0 * (a1 / d1 + a2 / d2);
-        double ci = -2.0 * eta * (1.0 / d1 + 1.0 / d2);
-        outr = cr * tr - ci * ti;
-        outi = cr * ti + ci * tr;
-      } else {
-        // c' = 2[-(a1 - i eta)^2/d1^2 + (a2 - i eta)^2/d2^2]
-        double q1r = (a1 * a1 - e2) / (d1 * d1), q1i = -2.0 * a1 * eta / (d1 * d1);
-        double q2r = (a2 * a2 - e2) / (d2 * d2), q2i = -2.0 * a2 * eta / (d2 * d2);
-        double cr = 2.0 * (-q1r + q2r), ci = 2.0 * (-q1i + q2i);
-        double t2r = tr * tr - ti * ti, t2i = 2.0 * tr * ti;
-        outr = cr * t2r - ci * t2i;
-        outi = cr * t2i + ci * t2r;
-      }
+      const double cr = 2.0 * (a1 / d1 + a2 / d2);
+      const double ci = -2.0 * eta * (1.0 / d1 + 1.0 / d2);
+      const double outr = cr * tr - ci * ti;
+      const double outi = cr * ti + ci * tr;
       U[(long)r * n_ov + k] = (T)outr;
       U[(long)(r + 1) * n_ov + k] = (T)outi;
     }
