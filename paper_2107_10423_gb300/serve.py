@@ -36,13 +36,14 @@ class Job:
 
 
 def footprint_bytes(system, mixed: bool = True, workspace_mb: int = 0) -> int:
-    """Device bytes a job holds: B_ia and B_nm in FP64, their FP32 copies and BF16 split operands (mixed), plus the
+    """Device bytes a job holds: B_ia and B_nm in FP64, and in mixed mode their FP32 copies, the three BF16 parts of
+    B_ia, of its transpose and of B_nm, and the FP32 pair of B_ia for the double-float refinement residual; plus the
     work-space classes (frequency matrices, split operands, fallback matrices), each capped by workspace_mb."""
     n_aux, n_ov = system.n_aux, system.n_ov
     nbn = len(system.targets) * system.n_bas * n_aux
     b = 8 * (n_aux * n_ov + nbn)
     if mixed:
-        b += 4 * (n_aux * n_ov + nbn) + 4 * n_aux * n_ov * 2 + 6 * nbn
+        b += 4 * (n_aux * n_ov + nbn) + 2 * 3 * n_aux * n_ov * 2 + 6 * nbn + 8 * n_aux * n_ov
     ws = (workspace_mb if workspace_mb > 0 else 8192) << 20
     per_mat = n_aux * n_aux * (36 if mixed else 8)
     b += min(ws, 129 * per_mat) + min(ws, 2 * n_aux * n_ov * 4 * 2) + min(ws, 64 * 2 * n_aux * n_aux * 4)
