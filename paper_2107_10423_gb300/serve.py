@@ -76,9 +76,10 @@ def run_job(job: Job, precision: str = "mixed", qp: str = "linearised") -> dict:
 
 
 class Server:
-    """Arrival-driven continuous batching with admission by slots and HBM footprint."""
+    """Arrival-driven continuous batching with admission by slots and HBM footprint (default budget 250 GiB of the
+    GB300's 284 GB, which admits the largest job of the stream, (H2O)_64 in mixed precision, alone)."""
 
-    def __init__(self, max_slots: int = 4, hbm_budget: int = 200 << 30, executor=None, poll_s: float = 0.001):
+    def __init__(self, max_slots: int = 4, hbm_budget: int = 250 << 30, executor=None, poll_s: float = 0.001):
         self.max_slots = max_slots
         self.hbm_budget = hbm_budget
         self.executor = executor or run_job
