@@ -175,8 +175,20 @@ typedef struct {
   double flops_kernel[GW_N_KERNEL_CLASSES];
   long long launches_kernel[GW_N_KERNEL_CLASSES];
   long long n_refine_fp64;     /* dense-fallback solves that took the FP64-operator refinement step */
+  long long bytes_device;      /* device bytes the plan holds now (inputs it copied, their mixed-precision copies,
+                                  the W table and every work-space buffer) */
+  long long bytes_device_peak; /* largest bytes_device since plan creation */
 } gw_stats;
 gw_status gw_get_stats(gw_plan_t plan, gw_stats* out);
+
+/* Upper bound on the device bytes a plan with this configuration can hold (host only, no GPU needed), for
+ * admission by HBM footprint: the inputs it copies (none of B_ia and B_nm with GW_BORROW_DEVICE_PTRS), their
+ * mixed-precision copies, the W table, and every work-space class at the size cfg->workspace_mb caps it to (a class
+ * whose single item is larger than the cap is counted at that item's size).  Work space that grows with a call's
+ * own arguments is not included: gw_polarizability with explicit frequencies (n_xi matrices) and the right-hand-side
+ * lists of gw_residues_minres beyond n_targets * n_bas entries.  *bytes receives the bound.  Returns GW_ERR_ARG for
+ * NULL pointers or non-positive sizes. */
+gw_status gw_plan_footprint(const gw_config* cfg, int n_targets, unsigned flags, unsigned long long* bytes);
 
 /* The built-in imaginary-frequency grid (host only, no GPU needed): modified Gauss-Legendre
  * (Sec. 3.3, text after eq. "inn"): Legendre nodes t_k on [-1, 1] mapped by

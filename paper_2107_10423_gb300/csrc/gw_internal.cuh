@@ -25,8 +25,8 @@ void launch_cholesky(T* base, int n, long stride, int batch, int* info, cudaStre
 // W table from Cholesky factors: for matrices g in [0, n_g): y = L_g^-1 b_r for rows r of Bn [R][n],
 // W[r*w_ld + g_out[g]] = |y|^2 - |b|^2 = b^T(eps^-1 - 1)b.  scratch: [n_cta][n][64] elements of T.
 template <typename T>
-void launch_trsm_w(const T* Lbase, long Lstride, int n, int n_g, const int* g_out, const T* Bn, int R, double* W,
-                   int w_ld, T* scratch, int n_cta, cudaStream_t s);
+cudaError_t launch_trsm_w(const T* Lbase, long Lstride, int n, int n_g, const int* g_out, const T* Bn, int R,
+                          double* W, int w_ld, T* scratch, int n_cta, cudaStream_t s);
 template <typename T>
 size_t trsm_w_scratch_elems(int n, int n_cta);
 int trsm_w_default_ctas();

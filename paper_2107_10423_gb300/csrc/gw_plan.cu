@@ -126,16 +126,31 @@ gw_status fail(gw_plan* p, gw_status st, const char* fmt, ...) {
     if (s_ != GW_OK) return s_;                                                                    \
   } while (0)
 
+void count_bytes(gw_plan* P, long long delta) {
+  P->stats.bytes_device += delta;
+  P->stats.bytes_device_peak = std::max(P->stats.bytes_device_peak, P->stats.bytes_device);
+}
+
+// Device allocation counted in gw_stats.bytes_device.
+template <typename T>
+gw_status dmalloc(gw_plan* P, T** p, size_t bytes) {
+  CK(cudaMalloc(reinterpret_cast<void**>(p), bytes));
+  count_bytes(P, (long long)bytes);
+  return GW_OK;
+}
+
 gw_status ensure(gw_plan* P, DevBuf& b, size_t bytes) {
   if (b.bytes >= bytes && b.p) return GW_OK;
   if (b.p) {
     CK(cudaStreamSynchronize(P->stream));
     cudaFree(b.p);
+    count_bytes(P, -(long long)b.bytes);
     b.p = nullptr;
     b.bytes = 0;
   }
   if (bytes == 0) bytes = 16;
   CK(cudaMalloc(&b.p, bytes));
+  count_bytes(P, (long long)bytes);
   b.bytes = bytes;
   return GW_OK;
 }
@@ -184,8 +199,10 @@ double now_ms(gw_plan* P, cudaEvent_t a, cudaEvent_t b) {
 }
 
 // Tensor-core weighted SYRK for `nb` batch entries: out_b = f(B diag(w_b) B^T) with (kind, param) per entry.
+// reset_err = false keeps a bounded-wait code that earlier launches of the caller left in tc_err, so that the
+// check at the end reports it.
 gw_status tc_weighted_syrk(gw_plan* P, const int* kinds, const double* params, int nb, int mode_even, int mode_odd,
-                           float* out, int cls) {
+                           float* out, int cls, bool reset_err = true) {
   const int n = P->cfg.n_aux, K = P->n_ov, ld = gw::tc_ld(K);
   TRY(ensure(P, P->tc_Ahi, sizeof(__nv_bfloat16) * (size_t)nb * n * ld));
   TRY(ensure(P, P->tc_Alo, sizeof(__nv_bfloat16) * (size_t)nb * n * ld));
@@ -195,7 +212,7 @@ gw_status tc_weighted_syrk(gw_plan* P, const int* kinds, const double* params, i
   TRY(ensure(P, P->tc_w, sizeof(float) * (size_t)nb * K));
   CK(cudaMemcpyAsync(P->tc_kind.p, kinds, sizeof(int) * nb, cudaMemcpyHostToDevice, P->stream));
   CK(cudaMemcpyAsync(P->tc_par.p, params, sizeof(double) * nb, cudaMemcpyHostToDevice, P->stream));
-  CK(cudaMemsetAsync(P->tc_err.p, 0, sizeof(int), P->stream));
+  if (reset_err) CK(cudaMemsetAsync(P->tc_err.p, 0, sizeof(int), P->stream));
   const size_t t0 = tick(P);
   CK(gw::tc_scale_split(P->d_B_ia_f, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, K, as<int>(P->tc_kind),
                         as<double>(P->tc_par), P->cfg.eta, nb, as<float>(P->tc_w), as<__nv_bfloat16>(P->tc_Ahi),
@@ -368,7 +385,7 @@ gw_status ns_w_table(gw_plan* P, int g0, int nc) {
     for (int b = 0; b < nb; ++b) xis[b] = P->h_xi[g0 + b0 + b - 1];
     // M_b in FP32 (ws_mat: eps is no longer needed) and split (ns_E)
     float* Mf = as<float>(P->ws_mat);
-    TRY(tc_weighted_syrk(P, kinds.data(), xis.data(), nb, 0, 0, Mf, 0));
+    TRY(tc_weighted_syrk(P, kinds.data(), xis.data(), nb, 0, 0, Mf, 0, /*reset_err=*/false));
     const size_t t2 = tick(P);
     CK(gw::tc_split_rows(Mf, nb * n, n, n, const_cast<__nv_bfloat16*>(E.p[0]), const_cast<__nv_bfloat16*>(E.p[1]),
                          P->stream, const_cast<__nv_bfloat16*>(E.p[2])));
@@ -1095,13 +1112,13 @@ static gw_status plan_create_impl(gw_plan* P, const gw_config* cfg, const double
   }
   std::vector<double> xi_all(P->h_xi);
   xi_all.push_back(0.0);
-  CK(cudaMalloc(&P->d_eps, sizeof(double) * P->n_bas));
-  CK(cudaMalloc(&P->d_xi, sizeof(double) * (P->n_g + 1)));
-  CK(cudaMalloc(&P->d_wt, sizeof(double) * std::max(1, P->n_g)));
-  CK(cudaMalloc(&P->d_sx, sizeof(double) * std::max(1, n_targets)));
-  CK(cudaMalloc(&P->d_shift, sizeof(double) * std::max(1, n_targets)));
-  CK(cudaMalloc(&P->d_en, sizeof(double) * std::max(1, n_targets)));
-  CK(cudaMalloc(&P->d_W, sizeof(double) * (size_t)n_targets * P->n_bas * (P->n_g + 1)));
+  TRY(dmalloc(P, &P->d_eps, sizeof(double) * P->n_bas));
+  TRY(dmalloc(P, &P->d_xi, sizeof(double) * (P->n_g + 1)));
+  TRY(dmalloc(P, &P->d_wt, sizeof(double) * std::max(1, P->n_g)));
+  TRY(dmalloc(P, &P->d_sx, sizeof(double) * std::max(1, n_targets)));
+  TRY(dmalloc(P, &P->d_shift, sizeof(double) * std::max(1, n_targets)));
+  TRY(dmalloc(P, &P->d_en, sizeof(double) * std::max(1, n_targets)));
+  TRY(dmalloc(P, &P->d_W, sizeof(double) * (size_t)n_targets * P->n_bas * (P->n_g + 1)));
   CK(cudaMemcpyAsync(P->d_eps, eps, sizeof(double) * P->n_bas, cudaMemcpyHostToDevice, P->stream));
   CK(cudaMemcpyAsync(P->d_xi, xi_all.data(), sizeof(double) * (P->n_g + 1), cudaMemcpyHostToDevice, P->stream));
   CK(cudaMemcpyAsync(P->d_wt, P->h_wt.data(), sizeof(double) * P->n_g, cudaMemcpyHostToDevice, P->stream));
@@ -1112,37 +1129,37 @@ static gw_status plan_create_impl(gw_plan* P, const gw_config* cfg, const double
     P->d_B_nm = const_cast<double*>(B_nm);
   } else {
     P->own_B = true;
-    CK(cudaMalloc(&P->d_B_ia, sizeof(double) * nB));
-    CK(cudaMalloc(&P->d_B_nm, sizeof(double) * nBn));
+    TRY(dmalloc(P, &P->d_B_ia, sizeof(double) * nB));
+    TRY(dmalloc(P, &P->d_B_nm, sizeof(double) * nBn));
     cudaMemcpyKind kind = (flags & GW_INPUT_ON_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     CK(cudaMemcpyAsync(P->d_B_ia, B_ia, sizeof(double) * nB, kind, P->stream));
     CK(cudaMemcpyAsync(P->d_B_nm, B_nm, sizeof(double) * nBn, kind, P->stream));
   }
   if (cfg->precision == GW_PREC_MIXED) {
-    CK(cudaMalloc(&P->d_B_ia_f, sizeof(float) * nB));
-    CK(cudaMalloc(&P->d_B_nm_f, sizeof(float) * nBn));
+    TRY(dmalloc(P, &P->d_B_ia_f, sizeof(float) * nB));
+    TRY(dmalloc(P, &P->d_B_nm_f, sizeof(float) * nBn));
     LAUNCH((convert_f64_f32_kernel<<<1024, 256, 0, P->stream>>>(P->d_B_ia, P->d_B_ia_f, nB)));
     LAUNCH((convert_f64_f32_kernel<<<1024, 256, 0, P->stream>>>(P->d_B_nm, P->d_B_nm_f, nBn)));
     const size_t nsplit = (size_t)n * gw::tc_ld(P->n_ov);
-    CK(cudaMalloc(&P->d_Bhi, sizeof(__nv_bfloat16) * nsplit));
-    CK(cudaMalloc(&P->d_Blo, sizeof(__nv_bfloat16) * nsplit));
-    CK(cudaMalloc(&P->d_Blo2, sizeof(__nv_bfloat16) * nsplit));
+    TRY(dmalloc(P, &P->d_Bhi, sizeof(__nv_bfloat16) * nsplit));
+    TRY(dmalloc(P, &P->d_Blo, sizeof(__nv_bfloat16) * nsplit));
+    TRY(dmalloc(P, &P->d_Blo2, sizeof(__nv_bfloat16) * nsplit));
     CK(gw::tc_split_rows(P->d_B_ia_f, n, P->n_ov, P->n_ov, P->d_Bhi, P->d_Blo, P->stream, P->d_Blo2));
     const size_t nsplitN = (size_t)n_targets * P->n_bas * gw::tc_ld(n);
-    CK(cudaMalloc(&P->d_Bnhi, sizeof(__nv_bfloat16) * nsplitN));
-    CK(cudaMalloc(&P->d_Bnlo, sizeof(__nv_bfloat16) * nsplitN));
-    CK(cudaMalloc(&P->d_Bnlo2, sizeof(__nv_bfloat16) * nsplitN));
+    TRY(dmalloc(P, &P->d_Bnhi, sizeof(__nv_bfloat16) * nsplitN));
+    TRY(dmalloc(P, &P->d_Bnlo, sizeof(__nv_bfloat16) * nsplitN));
+    TRY(dmalloc(P, &P->d_Bnlo2, sizeof(__nv_bfloat16) * nsplitN));
     CK(gw::tc_split_rows(P->d_B_nm_f, n_targets * P->n_bas, n, n, P->d_Bnhi, P->d_Bnlo, P->stream, P->d_Bnlo2));
     const size_t nsplitT = (size_t)P->n_ov * gw::tc_ld(n);
-    CK(cudaMalloc(&P->d_BThi, sizeof(__nv_bfloat16) * nsplitT));
-    CK(cudaMalloc(&P->d_BTlo, sizeof(__nv_bfloat16) * nsplitT));
-    CK(cudaMalloc(&P->d_BTlo2, sizeof(__nv_bfloat16) * nsplitT));
+    TRY(dmalloc(P, &P->d_BThi, sizeof(__nv_bfloat16) * nsplitT));
+    TRY(dmalloc(P, &P->d_BTlo, sizeof(__nv_bfloat16) * nsplitT));
+    TRY(dmalloc(P, &P->d_BTlo2, sizeof(__nv_bfloat16) * nsplitT));
     CK(gw::tc_transpose_split(P->d_B_ia_f, n, P->n_ov, P->d_BThi, P->d_BTlo, P->stream, P->d_BTlo2));
     {
       std::vector<double> D((size_t)P->n_ov);
       for (int i = 0; i < cfg->n_occ; ++i)
         for (int a = 0; a < cfg->n_virt; ++a) D[(size_t)i * cfg->n_virt + a] = eps[cfg->n_occ + a] - eps[i];
-      CK(cudaMalloc(&P->d_D, sizeof(double) * P->n_ov));
+      TRY(dmalloc(P, &P->d_D, sizeof(double) * P->n_ov));
       CK(cudaMemcpyAsync(P->d_D, D.data(), sizeof(double) * P->n_ov, cudaMemcpyHostToDevice, P->stream));
       std::vector<int> order((size_t)P->n_ov);
       for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
@@ -1150,8 +1167,8 @@ static gw_status plan_create_impl(gw_plan* P, const gw_config* cfg, const double
       std::vector<double> Ds(order.size());
       for (size_t k = 0; k < order.size(); ++k) Ds[k] = D[order[k]];
       P->D_min = Ds.empty() ? 0.0 : Ds[0];
-      CK(cudaMalloc(&P->d_Dsort, sizeof(double) * P->n_ov));
-      CK(cudaMalloc(&P->d_Dkidx, sizeof(int) * P->n_ov));
+      TRY(dmalloc(P, &P->d_Dsort, sizeof(double) * P->n_ov));
+      TRY(dmalloc(P, &P->d_Dkidx, sizeof(int) * P->n_ov));
       CK(cudaMemcpyAsync(P->d_Dsort, Ds.data(), sizeof(double) * P->n_ov, cudaMemcpyHostToDevice, P->stream));
       CK(cudaMemcpyAsync(P->d_Dkidx, order.data(), sizeof(int) * P->n_ov, cudaMemcpyHostToDevice, P->stream));
       CK(cudaStreamSynchronize(P->stream));
@@ -1366,6 +1383,58 @@ gw_status gw_qp_solve(gw_plan_t P, gw_qp_mode mode, double* e_qp, double* z_fact
     if (state_status) state_status[t] = s;
   }
   return all_ok ? GW_OK : GW_ERR_NOT_CONVERGED;
+}
+
+gw_status gw_plan_footprint(const gw_config* c, int n_t, unsigned flags, unsigned long long* bytes) {
+  if (!c || !bytes || c->n_occ <= 0 || c->n_virt <= 0 || c->n_aux <= 0 || c->n_freq <= 0 || n_t <= 0)
+    return GW_ERR_ARG;
+  // Mirrors the allocations of plan_create_impl and of every ensure() class below, each at its cap.
+  typedef unsigned long long u64;
+  const bool mixed = c->precision == GW_PREC_MIXED;
+  const u64 n = c->n_aux, n_ov = (u64)c->n_occ * c->n_virt, n_bas = (u64)c->n_occ + c->n_virt;
+  const u64 n_g1 = (u64)c->n_freq + 1, ts = mixed ? 4 : 8;
+  const u64 ws = (u64)(c->workspace_mb > 0 ? c->workspace_mb : 8192) << 20;
+  const u64 ldo = (u64)gw::tc_ld((int)std::min<u64>(n_ov, 2147483647ull)), ldn = (u64)gw::tc_ld(c->n_aux);
+  const u64 rows = (u64)n_t * n_bas, nBn = rows * n;
+  auto capped = [ws](u64 item, u64 want) { return std::max(item, std::min(ws / std::max<u64>(item, 1) * item, want)); };
+  u64 b = 8 * (n_bas + 2 * n_g1 + 3 * (u64)n_t) + 8 * rows * n_g1;         // energies, grid, shifts, W table
+  if (!(flags & GW_BORROW_DEVICE_PTRS)) b += 8 * (n * n_ov + nBn);           // B_ia, B_nm
+  if (mixed) {
+    b += 4 * (n * n_ov + nBn);                                               // FP32 copies
+    b += 6 * (n * ldo + rows * ldn + n_ov * ldn);                             // three BF16 parts of B, B_nm, B^T
+    b += 20 * n_ov;                                                          // D, sorted D, pair index
+  }
+  // imaginary-axis stage: frequency matrices, info/index lists
+  b += capped(n * n * ts, n * n * ts * n_g1) + 24 * n_g1;
+  if (mixed) {
+    const u64 per_split = n * ldo * 4;                                       // weighted operand, hi + lo
+    const u64 nb = std::max<u64>(2, ws / std::max<u64>(per_split, 1));
+    b += capped(per_split, per_split * std::max<u64>(n_g1, 2)) + 4 * nb * n_ov + 16 * nb;
+    const u64 per_ns = n * ldn * 24 + n * n * 8;                             // Newton-Schulz split/FP32 iterates
+    b += capped(per_ns, per_ns * n_g1) + 6 * n * ldn + 4 * n_g1;             // + the split eps(0)^-1 - 1
+  } else {
+    b += 8 * (u64)gw::trsm_w_scratch_elems<double>(c->n_aux, gw::trsm_w_default_ctas());
+  }
+  // residue batch (at most one right-hand side per target and state at a time)
+  u64 batch = c->max_rhs_batch > 0 ? (u64)c->max_rhs_batch
+                                   : std::max<u64>(1, std::min<u64>((ws / 2) / (2 * n_ov * ts), 2048));
+  batch = std::min(batch, std::max<u64>(1, rows));
+  b += batch * (4 * n * ts + 2 * n_ov * ts + 10 * n * 8 + 64);               // V, S, U, Lanczos vectors, state
+  if (mixed) {
+    b += batch * (16 * n + 8 * ldn + 8 * ldo);                               // FP64 solutions, split V and U
+    if (c->op_parts >= 3) b += batch * (4 * ldn + 4 * ldo);
+  }
+  b += 48 * std::max<u64>(1, rows) + 8 * 6 * (u64)n_t + 64;                  // residue lists, Sigma scratch
+  // dense fallback batch
+  const u64 mat2 = 2 * n * n * ts;
+  const u64 fb = std::max<u64>(1, ws / mat2);
+  b += capped(mat2, mat2 * fb) + fb * (2 * n * ts + 8 * n + 8);
+  if (mixed) {
+    b += fb * (16 * n + 16 * n + 12 * ldn + 12 * ldo + 40);                  // FP64 solutions, V/S, split parts
+    b += fb * (32 * n + 16 * n_ov) + 8 * n * n_ov;                           // FP64-residual vectors, df split of B
+  }
+  *bytes = b;
+  return GW_OK;
 }
 
 gw_status gw_grid(int N, double x0, double* xi, double* wt) {

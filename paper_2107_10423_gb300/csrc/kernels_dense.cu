@@ -830,14 +830,18 @@ size_t trsm_w_scratch_elems(int n, int n_cta) {
 }
 
 template <typename T>
-void launch_trsm_w(const T* Lbase, long Lstride, int n, int n_g, const int* g_out, const T* Bn, int R, double* W,
-                   int w_ld, T* scratch, int n_cta, cudaStream_t s) {
+cudaError_t launch_trsm_w(const T* Lbase, long Lstride, int n, int n_g, const int* g_out, const T* Bn, int R,
+                          double* W, int w_ld, T* scratch, int n_cta, cudaStream_t s) {
   size_t smem = sizeof(T) * (2 * TK * (TM + 4) + 2 * 64 * 65) + sizeof(double) * 2 * 16 * 64;
-  cudaFuncSetAttribute(trsm_w_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(trsm_w_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   long items = (long)n_g * ((R + 63) / 64);
   int grid = (int)(items < n_cta ? items : n_cta);
-  if (grid <= 0) return;
-  trsm_w_kernel<T><<<grid, NT, smem, s>>>(Lbase, Lstride, n, n_g, g_out, Bn, R, W, w_ld, scratch);
+  if (grid <= 0) return cudaSuccess;
+  // cudaLaunchKernel returns this launch's own status (an earlier error pending on the thread is left alone)
+  void* args[] = {(void*)&Lbase, (void*)&Lstride, (void*)&n, (void*)&n_g, (void*)&g_out, (void*)&Bn,
+                  (void*)&R, (void*)&W, (void*)&w_ld, (void*)&scratch};
+  return cudaLaunchKernel((const void*)trsm_w_kernel<T>, dim3(grid), dim3(NT), args, smem, s);
 }
 
 template <typename T>
@@ -860,8 +864,8 @@ void launch_op_gemm2(const T* U, const T* B, int n_aux, int n_ov, int nr, const 
                                   cudaStream_t);                                                                \
   template void launch_cholesky<T>(T*, int, long, int, int*, cudaStream_t);                                     \
   template size_t trsm_w_scratch_elems<T>(int, int);                                                            \
-  template void launch_trsm_w<T>(const T*, long, int, int, const int*, const T*, int, double*, int, T*, int,    \
-                                 cudaStream_t);                                                                 \
+  template cudaError_t launch_trsm_w<T>(const T*, long, int, int, const int*, const T*, int, double*, int, T*,   \
+                                        int, cudaStream_t);                                                     \
   template void launch_op_gemm1<T>(const T*, const T*, const double*, int, int, int, const double*, double, int, \
                                    T*, int, cudaStream_t, double*, double);                                     \
   template void launch_op_gemm2<T>(const T*, const T*, int, int, int, const T*, T*, int, cudaStream_t);
@@ -925,7 +929,10 @@ extern "C" gw_status gw_w_table_noalloc(const double* L, int n_aux, int n_mats, 
   int n_cta = (int)(GW_NOALLOC_SCRATCH_BYTES / slice);
   const int full = gw::trsm_w_default_ctas();
   n_cta = n_cta < full ? n_cta : full;
-  gw::launch_trsm_w<double>(L, (long)n_aux * n_aux, n_aux, n_mats, d.index, Bn, n_rows, W, w_ld,
-                            static_cast<double*>(d.scratch), n_cta, static_cast<cudaStream_t>(stream));
-  return cudaGetLastError() == cudaSuccess ? GW_OK : GW_ERR_CUDA;
+  // the status is this launch's own (cudaFuncSetAttribute, then cudaLaunchKernel): an error that other work left
+  // pending on the thread is neither reported here nor cleared
+  const cudaError_t e = gw::launch_trsm_w<double>(L, (long)n_aux * n_aux, n_aux, n_mats, d.index, Bn, n_rows, W,
+                                                  w_ld, static_cast<double*>(d.scratch), n_cta,
+                                                  static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? GW_OK : GW_ERR_CUDA;
 }

@@ -17,7 +17,8 @@ GW_QP_LINEARISED, GW_QP_STEPTREE = 0, 1
 GW_INPUT_ON_DEVICE, GW_BORROW_DEVICE_PTRS = 1, 2
 
 EXPORTED = ["gw_config_default", "gw_plan_create", "gw_polarizability", "gw_sigma_cd", "gw_residues_minres",
-            "gw_qp_solve", "gw_grid", "gw_w_table", "gw_w_table_noalloc", "gw_get_stats", "gw_plan_destroy", "gw_last_error"]
+            "gw_qp_solve", "gw_grid", "gw_w_table", "gw_w_table_noalloc", "gw_get_stats", "gw_plan_destroy", "gw_last_error",
+            "gw_plan_footprint"]
 
 
 class GWError(RuntimeError):
@@ -41,7 +42,8 @@ class Stats(ctypes.Structure):
                 ("n_minres_iters", ctypes.c_longlong), ("n_fallback", ctypes.c_longlong),
                 ("n_sigma_evals", ctypes.c_longlong), ("n_kernel_launches", ctypes.c_longlong),
                 ("ms_kernel", ctypes.c_double * 9), ("flops_kernel", ctypes.c_double * 9),
-                ("launches_kernel", ctypes.c_longlong * 9), ("n_refine_fp64", ctypes.c_longlong)]
+                ("launches_kernel", ctypes.c_longlong * 9), ("n_refine_fp64", ctypes.c_longlong),
+                ("bytes_device", ctypes.c_longlong), ("bytes_device_peak", ctypes.c_longlong)]
 
 
 KERNEL_CLASSES = ["pi_tcgen05", "pi_simt", "w_table_factor", "w_table_reduce", "minres_operator_gemm", "minres_recurrence",
@@ -75,6 +77,9 @@ def load(path: str = LIB_PATH):
     lib.gw_w_table_noalloc.restype = ctypes.c_int
     lib.gw_w_table.argtypes = [_P, _P]
     lib.gw_w_table.restype = ctypes.c_int
+    lib.gw_plan_footprint.argtypes = [ctypes.POINTER(Config), ctypes.c_int, ctypes.c_uint,
+                                      ctypes.POINTER(ctypes.c_ulonglong)]
+    lib.gw_plan_footprint.restype = ctypes.c_int
     lib.gw_grid.argtypes = [ctypes.c_int, ctypes.c_double, _P, _P]
     lib.gw_grid.restype = ctypes.c_int
     lib.gw_plan_destroy.argtypes = [_P]
@@ -105,6 +110,17 @@ def grid(n: int, x0: float = 0.5):
     if st != GW_OK:
         raise GWError(st, "gw_grid")
     return xi, wt
+
+
+def footprint(n_occ, n_virt, n_aux, n_targets, borrow=False, **config) -> int:
+    """Upper bound on a plan's device bytes (gw_plan_footprint; host only)."""
+    cfg = default_config(n_occ=int(n_occ), n_virt=int(n_virt), n_aux=int(n_aux), **config)
+    out = ctypes.c_ulonglong()
+    st = load().gw_plan_footprint(ctypes.byref(cfg), int(n_targets), GW_BORROW_DEVICE_PTRS if borrow else 0,
+                                  ctypes.byref(out))
+    if st != GW_OK:
+        raise GWError(st, "gw_plan_footprint")
+    return int(out.value)
 
 
 def _ptr(a):

@@ -36,18 +36,11 @@ class Job:
 
 
 def footprint_bytes(system, mixed: bool = True, workspace_mb: int = 0) -> int:
-    """Device bytes a job holds: B_ia and B_nm in FP64, and in mixed mode their FP32 copies, the three BF16 parts of
-    B_ia, of its transpose and of B_nm, and the FP32 pair of B_ia for the double-float refinement residual; plus the
-    work-space classes (frequency matrices, split operands, fallback matrices), each capped by workspace_mb."""
-    n_aux, n_ov = system.n_aux, system.n_ov
-    nbn = len(system.targets) * system.n_bas * n_aux
-    b = 8 * (n_aux * n_ov + nbn)
-    if mixed:
-        b += 4 * (n_aux * n_ov + nbn) + 2 * 3 * n_aux * n_ov * 2 + 6 * nbn + 8 * n_aux * n_ov
-    ws = (workspace_mb if workspace_mb > 0 else 8192) << 20
-    per_mat = n_aux * n_aux * (36 if mixed else 8)
-    b += min(ws, 129 * per_mat) + min(ws, 2 * n_aux * n_ov * 4 * 2) + min(ws, 64 * 2 * n_aux * n_aux * 4)
-    return int(b)
+    """Device bytes a job may hold: the library's own bound for a plan of this size (gw_plan_footprint, computed from
+    the same caps the plan allocates by), with B_ia and B_nm copied in from the host."""
+    from . import gw
+    return gw.footprint(system.n_occ, system.n_virt, system.n_aux, len(system.targets), borrow=False,
+                        precision=gw.GW_PREC_MIXED if mixed else gw.GW_PREC_FP64, workspace_mb=workspace_mb)
 
 
 def workspace_for(system) -> int:
@@ -60,12 +53,14 @@ def run_job(job: Job, precision: str = "mixed", qp: str = "linearised") -> dict:
     """Default executor: one plan (own CUDA stream) for the job, screening + QP solve; FP64 re-run on failure."""
     from . import gw
     s = job.system
+    B_ia = job.B_ia if job.B_ia is not None else s.b_ia()     # inputs are generated when the job is admitted
+    B_nm = job.B_nm if job.B_nm is not None else s.b_nm()
     mode = gw.GW_QP_LINEARISED if qp == "linearised" else gw.GW_QP_STEPTREE
     tries = [gw.GW_PREC_MIXED, gw.GW_PREC_FP64] if precision == "mixed" else [gw.GW_PREC_FP64]
     last = None
     for prec in tries:
         try:
-            with gw.Plan(s.eps, s.n_occ, job.B_ia, job.B_nm, s.targets, precision=prec,
+            with gw.Plan(s.eps, s.n_occ, B_ia, B_nm, s.targets, precision=prec,
                          workspace_mb=workspace_for(s)) as p:
                 p.screening()
                 e, z, st = p.qp_solve(mode)
@@ -150,13 +145,15 @@ def summarize(jobs, makespan: float = None) -> dict:
             "fp64_fallbacks": sum(1 for j in ok if j.result.get("precision") == "fp64")}
 
 
-def make_jobs(stream, n_max: int = None, limit: int = None, mixed: bool = True):
-    """Jobs from synth.serving_stream(): (arrival, System) pairs, inputs generated up front."""
+def make_jobs(stream, n_max: int = None, limit: int = None, mixed: bool = True, inputs: bool = False):
+    """Jobs from synth.serving_stream(): (arrival, System) pairs.  The queue keeps the System (sizes, seed, targets)
+    and the footprint; the executor generates the host inputs when it runs the job (``inputs=True`` generates them
+    here instead)."""
     jobs = []
     for k, (arr, s) in enumerate(stream):
         if n_max is not None and s.meta.get("n_water", 0) > n_max:
             continue
-        j = Job(k, arr, s, s.b_ia(), s.b_nm())
+        j = Job(k, arr, s, s.b_ia() if inputs else None, s.b_nm() if inputs else None)
         j.footprint = footprint_bytes(s, mixed, workspace_for(s))
         jobs.append(j)
         if limit is not None and len(jobs) >= limit:

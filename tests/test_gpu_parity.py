@@ -136,3 +136,28 @@ def test_qp_paper_minres_defaults(gw):
     print("paper-mode linearised |error| meV:", np.round(err / 3.6749322175655e-5, 4))
     assert np.all(err < 3.6749322175655e-5)
     assert stats["n_rhs_solved"] > 0
+
+
+@pytest.mark.parametrize("kind,ws_mb", [("water2", 2), ("water3_core", 4)])
+def test_chunked_workspace_fp64_vs_oracle(gw, kind, ws_mb):
+    """The code paths of full-size jobs on a small system: a workspace cap of a few MiB splits the 129 frequency
+    matrices into chunks of 1-4 (several Cholesky/triangular-solve launches), and max_rhs_batch = 5 splits the
+    residues into several MINRES sub-batches; Sigma_c, dSigma_c and the linearised QP energies still match the
+    oracle at the FP64 bars."""
+    s = _sys(kind)
+    B, Bn = s.b_ia(), s.b_nm()
+    xi, wt = O.mgl_grid(128, 0.5)
+    cd = O.CDSelfEnergy(s.eps, s.n_occ, B, Bn, s.targets, xi, wt, eta=1e-3)
+    om = s.eps[s.targets]
+    with gw.Plan(s.eps, s.n_occ, B, Bn, s.targets, workspace_mb=ws_mb, max_rhs_batch=5, **TIGHT) as p:
+        sc, dsc, _ = p.sigma_cd(om)
+        e, z, st = p.qp_solve(gw.GW_QP_LINEARISED)
+        stats = p.stats()
+    per = s.n_aux * s.n_aux * 8
+    assert stats["launches_kernel"][2] >= 129 // max(1, (ws_mb << 20) // per)      # one Cholesky launch per chunk
+    for t in range(len(s.targets)):
+        ref, dref = cd.sigma_c(t, om[t])
+        assert abs(sc[t] - ref) < 1e-9, (t, sc[t], ref)
+        assert abs(dsc[t] - dref) < 1e-7 * max(1.0, abs(dref)), (t, dsc[t], dref)
+    ref = O.g0w0_cd(s.eps, s.n_occ, B, Bn, s.targets, eta=1e-3, mode="linearised")
+    np.testing.assert_allclose(e, ref["e_qp"], rtol=0, atol=1e-5)

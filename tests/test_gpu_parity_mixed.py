@@ -114,3 +114,50 @@ def test_double_float_refinement_residual_matches_fp64(gw):
             assert p.stats()["n_refine_fp64"] > 0
     assert np.abs(out[1] - out[0]).max() < 0.01 * MEV, np.abs(out[1] - out[0]).max() / MEV
     assert np.abs(out[1] - ref["e_qp"]).max() < 1 * MEV, np.abs(out[1] - ref["e_qp"]).max() / MEV
+
+
+def test_chunked_workspace_mixed_vs_oracle(gw):
+    """The chunked code that full-size mixed jobs run, forced on (H2O)_3 by a 12 MiB workspace cap: two frequency
+    matrices per Newton-Schulz chunk (65 chunks), so the difference-form columns of the lowest grid points span many
+    chunks after the first and use its stored eps(0)^-1; split-operand sub-batches of the dense fallback; and
+    max_rhs_batch = 7 MINRES sub-batches.  Sigma_c, dSigma_c and the linearised QP energies against the oracle at
+    the same bars as the unchunked tests."""
+    s = synth.water_cluster(3, 43, targets="valence")
+    B, Bn = s.b_ia(), s.b_nm()
+    xi, wt = O.mgl_grid(128, 0.5)
+    cd = O.CDSelfEnergy(s.eps, s.n_occ, B, Bn, s.targets, xi, wt, eta=1e-3)
+    om = s.eps[s.targets]
+    with gw.Plan(s.eps, s.n_occ, B, Bn, s.targets, precision=gw.GW_PREC_MIXED, workspace_mb=12,
+                 max_rhs_batch=7) as p:
+        sc, dsc, _ = p.sigma_cd(om)
+        e, z, st = p.qp_solve(gw.GW_QP_LINEARISED)
+        stats = p.stats()
+    assert stats["launches_kernel"][0] >= 60          # Pi(i xi) in many chunks
+    assert stats["n_fallback"] > 7                    # more than one fallback sub-batch
+    ref = np.array([cd.sigma_c(t, om[t]) for t in range(len(s.targets))])
+    assert np.all(np.abs(sc - ref[:, 0]) < 1 * MEV), np.abs(sc - ref[:, 0]) / MEV
+    assert np.all(np.abs(dsc - ref[:, 1]) < 2e-5), np.abs(dsc - ref[:, 1])
+    qref = O.g0w0_cd(s.eps, s.n_occ, B, Bn, s.targets, eta=1e-3, mode="linearised")
+    err = np.abs(e - qref["e_qp"])
+    print("chunked mixed linearised |error| meV:", np.round(err / MEV, 4))
+    assert np.all(err < 5 * MEV), err / MEV
+
+
+def test_footprint_bound_holds(gw):
+    """The plan's device bytes (counted at every allocation) stay below gw_plan_footprint's bound, and the device's
+    own free-memory drop agrees with the count, on a mixed job forced through the dense fallback."""
+    import torch
+    s = synth.water_cluster(3, 43, targets="valence")
+    B, Bn = s.b_ia(), s.b_nm()
+    bound = gw.footprint(s.n_occ, s.n_virt, s.n_aux, len(s.targets), precision=gw.GW_PREC_MIXED, workspace_mb=64)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    with gw.Plan(s.eps, s.n_occ, B, Bn, s.targets, precision=gw.GW_PREC_MIXED, workspace_mb=64) as p:
+        p.qp_solve(gw.GW_QP_LINEARISED)
+        st = p.stats()
+        free1, _ = torch.cuda.mem_get_info()
+    assert st["n_fallback"] > 0
+    assert 0 < st["bytes_device"] <= st["bytes_device_peak"] <= bound, (st["bytes_device_peak"], bound)
+    used = free0 - free1
+    # allocation granularity: at most 2 MiB per buffer on top of the counted bytes
+    assert st["bytes_device"] - (1 << 20) <= used <= st["bytes_device"] + 200 * (2 << 20), (used, st["bytes_device"])

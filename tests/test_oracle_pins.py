@@ -279,3 +279,137 @@ def test_steptree_uses_golden_section_when_z_small():
     w, Z, st, n, trace = O.qp_steptree(e, 0.0, fn, tol=1e-10, maxit=200)
     f = lambda w: e + A / (w - p) - w
     assert st == 0 and abs(f(w)) < 1e-10
+
+
+# ---------------------------------------------------------------- real-axis W at finite eta
+def _pair_space_w(eps, n_occ, B, b, x, eta):
+    """W^c_eta(x) and dW/dx by a route that never forms Pi: the two pole terms of Pi(x) (Sec. 3.3) combine to
+    1/(x - D + i eta) + 1/(-x - D + i eta) = -2 Dt/(Dt^2 - x^2) with the complex pair energy Dt = D - i eta, so
+    Pi_eta(x) = -C (Dt^2 - x^2)^-1 C^T with C = 2 B Dt^(1/2).  The Woodbury identity then gives
+    W^c = b^T[(1 - Pi)^-1 - 1]b = -u^T (M - x^2)^-1 u with u = C^T b and M = Dt^(1/2)(Dt + 4K)Dt^(1/2), the
+    Casida matrix of Sec. 3.2 with K = B^T B, here complex symmetric; dW/dx = -2x v^T v with v = (M - x^2)^-1 u."""
+    D = O.pair_energies(eps, n_occ)
+    Dt = D - 1j * eta
+    sD = np.sqrt(Dt)
+    K = B.T @ B
+    M = sD[:, None] * (np.diag(Dt) + 4.0 * K) * sD[None, :]
+    u = 2.0 * sD * (B.T @ b)
+    v = np.linalg.solve(M - x * x * np.eye(len(D)), u)
+    return -(u @ v), -2.0 * x * (v @ v)
+
+
+@pytest.mark.parametrize("seed", [None, 1, 2])
+def test_residue_w_at_finite_eta_matches_pair_space_route(seed):
+    """Pins pi_complex, dpi_complex and residue_w at eta != 0 (the placement and factor of i eta in both pole
+    terms): the N_aux-dimensional dense solve against the N_ov-dimensional Casida form, including frequencies
+    within a few eta of a pair energy, where a wrong eta factor or placement changes W at first order."""
+    if seed is None:
+        s = synth.workload(0)
+        B, Bn = s.b_ia(), s.b_nm()
+        eps, n_occ, rows = s.eps, s.n_occ, [Bn[1, 3], Bn[0, 10]]
+    else:
+        rng = np.random.default_rng(seed)
+        n_occ, n_virt, n_aux = 2, 4, 5
+        eps = np.sort(np.concatenate([rng.uniform(-1.5, -0.3, n_occ), rng.uniform(0.1, 2.0, n_virt)]))
+        B = rng.normal(0, 0.3, (n_aux, n_occ * n_virt))
+        rows = [rng.normal(0, 0.3, n_aux) for _ in range(2)]
+    D = O.pair_energies(eps, n_occ)
+    xs = [0.0, 0.31, -0.7, D.min() + 0.002, D.max() - 0.004, -D[len(D) // 2] + 0.001, 1.93]
+    for eta in (1e-3, 1e-2, 0.07):
+        for x in xs:
+            for b in rows:
+                cd = O.CDSelfEnergy.__new__(O.CDSelfEnergy)        # residue_w only needs these fields
+                cd.eps, cd.n_occ, cd.B_ia, cd.eta, cd.n_residue_solves = eps, n_occ, B, eta, 0
+                cd.B_nm = b[None, None, :]
+                w, dw = cd.residue_w(0, 0, x)
+                wr, dwr = _pair_space_w(eps, n_occ, B, b, x, eta)
+                # both routes are FP64 LU solves; near a resonance their condition number grows like 1/eta
+                assert abs(w - wr) < 1e-9 * max(1.0, abs(wr)), (eta, x, w, wr)
+                assert abs(dw - dwr) < 1e-8 * max(1.0, abs(dwr)), (eta, x, dw, dwr)
+
+
+def test_pi_complex_properties_at_finite_eta():
+    """Consequences of the paper's Pi(x) that hold for any eta: even in x, complex symmetric, -Im Pi positive
+    semidefinite, and at an isolated resonance x = D_k, eta Im Pi -> -2 B_k B_k^T as eta -> 0 (the closed-shell
+    factor 2 over a unit-residue pole term)."""
+    rng = np.random.default_rng(4)
+    n_occ, n_virt, n_aux = 2, 3, 4
+    eps = np.sort(np.concatenate([[-1.1, -0.6], [0.2, 0.9, 1.7]]))
+    B = rng.normal(0, 0.4, (n_aux, n_occ * n_virt))
+    eta = 0.05
+    for x in (0.0, 0.4, 1.3, 2.6):
+        P = O.pi_complex(eps, n_occ, B, x, eta)
+        np.testing.assert_allclose(P, O.pi_complex(eps, n_occ, B, -x, eta), atol=1e-14)
+        np.testing.assert_allclose(P, P.T, atol=1e-14)
+        assert np.linalg.eigvalsh(-P.imag).min() > -1e-13
+    # isolated resonance: the lowest pair energy is well separated from the others
+    D = O.pair_energies(eps, n_occ)
+    k = int(np.argmin(D))
+    for e in (1e-4, 1e-6):
+        P = O.pi_complex(eps, n_occ, B, D[k], e)
+        np.testing.assert_allclose(e * P.imag, -2.0 * np.outer(B[:, k], B[:, k]), atol=50 * e)
+
+
+# ---------------------------------------------------------------- step tree, worked by hand
+# Each case uses a Sigma whose f(w) = e + Sigma(w) - w and Z = 1/(1 - Sigma'(w)) are simple enough to follow
+# Fig. "steptree" (Sec. 3.4) by hand; the expected iterates below are those hand computations, written with the
+# golden fraction G = (3 - sqrt 5)/2.
+G = (3.0 - math.sqrt(5.0)) / 2.0
+
+
+def _iterates(sigma, e=0.0, maxit=50, tol=1e-8):
+    w, Z, st, n, trace = O.qp_steptree(e, 0.0, sigma, tol=tol, maxit=maxit)
+    return [t[0] for t in trace], [t[1] for t in trace], st, Z
+
+
+def test_steptree_capped_residual_then_newton():
+    # Sigma = 0.5 - w: f = 0.5 - 2w, Z = 1/2.  Iteration 0: residual step capped at 0.1 (|f| = 0.5);
+    # iteration 1: Z >= 0.3, Newton w += Z f = 0.1 + 0.15 lands on the root 0.25.
+    ws, fs, st, Z = _iterates(lambda w: (0.5 - w, -1.0))
+    assert st == 0 and Z == 0.5
+    np.testing.assert_allclose(ws, [0.0, 0.1, 0.25], atol=1e-15)
+    np.testing.assert_allclose(fs, [0.5, 0.3, 0.0], atol=1e-15)
+
+
+def test_steptree_scaled_newton_without_bracket():
+    # Sigma = 1 - 4w: f = 1 - 5w, Z = 0.2 (below 0.3, at least 0.1).  Iteration 0: capped step 0.1 (f = 1 -> 0.5,
+    # same sign, |f| shrinks: no bracket).  Then w += 0.7 Z f = 0.14 f each time, so f_{k+1} = (1 - 5*0.14) f_k
+    # = 0.3 f_k: w = 0.1, 0.17, 0.191, 0.1973, ...
+    ws, fs, st, Z = _iterates(lambda w: (1.0 - 4.0 * w, -4.0))
+    assert st == 0 and abs(Z - 0.2) < 1e-15
+    np.testing.assert_allclose(ws[:5], [0.0, 0.1, 0.17, 0.191, 0.1973], atol=1e-14)
+    for k in range(1, len(fs) - 1):
+        assert abs(fs[k + 1] - 0.3 * fs[k]) < 1e-14
+    assert len(ws) == 17 and abs(fs[-1]) < 1e-8 <= abs(fs[-2])     # f_16 = 0.5 * 0.3^15 < 1e-8 <= f_15
+
+
+def test_steptree_residual_steps_then_golden_in_sign_bracket():
+    # Sigma = 5 - 19w: f = 5 - 20w, Z = 0.05 (below 0.1).  Capped residual steps of 0.1 (f = 5, 3, 1, -1); the sign
+    # change between w = 0.2 and 0.3 opens the bracket [0.2, 0.3] with f = 1 and -1.  Bracketed and Z < 0.3:
+    # golden points from the end with the smaller |f| (the lower end on a tie):
+    #   0.2 + 0.1 G (f = 1 - 2G > 0: replaces the lower end), then
+    #   a + G (0.3 - a) with a = 0.2 + 0.1 G (f < 0: replaces the upper end), ...
+    ws, fs, st, Z = _iterates(lambda w: (5.0 - 19.0 * w, -19.0), maxit=8)
+    w4 = 0.2 + 0.1 * G
+    w5 = w4 + G * (0.3 - w4)
+    np.testing.assert_allclose(ws[:6], [0.0, 0.1, 0.2, 0.3, w4, w5], atol=1e-14)
+    np.testing.assert_allclose(fs[:4], [5.0, 3.0, 1.0, -1.0], atol=1e-13)
+    assert fs[4] > 0 > fs[5]
+    # at w5 both ends have |f| = 20 |w - 0.25| equal by the golden symmetry: the lower end wins the tie
+    w6 = w4 + G * (w5 - w4)
+    assert abs(ws[6] - w6) < 1e-14 and st == 1
+
+
+def test_steptree_same_sign_bracket_turns_into_sign_bracket():
+    # f = -0.01 + 4|w - 0.04| (roots 0.0375 and 0.0425): Sigma' = -3 left of 0.04 (Z = 0.25), +5 right of it
+    # (Z = -0.25); Z < 0.3 everywhere, so Newton never runs.  Iteration 0: capped step 0.1 from f = 0.15 to 0.23:
+    # same sign and growing |f| -> "same" bracket [0, 0.1] around x = 0.  Golden point x + G (b - x) = 0.1 G has
+    # f = -0.01 + 4 (0.04 - 0.1 G) < 0: the bracket becomes a sign bracket [0, 0.1 G] with f(0) = 0.15; then
+    # golden from the end with the smaller |f| (the upper one): b - G (b - a) = 0.1 G (1 - G).
+    def sig(w):
+        f = -0.01 + 4.0 * abs(w - 0.04)
+        return f + w, (-3.0 if w < 0.04 else 5.0)
+    ws, fs, st, Z = _iterates(sig, maxit=6)
+    np.testing.assert_allclose(ws[:4], [0.0, 0.1, 0.1 * G, 0.1 * G * (1.0 - G)], atol=1e-15)
+    np.testing.assert_allclose(fs[:2], [0.15, 0.23], atol=1e-15)
+    assert fs[2] < 0 < fs[3]

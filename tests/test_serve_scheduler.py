@@ -91,3 +91,18 @@ def test_footprint_grows_with_size():
     a = serve.footprint_bytes(synth.water_cluster(2, 1, targets="homo_lumo"))
     b = serve.footprint_bytes(synth.water_cluster(8, 1, targets="homo_lumo"))
     assert 0 < a < b
+
+
+def test_library_footprint_bound_properties():
+    """gw_plan_footprint (host only): grows with the system, borrowing B saves exactly its FP64 bytes, the work-space
+    cap bounds the work space, and the largest job of the serving stream fits the default HBM budget."""
+    from paper_2107_10423_gb300 import gw, synth
+    s = synth.water_cluster(8, 1, targets="homo_lumo")
+    own = gw.footprint(s.n_occ, s.n_virt, s.n_aux, 2, precision=gw.GW_PREC_MIXED)
+    bor = gw.footprint(s.n_occ, s.n_virt, s.n_aux, 2, borrow=True, precision=gw.GW_PREC_MIXED)
+    assert own - bor == 8 * (s.n_aux * s.n_ov + 2 * s.n_bas * s.n_aux)
+    small = gw.footprint(s.n_occ, s.n_virt, s.n_aux, 2, precision=gw.GW_PREC_MIXED, workspace_mb=64)
+    assert small < own
+    big = synth.water_cluster(64, 1, targets="homo_lumo")
+    fp = serve.footprint_bytes(big, True, serve.workspace_for(big))
+    assert fp < serve.Server().hbm_budget

@@ -1,6 +1,7 @@
 """gw_w_table_noalloc: the W-table triangular solves for callers that cannot allocate device memory
 (a process that gives all GPU memory to its own pool, an allocator that forbids cudaMalloc after start-up).
-Its output must equal the plan-based W table of gw_w_table, on two calls in a row.  This file is collected
+Its output must equal the plan-based W table of gw_w_table and the oracle's dense-LU W^c on the same Pi(i xi),
+on two calls in a row.  This file is collected
 last so that a stop at the first failure has already run every other test."""
 import ctypes
 
@@ -23,7 +24,10 @@ def test_noalloc_w_table_matches_plan(gwlib):
     xi, _ = gw.grid(128, 0.5)
     xis = np.concatenate([xi, [0.0]])
     n = s.n_aux
-    L = np.stack([np.linalg.cholesky(np.eye(n) - O.pi_imag(s.eps, s.n_occ, B, x)) for x in xis])
+    Pis = [O.pi_imag(s.eps, s.n_occ, B, x) for x in xis]
+    L = np.stack([np.linalg.cholesky(np.eye(n) - Pi) for Pi in Pis])
+    # the oracle's W^c = b^T[(1 - Pi)^-1 - 1]b by dense LU with the same Pi(i xi) the factors come from
+    ora = np.stack([np.stack([O.w_corr(Pi, Bn[t].T) for Pi in Pis], axis=-1) for t in range(len(s.targets))])
     dev = torch.device("cuda", 0)
     L_d = torch.from_numpy(np.ascontiguousarray(L)).to(dev)
     rows = np.ascontiguousarray(Bn.reshape(-1, n))
@@ -37,6 +41,8 @@ def test_noalloc_w_table_matches_plan(gwlib):
         torch.cuda.synchronize()
         W = W_d.cpu().numpy().reshape(ref.shape)
         np.testing.assert_allclose(W, ref, rtol=0, atol=1e-12 * max(1.0, np.abs(ref).max()), err_msg=f"call {call}")
+        # |L^-1 b|^2 - |b|^2 cancels where W is small (large xi): the FP64 bound is a few ulp of |b|^2
+        np.testing.assert_allclose(W, ora, rtol=0, atol=1e-12 * max(1.0, np.abs(ora).max()), err_msg=f"oracle {call}")
 
 
 def test_noalloc_rejects_oversize(gwlib):
