@@ -87,6 +87,8 @@ typedef struct {
                                   resonance (x = +-D_ia) */
   int refine_df;               /* mixed: the FP64-accurate refinement residual in double-float arithmetic (FP32
                                   pairs, 48-bit, on the FP32 pipes: 1, default) or in FP64 (0) */
+  int tc_max_ctas;             /* mixed: cap on the persistent grid of the Pi kernel (CTAs, one per SM at most);
+                                  0 = every SM.  A smaller grid leaves SMs to work that runs beside it */
 } gw_config;
 
 typedef struct gw_plan* gw_plan_t;

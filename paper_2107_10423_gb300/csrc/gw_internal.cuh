@@ -41,7 +41,7 @@ int trsm_w_default_ctas();
 template <typename T>
 void launch_op_gemm1(const T* V, const T* B, const double* eps, int n_occ, int n_virt, int n_aux, const double* x,
                      double eta, int nr, T* U, int mode, cudaStream_t s, double* dw = nullptr,
-                     double cut = 0.0);
+                     double cut = 0.0, long ldb = 0);   // ldb: row length of B (0 = n_occ * n_virt)
 // Double-float (FP32 pair, 48-bit) versions of op_gemm1 mode 0 and op_gemm2 mode 1 for the refinement residual:
 // V, U, out FP64; B as its split Bh + Bl (launch_df_split of the FP64 B_ia).
 void launch_df_split(const double* x, long n, float* h, float* l, cudaStream_t s);

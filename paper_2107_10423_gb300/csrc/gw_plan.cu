@@ -44,7 +44,8 @@ struct gw_plan {
   double* d_shift = nullptr;
   double* d_en = nullptr;
   double* d_W = nullptr;      // [n_t][n_bas][n_g + 1]
-  float* d_B_ia_f = nullptr;  // mixed: FP32 copy of B_ia
+  float* d_B_ia_f = nullptr;  // mixed: FP32 copy of B_ia, rows of ld_f elements (16-byte rows for TMA)
+  long ld_f = 0;
   float* d_B_nm_f = nullptr;  // mixed: FP32 copy of B_nm
   __nv_bfloat16* d_Bhi = nullptr;   // mixed: BF16 hi/lo split of B_ia, [n_aux][tc_ld(n_ov)]
   __nv_bfloat16* d_Blo = nullptr;
@@ -65,7 +66,7 @@ struct gw_plan {
   int ns_kmax = 0;
   int ns_ndiff = 0;           // lowest grid points whose W column is built in the difference form
   std::vector<DevBuf*> bufs;
-  DevBuf ws_mat, ws_info, ws_scratch, ws_gout, ws_xi, tc_Ahi, tc_Alo, tc_kind, tc_par, tc_err, tc_w, ns_E, ns_X, ns_X2, ns_Xa, ns_Xb, ns_T, ns_lam,
+  DevBuf ws_mat, ws_info, ws_scratch, ws_gout, ws_xi, tc_kind, tc_par, tc_err, tc_w, ns_E, ns_X, ns_X2, ns_Xa, ns_Xb, ns_T, ns_lam,
       ns_E0;
   DevBuf mr_V, mr_U, mr_S, mr_vprev, mr_v, mr_d1, mr_d2, mr_x, mr_st, mr_rt, mr_rm, mr_xf, mr_wre, mr_wim,
       mr_dwre, mr_it, mr_res, mr_cnt, mr_Vhi, mr_Vlo, mr_Uhi, mr_Ulo, mr_Vlo2, mr_Ulo2, mr_V64;
@@ -83,7 +84,7 @@ struct gw_plan {
   std::vector<Mark> marks;
 
   gw_plan() {
-    DevBuf* all[] = {&ws_mat, &ws_info, &ws_scratch, &ws_gout, &ws_xi, &tc_Ahi, &tc_Alo, &tc_kind, &tc_par, &tc_err, &tc_w, &ns_E, &ns_X, &ns_X2, &ns_Xa, &ns_Xb, &ns_T, &ns_lam, &ns_E0, &mr_V, &mr_U, &mr_S, &mr_vprev,
+    DevBuf* all[] = {&ws_mat, &ws_info, &ws_scratch, &ws_gout, &ws_xi, &tc_kind, &tc_par, &tc_err, &tc_w, &ns_E, &ns_X, &ns_X2, &ns_Xa, &ns_Xb, &ns_T, &ns_lam, &ns_E0, &mr_V, &mr_U, &mr_S, &mr_vprev,
                      &mr_v, &mr_d1, &mr_d2, &mr_x, &mr_st, &mr_rt, &mr_rm, &mr_xf, &mr_wre, &mr_wim,
                      &mr_dwre, &mr_it, &mr_res, &mr_cnt, &mr_Vhi, &mr_Vlo, &mr_Uhi, &mr_Ulo, &mr_Vlo2, &mr_Ulo2, &mr_V64, &sg_I, &sg_dI, &sg_R, &sg_dR, &sg_om, &sg_start,
                      &sg_coef, &sg_act, &qp_st, &fb_A, &fb_y, &fb_piv, &fb_info, &fb_idx, &fb_y64, &fb_V32, &fb_S32, &fb_Vp, &fb_Up, &fb_x, &fb_V64, &fb_U64, &fb_S64, &fb_sel, &fb_pos, &fb_rho, &fb_xs, &fb_Bh, &fb_Bl};
@@ -198,27 +199,24 @@ double now_ms(gw_plan* P, cudaEvent_t a, cudaEvent_t b) {
   return (double)ms;
 }
 
-// Tensor-core weighted SYRK for `nb` batch entries: out_b = f(B diag(w_b) B^T) with (kind, param) per entry.
-// reset_err = false keeps a bounded-wait code that earlier launches of the caller left in tc_err, so that the
-// check at the end reports it.
+// Tensor-core weighted SYRK for `nb` batch entries: out_b = f(B diag(w_b) B^T) with (kind, param) per entry,
+// the weights applied inside the kernel (tc_pi_fused).  reset_err = false keeps a bounded-wait code that earlier
+// launches of the caller left in tc_err, so that the check at the end reports it.
 gw_status tc_weighted_syrk(gw_plan* P, const int* kinds, const double* params, int nb, int mode_even, int mode_odd,
                            float* out, int cls, bool reset_err = true) {
-  const int n = P->cfg.n_aux, K = P->n_ov, ld = gw::tc_ld(K);
-  TRY(ensure(P, P->tc_Ahi, sizeof(__nv_bfloat16) * (size_t)nb * n * ld));
-  TRY(ensure(P, P->tc_Alo, sizeof(__nv_bfloat16) * (size_t)nb * n * ld));
+  const int n = P->cfg.n_aux, K = P->n_ov;
   TRY(ensure(P, P->tc_kind, sizeof(int) * nb));
   TRY(ensure(P, P->tc_par, sizeof(double) * nb));
   TRY(ensure(P, P->tc_err, sizeof(int)));
-  TRY(ensure(P, P->tc_w, sizeof(float) * (size_t)nb * K));
+  TRY(ensure(P, P->tc_w, sizeof(float) * (size_t)nb * gw::pf_ldw(K)));
   CK(cudaMemcpyAsync(P->tc_kind.p, kinds, sizeof(int) * nb, cudaMemcpyHostToDevice, P->stream));
   CK(cudaMemcpyAsync(P->tc_par.p, params, sizeof(double) * nb, cudaMemcpyHostToDevice, P->stream));
   if (reset_err) CK(cudaMemsetAsync(P->tc_err.p, 0, sizeof(int), P->stream));
   const size_t t0 = tick(P);
-  CK(gw::tc_scale_split(P->d_B_ia_f, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, K, as<int>(P->tc_kind),
-                        as<double>(P->tc_par), P->cfg.eta, nb, as<float>(P->tc_w), as<__nv_bfloat16>(P->tc_Ahi),
-                        as<__nv_bfloat16>(P->tc_Alo), P->stream));
-  CK(gw::tc_gemm(as<__nv_bfloat16>(P->tc_Ahi), as<__nv_bfloat16>(P->tc_Alo), nb, P->d_Bhi, P->d_Blo, n, n, K, 1,
-                 mode_even, mode_odd, out, as<int>(P->tc_err), P->stream));
+  CK(gw::tc_pair_weights(P->d_eps, P->cfg.n_occ, P->cfg.n_virt, K, as<int>(P->tc_kind), as<double>(P->tc_par),
+                         P->cfg.eta, nb, as<float>(P->tc_w), P->stream));
+  CK(gw::tc_pi_fused(P->d_B_ia_f, P->ld_f, n, K, as<float>(P->tc_w), nb, P->d_Bhi, P->d_Blo, mode_even, mode_odd,
+                     out, (long)n * n, n, as<int>(P->tc_err), P->stream, P->cfg.tc_max_ctas));
   mark(P, cls, t0, (double)nb * n * n * K);     // symmetric rank-K update: n^2 K flops per entry
   P->stats.n_kernel_launches += 2;
   int herr = 0;
@@ -226,13 +224,6 @@ gw_status tc_weighted_syrk(gw_plan* P, const int* kinds, const double* params, i
   CK(cudaStreamSynchronize(P->stream));
   if (herr != 0) return fail(P, GW_ERR_TIMEOUT, "tensor-core GEMM: bounded wait ran out (code %d)", herr);
   return GW_OK;
-}
-
-// Largest batch of split operands that fits in ~8 GiB.
-int tc_chunk(gw_plan* P, int want) {
-  const size_t per = (size_t)P->cfg.n_aux * gw::tc_ld(P->n_ov) * 4;   // hi + lo
-  size_t c = ws_bytes(P) / (per ? per : 1);
-  return (int)std::max<size_t>(1, std::min<size_t>((size_t)want, c));
 }
 
 // W table on the tensor cores (mixed precision) for nc frequency matrices eps_b = 1 - Pi_b held FP32 in ws_mat:
@@ -446,7 +437,6 @@ gw_status screening_T(gw_plan* P, const T* B, const T* Bn) {
   const size_t per = (size_t)n * n * sizeof(T);
   int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_g1, ws_bytes(P) / per));
   if (use_tc) {
-    chunk = tc_chunk(P, chunk);
     const size_t per_ns = (size_t)n * gw::tc_ld(n) * 24 + (size_t)n * n * 8;   // split E, Xa, Xb, T; FP32 X, eps
     chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)chunk, ws_bytes(P) / per_ns));
   }
@@ -534,6 +524,7 @@ gw_status ensure_screening(gw_plan* P) {
 }
 
 gw_status tc_operator3(gw_plan* P, int nf, const double* xf, const float* V32, float* S32);
+gw_status ensure_third_parts(gw_plan* P);
 
 // Half-width (Ha) of the window around each resonance x = +-D_ia whose derivative terms are computed in FP64.
 constexpr double kResonantCut = 0.1;
@@ -551,7 +542,7 @@ gw_status dense_fallback(gw_plan* P, const std::vector<int>& need, const int* rt
   // sub-batches sized by the split-operand budget
   int fb = (int)std::max<size_t>(1, ws_bytes(P) / (2 * mat * sizeof(T)));
   fb = std::min(fb, nneed);
-  const int sub = (sizeof(T) == 4) ? std::max(1, tc_chunk(P, 2 * fb) / 2) : fb;
+  const int sub = fb;
   TRY(ensure(P, P->fb_A, sizeof(T) * 2 * mat * fb));
   TRY(ensure(P, P->fb_y, sizeof(T) * 2 * (size_t)n * fb));
   TRY(ensure(P, P->fb_piv, sizeof(int) * (size_t)n * fb));
@@ -716,6 +707,7 @@ gw_status tc_operator(gw_plan* P, int nr, const double* xf, const float* V32, fl
   const int n = P->cfg.n_aux, n_ov = P->n_ov;
   const int ldov = gw::tc_ld(n_ov);
   const bool three = P->cfg.op_parts >= 3;
+  if (three) TRY(ensure_third_parts(P));
   __nv_bfloat16* vlo2 = three ? as<__nv_bfloat16>(P->mr_Vlo2) : nullptr;
   __nv_bfloat16* ulo2 = three ? as<__nv_bfloat16>(P->mr_Ulo2) : nullptr;
   CK(gw::tc_split_rows(V32, 2 * nr, n, n, as<__nv_bfloat16>(P->mr_Vhi), as<__nv_bfloat16>(P->mr_Vlo), P->stream,
@@ -749,6 +741,7 @@ gw_status tc_operator(gw_plan* P, int nr, const double* xf, const float* V32, fl
 // Three-part (about FP32-accurate) residue operator for the refinement of dense fallback solves: the embedding
 // output S32 = [Re; Im]((1 - Pi(x)) z) for nf right-hand sides z held as (u, v) rows in V32.
 gw_status tc_operator3(gw_plan* P, int nf, const double* xf, const float* V32, float* S32) {
+  TRY(ensure_third_parts(P));
   const int n = P->cfg.n_aux, n_ov = P->n_ov;
   const size_t sv = 2 * (size_t)nf * gw::tc_ld(n), su = 2 * (size_t)nf * gw::tc_ld(n_ov);
   __nv_bfloat16* vp = as<__nv_bfloat16>(P->fb_Vp);
@@ -897,7 +890,7 @@ gw_status residues_T(gw_plan* P, int nr_total, const int* d_rt, const int* d_rm,
                                          nullptr, 2, P->stream, dw_re + j0));
     } else if (sizeof(T) == 4) {
       LAUNCH(gw::launch_op_gemm1<T>(as<T>(P->mr_V), B, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, xf, eta, nr,
-                                    nullptr, 2, P->stream, dw_re + j0, kResonantCut));
+                                    nullptr, 2, P->stream, dw_re + j0, kResonantCut, P->ld_f));
       LAUNCH(gw::launch_deriv_resonant(V64, P->d_B_ia, n_ov, n, P->d_Dsort, P->d_Dkidx, xf, nr, eta, kResonantCut,
                                        dw_re + j0, P->stream));
     } else {
@@ -1021,6 +1014,27 @@ __global__ void convert_f64_f32_kernel(const double* __restrict__ a, float* __re
     b[i] = (float)a[i];
 }
 
+// rows x cols FP64 (contiguous) to FP32 rows of ldb elements, zero padded.
+__global__ void convert_rows_kernel(const double* __restrict__ a, int rows, int cols, float* __restrict__ b,
+                                    long ldb) {
+  for (int r = blockIdx.y; r < rows; r += gridDim.y)
+    for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < ldb; c += (long)gridDim.x * blockDim.x)
+      b[(long)r * ldb + c] = c < cols ? (float)a[(long)r * cols + c] : 0.f;
+}
+
+// Third BF16 parts of B_ia and B_ia^T, made when a three-part operator first needs them (the hi and lo parts are
+// rewritten with the same values).
+gw_status ensure_third_parts(gw_plan* P) {
+  if (P->d_Blo2) return GW_OK;
+  const int n = P->cfg.n_aux;
+  TRY(dmalloc(P, &P->d_Blo2, sizeof(__nv_bfloat16) * (size_t)n * gw::tc_ld(P->n_ov)));
+  TRY(dmalloc(P, &P->d_BTlo2, sizeof(__nv_bfloat16) * (size_t)P->n_ov * gw::tc_ld(n)));
+  CK(gw::tc_split_rows(P->d_B_ia_f, n, P->n_ov, (int)P->ld_f, P->d_Bhi, P->d_Blo, P->stream, P->d_Blo2));
+  CK(gw::tc_transpose_split(P->d_B_ia_f, n, P->n_ov, P->d_BThi, P->d_BTlo, P->stream, P->d_BTlo2, P->ld_f));
+  P->stats.n_kernel_launches += 2;
+  return GW_OK;
+}
+
 }  // namespace
 
 // ==================================================================== C ABI
@@ -1136,15 +1150,17 @@ static gw_status plan_create_impl(gw_plan* P, const gw_config* cfg, const double
     CK(cudaMemcpyAsync(P->d_B_nm, B_nm, sizeof(double) * nBn, kind, P->stream));
   }
   if (cfg->precision == GW_PREC_MIXED) {
-    TRY(dmalloc(P, &P->d_B_ia_f, sizeof(float) * nB));
+    // FP32 B_ia with rows padded to 16 bytes (the fused Pi kernel reads it by TMA)
+    P->ld_f = gw::pf_ldw(P->n_ov);
+    TRY(dmalloc(P, &P->d_B_ia_f, sizeof(float) * (size_t)n * P->ld_f));
     TRY(dmalloc(P, &P->d_B_nm_f, sizeof(float) * nBn));
-    LAUNCH((convert_f64_f32_kernel<<<1024, 256, 0, P->stream>>>(P->d_B_ia, P->d_B_ia_f, nB)));
+    LAUNCH((convert_rows_kernel<<<dim3(64, std::min(n, 65535)), 256, 0, P->stream>>>(P->d_B_ia, n, P->n_ov,
+                                                                                   P->d_B_ia_f, P->ld_f)));
     LAUNCH((convert_f64_f32_kernel<<<1024, 256, 0, P->stream>>>(P->d_B_nm, P->d_B_nm_f, nBn)));
     const size_t nsplit = (size_t)n * gw::tc_ld(P->n_ov);
     TRY(dmalloc(P, &P->d_Bhi, sizeof(__nv_bfloat16) * nsplit));
     TRY(dmalloc(P, &P->d_Blo, sizeof(__nv_bfloat16) * nsplit));
-    TRY(dmalloc(P, &P->d_Blo2, sizeof(__nv_bfloat16) * nsplit));
-    CK(gw::tc_split_rows(P->d_B_ia_f, n, P->n_ov, P->n_ov, P->d_Bhi, P->d_Blo, P->stream, P->d_Blo2));
+    CK(gw::tc_split_rows(P->d_B_ia_f, n, P->n_ov, (int)P->ld_f, P->d_Bhi, P->d_Blo, P->stream));
     const size_t nsplitN = (size_t)n_targets * P->n_bas * gw::tc_ld(n);
     TRY(dmalloc(P, &P->d_Bnhi, sizeof(__nv_bfloat16) * nsplitN));
     TRY(dmalloc(P, &P->d_Bnlo, sizeof(__nv_bfloat16) * nsplitN));
@@ -1153,8 +1169,7 @@ static gw_status plan_create_impl(gw_plan* P, const gw_config* cfg, const double
     const size_t nsplitT = (size_t)P->n_ov * gw::tc_ld(n);
     TRY(dmalloc(P, &P->d_BThi, sizeof(__nv_bfloat16) * nsplitT));
     TRY(dmalloc(P, &P->d_BTlo, sizeof(__nv_bfloat16) * nsplitT));
-    TRY(dmalloc(P, &P->d_BTlo2, sizeof(__nv_bfloat16) * nsplitT));
-    CK(gw::tc_transpose_split(P->d_B_ia_f, n, P->n_ov, P->d_BThi, P->d_BTlo, P->stream, P->d_BTlo2));
+    CK(gw::tc_transpose_split(P->d_B_ia_f, n, P->n_ov, P->d_BThi, P->d_BTlo, P->stream, nullptr, P->ld_f));
     {
       std::vector<double> D((size_t)P->n_ov);
       for (int i = 0; i < cfg->n_occ; ++i)
@@ -1208,6 +1223,7 @@ gw_status gw_plan_create(const gw_config* cfg, const double* eps, const double* 
   if (!(cfg->x0 > 0.0) && !xi) return fail(nullptr, GW_ERR_ARG, "x0 must be positive");
   if (!(cfg->eta >= 0.0)) return fail(nullptr, GW_ERR_ARG, "eta must be >= 0");
   if (cfg->minres_maxit < 0 || cfg->qp_maxit <= 0) return fail(nullptr, GW_ERR_ARG, "bad iteration caps");
+  if (cfg->tc_max_ctas < 0) return fail(nullptr, GW_ERR_ARG, "tc_max_ctas must be >= 0");
   if (cfg->op_parts != 2 && cfg->op_parts != 3)
     return fail(nullptr, GW_ERR_ARG, "op_parts must be 2 or 3 (got %d)", cfg->op_parts);
   const int n_bas = cfg->n_occ + cfg->n_virt;
@@ -1249,12 +1265,8 @@ gw_status gw_polarizability(gw_plan_t P, const double* xi, int n_xi, double* pi_
   CK(cudaEventRecord(P->ev0, P->stream));
   if (P->cfg.precision == GW_PREC_MIXED) {
     TRY(ensure(P, P->ws_mat, sizeof(float) * (size_t)n * n * n_xi));
-    const int chunk = tc_chunk(P, n_xi);
-    for (int g0 = 0; g0 < n_xi; g0 += chunk) {
-      const int nc = std::min(chunk, n_xi - g0);
-      std::vector<int> kinds(nc, 0);
-      TRY(tc_weighted_syrk(P, kinds.data(), xi + g0, nc, 0, 0, as<float>(P->ws_mat) + (size_t)g0 * n * n, 0));
-    }
+    std::vector<int> kinds(n_xi, 0);
+    TRY(tc_weighted_syrk(P, kinds.data(), xi, n_xi, 0, 0, as<float>(P->ws_mat), 0));
     CK(cudaEventRecord(P->ev1, P->stream));
     if (pi_out) {
       std::vector<float> h((size_t)n * n * n_xi);
@@ -1399,17 +1411,18 @@ gw_status gw_plan_footprint(const gw_config* c, int n_t, unsigned flags, unsigne
   auto capped = [ws](u64 item, u64 want) { return std::max(item, std::min(ws / std::max<u64>(item, 1) * item, want)); };
   u64 b = 8 * (n_bas + 2 * n_g1 + 3 * (u64)n_t) + 8 * rows * n_g1;         // energies, grid, shifts, W table
   if (!(flags & GW_BORROW_DEVICE_PTRS)) b += 8 * (n * n_ov + nBn);           // B_ia, B_nm
+  const u64 ldf = (u64)gw::pf_ldw((int)std::min<u64>(n_ov, 2147483647ull));
   if (mixed) {
-    b += 4 * (n * n_ov + nBn);                                               // FP32 copies
+    b += 4 * (n * ldf + nBn);                                                // FP32 copies
     b += 6 * (n * ldo + rows * ldn + n_ov * ldn);                             // three BF16 parts of B, B_nm, B^T
     b += 20 * n_ov;                                                          // D, sorted D, pair index
   }
   // imaginary-axis stage: frequency matrices, info/index lists
   b += capped(n * n * ts, n * n * ts * n_g1) + 24 * n_g1;
   if (mixed) {
-    const u64 per_split = n * ldo * 4;                                       // weighted operand, hi + lo
-    const u64 nb = std::max<u64>(2, ws / std::max<u64>(per_split, 1));
-    b += capped(per_split, per_split * std::max<u64>(n_g1, 2)) + 4 * nb * n_ov + 16 * nb;
+    // weight table of one Pi launch: a screening chunk or two entries per fallback matrix
+    const u64 nb = std::max<u64>(n_g1, 2 * std::max<u64>(1, ws / (2 * n * n * ts)));
+    b += 4 * nb * ldf + 16 * nb;
     const u64 per_ns = n * ldn * 24 + n * n * 8;                             // Newton-Schulz split/FP32 iterates
     b += capped(per_ns, per_ns * n_g1) + 6 * n * ldn + 4 * n_g1;             // + the split eps(0)^-1 - 1
   } else {

@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(NT) op_gemm1_kernel(const T* __restrict__ V, c
                                                       const double* __restrict__ eps, int n_occ, int n_virt,
                                                       int n_aux, const double* __restrict__ xs, double eta, int nr,
                                                       T* __restrict__ U, int mode, double* __restrict__ dw,
-                                                      double cut) {
+                                                      double cut, long ldb) {
   __shared__ T As[TK][TM + 4];
   __shared__ T Bs[TK][TN + 4];
   const long n_ov = (long)n_occ * n_virt;
@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(NT) op_gemm1_kernel(const T* __restrict__ V, c
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         long k = k0c + c4 + u;
-        Bs[kr][c4 + u] = (P < n_aux && k < n_ov) ? B[(long)P * n_ov + k] : T(0);
+        Bs[kr][c4 + u] = (P < n_aux && k < n_ov) ? B[(long)P * ldb + k] : T(0);
       }
     }
     __syncthreads();
@@ -846,10 +846,11 @@ cudaError_t launch_trsm_w(const T* Lbase, long Lstride, int n, int n_g, const in
 
 template <typename T>
 void launch_op_gemm1(const T* V, const T* B, const double* eps, int n_occ, int n_virt, int n_aux, const double* x,
-                     double eta, int nr, T* U, int mode, cudaStream_t s, double* dw, double cut) {
+                     double eta, int nr, T* U, int mode, cudaStream_t s, double* dw, double cut, long ldb) {
   long n_ov = (long)n_occ * n_virt;
   dim3 grid((unsigned)((n_ov + TN - 1) / TN), (2 * nr + TM - 1) / TM);
-  op_gemm1_kernel<T><<<grid, NT, 0, s>>>(V, B, eps, n_occ, n_virt, n_aux, x, eta, nr, U, mode, dw, cut);
+  op_gemm1_kernel<T><<<grid, NT, 0, s>>>(V, B, eps, n_occ, n_virt, n_aux, x, eta, nr, U, mode, dw, cut,
+                                         ldb > 0 ? ldb : n_ov);
 }
 
 template <typename T>
@@ -867,7 +868,7 @@ void launch_op_gemm2(const T* U, const T* B, int n_aux, int n_ov, int nr, const 
   template cudaError_t launch_trsm_w<T>(const T*, long, int, int, const int*, const T*, int, double*, int, T*,   \
                                         int, cudaStream_t);                                                     \
   template void launch_op_gemm1<T>(const T*, const T*, const double*, int, int, int, const double*, double, int, \
-                                   T*, int, cudaStream_t, double*, double);                                     \
+                                   T*, int, cudaStream_t, double*, double, long);                               \
   template void launch_op_gemm2<T>(const T*, const T*, int, int, int, const T*, T*, int, cudaStream_t);
 GW_INST(double)
 GW_INST(float)

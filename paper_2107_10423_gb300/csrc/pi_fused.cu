@@ -1,0 +1,470 @@
+// Weighted symmetric rank-K products on the tcgen05 tensor cores with the weight applied inside the kernel:
+//
+//   out_b = f( B diag(w_b) B^T ),   B = B_ia [n][K] (FP32), w_b = row b of a weight table [nb][ldw] (FP32),
+//
+// for every batch entry b, lower-triangular 128 x 128 tiles mirrored into the upper triangle.  This is
+//   * Pi(i xi) on the imaginary grid (Sec. 3.3, equation after "wauxbas"): w = -4 D_ia/(D_ia^2 + xi^2);
+//   * the dense real-axis Pi(x) of the residue fallback (same section, Pi(z) with +i eta in both pole terms):
+//     w = Re c(x) and Im c(x), c = 2[1/(x - D + i eta) + 1/(-x - D + i eta)], as the two entries of one pair;
+//   * the difference-form products Pi(i xi) - Pi(0): w = 4 xi^2/(D (D^2 + xi^2)).
+//
+// Design (one CTA per SM, persistent over work items = (lower tile, pair of batch entries)):
+//   * TMA streams, per 32-wide k-block, the FP32 rows of the weighted side (128 x 32), the BF16 hi/lo parts of
+//     the unweighted side (2 x 128 x 32) and the two weight rows (2 x 32) into a 3-stage source ring.
+//   * A transform warpgroup (one thread per row) multiplies the FP32 rows by the weights of both entries and
+//     splits the products into BF16 hi/lo tiles (64-byte swizzle, the tensor core's K-major layout) in a
+//     3-stage ring.  The weight never round-trips through HBM and the source tile serves both entries, which
+//     halves the L2 bytes per tensor-core flop against one entry per pass.
+//   * One thread issues tcgen05.mma (M128 N128 K16, BF16 in, FP32 accumulate in TMEM): hi*hi + hi*lo + lo*hi.
+//   * Every CHUNK = 2 k-blocks an entry's TMEM partial is added (round to nearest) into its FP32 sum, also kept
+//     in TMEM, by the drain warpgroup, so no partial runs through more than 12 tensor-core accumulates.  The two
+//     entries' chunks are staggered by one k-block: while one entry's partial drains, the tensor core works on the
+//     other entry.
+//   * TMEM: partials of entries 0/1 in columns [0, 256), FP32 sums in [256, 512).
+// Every mbarrier wait is bounded; on timeout the kernel records a code in *err, stops every role, waits for its
+// copies and tensor-core work in flight, frees TMEM and returns.
+#include "pi_tc.cuh"
+#include "tc_ptx.cuh"
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+
+namespace gw {
+namespace {
+using namespace ptx;
+
+constexpr int BM = 128, BK = 32;
+constexpr int SRC_STAGES = 3, TR_STAGES = 3;
+constexpr int A_BYTES = BM * BK * 4;            // FP32 rows of the weighted side: 16 KiB
+constexpr int H_BYTES = BM * BK * 2;            // one BF16 tile (128 rows x 64 bytes): 8 KiB
+constexpr int W_OFF = A_BYTES + 2 * H_BYTES;    // the two weight rows [2][BK] FP32 follow the tiles
+constexpr int SRC_BYTES = W_OFF + 1024;         // 33 KiB per source stage (keeps every stage 1 KiB aligned)
+constexpr int TR_BYTES = 4 * H_BYTES;           // transformed tiles [entry][hi, lo]: 32 KiB
+constexpr int TX_BYTES = A_BYTES + 2 * H_BYTES + 2 * BK * 4;
+constexpr int N_BARS = 4 * 3 + 2 + 2 + 1;       // src full/empty, tr full/empty, acc full/empty, final
+constexpr int SMEM_BYTES = SRC_STAGES * SRC_BYTES + TR_STAGES * TR_BYTES + 256 + 1024;
+constexpr int THREADS = 320;                    // warps 0-3 drain + epilogue, 4-7 transform, 8 TMA, 9 MMA
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t SBO64 = 8 * 64;              // 8-row groups of 64-byte rows
+constexpr uint32_t SWZ64 = 4;                   // descriptor swizzle mode: 64-byte
+// kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major, N = 128, M = 128
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+struct PfMaps {
+  CUtensorMap a, bh, bl, w;
+};
+
+// Chunk bookkeeping of entry f at k-block kb (nk k-blocks per item).  Entry 0: chunks {0,1}, {2,3}, ...;
+// entry 1: {0}, {1,2}, {3,4}, ...; both end at the last k-block.
+__device__ __forceinline__ bool chunk_first(int f, int kb) { return f == 0 ? (kb % 2 == 0) : (kb == 0 || kb % 2 == 1); }
+__device__ __forceinline__ bool chunk_last(int f, int kb, int nk) {
+  return kb == nk - 1 || (f == 0 ? (kb % 2 == 1) : (kb % 2 == 0));
+}
+// Issue order within k-block kb: the entry that does not start a chunk first (the other one may still be
+// draining its previous partial).
+__device__ __forceinline__ int entry_at(int kb, int o) { return (kb % 2 == 0 && kb > 0) ? 1 - o : o; }
+
+__device__ __forceinline__ void decode_item(long item, int n_tiles, int& bm, int& bn, int& pair) {
+  pair = (int)(item / n_tiles);
+  const int t = (int)(item % n_tiles);
+  int m = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while ((m + 1) * (m + 2) / 2 <= t) ++m;
+  while (m * (m + 1) / 2 > t) --m;
+  bm = m;
+  bn = t - m * (m + 1) / 2;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    pi_fused_kernel(const __grid_constant__ PfMaps maps, int n, int K, int nb, int mode_even, int mode_odd,
+                    float* __restrict__ out, long out_bstride, int ldo, int* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* smem = smem_raw + (base - raw);
+  const uint32_t src0 = base, tr0 = base + SRC_STAGES * SRC_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SRC_STAGES * SRC_BYTES + TR_STAGES * TR_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + N_BARS);
+  __shared__ int s_abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nbt = (n + BM - 1) / BM;
+  const int n_tiles = nbt * (nbt + 1) / 2;
+  const int n_pairs = (nb + 1) / 2;
+  const long items = (long)n_tiles * n_pairs;
+  const int nk = (K + BK - 1) / BK;
+
+  uint32_t src_full[SRC_STAGES], src_empty[SRC_STAGES], tr_full[TR_STAGES], tr_empty[TR_STAGES];
+  for (int s = 0; s < SRC_STAGES; ++s) {
+    src_full[s] = smem_u32(&bars[s]);
+    src_empty[s] = smem_u32(&bars[SRC_STAGES + s]);
+  }
+  for (int s = 0; s < TR_STAGES; ++s) {
+    tr_full[s] = smem_u32(&bars[2 * SRC_STAGES + s]);
+    tr_empty[s] = smem_u32(&bars[2 * SRC_STAGES + TR_STAGES + s]);
+  }
+  const int ab = 2 * SRC_STAGES + 2 * TR_STAGES;
+  const uint32_t acc_full[2] = {smem_u32(&bars[ab]), smem_u32(&bars[ab + 1])};
+  const uint32_t acc_empty[2] = {smem_u32(&bars[ab + 2]), smem_u32(&bars[ab + 3])};
+  const uint32_t fin = smem_u32(&bars[ab + 4]);
+
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int s = 0; s < SRC_STAGES; ++s) {
+      mbar_init(src_full[s], 1);
+      mbar_init(src_empty[s], 5);       // four transform warps + the MMA thread's commit
+    }
+    for (int s = 0; s < TR_STAGES; ++s) {
+      mbar_init(tr_full[s], 4);         // one arrival per transform warp
+      mbar_init(tr_empty[s], 1);
+    }
+    for (int f = 0; f < 2; ++f) {
+      mbar_init(acc_full[f], 1);
+      mbar_init(acc_empty[f], 4);       // one arrival per drain warp
+    }
+    mbar_init(fin, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fence_async_smem();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 8) {
+    if (lane == 0) {
+      // ------------------------------------------------------------ TMA producer
+      long g = 0, issued = 0;
+      bool ok = true;
+      for (long it = blockIdx.x; it < items && ok; it += gridDim.x) {
+        int bm, bn, pair;
+        decode_item(it, n_tiles, bm, bn, pair);
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = (int)(g % SRC_STAGES);
+          const long u = g / SRC_STAGES;
+          if (u > 0 && !mbar_wait(src_empty[s], (uint32_t)((u - 1) & 1), err, 11)) { ok = false; break; }
+          if (*(volatile int*)&s_abort) { ok = false; break; }
+          const uint32_t st = src0 + s * SRC_BYTES;
+          mbar_expect_tx(src_full[s], TX_BYTES);
+          tma_load_2d(st, &maps.a, kb * BK, bm * BM, src_full[s]);
+          tma_load_2d(st + A_BYTES, &maps.bh, kb * BK, bn * BM, src_full[s]);
+          tma_load_2d(st + A_BYTES + H_BYTES, &maps.bl, kb * BK, bn * BM, src_full[s]);
+          tma_load_2d(st + W_OFF, &maps.w, kb * BK, 2 * pair, src_full[s]);
+          issued = g + 1;
+        }
+      }
+      if (!ok) {
+        s_abort = 1;
+        // wait for the copies that may still be in flight (the latest phase of each stage)
+        for (long q = issued > SRC_STAGES ? issued - SRC_STAGES : 0; q < issued; ++q)
+          mbar_wait(src_full[q % SRC_STAGES], (uint32_t)((q / SRC_STAGES) & 1), err, 12);
+      }
+    }
+  } else if (warp == 9) {
+    if (lane == 0) {
+      // ------------------------------------------------------------ MMA issuer
+      long g = 0;
+      long cf[2] = {0, 0};                 // chunks started per entry
+      bool ok = true;
+      for (long it = blockIdx.x; it < items && ok; it += gridDim.x) {
+        int bm, bn, pair;
+        decode_item(it, n_tiles, bm, bn, pair);
+        const int nf = min(2, nb - 2 * pair);
+        for (int kb = 0; kb < nk && ok; ++kb, ++g) {
+          const int s = (int)(g % SRC_STAGES), ts = (int)(g % TR_STAGES);
+          if (*(volatile int*)&s_abort || !mbar_wait(src_full[s], (uint32_t)((g / SRC_STAGES) & 1), err, 21) ||
+              !mbar_wait(tr_full[ts], (uint32_t)((g / TR_STAGES) & 1), err, 22)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sb = src0 + s * SRC_BYTES, tb = tr0 + ts * TR_BYTES;
+          for (int o = 0; o < 2 && ok; ++o) {
+            const int f = entry_at(kb, o);
+            if (f >= nf) continue;
+            const bool first = chunk_first(f, kb);
+            if (first) {
+              if (cf[f] > 0 && !mbar_wait(acc_empty[f], (uint32_t)((cf[f] - 1) & 1), err, 23)) { ok = false; break; }
+              ++cf[f];
+              tc_fence_after();
+            }
+            const uint32_t d = tmem + (uint32_t)(f * 128);
+#pragma unroll
+            for (int k = 0; k < BK / 16; ++k) {
+              const uint32_t off = k * 32;
+              const uint64_t ah = sdesc(tb + (2 * f) * H_BYTES + off, SBO64, SWZ64);
+              const uint64_t al = sdesc(tb + (2 * f + 1) * H_BYTES + off, SBO64, SWZ64);
+              const uint64_t bh = sdesc(sb + A_BYTES + off, SBO64, SWZ64);
+              const uint64_t bl = sdesc(sb + A_BYTES + H_BYTES + off, SBO64, SWZ64);
+              mma_bf16(d, ah, bh, IDESC, (first && k == 0) ? 0u : 1u);
+              mma_bf16(d, ah, bl, IDESC, 1u);
+              mma_bf16(d, al, bh, IDESC, 1u);
+            }
+            if (chunk_last(f, kb, nk)) mma_commit(acc_full[f]);
+          }
+          if (!ok) break;
+          mma_commit(src_empty[s]);
+          mma_commit(tr_empty[ts]);
+        }
+      }
+      if (!ok) s_abort = 1;
+      // every tensor-core operation issued above has completed once `fin` flips
+      mma_commit(fin);
+      mbar_wait(fin, 0, err, 24);
+    }
+  } else if (warp >= 4) {
+    // -------------------------------------------------------------- transform: one thread per row of the tile
+    const int r = threadIdx.x - 128;
+    long g = 0;
+    bool ok = true;
+    for (long it = blockIdx.x; it < items && ok; it += gridDim.x) {
+      int bm, bn, pair;
+      decode_item(it, n_tiles, bm, bn, pair);
+      const int nf = min(2, nb - 2 * pair);
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int s = (int)(g % SRC_STAGES), ts = (int)(g % TR_STAGES);
+        bool w_ok = !*(volatile int*)&s_abort && mbar_wait(src_full[s], (uint32_t)((g / SRC_STAGES) & 1), err, 31);
+        if (w_ok && g >= TR_STAGES)
+          w_ok = mbar_wait(tr_empty[ts], (uint32_t)((g / TR_STAGES - 1) & 1), err, 32);
+        if (!__all_sync(0xffffffffu, w_ok)) { ok = false; break; }
+        const uint8_t* sp = smem + s * SRC_BYTES;
+        const float* wrow = reinterpret_cast<const float*>(sp + W_OFF);
+        float a[BK];
+#pragma unroll
+        for (int c = 0; c < BK / 4; ++c) {   // 128-byte swizzle: 16-byte chunk c of row r sits at c ^ (r & 7)
+          const float4 v = *reinterpret_cast<const float4*>(sp + r * 128 + ((c ^ (r & 7)) << 4));
+          a[4 * c] = v.x;
+          a[4 * c + 1] = v.y;
+          a[4 * c + 2] = v.z;
+          a[4 * c + 3] = v.w;
+        }
+        uint8_t* tp = smem + SRC_STAGES * SRC_BYTES + ts * TR_BYTES;
+        for (int f = 0; f < nf; ++f) {
+          float wv[BK];                        // the entry's weights for this k-block (broadcast reads)
+#pragma unroll
+          for (int c = 0; c < BK / 4; ++c) {
+            const float4 t = *reinterpret_cast<const float4*>(wrow + f * BK + 4 * c);
+            wv[4 * c] = t.x;
+            wv[4 * c + 1] = t.y;
+            wv[4 * c + 2] = t.z;
+            wv[4 * c + 3] = t.w;
+          }
+#pragma unroll
+          for (int j = 0; j < BK / 8; ++j) {  // 64-byte swizzle: 16-byte chunk j of row r sits at j ^ ((r >> 1) & 3)
+            uint32_t hi[4], lo[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int k = 8 * j + 2 * e;
+              const float v0 = a[k] * wv[k], v1 = a[k + 1] * wv[k + 1];
+              hi[e] = pack_bf16(v0, v1);
+              const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&hi[e]);
+              lo[e] = pack_bf16(v0 - __low2float(h), v1 - __high2float(h));
+            }
+            const int off = r * 64 + ((j ^ ((r >> 1) & 3)) << 4);
+            *reinterpret_cast<uint4*>(tp + (2 * f) * H_BYTES + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4*>(tp + (2 * f + 1) * H_BYTES + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+          }
+        }
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(tr_full[ts]);
+          mbar_arrive(src_empty[s]);
+        }
+      }
+    }
+    if (!ok) s_abort = 1;
+  } else {
+    // -------------------------------------------------------------- drain + epilogue (TMEM lane quarter = warp)
+    const int q = warp;
+    long gd[2] = {0, 0};                  // drains done per entry
+    bool ok = true;
+    for (long it = blockIdx.x; it < items && ok; it += gridDim.x) {
+      int bm, bn, pair;
+      decode_item(it, n_tiles, bm, bn, pair);
+      const int nf = min(2, nb - 2 * pair);
+      const int m0 = bm * BM, n0 = bn * BM;
+      const int row = m0 + q * 32 + lane;
+      for (int kb = 0; kb < nk && ok; ++kb) {
+        for (int o = 0; o < 2; ++o) {
+          const int f = entry_at(kb, o);
+          if (f >= nf || !chunk_last(f, kb, nk)) continue;
+          const bool first_of_item = f == 0 ? kb <= 1 : kb == 0;
+          const bool final = kb == nk - 1;
+          bool w_ok = !*(volatile int*)&s_abort && mbar_wait(acc_full[f], (uint32_t)(gd[f] & 1), err, 41);
+          if (!__all_sync(0xffffffffu, w_ok)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
+          const int b = 2 * pair + f;
+          const int mode = (b & 1) ? mode_odd : mode_even;
+          float* ob = out + (long)b * out_bstride;
+#pragma unroll 1
+          for (int c = 0; c < 4; ++c) {
+            uint32_t v[32], w[32];
+            tmem_ld32(lane_addr + (uint32_t)(f * 128 + c * 32), v);
+            if (!first_of_item) tmem_ld32(lane_addr + (uint32_t)(256 + f * 128 + c * 32), w);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const float x = __uint_as_float(v[j]) + (first_of_item ? 0.f : __uint_as_float(w[j]));
+              v[j] = __float_as_uint(x);
+            }
+            if (!final) {
+              tmem_st32(lane_addr + (uint32_t)(256 + f * 128 + c * 32), v);
+              continue;
+            }
+            // epilogue: lower element (row, col <= row) in place, mirrored element (col, row) for col < row
+            const int c0 = n0 + c * 32;
+            if (row < n) {
+#pragma unroll
+              for (int j = 0; j < 32; ++j) {
+                const int col = c0 + j;
+                if (col > row || col >= n) continue;
+                const float x = __uint_as_float(v[j]);
+                ob[(long)row * ldo + col] = mode == 0 ? x : (mode == 1 ? ((col == row ? 1.f : 0.f) - x) : -x);
+              }
+            }
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int col = c0 + j;
+              if (row < n && col < row && col < n) {
+                const float x = __uint_as_float(v[j]);
+                ob[(long)col * ldo + row] = mode == 0 ? x : -x;
+              }
+            }
+          }
+          if (!final) tmem_wait_st();
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(acc_empty[f]);
+          ++gd[f];
+        }
+      }
+    }
+    if (!ok) s_abort = 1;
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// w[b][k] for k < K, in FP64 rounded to FP32 (one evaluation per entry and pair).  Kinds: 0 Pi(i xi):
+// -4D/(D^2 + xi^2); 1 Re c(x); 2 Im c(x) (broadening eta); 3 unit weight; 4 Pi(i xi) - Pi(0): 4 xi^2/(D (D^2+xi^2)).
+__device__ __forceinline__ double pair_weight(int kind, double D, double p, double eta) {
+  if (kind == 0) return -4.0 * D / (D * D + p * p);
+  if (kind == 3) return 1.0;
+  if (kind == 4) return 4.0 * p * p / (D * (D * D + p * p));
+  const double a1 = p - D, a2 = -p - D, e2 = eta * eta;
+  const double d1 = a1 * a1 + e2, d2 = a2 * a2 + e2;
+  if (kind == 1) return 2.0 * (a1 / d1 + a2 / d2);
+  return -2.0 * eta * (1.0 / d1 + 1.0 / d2);
+}
+
+__global__ void pf_weight_kernel(const double* __restrict__ eps, int n_occ, int n_virt, int K,
+                                 const int* __restrict__ kinds, const double* __restrict__ params, double eta,
+                                 float* __restrict__ w, int ldw) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+  if (k >= ldw) return;
+  float v = 0.f;
+  if (k < K) {
+    const int i = k / n_virt, a = k - i * n_virt;
+    v = (float)pair_weight(kinds[b], eps[n_occ + a] - eps[i], params[b], eta);
+  }
+  w[(long)b * ldw + k] = v;
+}
+
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+PFN_encodeTiled encoder() {
+  static PFN_encodeTiled fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_encodeTiled>(p);
+  }
+  return fn;
+}
+
+bool map2d(CUtensorMap* map, CUtensorMapDataType dt, int esize, const void* ptr, int cols, int rows, long ld,
+           int box_cols, int box_rows, CUtensorMapSwizzle swz) {
+  PFN_encodeTiled enc = encoder();
+  if (!enc || (reinterpret_cast<uintptr_t>(ptr) & 15) || ((ld * esize) & 15)) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * esize)};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  return enc(map, dt, 2, const_cast<void*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess)
+      n = 148;
+  }
+  return n;
+}
+
+}  // namespace
+
+int pf_ldw(int K) { return (K + 3) / 4 * 4; }
+
+cudaError_t tc_pair_weights(const double* eps, int n_occ, int n_virt, int K, const int* kinds, const double* params,
+                            double eta, int nb, float* w, cudaStream_t s) {
+  const int ldw = pf_ldw(K);
+  if (nb <= 0) return cudaSuccess;
+  pf_weight_kernel<<<dim3((ldw + 255) / 256, nb), 256, 0, s>>>(eps, n_occ, n_virt, K, kinds, params, eta, w, ldw);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_pi_fused(const float* B, long ldb, int n, int K, const float* w, int nb, const __nv_bfloat16* Bhi,
+                        const __nv_bfloat16* Blo, int mode_even, int mode_odd, float* out, long out_bstride, int ldo,
+                        int* err, cudaStream_t s, int max_ctas) {
+  if (nb <= 0 || n <= 0 || K <= 0) return cudaSuccess;
+  PfMaps maps;
+  const int ldh = tc_ld(K), ldw = pf_ldw(K);
+  if (!map2d(&maps.a, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, B, K, n, ldb, BK, BM, CU_TENSOR_MAP_SWIZZLE_128B) ||
+      !map2d(&maps.bh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Bhi, K, n, ldh, BK, BM, CU_TENSOR_MAP_SWIZZLE_64B) ||
+      !map2d(&maps.bl, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Blo, K, n, ldh, BK, BM, CU_TENSOR_MAP_SWIZZLE_64B) ||
+      !map2d(&maps.w, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, w, K, nb, ldw, BK, 2, CU_TENSOR_MAP_SWIZZLE_NONE))
+    return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(pi_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int nbt = (n + BM - 1) / BM;
+  const long items = (long)nbt * (nbt + 1) / 2 * ((nb + 1) / 2);
+  int grid = sm_count();
+  if (max_ctas > 0 && max_ctas < grid) grid = max_ctas;
+  if (items < grid) grid = (int)items;
+  pi_fused_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(maps, n, K, nb, mode_even, mode_odd, out, out_bstride, ldo, err);
+  return cudaGetLastError();
+}
+
+}  // namespace gw

@@ -41,6 +41,19 @@ struct TcEpi {
 
 // Row length (elements) of the split operand arrays for contraction length K (multiple of 8: 16-byte rows).
 int tc_ld(int K);
+// Row length (elements) of FP32 arrays read by TMA with contraction length K (multiple of 4: 16-byte rows).
+int pf_ldw(int K);
+// Weight table w [nb][pf_ldw(K)] (device, FP32, zero padded): w[b][k] = weight(kinds[b], D_k, params[b]) evaluated
+// in FP64, with the kinds of tc_scale_split below (0 Pi(i xi), 1 Re c(x), 2 Im c(x), 3 unit, 4 Pi(i xi) - Pi(0)).
+cudaError_t tc_pair_weights(const double* eps, int n_occ, int n_virt, int K, const int* kinds, const double* params,
+                            double eta, int nb, float* w, cudaStream_t s);
+// out_b = f(B diag(w_b) B^T) for b < nb on the tensor cores with the weight applied in the kernel (pi_fused.cu):
+// B FP32 [n][ldb] (ldb a multiple of 4), its BF16 hi/lo split Bhi/Blo [n][tc_ld(K)], w from tc_pair_weights;
+// out [nb][n][ldo] FP32 at batch stride out_bstride, full symmetric (lower tiles computed and mirrored);
+// mode_even / mode_odd for even / odd b: 0 v, 1 delta - v, 2 -v.  max_ctas > 0 caps the persistent grid.
+cudaError_t tc_pi_fused(const float* B, long ldb, int n, int K, const float* w, int nb, const __nv_bfloat16* Bhi,
+                        const __nv_bfloat16* Blo, int mode_even, int mode_odd, float* out, long out_bstride, int ldo,
+                        int* err, cudaStream_t s, int max_ctas = 0);
 // A_b[m][k] = B[m][k] * w(kinds[b], D_k, params[b]) split into BF16 hi/lo, [batch][M][tc_ld(K)].
 // kinds: 0 Pi(i xi) weight -4D/(D^2+xi^2) (param xi); 1 Re c(x); 2 Im c(x) (param x, broadening eta);
 // 3 unit weight.  kinds/params are device arrays of length batch.  B is FP32 [M][K].  The weights are evaluated
@@ -75,7 +88,7 @@ cudaError_t tc_ns_init(const float* A, int n, int batch, const float* lam, float
 // Y_b = (X_b + X_b^T)/2 for n x n FP32 matrices (out of place), with its split parts (rows of tc_ld(n)).
 cudaError_t tc_sym_split(const float* X, int n, int batch, float* Y, __nv_bfloat16* hi, __nv_bfloat16* lo,
                          __nv_bfloat16* lo2, cudaStream_t s);
-// out[k][m] = B[m][k] split into BF16 hi/lo with rows of tc_ld(M) elements (B FP32 [M][K]).
+// out[k][m] = B[m][k] split into BF16 hi/lo with rows of tc_ld(M) elements (B FP32 [M][ldb], ldb 0 = K).
 cudaError_t tc_transpose_split(const float* B, int M, int K, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s,
-                               __nv_bfloat16* lo2 = nullptr);
+                               __nv_bfloat16* lo2 = nullptr, long ldb = 0);
 }  // namespace gw

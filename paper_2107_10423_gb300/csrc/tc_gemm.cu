@@ -515,14 +515,14 @@ cudaError_t tc_gemm(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int batc
 }
 
 // B^T split: out[k][m] = B[m][k] as BF16 hi/lo, rows of length tc_ld(M).  32 x 32 tiles through shared memory.
-__global__ void transpose_split_kernel(const float* __restrict__ B, int M, int K, int ld,
+__global__ void transpose_split_kernel(const float* __restrict__ B, int M, int K, long ldb, int ld,
                                        __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
                                        __nv_bfloat16* __restrict__ lo2) {
   __shared__ float t[32][33];
   const int k0 = blockIdx.x * 32, m0 = blockIdx.y * 32;
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int m = m0 + r, k = k0 + threadIdx.x;
-    t[r][threadIdx.x] = (m < M && k < K) ? B[(long)m * K + k] : 0.f;
+    t[r][threadIdx.x] = (m < M && k < K) ? B[(long)m * ldb + k] : 0.f;
   }
   __syncthreads();
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
@@ -653,10 +653,10 @@ cudaError_t tc_sym_split(const float* X, int n, int batch, float* Y, __nv_bfloat
 }
 
 cudaError_t tc_transpose_split(const float* B, int M, int K, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s,
-                               __nv_bfloat16* lo2) {
+                               __nv_bfloat16* lo2, long ldb) {
   const int ld = tc_ld(M);
   dim3 grid((K + 31) / 32, (ld + 31) / 32);
-  transpose_split_kernel<<<grid, dim3(32, 8), 0, s>>>(B, M, K, ld, hi, lo, lo2);
+  transpose_split_kernel<<<grid, dim3(32, 8), 0, s>>>(B, M, K, ldb > 0 ? ldb : K, ld, hi, lo, lo2);
   return cudaGetLastError();
 }
 

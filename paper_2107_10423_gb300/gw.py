@@ -33,7 +33,8 @@ class Config(ctypes.Structure):
                 ("precision", ctypes.c_int), ("minres_maxit", ctypes.c_int), ("minres_tol", ctypes.c_double),
                 ("minres_fallback_tol", ctypes.c_double), ("qp_maxit", ctypes.c_int), ("qp_tol", ctypes.c_double),
                 ("static_subtraction", ctypes.c_int), ("max_rhs_batch", ctypes.c_int), ("workspace_mb", ctypes.c_int),
-                ("refine_tol", ctypes.c_double), ("op_parts", ctypes.c_int), ("deriv_fp64", ctypes.c_int), ("refine_df", ctypes.c_int)]
+                ("refine_tol", ctypes.c_double), ("op_parts", ctypes.c_int), ("deriv_fp64", ctypes.c_int), ("refine_df", ctypes.c_int),
+                ("tc_max_ctas", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
