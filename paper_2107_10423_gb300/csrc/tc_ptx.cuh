@@ -7,7 +7,7 @@
 namespace gw {
 namespace ptx {
 
-constexpr long long kWaitLimit = 1ll << 26;           // bounded spin on every mbarrier
+constexpr unsigned long long kWaitNs = 4000000000ull;   // every mbarrier wait gives up after 4 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -37,10 +37,21 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait; returns false (and records `code` in *err) if the phase did not complete in time.
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait; returns false (and records `code` in *err) if the phase did not complete within kWaitNs.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
-  for (long long i = 0; i < kWaitLimit; ++i)
-    if (mbar_try(bar, parity)) return true;
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  for (;;) {
+    for (int i = 0; i < 256; ++i)
+      if (mbar_try(bar, parity)) return true;
+    if (globaltimer_ns() - t0 > kWaitNs) break;
+  }
   atomicCAS(err, 0, code);
   return false;
 }

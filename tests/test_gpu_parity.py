@@ -102,25 +102,16 @@ def test_qp_linearised_fp64_vs_oracle(gw, kind):
 
 @pytest.mark.parametrize("kind", ["water1", "water2", "water3_core"])
 def test_qp_steptree_fp64_vs_oracle(gw, kind):
-    """Same step-tree path as the oracle gives the same root to 1e-5 Ha.  The QP equation of these synthetic
-    systems has many roots and near-pole Newton steps amplify 1e-12 differences, so a state whose path left
-    the oracle's must still be converged and sit on a root of the exact equation (|f Z| < 1e-5 Ha)."""
+    """The FP64 step tree on the GPU takes the oracle's step sequence (same branch constants and bracket rules,
+    Sec. 3.4) and so reaches the same root of the QP equation, for every state, to 1e-5 Ha."""
     s = _sys(kind)
     B, Bn = s.b_ia(), s.b_nm()
     ref = O.g0w0_cd(s.eps, s.n_occ, B, Bn, s.targets, eta=1e-3, qp_maxit=200)
     with gw.Plan(s.eps, s.n_occ, B, Bn, s.targets, qp_maxit=200, **TIGHT) as p:
         e, z, st = p.qp_solve(gw.GW_QP_STEPTREE)
-    cd = ref["cd"]
-    same = 0
-    for t, n in enumerate(s.targets):
-        if abs(e[t] - ref["e_qp"][t]) < 1e-5:
-            same += 1
-            continue
-        assert st[t] != 1, (t, e[t], ref["e_qp"][t])
-        sg, dsg = cd.sigma_c(t, e[t])
-        assert abs((s.eps[n] + sg - e[t]) / (1.0 - dsg)) < 1e-5, (t, e[t], ref["e_qp"][t])
-    print(f"{kind}: {same}/{len(s.targets)} states on the oracle's root")
-    assert same >= len(s.targets) // 2
+    assert np.all(st != 1) and np.all(ref["status"] == 0)
+    np.testing.assert_allclose(e, ref["e_qp"], rtol=0, atol=1e-5)
+    np.testing.assert_allclose(z, ref["Z"], rtol=0, atol=1e-5)
 
 
 def test_qp_paper_minres_defaults(gw):
