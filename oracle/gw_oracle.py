@@ -183,10 +183,15 @@ class CDSelfEnergy:
 
     Imaginary-axis table (Algorithm 1, loop over the imaginary grid): W^c_nm(i xi_g) for every
     grid point, plus the static W^c_nm(0), each from a dense LU solve with 1 - Pi(i xi).
-    Residues (eq. "rnn"): W^c_nm(e_m - omega) from a dense complex LU solve with 1 - Pi(x)."""
+    Residues (eq. "rnn"): W^c_nm(e_m - omega) from a dense complex LU solve with 1 - Pi(x).
 
-    def __init__(self, eps, n_occ, B_ia, B_nm, targets, xi, wt, eta=1e-3):
+    ``eps`` are the energies in Pi (the pair energies D_ia of W); ``eps_g`` (default ``eps``) are the poles of
+    G, the e_m of the I and R terms.  They differ inside the eigenvalue self-consistency loop of Algorithm 1
+    (``evgw``)."""
+
+    def __init__(self, eps, n_occ, B_ia, B_nm, targets, xi, wt, eta=1e-3, eps_g=None):
         self.eps = np.asarray(eps, dtype=np.float64)
+        self.eps_g = self.eps if eps_g is None else np.asarray(eps_g, dtype=np.float64)
         self.n_occ = int(n_occ)
         self.B_ia = B_ia
         self.B_nm = B_nm                       # [n_t, n_bas, n_aux]
@@ -214,7 +219,7 @@ class CDSelfEnergy:
         Literal form (Algorithm 1): (1/pi) sum_m sum_g w_g W_nm(i xi_g) a/(a^2 + xi_g^2), a = omega - e_m.
         Static-subtracted form: W_nm(i xi_g) -> W_nm(i xi_g) - W_nm(0) plus the exact
         W_nm(0) sgn(a)/2 (whose delta-function derivative cancels the theta jump of R)."""
-        a = omega - self.eps                                  # [n_bas]
+        a = omega - self.eps_g                                # [n_bas]
         xi2 = self.xi[None, :] ** 2
         a2 = a[:, None] ** 2
         if static_subtraction:
@@ -240,8 +245,8 @@ class CDSelfEnergy:
         """R_nn(omega) of eq. "rnn" (real part) and its omega-derivative."""
         R = 0.0
         dR = 0.0
-        for m, sgn, th in residue_set(self.eps, self.n_occ, omega):
-            x = self.eps[m] - omega
+        for m, sgn, th in residue_set(self.eps_g, self.n_occ, omega):
+            x = self.eps_g[m] - omega
             w, dw = (residue_fn or self.residue_w)(t, m, x)
             R += sgn * th * w.real
             dR -= sgn * th * dw.real          # d/domega W(e_m - omega) = -W'(x)
@@ -468,6 +473,73 @@ def g0w0_cd(eps, n_occ, B_ia, B_nm, targets, n_freq=128, x0=0.5, eta=1e-3, mode=
         sx.append(sxn)
     return {"e_qp": np.array(e_qp), "Z": np.array(Zs), "status": np.array(st), "sigma_x": np.array(sx),
             "n_residue_solves": cd.n_residue_solves, "cd": cd}
+
+
+# --------------------------------------------------------------------------
+# Eigenvalue self-consistency (Algorithm 1, outer loop over iter; Sec. 1 evGW0 / evGW)
+# --------------------------------------------------------------------------
+def scissor_energies(eps_ks, n_occ, targets, e_qp):
+    """Energies for the next cycle: the targets take their QP energies; every other occupied state moves by the
+    QP correction of the highest occupied target, every other virtual state by that of the lowest virtual
+    target (no shift where a class has no target)."""
+    eps_ks = np.asarray(eps_ks, dtype=np.float64)
+    out = eps_ks.copy()
+    occ = [(eps_ks[n], e - eps_ks[n]) for n, e in zip(targets, e_qp) if n < n_occ]
+    vir = [(eps_ks[n], e - eps_ks[n]) for n, e in zip(targets, e_qp) if n >= n_occ]
+    d_occ = max(occ)[1] if occ else 0.0
+    d_vir = min(vir)[1] if vir else 0.0
+    out[:n_occ] += d_occ
+    out[n_occ:] += d_vir
+    for n, e in zip(targets, e_qp):
+        out[n] = e
+    return out
+
+
+def evgw(eps, n_occ, B_ia, B_nm, targets, update_w=False, mode="steptree", max_iter=30, tol=1e-6, n_freq=128,
+         x0=0.5, eta=1e-3, qp_tol=1e-8, qp_maxit=50, static_subtraction=True):
+    """Eigenvalue self-consistent GW: each cycle of Algorithm 1's outer loop solves the QP equations
+    e_QP = e_KS + Re Sigma_c[G, W](e_QP) (V_xc := Sigma_x) with G built from the current energies (evGW0) and, if
+    ``update_w``, W built from them too (evGW); the energies are then updated (``scissor_energies``).  Cycle 0 is
+    G0W0.  The QP search of each cycle starts from the previous cycle's energy: one Newton step (linearised) or the
+    step tree.  Stops when no target moves by more than ``tol``.  Returns dict e_qp, Z, status, iterations."""
+    eps_ks = np.asarray(eps, dtype=np.float64)
+    xi, wt = mgl_grid(n_freq, x0)
+    cur = eps_ks.copy()
+    e_prev = np.array([eps_ks[n] for n in targets])
+    e_qp, Zs, st = e_prev.copy(), np.ones(len(targets)), np.zeros(len(targets), dtype=int)
+    it = 0
+    for it in range(1, max_iter + 1):
+        cd = CDSelfEnergy(cur if update_w else eps_ks, n_occ, B_ia, B_nm, targets, xi, wt, eta, eps_g=cur)
+        e_new, Zs, st = [], [], []
+        for t, n in enumerate(targets):
+            fn = lambda w, t=t: cd.sigma_c(t, w, static_subtraction)
+            if mode == "linearised":
+                w0 = e_prev[t]
+                sg, dsg = fn(w0)
+                Z = 1.0 / (1.0 - dsg)
+                e, s = w0 + Z * (eps_ks[n] + sg - w0), 0
+            else:
+                e, Z, s = _qp_steptree_from(eps_ks[n], e_prev[t], fn, qp_tol, qp_maxit)
+            e_new.append(e)
+            Zs.append(Z)
+            st.append(s)
+        e_new = np.array(e_new)
+        delta = np.max(np.abs(e_new - e_prev))
+        e_qp, e_prev = e_new, e_new
+        cur = scissor_energies(eps_ks, n_occ, targets, e_qp)
+        if delta < tol:
+            break
+    return {"e_qp": e_qp, "Z": np.array(Zs), "status": np.array(st), "iterations": it,
+            "converged": bool(delta < tol), "eps_final": cur}
+
+
+def _qp_steptree_from(e_ks, w0, sigma_fn, tol, maxit):
+    """The step tree of ``qp_steptree`` for f(w) = e_ks + Sigma_c(w) - w, started at w0 instead of e_ks."""
+    shifted = lambda w: sigma_fn(w)
+    # qp_steptree starts at its first argument and solves e + shift + Sigma(w) - w = 0: start at w0 with
+    # shift = e_ks - w0 so that the equation is unchanged
+    w, Z, st, n, trace = qp_steptree(w0, e_ks - w0, shifted, tol=tol, maxit=maxit)
+    return w, Z, st
 
 
 def g0w0_sd(eps, n_occ, B_ia, B_nm, targets, eta=0.0, mode="steptree", vxc=None, qp_tol=1e-8, qp_maxit=50):

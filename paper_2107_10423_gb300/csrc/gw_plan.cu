@@ -62,12 +62,11 @@ struct gw_plan {
   __nv_bfloat16* d_Bnlo2 = nullptr;
   bool screening_done = false;
   int ns_iters_last = 0;
-  float ns_lam_global = 0.f;   // spectrum bound of eps(i xi) for every xi: lambda_max(eps(0)), padded
   int ns_kmax = 0;
   int ns_ndiff = 0;           // lowest grid points whose W column is built in the difference form
   std::vector<DevBuf*> bufs;
   DevBuf ws_mat, ws_info, ws_scratch, ws_gout, ws_xi, tc_kind, tc_par, tc_err, tc_w, ns_E, ns_X, ns_X2, ns_Xa, ns_Xb, ns_T, ns_lam,
-      ns_E0;
+      ns_E0, ns_vec;
   DevBuf mr_V, mr_U, mr_S, mr_vprev, mr_v, mr_d1, mr_d2, mr_x, mr_st, mr_rt, mr_rm, mr_xf, mr_wre, mr_wim,
       mr_dwre, mr_it, mr_res, mr_cnt, mr_Vhi, mr_Vlo, mr_Uhi, mr_Ulo, mr_Vlo2, mr_Ulo2, mr_V64;
   DevBuf sg_I, sg_dI, sg_R, sg_dR, sg_om, sg_start, sg_coef, sg_act, qp_st;
@@ -84,7 +83,7 @@ struct gw_plan {
   std::vector<Mark> marks;
 
   gw_plan() {
-    DevBuf* all[] = {&ws_mat, &ws_info, &ws_scratch, &ws_gout, &ws_xi, &tc_kind, &tc_par, &tc_err, &tc_w, &ns_E, &ns_X, &ns_X2, &ns_Xa, &ns_Xb, &ns_T, &ns_lam, &ns_E0, &mr_V, &mr_U, &mr_S, &mr_vprev,
+    DevBuf* all[] = {&ws_mat, &ws_info, &ws_scratch, &ws_gout, &ws_xi, &tc_kind, &tc_par, &tc_err, &tc_w, &ns_E, &ns_X, &ns_X2, &ns_Xa, &ns_Xb, &ns_T, &ns_lam, &ns_E0, &ns_vec, &mr_V, &mr_U, &mr_S, &mr_vprev,
                      &mr_v, &mr_d1, &mr_d2, &mr_x, &mr_st, &mr_rt, &mr_rm, &mr_xf, &mr_wre, &mr_wim,
                      &mr_dwre, &mr_it, &mr_res, &mr_cnt, &mr_Vhi, &mr_Vlo, &mr_Uhi, &mr_Ulo, &mr_Vlo2, &mr_Ulo2, &mr_V64, &sg_I, &sg_dI, &sg_R, &sg_dR, &sg_om, &sg_start,
                      &sg_coef, &sg_act, &qp_st, &fb_A, &fb_y, &fb_piv, &fb_info, &fb_idx, &fb_y64, &fb_V32, &fb_S32, &fb_Vp, &fb_Up, &fb_x, &fb_V64, &fb_U64, &fb_S64, &fb_sel, &fb_pos, &fb_rho, &fb_xs, &fb_Bh, &fb_Bl};
@@ -241,7 +240,8 @@ gw_status ns_w_table(gw_plan* P, int g0, int nc) {
   TRY(ensure(P, P->ns_T, 3 * sizeof(__nv_bfloat16) * sz));
   TRY(ensure(P, P->ns_X, sizeof(float) * mat * nc));
   TRY(ensure(P, P->ns_X2, sizeof(float) * mat * nc));
-  TRY(ensure(P, P->ns_lam, sizeof(float) * nc));
+  TRY(ensure(P, P->ns_lam, sizeof(float) * 4 * nc));         // per matrix: lambda estimates, shift, a_b
+  TRY(ensure(P, P->ns_vec, sizeof(float) * 2 * (size_t)nc * n));
   TRY(ensure(P, P->tc_err, sizeof(int)));
   CK(cudaMemsetAsync(P->tc_err.p, 0, sizeof(int), P->stream));
   const float* eps = reinterpret_cast<const float*>(P->ws_mat.p);
@@ -253,33 +253,42 @@ gw_status ns_w_table(gw_plan* P, int g0, int nc) {
   const gw::TcOperand Xs[2] = {parts(P->ns_Xa), parts(P->ns_Xb)};
   float* X = as<float>(P->ns_X);
   const size_t t0 = tick(P);
-  // One spectrum bound and one iteration count for every frequency, so that every matrix goes through the
-  // same sequence of operations (errors then vary smoothly with xi, which the I-term derivative needs near
-  // xi = 0).  eps(i xi) <= eps(0) in the Loewner order, so lambda_max(eps(0)) bounds all of them; the first
-  // chunk holds xi = 0.  Power iteration under-estimates: pad by 25%.
-  if (g0 == 0 || P->ns_kmax == 0) {
-    CK(gw::tc_power_lmax(eps, n, nc, 30, as<float>(P->ns_lam), P->stream));
-    std::vector<float> lam(nc);
-    CK(cudaMemcpyAsync(lam.data(), P->ns_lam.p, sizeof(float) * nc, cudaMemcpyDeviceToHost, P->stream));
-    CK(cudaStreamSynchronize(P->stream));
-    float lmax = 1.0f;
-    for (int b = 0; b < nc; ++b) lmax = std::max(lmax, lam[b]);
-    P->ns_lam_global = lmax * 1.25f;
-    // iterate k has error rho0^(2^k), rho0 = (lmax - 1)/(lmax + 1): two-part iterations down to ~1e-5, then
-    // one three-part iteration (quadratic: to the FP32 floor)
-    const double rho0 = (P->ns_lam_global - 1.0) / (P->ns_lam_global + 1.0);
-    int k = 2;
-    if (rho0 > 0.0) k = std::max(2, (int)std::ceil(std::log2(11.5 / -std::log(rho0))) + 1);
-    P->ns_kmax = std::min(k, 24);
+  // Spectrum of each eps_b = 1 - Pi(i xi_b) in [L_b, H_b]: H_b = 1.25 x the power-iteration estimate of
+  // lambda_max (power iteration approaches it from below), L_b = max(1, 0.75 x the estimate of lambda_min from the
+  // shifted iteration, which approaches it from above); eps >= 1 because -Pi is positive semidefinite.  With
+  // a_b = 2/(L_b + H_b) the first iterate X = 2 a I - a^2 eps leaves I - X eps = (I - a eps)^2, every eigenvalue in
+  // [0, rho_b^2], rho_b = (H_b - L_b)/(H_b + L_b), and each Newton-Schulz step squares it.  An eigenvalue outside
+  // the estimates still converges (0 < a lambda < 2 for lambda < L_b + H_b), only more slowly.
+  // One iteration count for every frequency: the first chunk (xi = 0 and the lowest grid points, the widest
+  // spectra) fixes it; a later chunk that needs more takes more.
+  float* f_hi = as<float>(P->ns_lam);
+  float* f_lo = f_hi + nc;
+  float* f_ab = f_hi + 3 * nc;
+  CK(gw::tc_spectrum_bounds(eps, n, nc, 20, 1.25f, f_hi, f_lo, f_hi + 2 * nc, as<float>(P->ns_vec),
+                            as<float>(P->ns_vec) + (size_t)nc * n, P->stream));
+  P->stats.n_kernel_launches += 2 + 2 * 2 * 20 + 1;
+  std::vector<float> hl(2 * nc);
+  CK(cudaMemcpyAsync(hl.data(), f_hi, sizeof(float) * 2 * nc, cudaMemcpyDeviceToHost, P->stream));
+  CK(cudaStreamSynchronize(P->stream));
+  std::vector<float> ab(nc);
+  double rho = 0.0;
+  for (int b = 0; b < nc; ++b) {
+    const double H = 1.25 * std::max(1.0f, hl[b]);
+    const double L = std::max(1.0, 0.75 * (H - hl[nc + b]));
+    ab[b] = (float)(2.0 / (L + H));
+    rho = std::max(rho, (H - L) / (H + L));
   }
-  const int kmax = P->ns_kmax;
-  {
-    std::vector<float> lam(nc, P->ns_lam_global);
-    CK(cudaMemcpyAsync(P->ns_lam.p, lam.data(), sizeof(float) * nc, cudaMemcpyHostToDevice, P->stream));
-  }
+  CK(cudaMemcpyAsync(f_ab, ab.data(), sizeof(float) * nc, cudaMemcpyHostToDevice, P->stream));
+  // two-part iterations until rho^(2^k) <= e^-11.5 (about 1e-5), then one three-part iteration (quadratic: to
+  // the FP32 floor)
+  int k = 2;
+  if (rho > 0.0) k = std::max(2, (int)std::ceil(std::log2(11.5 / -std::log(rho))) + 1);
+  k = std::min(k, 24);
+  if (g0 == 0 || P->ns_kmax == 0) P->ns_kmax = k;
+  const int kmax = std::max(k, P->ns_kmax);
   CK(gw::tc_split_rows(eps, nc * n, n, n, const_cast<__nv_bfloat16*>(E.p[0]), const_cast<__nv_bfloat16*>(E.p[1]),
                        P->stream, const_cast<__nv_bfloat16*>(E.p[2])));
-  CK(gw::tc_ns_init(eps, n, nc, as<float>(P->ns_lam), X, const_cast<__nv_bfloat16*>(Xs[0].p[0]),
+  CK(gw::tc_ns_init(eps, n, nc, f_ab, X, const_cast<__nv_bfloat16*>(Xs[0].p[0]),
                     const_cast<__nv_bfloat16*>(Xs[0].p[1]), P->stream, const_cast<__nv_bfloat16*>(Xs[0].p[2])));
   int cur = 0;
   float* Xf[2] = {X, as<float>(P->ns_X2)};
@@ -1425,6 +1434,7 @@ gw_status gw_plan_footprint(const gw_config* c, int n_t, unsigned flags, unsigne
     b += 4 * nb * ldf + 16 * nb;
     const u64 per_ns = n * ldn * 24 + n * n * 8;                             // Newton-Schulz split/FP32 iterates
     b += capped(per_ns, per_ns * n_g1) + 6 * n * ldn + 4 * n_g1;             // + the split eps(0)^-1 - 1
+    b += 8 * n * n_g1 + 16 * n_g1;                                           // spectrum-estimate vectors
   } else {
     b += 8 * (u64)gw::trsm_w_scratch_elems<double>(c->n_aux, gw::trsm_w_default_ctas());
   }

@@ -78,12 +78,15 @@ cudaError_t tc_gemm_ex(const TcOperand& A, int batch, const TcOperand& B, int b_
 // rows x cols FP32 (row length lds) split into BF16 hi/lo rows of tc_ld(cols) elements (zero padded).
 cudaError_t tc_split_rows(const float* src, int rows, int cols, int lds, __nv_bfloat16* hi, __nv_bfloat16* lo,
                           cudaStream_t s, __nv_bfloat16* lo2 = nullptr);
-// Largest eigenvalue estimate of each SPD matrix A_b (n x n FP32, batch stride n*n) by `iters` power steps,
-// written to lam[b] (device).
-cudaError_t tc_power_lmax(const float* A, int n, int batch, int iters, float* lam, cudaStream_t s);
-// X_b = 2 a_b I - a_b^2 A_b with a_b = 2/(1 + lam_b) (first Newton-Schulz iterate), FP32 out [b][n][n] and split
+// Spectrum estimates of SPD matrices A_b (n x n FP32, batch stride n*n), by `iters` power steps each (device
+// outputs [batch]): hi_b, the Rayleigh quotient of A_b (an estimate of lambda_max from below), and lo_b = the
+// Rayleigh quotient of s_b I - A_b with s_b = pad * hi_b (so s_b - lo_b estimates lambda_min from above).
+// shift [batch], v and y [batch][n] are device work space.
+cudaError_t tc_spectrum_bounds(const float* A, int n, int batch, int iters, float pad, float* hi, float* lo,
+                               float* shift, float* v, float* y, cudaStream_t s);
+// X_b = 2 a_b I - a_b^2 A_b (first Newton-Schulz iterate) with a_b = ab[b] (device), FP32 out [b][n][n] and split
 // rows [b][n][tc_ld(n)].
-cudaError_t tc_ns_init(const float* A, int n, int batch, const float* lam, float* X, __nv_bfloat16* hi,
+cudaError_t tc_ns_init(const float* A, int n, int batch, const float* ab, float* X, __nv_bfloat16* hi,
                        __nv_bfloat16* lo, cudaStream_t s, __nv_bfloat16* lo2 = nullptr);
 // Y_b = (X_b + X_b^T)/2 for n x n FP32 matrices (out of place), with its split parts (rows of tc_ld(n)).
 cudaError_t tc_sym_split(const float* X, int n, int batch, float* Y, __nv_bfloat16* hi, __nv_bfloat16* lo,

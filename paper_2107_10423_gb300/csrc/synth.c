@@ -55,15 +55,20 @@ static inline double normal_at(uint64_t seed, uint32_t P, uint32_t p, uint32_t q
   return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
 }
 
-/* B_ia[P][i*n_virt + a] = sigma * N(seed; P, i, n_occ + a). */
-void synth_b_ia(uint64_t seed, double sigma, int n_aux, int n_occ, int n_virt, double* out) {
+/* Rows P0 .. P0 + n_rows - 1 of B_ia: out[P - P0][i*n_virt + a] = sigma * N(seed; P, i, n_occ + a). */
+void synth_b_ia_rows(uint64_t seed, double sigma, int P0, int n_rows, int n_occ, int n_virt, double* out) {
   long n_ov = (long)n_occ * n_virt;
 #pragma omp parallel for schedule(static)
-  for (long P = 0; P < n_aux; ++P)
+  for (long r = 0; r < n_rows; ++r)
     for (int i = 0; i < n_occ; ++i)
       for (int a = 0; a < n_virt; ++a)
-        out[P * n_ov + (long)i * n_virt + a] =
-            sigma * normal_at(seed, (uint32_t)P, (uint32_t)i, (uint32_t)(n_occ + a));
+        out[r * n_ov + (long)i * n_virt + a] =
+            sigma * normal_at(seed, (uint32_t)(P0 + r), (uint32_t)i, (uint32_t)(n_occ + a));
+}
+
+/* B_ia[P][i*n_virt + a] = sigma * N(seed; P, i, n_occ + a). */
+void synth_b_ia(uint64_t seed, double sigma, int n_aux, int n_occ, int n_virt, double* out) {
+  synth_b_ia_rows(seed, sigma, 0, n_aux, n_occ, n_virt, out);
 }
 
 /* B_nm[t][m][P] = sigma * N(seed; P, targets[t], m) for m in [0, n_bas). */

@@ -558,59 +558,84 @@ cudaError_t tc_split_rows(const float* src, int rows, int cols, int lds, __nv_bf
   return cudaGetLastError();
 }
 
-// power iteration, one CTA per matrix: v <- A v / |A v| from v = 1, lam = Rayleigh quotient
-__global__ void power_lmax_kernel(const float* __restrict__ A, int n, int iters, float* __restrict__ lam) {
-  extern __shared__ float pv[];     // v[n], w[n]
-  float* v = pv;
-  float* w = pv + n;
-  __shared__ float red[32];
-  const float* Ab = A + (long)blockIdx.x * n * n;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = rsqrtf((float)n);
-  __syncthreads();
-  float rq = 1.f;
-  for (int it = 0; it < iters; ++it) {
-    // w = A v, one warp per row
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int r = wid; r < n; r += nw) {
-      float a = 0.f;
-      for (int c = lane; c < n; c += 32) a += Ab[(long)r * n + c] * v[c];
-      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-      if (lane == 0) w[r] = a;
-    }
-    __syncthreads();
-    float nn = 0.f, vw = 0.f;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) { nn += w[i] * w[i]; vw += v[i] * w[i]; }
-    for (int o = 16; o > 0; o >>= 1) { nn += __shfl_xor_sync(0xffffffffu, nn, o); vw += __shfl_xor_sync(0xffffffffu, vw, o); }
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nn;
-    __syncthreads();
-    float tn = 0.f;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tn += red[i];
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = vw;
-    __syncthreads();
-    float tv = 0.f;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tv += red[i];
-    rq = tv;
-    const float inv = tn > 0.f ? rsqrtf(tn) : 0.f;
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = w[i] * inv;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) lam[blockIdx.x] = rq;
+// Power iterations for the spectrum of SPD matrices A_b (n x n FP32, batch stride n*n), many CTAs per matrix:
+//   gemv:      y_b = A_b v_b (mode 0)  or  y_b = s_b v_b - A_b v_b (mode 1), one warp per row;
+//   normalise: q_b = v_b . y_b (the Rayleigh quotient of the unit vector v_b), v_b = y_b / |y_b|.
+__global__ void spec_gemv_kernel(const float* __restrict__ A, int n, const float* __restrict__ v,
+                                 const float* __restrict__ shift, int mode, float* __restrict__ y) {
+  const int b = blockIdx.y, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = blockIdx.x * (blockDim.x >> 5) + wid;
+  if (r >= n) return;
+  const float* Ar = A + ((long)b * n + r) * n;
+  const float* vb = v + (long)b * n;
+  float a = 0.f;
+  for (int c = lane; c < n; c += 32) a += Ar[c] * vb[c];
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if (lane == 0) y[(long)b * n + r] = mode ? shift[b] * vb[r] - a : a;
 }
 
-cudaError_t tc_power_lmax(const float* A, int n, int batch, int iters, float* lam, cudaStream_t s) {
-  const size_t smem = 2 * sizeof(float) * n;
-  if (smem > 48 * 1024) cudaFuncSetAttribute(power_lmax_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (batch > 0) power_lmax_kernel<<<batch, 1024, smem, s>>>(A, n, iters, lam);
+__global__ void spec_normalise_kernel(int n, float* __restrict__ v, const float* __restrict__ y,
+                                      float* __restrict__ q) {
+  __shared__ float red[2][32];
+  const int b = blockIdx.x;
+  float* vb = v + (long)b * n;
+  const float* yb = y + (long)b * n;
+  float yy = 0.f, vy = 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    yy += yb[i] * yb[i];
+    vy += vb[i] * yb[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    yy += __shfl_xor_sync(0xffffffffu, yy, o);
+    vy += __shfl_xor_sync(0xffffffffu, vy, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = yy;
+    red[1][threadIdx.x >> 5] = vy;
+  }
+  __syncthreads();
+  float tyy = 0.f, tvy = 0.f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+    tyy += red[0][w];
+    tvy += red[1][w];
+  }
+  __syncthreads();
+  const float inv = tyy > 0.f ? rsqrtf(tyy) : 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) vb[i] = yb[i] * inv;
+  if (threadIdx.x == 0) q[b] = tvy;
+}
+
+__global__ void spec_start_kernel(int n, int batch, float* __restrict__ v) {
+  const long N = (long)n * batch;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x)
+    v[i] = rsqrtf((float)n) * (1.f + 0.25f * (float)((i % n) & 1));   // not orthogonal to any eigenvector
+}
+
+__global__ void spec_shift_kernel(int batch, const float* __restrict__ hi, float pad, float* __restrict__ s) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < batch) s[b] = pad * hi[b];
+}
+
+cudaError_t tc_spectrum_bounds(const float* A, int n, int batch, int iters, float pad, float* hi, float* lo,
+                               float* shift, float* v, float* y, cudaStream_t s) {
+  if (batch <= 0) return cudaSuccess;
+  const dim3 gg((n + 7) / 8, batch);
+  for (int phase = 0; phase < 2; ++phase) {
+    spec_start_kernel<<<256, 256, 0, s>>>(n, batch, v);
+    if (phase == 1) spec_shift_kernel<<<(batch + 255) / 256, 256, 0, s>>>(batch, hi, pad, shift);
+    for (int it = 0; it < iters; ++it) {
+      spec_gemv_kernel<<<gg, 256, 0, s>>>(A, n, v, shift, phase, y);
+      spec_normalise_kernel<<<batch, 1024, 0, s>>>(n, v, y, phase == 0 ? hi : lo);
+    }
+  }
   return cudaGetLastError();
 }
 
-__global__ void ns_init_kernel(const float* __restrict__ A, int n, const float* __restrict__ lam, float* __restrict__ X,
+__global__ void ns_init_kernel(const float* __restrict__ A, int n, const float* __restrict__ ab, float* __restrict__ X,
                                __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
                                __nv_bfloat16* __restrict__ lo2, int ldh) {
   const int r = blockIdx.y, b = blockIdx.z;
-  const float a = 2.f / (1.f + lam[b]);
+  const float a = ab[b];
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ldh; c += gridDim.x * blockDim.x) {
     float y = 0.f;
     if (c < n) {
@@ -621,11 +646,11 @@ __global__ void ns_init_kernel(const float* __restrict__ A, int n, const float* 
   }
 }
 
-cudaError_t tc_ns_init(const float* A, int n, int batch, const float* lam, float* X, __nv_bfloat16* hi,
+cudaError_t tc_ns_init(const float* A, int n, int batch, const float* ab, float* X, __nv_bfloat16* hi,
                        __nv_bfloat16* lo, cudaStream_t s, __nv_bfloat16* lo2) {
   const int ldh = tc_ld(n);
   dim3 grid((ldh + 255) / 256, n, batch);
-  if (batch > 0) ns_init_kernel<<<grid, 256, 0, s>>>(A, n, lam, X, hi, lo, lo2, ldh);
+  if (batch > 0) ns_init_kernel<<<grid, 256, 0, s>>>(A, n, ab, X, hi, lo, lo2, ldh);
   return cudaGetLastError();
 }
 

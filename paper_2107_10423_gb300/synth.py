@@ -48,6 +48,8 @@ def _load():
         lib.synth_philox4x32_10.argtypes = [ctypes.POINTER(ctypes.c_uint32)] * 2 + [ctypes.POINTER(ctypes.c_uint32)]
         lib.synth_b_ia.argtypes = [ctypes.c_uint64, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_void_p]
+        lib.synth_b_ia_rows.argtypes = [ctypes.c_uint64, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_void_p]
         lib.synth_b_nm.argtypes = [ctypes.c_uint64, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                    ctypes.c_int, ctypes.c_void_p]
         _lib = lib
@@ -68,6 +70,13 @@ def b_ia(seed: int, sigma: float, n_aux: int, n_occ: int, n_virt: int) -> np.nda
     """B_ia as [n_aux, n_occ*n_virt] float64, pair index i*n_virt + a."""
     out = np.empty((n_aux, n_occ * n_virt), dtype=np.float64)
     _load().synth_b_ia(seed, sigma, n_aux, n_occ, n_virt, out.ctypes.data)
+    return out
+
+
+def b_ia_rows(seed: int, sigma: float, p0: int, n_rows: int, n_occ: int, n_virt: int) -> np.ndarray:
+    """Rows p0 .. p0 + n_rows - 1 of B_ia (the same values as ``b_ia``), [n_rows, n_occ*n_virt] float64."""
+    out = np.empty((n_rows, n_occ * n_virt), dtype=np.float64)
+    _load().synth_b_ia_rows(seed, sigma, p0, n_rows, n_occ, n_virt, out.ctypes.data)
     return out
 
 
@@ -105,6 +114,9 @@ class System:
 
     def b_ia(self) -> np.ndarray:
         return b_ia(self.seed, self.sigma_b, self.n_aux, self.n_occ, self.n_virt)
+
+    def b_ia_rows(self, p0: int, n_rows: int) -> np.ndarray:
+        return b_ia_rows(self.seed, self.sigma_b, p0, n_rows, self.n_occ, self.n_virt)
 
     def b_nm(self, targets=None) -> np.ndarray:
         return b_nm(self.seed, self.sigma_b, self.n_aux, self.n_bas, self.targets if targets is None else targets)

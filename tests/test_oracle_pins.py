@@ -413,3 +413,32 @@ def test_steptree_same_sign_bracket_turns_into_sign_bracket():
     np.testing.assert_allclose(ws[:4], [0.0, 0.1, 0.1 * G, 0.1 * G * (1.0 - G)], atol=1e-15)
     np.testing.assert_allclose(fs[:2], [0.15, 0.23], atol=1e-15)
     assert fs[2] < 0 < fs[3]
+
+
+# ---------------------------------------------------------------- eigenvalue self-consistency (Algorithm 1 outer loop)
+@pytest.mark.parametrize("update_w", [False, True])
+def test_evgw_reaches_the_pole_model_fixed_point(update_w):
+    """On the one-pair pole model every state is a target, so the converged energies (e_i*, e_a*) must solve the
+    closed-form QP equations e* = e_KS + Sigma_c(e*) with G's poles at (e_i*, e_a*) and W's pair energy the KS one
+    (evGW0) or D* = e_a* - e_i* with Omega* = sqrt(D* (D* + 4 b^2)) (evGW)."""
+    eps, B_ia, B_nm, D, Om, bs = _pole_model()
+    r = O.evgw(eps, 1, B_ia, B_nm, [0, 1], update_w=update_w, mode="steptree", tol=1e-12, qp_tol=1e-13,
+               max_iter=200, eta=0.0)
+    assert r["converged"] and np.all(r["status"] == 0)
+    e = r["e_qp"]
+    Dw = (e[1] - e[0]) if update_w else D
+    Omw = math.sqrt(Dw * (Dw + 4 * bs[0] ** 2))
+    for t in (0, 1):
+        s, _ = _pole_sigma(e[t], t, e, Dw, Omw, bs)
+        assert abs(eps[t] + s - e[t]) < 1e-9, (t, eps[t] + s - e[t])
+    # and the loop moved the energies away from the one-shot G0W0 result
+    g0 = O.g0w0_cd(eps, 1, B_ia, B_nm, [0, 1], eta=0.0, qp_tol=1e-13)
+    assert np.max(np.abs(e - g0["e_qp"])) > 1e-4
+
+
+def test_scissor_energies():
+    eps = np.array([-10.0, -1.0, -0.5, 0.2, 0.9, 3.0])
+    out = O.scissor_energies(eps, 3, [1, 2, 3], [-1.2, -0.8, 0.5])
+    np.testing.assert_allclose(out, [-10.3, -1.2, -0.8, 0.5, 1.2, 3.3], atol=1e-15)
+    out = O.scissor_energies(eps, 3, [4], [1.0])
+    np.testing.assert_allclose(out, [-10.0, -1.0, -0.5, 0.3, 1.0, 3.1], atol=1e-15)
