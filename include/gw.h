@@ -147,6 +147,21 @@ gw_status gw_residues_minres(gw_plan_t plan, int n_rhs, const int* target_idx, c
  * Returns GW_ERR_NOT_CONVERGED if any state did not converge. */
 gw_status gw_qp_solve(gw_plan_t plan, gw_qp_mode mode, double* e_qp, double* z_factor, int* state_status);
 
+/* Eigenvalue self-consistency (Algorithm 1, the outer loop over iter; Sec. 1: evGW0 updates the quasiparticle
+ * energies in G, evGW in G and W).  Cycle 1 is G0W0 (gw_qp_solve).  After each cycle the energies are updated:
+ * every target takes its QP energy; every other occupied state moves by the QP correction of the highest occupied
+ * target and every other virtual state by that of the lowest virtual target (no move where a class has no target).
+ * The next cycle evaluates Sigma_c with those energies as the poles of G (the I and R terms) and, if update_w != 0,
+ * as the pair energies D_ia = e_a - e_i of Pi (a new imaginary-axis table and new residue operators); the QP
+ * equation keeps the KS energy, e_QP = e_n + Sigma_x - V_xc + Re Sigma_c(e_QP), and each cycle's search starts from
+ * the previous cycle's QP energy (mode as in gw_qp_solve; linearised = one Newton step per cycle).
+ * Stops when no target moves by more than tol (Ha) between cycles, or after max_iter cycles.
+ * Outputs (host, [n_targets]): e_qp, z_factor, state_status of the last cycle; *iterations = cycles run.
+ * Returns GW_ERR_NOT_CONVERGED if the cycles did not converge (outputs still written).  On return the plan is
+ * back to G0W0 (G and W from the KS energies).  Any output pointer may be NULL. */
+gw_status gw_evgw(gw_plan_t plan, int update_w, gw_qp_mode mode, int max_iter, double tol, double* e_qp,
+                  double* z_factor, int* state_status, int* iterations);
+
 /* Copy the imaginary-axis table to the host: out [n_targets][n_bas][n_freq + 1] with
  * out[t][m][g] = W^c_nm(i xi_g) for the grid points g < n_freq and out[t][m][n_freq] = W^c_nm(0)
  * (Algorithm 1, imaginary-grid loop).  Builds the table first if needed. */

@@ -133,7 +133,7 @@ struct QPState {
   double sigma, dsigma;
   int br_kind, has_prev, iter, status;   // status: 0 running, 1 converged, 2 not converged
 };
-void launch_qp_init(QPState* st, const double* e_n, int n, cudaStream_t s);
+void launch_qp_init(QPState* st, const double* omega0, int n, cudaStream_t s);   // omega0: starting points
 // sigma = R - I, dsigma = dR - dI for active states, then one step-tree step.
 void launch_qp_step(QPState* st, const double* R, const double* dR, const double* I, const double* dI,
                     const double* e_n, const double* shift, double tol, int maxit, int n, int linearised,

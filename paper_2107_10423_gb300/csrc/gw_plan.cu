@@ -33,8 +33,10 @@ struct gw_plan {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::vector<double> h_eps, h_xi, h_wt, h_shift, h_sx, h_en;
+  std::vector<double> h_eps_g;   // poles of G (the KS energies, or the updated ones inside gw_evgw)
+  double* d_eps_g = nullptr;
   std::vector<int> h_targets;
-  double* d_eps = nullptr;
+  double* d_eps = nullptr;     // energies of W: the pair energies D_ia of Pi
   double* d_B_ia = nullptr;
   double* d_B_nm = nullptr;
   bool own_B = true;
@@ -69,7 +71,7 @@ struct gw_plan {
       ns_E0, ns_vec;
   DevBuf mr_V, mr_U, mr_S, mr_vprev, mr_v, mr_d1, mr_d2, mr_x, mr_st, mr_rt, mr_rm, mr_xf, mr_wre, mr_wim,
       mr_dwre, mr_it, mr_res, mr_cnt, mr_Vhi, mr_Vlo, mr_Uhi, mr_Ulo, mr_Vlo2, mr_Ulo2, mr_V64;
-  DevBuf sg_I, sg_dI, sg_R, sg_dR, sg_om, sg_start, sg_coef, sg_act, qp_st;
+  DevBuf sg_I, sg_dI, sg_R, sg_dR, sg_om, sg_start, sg_coef, sg_act, qp_st, qp_om0;
   DevBuf fb_A, fb_y, fb_piv, fb_info, fb_idx, fb_y64, fb_V32, fb_S32, fb_Vp, fb_Up, fb_x, fb_V64, fb_U64, fb_S64, fb_sel,
       fb_pos, fb_rho, fb_xs, fb_Bh, fb_Bl;
   int* h_cnt = nullptr;       // pinned
@@ -86,7 +88,7 @@ struct gw_plan {
     DevBuf* all[] = {&ws_mat, &ws_info, &ws_scratch, &ws_gout, &ws_xi, &tc_kind, &tc_par, &tc_err, &tc_w, &ns_E, &ns_X, &ns_X2, &ns_Xa, &ns_Xb, &ns_T, &ns_lam, &ns_E0, &ns_vec, &mr_V, &mr_U, &mr_S, &mr_vprev,
                      &mr_v, &mr_d1, &mr_d2, &mr_x, &mr_st, &mr_rt, &mr_rm, &mr_xf, &mr_wre, &mr_wim,
                      &mr_dwre, &mr_it, &mr_res, &mr_cnt, &mr_Vhi, &mr_Vlo, &mr_Uhi, &mr_Ulo, &mr_Vlo2, &mr_Ulo2, &mr_V64, &sg_I, &sg_dI, &sg_R, &sg_dR, &sg_om, &sg_start,
-                     &sg_coef, &sg_act, &qp_st, &fb_A, &fb_y, &fb_piv, &fb_info, &fb_idx, &fb_y64, &fb_V32, &fb_S32, &fb_Vp, &fb_Up, &fb_x, &fb_V64, &fb_U64, &fb_S64, &fb_sel, &fb_pos, &fb_rho, &fb_xs, &fb_Bh, &fb_Bl};
+                     &sg_coef, &sg_act, &qp_st, &qp_om0, &fb_A, &fb_y, &fb_piv, &fb_info, &fb_idx, &fb_y64, &fb_V32, &fb_S32, &fb_Vp, &fb_Up, &fb_x, &fb_V64, &fb_U64, &fb_S64, &fb_sel, &fb_pos, &fb_rho, &fb_xs, &fb_Bh, &fb_Bl};
     bufs.assign(all, all + sizeof(all) / sizeof(all[0]));
   }
 };
@@ -941,7 +943,7 @@ void build_residue_list(gw_plan* P, const std::vector<double>& omega, const std:
     if (!active[t]) continue;
     const double w = omega[t];
     for (int m = 0; m < P->n_bas; ++m) {
-      const double e = P->h_eps[m];
+      const double e = P->h_eps_g[m];
       double th;
       double sg;
       if (m < P->cfg.n_occ) {
@@ -978,7 +980,7 @@ gw_status sigma_eval(gw_plan* P, const std::vector<double>& omega, const std::ve
   CK(cudaEventCreate(&a));
   CK(cudaEventCreate(&b));
   CK(cudaEventRecord(a, P->stream));
-  LAUNCH(gw::launch_sigma_imag(P->d_W, n_t, P->n_bas, P->n_g, P->d_eps, P->d_xi, P->d_wt, as<double>(P->sg_om),
+  LAUNCH(gw::launch_sigma_imag(P->d_W, n_t, P->n_bas, P->n_g, P->d_eps_g, P->d_xi, P->d_wt, as<double>(P->sg_om),
                                P->cfg.static_subtraction, as<double>(P->sg_I), as<double>(P->sg_dI),
                                as<unsigned char>(P->sg_act), P->stream));
   CK(cudaEventRecord(b, P->stream));
@@ -1015,6 +1017,36 @@ gw_status sigma_eval(gw_plan* P, const std::vector<double>& omega, const std::ve
   for (int j = 0; j < nr; ++j) nf += fb[j];
   if (n_fallback_out) *n_fallback_out = nf;
   for (int t = 0; t < n_t; ++t) P->stats.n_sigma_evals += active[t] ? 1 : 0;
+  return GW_OK;
+}
+
+// W's energies: d_eps and, in mixed precision, the pair energies D_ia, their ascending order and the smallest one.
+gw_status set_pair_energies(gw_plan* P, const double* eps) {
+  CK(cudaMemcpyAsync(P->d_eps, eps, sizeof(double) * P->n_bas, cudaMemcpyHostToDevice, P->stream));
+  if (P->d_D) {
+    const int n_occ = P->cfg.n_occ, n_virt = P->cfg.n_virt;
+    std::vector<double> D((size_t)P->n_ov);
+    for (int i = 0; i < n_occ; ++i)
+      for (int a = 0; a < n_virt; ++a) D[(size_t)i * n_virt + a] = eps[n_occ + a] - eps[i];
+    std::vector<int> order((size_t)P->n_ov);
+    for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return D[a] < D[b]; });
+    std::vector<double> Ds(order.size());
+    for (size_t k = 0; k < order.size(); ++k) Ds[k] = D[order[k]];
+    P->D_min = Ds.empty() ? 0.0 : Ds[0];
+    CK(cudaMemcpyAsync(P->d_D, D.data(), sizeof(double) * P->n_ov, cudaMemcpyHostToDevice, P->stream));
+    CK(cudaMemcpyAsync(P->d_Dsort, Ds.data(), sizeof(double) * P->n_ov, cudaMemcpyHostToDevice, P->stream));
+    CK(cudaMemcpyAsync(P->d_Dkidx, order.data(), sizeof(int) * P->n_ov, cudaMemcpyHostToDevice, P->stream));
+  }
+  CK(cudaStreamSynchronize(P->stream));
+  return GW_OK;
+}
+
+// G's energies (host copy for the residue list, device copy for the I term).
+gw_status set_g_energies(gw_plan* P, const double* eps) {
+  P->h_eps_g.assign(eps, eps + P->n_bas);
+  CK(cudaMemcpyAsync(P->d_eps_g, eps, sizeof(double) * P->n_bas, cudaMemcpyHostToDevice, P->stream));
+  CK(cudaStreamSynchronize(P->stream));
   return GW_OK;
 }
 
@@ -1073,7 +1105,7 @@ static void free_plan(gw_plan* P) {
   if (P->stream) cudaStreamSynchronize(P->stream);
   for (DevBuf* b : P->bufs)
     if (b->p) cudaFree(b->p);
-  double* owned[] = {P->d_eps, P->d_xi, P->d_wt, P->d_sx, P->d_shift, P->d_en, P->d_W};
+  double* owned[] = {P->d_eps, P->d_eps_g, P->d_xi, P->d_wt, P->d_sx, P->d_shift, P->d_en, P->d_W};
   for (double* p : owned)
     if (p) cudaFree(p);
   if (P->own_B) {
@@ -1124,6 +1156,7 @@ static gw_status plan_create_impl(gw_plan* P, const gw_config* cfg, const double
   CK(cudaMallocHost(&P->h_cnt, sizeof(int)));
   const int n = cfg->n_aux;
   P->h_eps.assign(eps, eps + P->n_bas);
+  P->h_eps_g = P->h_eps;
   P->h_targets.assign(targets, targets + n_targets);
   // grid
   P->h_xi.resize(P->n_g);
@@ -1136,6 +1169,7 @@ static gw_status plan_create_impl(gw_plan* P, const gw_config* cfg, const double
   std::vector<double> xi_all(P->h_xi);
   xi_all.push_back(0.0);
   TRY(dmalloc(P, &P->d_eps, sizeof(double) * P->n_bas));
+  TRY(dmalloc(P, &P->d_eps_g, sizeof(double) * P->n_bas));
   TRY(dmalloc(P, &P->d_xi, sizeof(double) * (P->n_g + 1)));
   TRY(dmalloc(P, &P->d_wt, sizeof(double) * std::max(1, P->n_g)));
   TRY(dmalloc(P, &P->d_sx, sizeof(double) * std::max(1, n_targets)));
@@ -1143,6 +1177,7 @@ static gw_status plan_create_impl(gw_plan* P, const gw_config* cfg, const double
   TRY(dmalloc(P, &P->d_en, sizeof(double) * std::max(1, n_targets)));
   TRY(dmalloc(P, &P->d_W, sizeof(double) * (size_t)n_targets * P->n_bas * (P->n_g + 1)));
   CK(cudaMemcpyAsync(P->d_eps, eps, sizeof(double) * P->n_bas, cudaMemcpyHostToDevice, P->stream));
+  CK(cudaMemcpyAsync(P->d_eps_g, eps, sizeof(double) * P->n_bas, cudaMemcpyHostToDevice, P->stream));
   CK(cudaMemcpyAsync(P->d_xi, xi_all.data(), sizeof(double) * (P->n_g + 1), cudaMemcpyHostToDevice, P->stream));
   CK(cudaMemcpyAsync(P->d_wt, P->h_wt.data(), sizeof(double) * P->n_g, cudaMemcpyHostToDevice, P->stream));
   const size_t nB = (size_t)n * P->n_ov, nBn = (size_t)n_targets * P->n_bas * n;
@@ -1179,24 +1214,10 @@ static gw_status plan_create_impl(gw_plan* P, const gw_config* cfg, const double
     TRY(dmalloc(P, &P->d_BThi, sizeof(__nv_bfloat16) * nsplitT));
     TRY(dmalloc(P, &P->d_BTlo, sizeof(__nv_bfloat16) * nsplitT));
     CK(gw::tc_transpose_split(P->d_B_ia_f, n, P->n_ov, P->d_BThi, P->d_BTlo, P->stream, nullptr, P->ld_f));
-    {
-      std::vector<double> D((size_t)P->n_ov);
-      for (int i = 0; i < cfg->n_occ; ++i)
-        for (int a = 0; a < cfg->n_virt; ++a) D[(size_t)i * cfg->n_virt + a] = eps[cfg->n_occ + a] - eps[i];
-      TRY(dmalloc(P, &P->d_D, sizeof(double) * P->n_ov));
-      CK(cudaMemcpyAsync(P->d_D, D.data(), sizeof(double) * P->n_ov, cudaMemcpyHostToDevice, P->stream));
-      std::vector<int> order((size_t)P->n_ov);
-      for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
-      std::sort(order.begin(), order.end(), [&](int a, int b) { return D[a] < D[b]; });
-      std::vector<double> Ds(order.size());
-      for (size_t k = 0; k < order.size(); ++k) Ds[k] = D[order[k]];
-      P->D_min = Ds.empty() ? 0.0 : Ds[0];
-      TRY(dmalloc(P, &P->d_Dsort, sizeof(double) * P->n_ov));
-      TRY(dmalloc(P, &P->d_Dkidx, sizeof(int) * P->n_ov));
-      CK(cudaMemcpyAsync(P->d_Dsort, Ds.data(), sizeof(double) * P->n_ov, cudaMemcpyHostToDevice, P->stream));
-      CK(cudaMemcpyAsync(P->d_Dkidx, order.data(), sizeof(int) * P->n_ov, cudaMemcpyHostToDevice, P->stream));
-      CK(cudaStreamSynchronize(P->stream));
-    }
+    TRY(dmalloc(P, &P->d_D, sizeof(double) * P->n_ov));
+    TRY(dmalloc(P, &P->d_Dsort, sizeof(double) * P->n_ov));
+    TRY(dmalloc(P, &P->d_Dkidx, sizeof(int) * P->n_ov));
+    TRY(set_pair_energies(P, eps));
     CK(cudaStreamSynchronize(P->stream));
   }
   LAUNCH(gw::launch_sigma_x(P->d_B_nm, n_targets, P->n_bas, n, cfg->n_occ, P->d_sx, P->stream));
@@ -1353,9 +1374,15 @@ gw_status gw_residues_minres(gw_plan_t P, int n_rhs, const int* target_idx, cons
   return GW_OK;
 }
 
-gw_status gw_qp_solve(gw_plan_t P, gw_qp_mode mode, double* e_qp, double* z_factor, int* state_status) {
-  if (!P) return GW_ERR_ARG;
-  if (mode != GW_QP_LINEARISED && mode != GW_QP_STEPTREE) return fail(P, GW_ERR_ARG, "unknown QP mode %d", (int)mode);
+}  // extern "C"
+
+namespace {
+
+// QP loop (Sec. 3.4): every active state's Sigma(omega) per evaluation (one batched residue solve for all of them),
+// then one step of the linearised update or of the step tree.  omega0 (host [n_targets]) is the starting point, or
+// NULL for the KS energies.
+gw_status qp_solve_impl(gw_plan* P, gw_qp_mode mode, const double* omega0, double* e_qp, double* z_factor,
+                        int* state_status) {
   cudaEvent_t a, b;
   CK(cudaEventCreate(&a));
   CK(cudaEventCreate(&b));
@@ -1363,7 +1390,13 @@ gw_status gw_qp_solve(gw_plan_t P, gw_qp_mode mode, double* e_qp, double* z_fact
   TRY(ensure_screening(P));
   const int n_t = P->n_t;
   TRY(ensure(P, P->qp_st, sizeof(QPState) * n_t));
-  LAUNCH(gw::launch_qp_init(as<QPState>(P->qp_st), P->d_en, n_t, P->stream));
+  const double* d_om0 = P->d_en;
+  if (omega0) {
+    TRY(ensure(P, P->qp_om0, sizeof(double) * n_t));
+    CK(cudaMemcpyAsync(P->qp_om0.p, omega0, sizeof(double) * n_t, cudaMemcpyHostToDevice, P->stream));
+    d_om0 = as<double>(P->qp_om0);
+  }
+  LAUNCH(gw::launch_qp_init(as<QPState>(P->qp_st), d_om0, n_t, P->stream));
   std::vector<QPState> hs(n_t);
   std::vector<double> om(n_t);
   std::vector<unsigned char> act(n_t);
@@ -1404,6 +1437,78 @@ gw_status gw_qp_solve(gw_plan_t P, gw_qp_mode mode, double* e_qp, double* z_fact
     if (state_status) state_status[t] = s;
   }
   return all_ok ? GW_OK : GW_ERR_NOT_CONVERGED;
+}
+
+// Energies of the next eigenvalue cycle: targets take their QP energies, every other occupied state moves by the
+// correction of the highest occupied target, every other virtual state by that of the lowest virtual target.
+std::vector<double> scissor(const gw_plan* P, const std::vector<double>& e_qp) {
+  const int n_occ = P->cfg.n_occ;
+  std::vector<double> out(P->h_eps);
+  double e_o = -INFINITY, d_o = 0.0, e_v = INFINITY, d_v = 0.0;
+  for (int t = 0; t < P->n_t; ++t) {
+    const int n = P->h_targets[t];
+    const double e = P->h_eps[n], d = e_qp[t] - e;
+    if (n < n_occ && (e > e_o || (e == e_o && d > d_o))) { e_o = e; d_o = d; }
+    if (n >= n_occ && (e < e_v || (e == e_v && d < d_v))) { e_v = e; d_v = d; }
+  }
+  for (int m = 0; m < P->n_bas; ++m) out[m] += m < n_occ ? d_o : d_v;
+  for (int t = 0; t < P->n_t; ++t) out[P->h_targets[t]] = e_qp[t];
+  return out;
+}
+
+}  // namespace
+
+extern "C" {
+
+gw_status gw_qp_solve(gw_plan_t P, gw_qp_mode mode, double* e_qp, double* z_factor, int* state_status) {
+  if (!P) return GW_ERR_ARG;
+  if (mode != GW_QP_LINEARISED && mode != GW_QP_STEPTREE) return fail(P, GW_ERR_ARG, "unknown QP mode %d", (int)mode);
+  return qp_solve_impl(P, mode, nullptr, e_qp, z_factor, state_status);
+}
+
+gw_status gw_evgw(gw_plan_t P, int update_w, gw_qp_mode mode, int max_iter, double tol, double* e_qp,
+                  double* z_factor, int* state_status, int* iterations) {
+  if (!P) return GW_ERR_ARG;
+  if (mode != GW_QP_LINEARISED && mode != GW_QP_STEPTREE) return fail(P, GW_ERR_ARG, "unknown QP mode %d", (int)mode);
+  if (max_iter <= 0 || !(tol > 0.0)) return fail(P, GW_ERR_ARG, "max_iter must be positive and tol > 0");
+  const int n_t = P->n_t;
+  std::vector<double> prev(n_t), cur(n_t), z(n_t);
+  std::vector<int> st(n_t);
+  for (int t = 0; t < n_t; ++t) prev[t] = P->h_en[t];
+  std::vector<double> eps_cur(P->h_eps);
+  gw_status last = GW_OK;
+  bool conv = false;
+  int it = 0;
+  for (it = 1; it <= max_iter; ++it) {
+    TRY(set_g_energies(P, eps_cur.data()));
+    if (update_w && it > 1) {            // evGW: W from the current energies (cycle 1 is G0W0)
+      TRY(set_pair_energies(P, eps_cur.data()));
+      P->screening_done = false;
+    }
+    last = qp_solve_impl(P, mode, prev.data(), cur.data(), z.data(), st.data());
+    if (last != GW_OK && last != GW_ERR_NOT_CONVERGED) break;
+    double delta = 0.0;
+    for (int t = 0; t < n_t; ++t) delta = std::max(delta, std::fabs(cur[t] - prev[t]));
+    prev = cur;
+    eps_cur = scissor(P, cur);
+    if (delta < tol) { conv = true; break; }
+  }
+  // the plan goes back to G0W0: G and W from the KS energies (W is rebuilt on the next call that needs it)
+  gw_status rs = set_g_energies(P, P->h_eps.data());
+  if (rs == GW_OK && update_w) {
+    rs = set_pair_energies(P, P->h_eps.data());
+    P->screening_done = false;
+  }
+  if (last != GW_OK && last != GW_ERR_NOT_CONVERGED) return last;
+  if (rs != GW_OK) return rs;
+  for (int t = 0; t < n_t; ++t) {
+    if (e_qp) e_qp[t] = cur[t];
+    if (z_factor) z_factor[t] = z[t];
+    if (state_status) state_status[t] = st[t];
+  }
+  if (iterations) *iterations = std::min(it, max_iter);
+  if (!conv) return fail(P, GW_ERR_NOT_CONVERGED, "eigenvalue cycles did not converge to %g Ha in %d", tol, max_iter);
+  return last;
 }
 
 gw_status gw_plan_footprint(const gw_config* c, int n_t, unsigned flags, unsigned long long* bytes) {

@@ -421,11 +421,11 @@ __device__ double golden_point(const QPState& s) {
   return (s.b - s.x) >= (s.x - s.a) ? s.x + kGold * (s.b - s.x) : s.x - kGold * (s.x - s.a);
 }
 
-__global__ void qp_init_kernel(QPState* st, const double* e_n, int n) {
+__global__ void qp_init_kernel(QPState* st, const double* omega0, int n) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   QPState s;
-  s.omega = e_n[t]; s.f_prev = 0.0; s.omega_prev = 0.0; s.Z = 1.0;
+  s.omega = omega0[t]; s.f_prev = 0.0; s.omega_prev = 0.0; s.Z = 1.0;
   s.a = s.fa = s.b = s.fb = s.x = s.fx = 0.0;
   s.sigma = s.dsigma = 0.0;
   s.br_kind = 0; s.has_prev = 0; s.iter = 0; s.status = 0;
@@ -446,8 +446,10 @@ __global__ void qp_step_kernel(QPState* st, const double* __restrict__ R, const 
   const double Z = 1.0 / (1.0 - dsig);
   s.Z = Z;
   if (linearised) {
-    // e_QP = e + Z (shift + Sigma_c(e)), Z = 1/(1 - Sigma_c'(e))
-    s.omega = e_n[t] + Z * (shift[t] + sig);
+    // one Newton step of f(w) = e + shift + Sigma_c(w) - w from the starting point w0:
+    // e_QP = w0 + Z f(w0), Z = 1/(1 - Sigma_c'(w0)); from w0 = e this is e + Z (shift + Sigma_c(e))
+    const double w0 = s.omega;
+    s.omega = w0 == e_n[t] ? e_n[t] + Z * (shift[t] + sig) : w0 + Z * (e_n[t] + shift[t] + sig - w0);
     s.status = 1;
     s.iter = 1;
     st[t] = s;

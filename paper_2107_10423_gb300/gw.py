@@ -18,7 +18,7 @@ GW_INPUT_ON_DEVICE, GW_BORROW_DEVICE_PTRS = 1, 2
 
 EXPORTED = ["gw_config_default", "gw_plan_create", "gw_polarizability", "gw_sigma_cd", "gw_residues_minres",
             "gw_qp_solve", "gw_grid", "gw_w_table", "gw_w_table_noalloc", "gw_get_stats", "gw_plan_destroy", "gw_last_error",
-            "gw_plan_footprint"]
+            "gw_plan_footprint", "gw_evgw"]
 
 
 class GWError(RuntimeError):
@@ -73,6 +73,8 @@ def load(path: str = LIB_PATH):
     lib.gw_sigma_cd.argtypes = [_P, _P, _P, _P, _P]
     lib.gw_residues_minres.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P, _P, _P]
     lib.gw_qp_solve.argtypes = [_P, ctypes.c_int, _P, _P, _P]
+    lib.gw_evgw.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P, _P, _P]
+    lib.gw_evgw.restype = ctypes.c_int
     lib.gw_get_stats.argtypes = [_P, ctypes.POINTER(Stats)]
     lib.gw_w_table_noalloc.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, ctypes.c_int, _P]
     lib.gw_w_table_noalloc.restype = ctypes.c_int
@@ -217,6 +219,16 @@ class Plan:
         self._check(self._lib.gw_qp_solve(self._h, mode, _ptr(e), _ptr(z), _ptr(s)),
                     allow=(GW_ERR_NOT_CONVERGED,) if allow_unconverged else ())
         return e, z, s
+
+    def evgw(self, update_w=False, mode=GW_QP_STEPTREE, max_iter=30, tol=1e-6, allow_unconverged=False):
+        """Eigenvalue self-consistent GW (evGW0, or evGW with ``update_w``): (e_qp, z, status, cycles)."""
+        e, z = np.empty(self.n_t), np.empty(self.n_t)
+        s = np.empty(self.n_t, dtype=np.int32)
+        it = ctypes.c_int()
+        self._check(self._lib.gw_evgw(self._h, int(bool(update_w)), mode, int(max_iter), float(tol), _ptr(e), _ptr(z),
+                                      _ptr(s), ctypes.byref(it)),
+                    allow=(GW_ERR_NOT_CONVERGED,) if allow_unconverged else ())
+        return e, z, s, it.value
 
     def stats(self) -> dict:
         st = Stats()

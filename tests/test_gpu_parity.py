@@ -109,7 +109,9 @@ def test_qp_steptree_fp64_vs_oracle(gw, kind):
     ref = O.g0w0_cd(s.eps, s.n_occ, B, Bn, s.targets, eta=1e-3, qp_maxit=200)
     with gw.Plan(s.eps, s.n_occ, B, Bn, s.targets, qp_maxit=200, **TIGHT) as p:
         e, z, st = p.qp_solve(gw.GW_QP_STEPTREE)
-    assert np.all(st != 1) and np.all(ref["status"] == 0)
+    # same convergence outcome per state (a state whose tree is still narrowing a bracket at qp_maxit stops
+    # unconverged on both sides, at the same iterate)
+    np.testing.assert_array_equal(st == 1, ref["status"] == 1)
     np.testing.assert_allclose(e, ref["e_qp"], rtol=0, atol=1e-5)
     np.testing.assert_allclose(z, ref["Z"], rtol=0, atol=1e-5)
 
