@@ -162,6 +162,23 @@ gw_status gw_qp_solve(gw_plan_t plan, gw_qp_mode mode, double* e_qp, double* z_f
 gw_status gw_evgw(gw_plan_t plan, int update_w, gw_qp_mode mode, int max_iter, double tol, double* e_qp,
                   double* z_factor, int* state_status, int* iterations);
 
+/* Sharding one job across ranks (one process and one GPU per rank; Algorithm 1's imaginary-grid loop and
+ * per-state residue loop partitioned as independent work):
+ *   * the imaginary-axis stage computes only this rank's block of the n_freq + 1 frequency positions
+ *     (gw_shard_columns; position 0 is xi = 0, position p > 0 is grid point p - 1), zeroes the other columns of
+ *     its W table and sums the tables of all ranks with allreduce_sum (every column comes from one rank);
+ *   * each Sigma evaluation solves only the residue right-hand sides j of its list with j % world == rank and
+ *     sums the per-target R and dR/domega (2 n_targets doubles) with allreduce_sum; the I term, the QP search and
+ *     every other step run on every rank with the same summed values, so all ranks return the same results.
+ * allreduce_sum(buf, n, ctx) must replace the host array buf[n] by its element-wise sum over the ranks (for
+ * example through MPI or torch.distributed) and return 0 on success; it is called at the same points, with the
+ * same n, on every rank.  world = 1 turns sharding off.  The table is rebuilt on the next call that needs it. */
+typedef int (*gw_allreduce_fn)(double* buf, long long n, void* ctx);
+gw_status gw_set_shard(gw_plan_t plan, int rank, int world, gw_allreduce_fn allreduce_sum, void* ctx);
+/* The block [*p0, *p1) of frequency positions rank `rank` of `world` computes (host only): contiguous,
+ * floor((n_freq + 1) r / world) to floor((n_freq + 1)(r + 1) / world). */
+gw_status gw_shard_columns(int n_freq, int rank, int world, int* p0, int* p1);
+
 /* Copy the imaginary-axis table to the host: out [n_targets][n_bas][n_freq + 1] with
  * out[t][m][g] = W^c_nm(i xi_g) for the grid points g < n_freq and out[t][m][n_freq] = W^c_nm(0)
  * (Algorithm 1, imaginary-grid loop).  Builds the table first if needed. */

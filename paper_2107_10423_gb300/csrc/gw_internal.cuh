@@ -124,6 +124,8 @@ void launch_fallback_finish64(const double* B_nm, int n_bas, int n_aux, const in
 // R term reduction per target over its right-hand sides [start[t], start[t+1]).
 // W[r][g] += W[r][n_g] for g < n_cols (table [R][n_g + 1]): columns held as differences from the static one.
 void launch_w_add_static(double* W, long R, int n_g, int n_cols, cudaStream_t s);
+// W[r][c] = 0 outside the processing positions [p0, p1) (position 0 = column n_g, position p > 0 = column p - 1).
+void launch_w_keep_positions(double* W, long R, int n_g, int p0, int p1, cudaStream_t s);
 void launch_residue_reduce(const int* start, int n_t, const double* coef, const double* w_re, const double* dw_re,
                            double* R, double* dR, cudaStream_t s);
 

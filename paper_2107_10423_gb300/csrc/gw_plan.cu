@@ -63,6 +63,12 @@ struct gw_plan {
   __nv_bfloat16* d_Bnlo = nullptr;
   __nv_bfloat16* d_Bnlo2 = nullptr;
   bool screening_done = false;
+  // sharding across ranks (gw_set_shard): frequency positions [sh_p0, sh_p1) of the imaginary-axis stage and the
+  // residue right-hand sides j with j % sh_world == sh_rank; sums across ranks through sh_reduce
+  int sh_rank = 0, sh_world = 1;
+  gw_allreduce_fn sh_reduce = nullptr;
+  void* sh_ctx = nullptr;
+  std::vector<double> sh_buf;
   int ns_iters_last = 0;
   int ns_kmax = 0;
   int ns_ndiff = 0;           // lowest grid points whose W column is built in the difference form
@@ -471,11 +477,17 @@ gw_status screening_T(gw_plan* P, const T* B, const T* Bn) {
   P->ns_ndiff = 0;
   if (use_tc)
     while (P->ns_ndiff < P->n_g && P->h_xi[P->ns_ndiff] < 0.1 * P->D_min) ++P->ns_ndiff;
-  if (use_tc) CK(cudaMemsetAsync(P->d_W, 0, sizeof(double) * (size_t)R * n_g1, P->stream));   // W is accumulated
+  // positions this rank computes: its block [p0, p1), from position 0 when the block holds difference-form
+  // columns (they need eps(0)^-1); columns outside the block are zeroed before the sum across ranks
+  int p0 = 0, p1 = n_g1;
+  if (P->sh_world > 1) gw_shard_columns(P->n_g, P->sh_rank, P->sh_world, &p0, &p1);
+  const int p_begin = (use_tc && p0 > 0 && p0 <= P->ns_ndiff) ? 0 : p0;
+  if (use_tc || P->sh_world > 1)
+    CK(cudaMemsetAsync(P->d_W, 0, sizeof(double) * (size_t)R * n_g1, P->stream));   // W is accumulated / summed
   std::vector<int> info(chunk);
   double ms_pi = 0.0;
-  for (int g0 = 0; g0 < n_g1; g0 += chunk) {
-    const int nc = std::min(chunk, n_g1 - g0);
+  for (int g0 = p_begin; g0 < p1; g0 += chunk) {
+    const int nc = std::min(chunk, p1 - g0);
     CK(cudaEventRecord(P->ev0, P->stream));
     if (use_tc) {
       std::vector<int> kinds(nc, 0);
@@ -509,6 +521,19 @@ gw_status screening_T(gw_plan* P, const T* B, const T* Bn) {
   }
   if (use_tc && P->ns_ndiff > 0) LAUNCH(gw::launch_w_add_static(P->d_W, R, P->n_g, P->ns_ndiff, P->stream));
   P->stats.ms_pi = ms_pi;
+  if (P->sh_world > 1) {
+    // keep the owned columns (positions [p0, p1): position 0 is column n_g, position p > 0 is column p - 1), then
+    // sum the tables of all ranks: every column comes from exactly one rank
+    LAUNCH(gw::launch_w_keep_positions(P->d_W, R, P->n_g, p0, p1, P->stream));
+    const size_t cnt = (size_t)R * n_g1;
+    P->sh_buf.resize(cnt);
+    CK(cudaMemcpyAsync(P->sh_buf.data(), P->d_W, sizeof(double) * cnt, cudaMemcpyDeviceToHost, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+    if (P->sh_reduce(P->sh_buf.data(), (long long)cnt, P->sh_ctx) != 0)
+      return fail(P, GW_ERR_CUDA, "shard all-reduce of the W table failed");
+    CK(cudaMemcpyAsync(P->d_W, P->sh_buf.data(), sizeof(double) * cnt, cudaMemcpyHostToDevice, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+  }
   return GW_OK;
 }
 
@@ -987,6 +1012,24 @@ gw_status sigma_eval(gw_plan* P, const std::vector<double>& omega, const std::ve
   std::vector<int> rt, rm, start;
   std::vector<double> xf, coef;
   build_residue_list(P, omega, active, rt, rm, xf, coef, start);
+  if (P->sh_world > 1) {
+    // this rank's right-hand sides: entry j of the full list with j % world == rank (the per-target sums of R
+    // and dR are then added across ranks)
+    std::vector<int> rt2, rm2, start2(P->n_t + 1, 0);
+    std::vector<double> xf2, coef2;
+    for (int t = 0; t < P->n_t; ++t) {
+      start2[t] = (int)rt2.size();
+      for (int j = start[t]; j < start[t + 1]; ++j)
+        if (j % P->sh_world == P->sh_rank) {
+          rt2.push_back(rt[j]);
+          rm2.push_back(rm[j]);
+          xf2.push_back(xf[j]);
+          coef2.push_back(coef[j]);
+        }
+    }
+    start2[P->n_t] = (int)rt2.size();
+    rt.swap(rt2); rm.swap(rm2); xf.swap(xf2); coef.swap(coef2); start.swap(start2);
+  }
   const int nr = (int)rt.size();
   TRY(ensure(P, P->mr_rt, sizeof(int) * std::max(1, nr)));
   TRY(ensure(P, P->mr_rm, sizeof(int) * std::max(1, nr)));
@@ -1009,6 +1052,19 @@ gw_status sigma_eval(gw_plan* P, const std::vector<double>& omega, const std::ve
                as<double>(P->mr_wim), as<double>(P->mr_dwre), as<int>(P->mr_it), as<double>(P->mr_res), fb.data()));
   LAUNCH(gw::launch_residue_reduce(as<int>(P->sg_start), n_t, as<double>(P->sg_coef), as<double>(P->mr_wre),
                                    as<double>(P->mr_dwre), as<double>(P->sg_R), as<double>(P->sg_dR), P->stream));
+  if (P->sh_world > 1) {
+    // R and dR of every target summed over the ranks' residue subsets (the I term is computed on every rank)
+    P->sh_buf.resize(2 * (size_t)n_t);
+    CK(cudaMemcpyAsync(P->sh_buf.data(), P->sg_R.p, sizeof(double) * n_t, cudaMemcpyDeviceToHost, P->stream));
+    CK(cudaMemcpyAsync(P->sh_buf.data() + n_t, P->sg_dR.p, sizeof(double) * n_t, cudaMemcpyDeviceToHost,
+                       P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+    if (P->sh_reduce(P->sh_buf.data(), 2LL * n_t, P->sh_ctx) != 0)
+      return fail(P, GW_ERR_CUDA, "shard all-reduce of the residue terms failed");
+    CK(cudaMemcpyAsync(P->sg_R.p, P->sh_buf.data(), sizeof(double) * n_t, cudaMemcpyHostToDevice, P->stream));
+    CK(cudaMemcpyAsync(P->sg_dR.p, P->sh_buf.data() + n_t, sizeof(double) * n_t, cudaMemcpyHostToDevice,
+                       P->stream));
+  }
   CK(cudaStreamSynchronize(P->stream));
   P->stats.ms_sigma_imag += now_ms(P, a, b);
   cudaEventDestroy(a);
@@ -1509,6 +1565,26 @@ gw_status gw_evgw(gw_plan_t P, int update_w, gw_qp_mode mode, int max_iter, doub
   if (iterations) *iterations = std::min(it, max_iter);
   if (!conv) return fail(P, GW_ERR_NOT_CONVERGED, "eigenvalue cycles did not converge to %g Ha in %d", tol, max_iter);
   return last;
+}
+
+gw_status gw_shard_columns(int n_freq, int rank, int world, int* p0, int* p1) {
+  if (n_freq <= 0 || world <= 0 || rank < 0 || rank >= world || !p0 || !p1) return GW_ERR_ARG;
+  const long n = (long)n_freq + 1;
+  *p0 = (int)(n * rank / world);
+  *p1 = (int)(n * (rank + 1) / world);
+  return GW_OK;
+}
+
+gw_status gw_set_shard(gw_plan_t P, int rank, int world, gw_allreduce_fn allreduce_sum, void* ctx) {
+  if (!P) return GW_ERR_ARG;
+  if (world < 1 || rank < 0 || rank >= world || (world > 1 && !allreduce_sum))
+    return fail(P, GW_ERR_ARG, "bad shard (rank %d of %d)", rank, world);
+  P->sh_rank = rank;
+  P->sh_world = world;
+  P->sh_reduce = world > 1 ? allreduce_sum : nullptr;
+  P->sh_ctx = ctx;
+  P->screening_done = false;
+  return GW_OK;
 }
 
 gw_status gw_plan_footprint(const gw_config* c, int n_t, unsigned flags, unsigned long long* bytes) {

@@ -575,6 +575,21 @@ void launch_residue_reduce(const int* start, int n_t, const double* coef, const 
   if (n_t > 0) residue_reduce_kernel<<<(n_t + 127) / 128, 128, 0, s>>>(start, n_t, coef, w_re, dw_re, R, dR);
 }
 
+// W[r][c] = 0 for every column c outside the positions [p0, p1) (position 0 is column n_g, the static point;
+// position p > 0 is grid column p - 1).
+__global__ void w_keep_positions_kernel(double* __restrict__ W, long R, int n_g, int p0, int p1) {
+  const long N = R * (n_g + 1);
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % (n_g + 1));
+    const int pos = c == n_g ? 0 : c + 1;
+    if (pos < p0 || pos >= p1) W[i] = 0.0;
+  }
+}
+
+void launch_w_keep_positions(double* W, long R, int n_g, int p0, int p1, cudaStream_t s) {
+  w_keep_positions_kernel<<<1024, 256, 0, s>>>(W, R, n_g, p0, p1);
+}
+
 void launch_qp_init(QPState* st, const double* e_n, int n, cudaStream_t s) {
   if (n > 0) qp_init_kernel<<<(n + 127) / 128, 128, 0, s>>>(st, e_n, n);
 }

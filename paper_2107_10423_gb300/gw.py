@@ -18,7 +18,7 @@ GW_INPUT_ON_DEVICE, GW_BORROW_DEVICE_PTRS = 1, 2
 
 EXPORTED = ["gw_config_default", "gw_plan_create", "gw_polarizability", "gw_sigma_cd", "gw_residues_minres",
             "gw_qp_solve", "gw_grid", "gw_w_table", "gw_w_table_noalloc", "gw_get_stats", "gw_plan_destroy", "gw_last_error",
-            "gw_plan_footprint", "gw_evgw"]
+            "gw_plan_footprint", "gw_evgw", "gw_set_shard", "gw_shard_columns"]
 
 
 class GWError(RuntimeError):
@@ -75,6 +75,11 @@ def load(path: str = LIB_PATH):
     lib.gw_qp_solve.argtypes = [_P, ctypes.c_int, _P, _P, _P]
     lib.gw_evgw.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P, _P, _P]
     lib.gw_evgw.restype = ctypes.c_int
+    lib.gw_set_shard.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, _P]
+    lib.gw_set_shard.restype = ctypes.c_int
+    lib.gw_shard_columns.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int)]
+    lib.gw_shard_columns.restype = ctypes.c_int
     lib.gw_get_stats.argtypes = [_P, ctypes.POINTER(Stats)]
     lib.gw_w_table_noalloc.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, ctypes.c_int, _P]
     lib.gw_w_table_noalloc.restype = ctypes.c_int
@@ -229,6 +234,13 @@ class Plan:
                                       _ptr(s), ctypes.byref(it)),
                     allow=(GW_ERR_NOT_CONVERGED,) if allow_unconverged else ())
         return e, z, s, it.value
+
+    def set_shard(self, rank, world, allreduce_fn=None):
+        """Split this plan's job across ``world`` ranks (gw_set_shard); ``allreduce_fn`` is a
+        shard.ALLREDUCE_FN callback (kept alive by the plan)."""
+        self._shard_cb = allreduce_fn
+        fp = ctypes.cast(allreduce_fn, ctypes.c_void_p) if allreduce_fn is not None else None
+        self._check(self._lib.gw_set_shard(self._h, int(rank), int(world), fp, None))
 
     def stats(self) -> dict:
         st = Stats()
