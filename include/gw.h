@@ -186,10 +186,12 @@ gw_status gw_w_table(gw_plan_t plan, double* out);
 
 /* Timing and counters accumulated since plan creation (host, milliseconds / counts).  ms_kernel and
  * flops_kernel are per kernel class, timed with CUDA events on the plan's stream:
- *   0 Pi on tensor cores (tcgen05, incl. operand split)   1 Pi (SIMT)
+ *   0 Pi on tensor cores (tcgen05, weights applied in the kernel)   1 Pi (SIMT)
  *   2 W-table factorisation (Cholesky of 1 - Pi, or the tensor-core Newton-Schulz inverse in mixed mode)
- *   3 W-table reduction (triangular solves, or the tensor-core GEMM into W)   4 MINRES operator GEMMs
- *   5 MINRES recurrences                                    6 dense Pi(x) of fallback solves
+ *   3 W-table reduction (triangular solves, or the tensor-core GEMM into W)
+ *   4 MINRES iterations (the operator GEMMs and, since the iterations run as one CUDA graph per batch, the
+ *     recurrence steps; flops count the operator of the iterations that ran) and the derivative pass
+ *   5 MINRES recurrences outside the graph (initialisation)  6 dense Pi(x) of fallback solves
  *   7 batched complex LU + solve                          8 residual operators of the mixed-precision refinement
  *                                                           (three-part tensor-core, and FP64 where selected)
  * flops_kernel counts algorithmic floating-point operations (a multiply-add is 2). */
@@ -212,6 +214,7 @@ typedef struct {
   long long bytes_device;      /* device bytes the plan holds now (inputs it copied, their mixed-precision copies,
                                   the W table and every work-space buffer) */
   long long bytes_device_peak; /* largest bytes_device since plan creation */
+  long long n_graph_launches;  /* CUDA graph launches (one per MINRES batch: all of its iterations) */
 } gw_stats;
 gw_status gw_get_stats(gw_plan_t plan, gw_stats* out);
 

@@ -41,7 +41,8 @@ int trsm_w_default_ctas();
 template <typename T>
 void launch_op_gemm1(const T* V, const T* B, const double* eps, int n_occ, int n_virt, int n_aux, const double* x,
                      double eta, int nr, T* U, int mode, cudaStream_t s, double* dw = nullptr,
-                     double cut = 0.0, long ldb = 0);   // ldb: row length of B (0 = n_occ * n_virt)
+                     double cut = 0.0, long ldb = 0,    // ldb: row length of B (0 = n_occ * n_virt)
+                     const int* run_if = nullptr);      // device flag: the launch does nothing if *run_if == 0
 // Double-float (FP32 pair, 48-bit) versions of op_gemm1 mode 0 and op_gemm2 mode 1 for the refinement residual:
 // V, U, out FP64; B as its split Bh + Bl (launch_df_split of the FP64 B_ia).
 void launch_df_split(const double* x, long n, float* h, float* l, cudaStream_t s);
@@ -56,7 +57,7 @@ void launch_deriv_resonant(const double* V64, const double* B, long n_ov, int n_
                            cudaStream_t s);
 template <typename T>
 void launch_op_gemm2(const T* U, const T* B, int n_aux, int n_ov, int nr, const T* V, T* out, int mode,
-                     cudaStream_t s);
+                     cudaStream_t s, const int* run_if = nullptr);
 
 // ---------------------------------------------------------------- CD kernels (kernels_cd.cu)
 void launch_sigma_x(const double* B_nm, int n_t, int n_bas, int n_aux, int n_occ, double* sx, cudaStream_t s);

@@ -739,7 +739,8 @@ gw_status dense_fallback(gw_plan* P, const std::vector<int>& need, const int* rt
 // Residue operator on the tensor cores (mixed precision), for nr right-hand sides held in V32 [2nr][n]:
 // GEMM1 t = B^T z with the complex weights c_ia(x_j) fused into its epilogue (written as split BF16),
 // GEMM2 B w with either the plain store (mode 0: [Re; Im] of Pi z) or the 2n embedding of (1 - Pi) z (mode 1).
-gw_status tc_operator(gw_plan* P, int nr, const double* xf, const float* V32, float* S32, int mode) {
+gw_status tc_operator(gw_plan* P, int nr, const double* xf, const float* V32, float* S32, int mode,
+                      const int* run_if = nullptr) {
   const int n = P->cfg.n_aux, n_ov = P->n_ov;
   const int ldov = gw::tc_ld(n_ov);
   const bool three = P->cfg.op_parts >= 3;
@@ -757,6 +758,7 @@ gw_status tc_operator(gw_plan* P, int nr, const double* xf, const float* V32, fl
   e1.olo = as<__nv_bfloat16>(P->mr_Ulo);
   e1.olo2 = ulo2;
   e1.ldh = ldov;
+  e1.run_if = run_if;
   const gw::TcOperand Vop{{as<__nv_bfloat16>(P->mr_Vhi), as<__nv_bfloat16>(P->mr_Vlo), vlo2}};
   const gw::TcOperand BT{{P->d_BThi, P->d_BTlo, three ? P->d_BTlo2 : nullptr}};
   const int ns = three ? 3 : 2;
@@ -767,6 +769,7 @@ gw_status tc_operator(gw_plan* P, int nr, const double* xf, const float* V32, fl
   e2.ldo = n;
   e2.vin = V32;
   e2.ldv = n;
+  e2.run_if = run_if;
   const gw::TcOperand Uop{{as<__nv_bfloat16>(P->mr_Uhi), as<__nv_bfloat16>(P->mr_Ulo), ulo2}};
   const gw::TcOperand Bop{{P->d_Bhi, P->d_Blo, three ? P->d_Blo2 : nullptr}};
   CK(gw::tc_gemm_ex(Uop, 1, Bop, 0, ns, 2 * nr, n, n_ov, 0, e2, as<int>(P->tc_err), P->stream));
@@ -870,31 +873,61 @@ gw_status residues_T(gw_plan* P, int nr_total, const int* d_rt, const int* d_rm,
                                      as<double>(P->mr_d1), as<double>(P->mr_d2), as<double>(P->mr_x),
                                      as<MinresState>(P->mr_st), as<T>(P->mr_V), P->stream));
     const double op_flops = 2.0 * 2.0 * (2.0 * nr) * n * (double)n_ov;   // two GEMMs, 2nr columns each
-    for (int it = 0; it < P->cfg.minres_maxit; ++it) {
-      size_t tg = tick(P);
-      if (tcop) {
-        TRY(tc_operator(P, nr, xf, reinterpret_cast<const float*>(P->mr_V.p), reinterpret_cast<float*>(P->mr_S.p),
-                        1));
-      } else {
-        LAUNCH(gw::launch_op_gemm1<T>(as<T>(P->mr_V), B, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, xf, eta, nr,
-                                      as<T>(P->mr_U), 0, P->stream));
-        LAUNCH(gw::launch_op_gemm2<T>(as<T>(P->mr_U), B, n, n_ov, nr, as<T>(P->mr_V), as<T>(P->mr_S), 1,
-                                      P->stream));
+    // The minres_maxit iterations (operator, then one MINRES step of every right-hand side) are captured as one
+    // CUDA graph and launched without host synchronisation.  mr_cnt holds the number of right-hand sides still
+    // active after the last step; once it is 0 the operator launches of the remaining iterations return at once
+    // and the step kernel leaves every converged right-hand side frozen.
+    int* cnt = as<int>(P->mr_cnt);
+    CK(cudaMemcpyAsync(cnt, &nr, sizeof(int), cudaMemcpyHostToDevice, P->stream));
+    if (P->cfg.minres_maxit > 0) {
+      cudaGraph_t graph = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      CK(cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal));
+      gw_status cap = GW_OK;
+      for (int it = 0; it < P->cfg.minres_maxit && cap == GW_OK; ++it) {
+        if (tcop) {
+          cap = tc_operator(P, nr, xf, reinterpret_cast<const float*>(P->mr_V.p),
+                            reinterpret_cast<float*>(P->mr_S.p), 1, cnt);
+        } else {
+          gw::launch_op_gemm1<T>(as<T>(P->mr_V), B, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, xf, eta, nr,
+                                 as<T>(P->mr_U), 0, P->stream, nullptr, 0.0, 0, cnt);
+          gw::launch_op_gemm2<T>(as<T>(P->mr_U), B, n, n_ov, nr, as<T>(P->mr_V), as<T>(P->mr_S), 1, P->stream,
+                                 cnt);
+          P->stats.n_kernel_launches += 2;
+        }
+        if (cudaMemsetAsync(cnt, 0, sizeof(int), P->stream) != cudaSuccess) cap = GW_ERR_CUDA;
+        gw::launch_minres_step<T>(as<T>(P->mr_S), nr, n, P->cfg.minres_tol, as<double>(P->mr_vprev),
+                                  as<double>(P->mr_v), as<double>(P->mr_d1), as<double>(P->mr_d2),
+                                  as<double>(P->mr_x), as<MinresState>(P->mr_st), as<T>(P->mr_V), cnt, P->stream);
+        P->stats.n_kernel_launches++;
       }
-      mark(P, 4, tg, op_flops);
-      CK(cudaMemsetAsync(P->mr_cnt.p, 0, sizeof(int), P->stream));
-      tg = tick(P);
-      LAUNCH(gw::launch_minres_step<T>(as<T>(P->mr_S), nr, n, P->cfg.minres_tol, as<double>(P->mr_vprev),
-                                       as<double>(P->mr_v), as<double>(P->mr_d1), as<double>(P->mr_d2),
-                                       as<double>(P->mr_x), as<MinresState>(P->mr_st), as<T>(P->mr_V),
-                                       as<int>(P->mr_cnt), P->stream));
-      mark(P, 5, tg, 0.0);
-      // poll the active count every 8 iterations (finished right-hand sides are frozen by the step kernel)
-      if ((it & 7) == 7 || it + 1 == P->cfg.minres_maxit) {
-        CK(cudaMemcpyAsync(P->h_cnt, P->mr_cnt.p, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
-        CK(cudaStreamSynchronize(P->stream));
-        if (*P->h_cnt == 0) break;
+      const cudaError_t ec = cudaStreamEndCapture(P->stream, &graph);
+      if (cap != GW_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return cap == GW_ERR_CUDA ? fail(P, GW_ERR_CUDA, "MINRES graph capture failed") : cap;
       }
+      CK(ec);
+      const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      CK(ei);
+      const size_t tg = tick(P);
+      const cudaError_t el = cudaGraphLaunch(exec, P->stream);
+      const size_t tg1 = tick(P);
+      if (el != cudaSuccess) {
+        cudaGraphExecDestroy(exec);
+        CK(el);
+      }
+      CK(cudaStreamSynchronize(P->stream));
+      cudaGraphExecDestroy(exec);
+      P->stats.n_graph_launches++;
+      // operator iterations that ran: the largest MINRES iteration count of the batch (states of converged
+      // right-hand sides are frozen)
+      std::vector<MinresState> hst(nr);
+      CK(cudaMemcpy(hst.data(), P->mr_st.p, sizeof(MinresState) * nr, cudaMemcpyDeviceToHost));
+      int ran = 0;
+      for (const auto& x : hst) ran = std::max(ran, x.iters);
+      if (tg != (size_t)-1 && tg1 != (size_t)-1) P->marks.push_back({4, tg, tg1, op_flops * ran});
+      P->stats.launches_kernel[4] += ran;
     }
     if (tcop) {
       int herr = 0;

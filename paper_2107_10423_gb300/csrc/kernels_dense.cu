@@ -363,7 +363,8 @@ __global__ void __launch_bounds__(NT) op_gemm1_kernel(const T* __restrict__ V, c
                                                       const double* __restrict__ eps, int n_occ, int n_virt,
                                                       int n_aux, const double* __restrict__ xs, double eta, int nr,
                                                       T* __restrict__ U, int mode, double* __restrict__ dw,
-                                                      double cut, long ldb) {
+                                                      double cut, long ldb, const int* __restrict__ run_if) {
+  if (run_if && *run_if == 0) return;
   __shared__ T As[TK][TM + 4];
   __shared__ T Bs[TK][TN + 4];
   const long n_ov = (long)n_occ * n_virt;
@@ -541,7 +542,8 @@ __global__ void __launch_bounds__(256) deriv_resonant_kernel(const double* __res
 template <typename T>
 __global__ void __launch_bounds__(NT) op_gemm2_kernel(const T* __restrict__ U, const T* __restrict__ B, int n_aux,
                                                       long n_ov, int nr, const T* __restrict__ V,
-                                                      T* __restrict__ out, int mode) {
+                                                      T* __restrict__ out, int mode, const int* __restrict__ run_if) {
+  if (run_if && *run_if == 0) return;
   __shared__ T As[TK][TM + 4];
   __shared__ T Bs[TK][TN + 4];
   const int M = 2 * nr;
@@ -846,18 +848,19 @@ cudaError_t launch_trsm_w(const T* Lbase, long Lstride, int n, int n_g, const in
 
 template <typename T>
 void launch_op_gemm1(const T* V, const T* B, const double* eps, int n_occ, int n_virt, int n_aux, const double* x,
-                     double eta, int nr, T* U, int mode, cudaStream_t s, double* dw, double cut, long ldb) {
+                     double eta, int nr, T* U, int mode, cudaStream_t s, double* dw, double cut, long ldb,
+                     const int* run_if) {
   long n_ov = (long)n_occ * n_virt;
   dim3 grid((unsigned)((n_ov + TN - 1) / TN), (2 * nr + TM - 1) / TM);
   op_gemm1_kernel<T><<<grid, NT, 0, s>>>(V, B, eps, n_occ, n_virt, n_aux, x, eta, nr, U, mode, dw, cut,
-                                         ldb > 0 ? ldb : n_ov);
+                                         ldb > 0 ? ldb : n_ov, run_if);
 }
 
 template <typename T>
 void launch_op_gemm2(const T* U, const T* B, int n_aux, int n_ov, int nr, const T* V, T* out, int mode,
-                     cudaStream_t s) {
+                     cudaStream_t s, const int* run_if) {
   dim3 grid((n_aux + TN - 1) / TN, (2 * nr + TM - 1) / TM);
-  op_gemm2_kernel<T><<<grid, NT, 0, s>>>(U, B, n_aux, (long)n_ov, nr, V, out, mode);
+  op_gemm2_kernel<T><<<grid, NT, 0, s>>>(U, B, n_aux, (long)n_ov, nr, V, out, mode, run_if);
 }
 
 #define GW_INST(T)                                                                                              \
@@ -868,8 +871,9 @@ void launch_op_gemm2(const T* U, const T* B, int n_aux, int n_ov, int nr, const 
   template cudaError_t launch_trsm_w<T>(const T*, long, int, int, const int*, const T*, int, double*, int, T*,   \
                                         int, cudaStream_t);                                                     \
   template void launch_op_gemm1<T>(const T*, const T*, const double*, int, int, int, const double*, double, int, \
-                                   T*, int, cudaStream_t, double*, double, long);                               \
-  template void launch_op_gemm2<T>(const T*, const T*, int, int, int, const T*, T*, int, cudaStream_t);
+                                   T*, int, cudaStream_t, double*, double, long, const int*);                   \
+  template void launch_op_gemm2<T>(const T*, const T*, int, int, int, const T*, T*, int, cudaStream_t,          \
+                                   const int*);
 GW_INST(double)
 GW_INST(float)
 #undef GW_INST

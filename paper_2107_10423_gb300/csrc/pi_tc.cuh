@@ -37,6 +37,8 @@ struct TcEpi {
   const int* gidx;
   const float* bvec;
   int ldb;
+  // if not NULL: the whole launch does nothing when *run_if == 0 (device flag, read once at kernel start)
+  const int* run_if;
 };
 
 // Row length (elements) of the split operand arrays for contraction length K (multiple of 8: 16-byte rows).

@@ -222,6 +222,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   constexpr int STAGES = TcCfg<NSP>::STAGES;
   constexpr int STAGE_BYTES = TcCfg<NSP>::STAGE_BYTES;
   constexpr int CHUNK = TcCfg<NSP>::CHUNK;
+  if (ep.run_if && *ep.run_if == 0) return;     // uniform over the grid: nothing is allocated yet
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;

@@ -44,7 +44,8 @@ class Stats(ctypes.Structure):
                 ("n_sigma_evals", ctypes.c_longlong), ("n_kernel_launches", ctypes.c_longlong),
                 ("ms_kernel", ctypes.c_double * 9), ("flops_kernel", ctypes.c_double * 9),
                 ("launches_kernel", ctypes.c_longlong * 9), ("n_refine_fp64", ctypes.c_longlong),
-                ("bytes_device", ctypes.c_longlong), ("bytes_device_peak", ctypes.c_longlong)]
+                ("bytes_device", ctypes.c_longlong), ("bytes_device_peak", ctypes.c_longlong),
+                ("n_graph_launches", ctypes.c_longlong)]
 
 
 KERNEL_CLASSES = ["pi_tcgen05", "pi_simt", "w_table_factor", "w_table_reduce", "minres_operator_gemm", "minres_recurrence",
