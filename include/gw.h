@@ -89,6 +89,10 @@ typedef struct {
                                   pairs, 48-bit, on the FP32 pipes: 1, default) or in FP64 (0) */
   int tc_max_ctas;             /* mixed: cap on the persistent grid of the Pi kernel (CTAs, one per SM at most);
                                   0 = every SM.  A smaller grid leaves SMs to work that runs beside it */
+  int pi_ksplit;               /* mixed: K ranges per (tile, frequency pair) of the Pi kernel: 0 = autotuned per
+                                  problem shape (n_aux, n_occ n_virt, batch; every feasible split timed once per
+                                  process, the fastest kept; only shapes whose tiles do not fill the GPU split),
+                                  or 1, 2, 4, 8 forced.  Default 0 */
 } gw_config;
 
 typedef struct gw_plan* gw_plan_t;
@@ -215,6 +219,7 @@ typedef struct {
                                   the W table and every work-space buffer) */
   long long bytes_device_peak; /* largest bytes_device since plan creation */
   long long n_graph_launches;  /* CUDA graph launches (one per MINRES batch: all of its iterations) */
+  int pi_ksplit_last;          /* K split of the last Pi-kernel launch (autotuned or forced) */
 } gw_stats;
 gw_status gw_get_stats(gw_plan_t plan, gw_stats* out);
 

@@ -73,7 +73,7 @@ struct gw_plan {
   int ns_kmax = 0;
   int ns_ndiff = 0;           // lowest grid points whose W column is built in the difference form
   std::vector<DevBuf*> bufs;
-  DevBuf ws_mat, ws_info, ws_scratch, ws_gout, ws_xi, tc_kind, tc_par, tc_err, tc_w, ns_E, ns_X, ns_X2, ns_Xa, ns_Xb, ns_T, ns_lam,
+  DevBuf ws_mat, ws_info, ws_scratch, ws_gout, ws_xi, tc_part, tc_kind, tc_par, tc_err, tc_w, ns_E, ns_X, ns_X2, ns_Xa, ns_Xb, ns_T, ns_lam,
       ns_E0, ns_vec;
   DevBuf mr_V, mr_U, mr_S, mr_vprev, mr_v, mr_d1, mr_d2, mr_x, mr_st, mr_rt, mr_rm, mr_xf, mr_wre, mr_wim,
       mr_dwre, mr_it, mr_res, mr_cnt, mr_Vhi, mr_Vlo, mr_Uhi, mr_Ulo, mr_Vlo2, mr_Ulo2, mr_V64;
@@ -91,7 +91,7 @@ struct gw_plan {
   std::vector<Mark> marks;
 
   gw_plan() {
-    DevBuf* all[] = {&ws_mat, &ws_info, &ws_scratch, &ws_gout, &ws_xi, &tc_kind, &tc_par, &tc_err, &tc_w, &ns_E, &ns_X, &ns_X2, &ns_Xa, &ns_Xb, &ns_T, &ns_lam, &ns_E0, &ns_vec, &mr_V, &mr_U, &mr_S, &mr_vprev,
+    DevBuf* all[] = {&ws_mat, &ws_info, &ws_scratch, &ws_gout, &ws_xi, &tc_part, &tc_kind, &tc_par, &tc_err, &tc_w, &ns_E, &ns_X, &ns_X2, &ns_Xa, &ns_Xb, &ns_T, &ns_lam, &ns_E0, &ns_vec, &mr_V, &mr_U, &mr_S, &mr_vprev,
                      &mr_v, &mr_d1, &mr_d2, &mr_x, &mr_st, &mr_rt, &mr_rm, &mr_xf, &mr_wre, &mr_wim,
                      &mr_dwre, &mr_it, &mr_res, &mr_cnt, &mr_Vhi, &mr_Vlo, &mr_Uhi, &mr_Ulo, &mr_Vlo2, &mr_Ulo2, &mr_V64, &sg_I, &sg_dI, &sg_R, &sg_dR, &sg_om, &sg_start,
                      &sg_coef, &sg_act, &qp_st, &qp_om0, &fb_A, &fb_y, &fb_piv, &fb_info, &fb_idx, &fb_y64, &fb_V32, &fb_S32, &fb_Vp, &fb_Up, &fb_x, &fb_V64, &fb_U64, &fb_S64, &fb_sel, &fb_pos, &fb_rho, &fb_xs, &fb_Bh, &fb_Bl};
@@ -222,8 +222,20 @@ gw_status tc_weighted_syrk(gw_plan* P, const int* kinds, const double* params, i
   const size_t t0 = tick(P);
   CK(gw::tc_pair_weights(P->d_eps, P->cfg.n_occ, P->cfg.n_virt, K, as<int>(P->tc_kind), as<double>(P->tc_par),
                          P->cfg.eta, nb, as<float>(P->tc_w), P->stream));
+  // split-K partials (only small problems, whose tiles x entry pairs do not fill the GPU, consider a split)
+  const long nbt = (n + 127) / 128;
+  float* part = nullptr;
+  size_t part_bytes = 0;
+  if (P->cfg.pi_ksplit != 1 && nbt * (nbt + 1) / 2 * ((nb + 1) / 2) < 2L * 152) {
+    part_bytes = std::min(ws_bytes(P), (size_t)(P->cfg.pi_ksplit > 0 ? P->cfg.pi_ksplit : 8) * nb * n * n * 4);
+    TRY(ensure(P, P->tc_part, part_bytes));
+    part = as<float>(P->tc_part);
+  }
+  int chosen = 1;
   CK(gw::tc_pi_fused(P->d_B_ia_f, P->ld_f, n, K, as<float>(P->tc_w), nb, P->d_Bhi, P->d_Blo, mode_even, mode_odd,
-                     out, (long)n * n, n, as<int>(P->tc_err), P->stream, P->cfg.tc_max_ctas));
+                     out, (long)n * n, n, as<int>(P->tc_err), P->stream, P->cfg.tc_max_ctas, P->cfg.pi_ksplit, part,
+                     part_bytes, &chosen));
+  P->stats.pi_ksplit_last = chosen;
   mark(P, cls, t0, (double)nb * n * n * K);     // symmetric rank-K update: n^2 K flops per entry
   P->stats.n_kernel_launches += 2;
   int herr = 0;
@@ -1343,6 +1355,8 @@ gw_status gw_plan_create(const gw_config* cfg, const double* eps, const double* 
   if (!(cfg->eta >= 0.0)) return fail(nullptr, GW_ERR_ARG, "eta must be >= 0");
   if (cfg->minres_maxit < 0 || cfg->qp_maxit <= 0) return fail(nullptr, GW_ERR_ARG, "bad iteration caps");
   if (cfg->tc_max_ctas < 0) return fail(nullptr, GW_ERR_ARG, "tc_max_ctas must be >= 0");
+  if (cfg->pi_ksplit != 0 && cfg->pi_ksplit != 1 && cfg->pi_ksplit != 2 && cfg->pi_ksplit != 4 && cfg->pi_ksplit != 8)
+    return fail(nullptr, GW_ERR_ARG, "pi_ksplit must be 0 (autotune), 1, 2, 4 or 8 (got %d)", cfg->pi_ksplit);
   if (cfg->op_parts != 2 && cfg->op_parts != 3)
     return fail(nullptr, GW_ERR_ARG, "op_parts must be 2 or 3 (got %d)", cfg->op_parts);
   const int n_bas = cfg->n_occ + cfg->n_virt;
@@ -1646,6 +1660,7 @@ gw_status gw_plan_footprint(const gw_config* c, int n_t, unsigned flags, unsigne
     // weight table of one Pi launch: a screening chunk or two entries per fallback matrix
     const u64 nb = std::max<u64>(n_g1, 2 * std::max<u64>(1, ws / (2 * n * n * ts)));
     b += 4 * nb * ldf + 16 * nb;
+    b += std::min(ws, 8 * nb * n * n * 4);                                     // split-K partials (small problems)
     const u64 per_ns = n * ldn * 24 + n * n * 8;                             // Newton-Schulz split/FP32 iterates
     b += capped(per_ns, per_ns * n_g1) + 6 * n * ldn + 4 * n_g1;             // + the split eps(0)^-1 - 1
     b += 8 * n * n_g1 + 16 * n_g1;                                           // spectrum-estimate vectors

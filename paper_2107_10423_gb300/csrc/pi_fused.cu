@@ -28,7 +28,12 @@
 
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <algorithm>
 #include <cstdint>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
 
 namespace gw {
 namespace {
@@ -66,7 +71,11 @@ __device__ __forceinline__ bool chunk_last(int f, int kb, int nk) {
 // draining its previous partial).
 __device__ __forceinline__ int entry_at(int kb, int o) { return (kb % 2 == 0 && kb > 0) ? 1 - o : o; }
 
-__device__ __forceinline__ void decode_item(long item, int n_tiles, int& bm, int& bn, int& pair) {
+// Work item -> (lower tile (bm, bn), entry pair, K split ks).
+__device__ __forceinline__ void decode_item(long item, int n_tiles, int ksplit, int& bm, int& bn, int& pair,
+                                            int& ks) {
+  ks = (int)(item % ksplit);
+  item /= ksplit;
   pair = (int)(item / n_tiles);
   const int t = (int)(item % n_tiles);
   int m = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
@@ -81,9 +90,13 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
+// With ksplit > 1 the k-blocks of every (tile, pair) are cut into ksplit contiguous ranges, each a work item of its
+// own, which writes its raw partial product (lower and mirrored) to part [ksplit][nb][n][n]; pf_reduce_kernel
+// then adds the partials in a fixed order (deterministic) and applies the output mode.
 __global__ void __launch_bounds__(THREADS, 1)
     pi_fused_kernel(const __grid_constant__ PfMaps maps, int n, int K, int nb, int mode_even, int mode_odd,
-                    float* __restrict__ out, long out_bstride, int ldo, int* __restrict__ err) {
+                    float* __restrict__ out, long out_bstride, int ldo, int ksplit, float* __restrict__ part,
+                    int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -97,7 +110,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int nbt = (n + BM - 1) / BM;
   const int n_tiles = nbt * (nbt + 1) / 2;
   const int n_pairs = (nb + 1) / 2;
-  const long items = (long)n_tiles * n_pairs;
+  const long items = (long)n_tiles * n_pairs * ksplit;
   const int nk = (K + BK - 1) / BK;
 
   uint32_t src_full[SRC_STAGES], src_empty[SRC_STAGES], tr_full[TR_STAGES], tr_empty[TR_STAGES];
@@ -149,19 +162,21 @@ __global__ void __launch_bounds__(THREADS, 1)
       long g = 0, issued = 0;
       bool ok = true;
       for (long it = blockIdx.x; it < items && ok; it += gridDim.x) {
-        int bm, bn, pair;
-        decode_item(it, n_tiles, bm, bn, pair);
-        for (int kb = 0; kb < nk; ++kb, ++g) {
+        int bm, bn, pair, ks;
+        decode_item(it, n_tiles, ksplit, bm, bn, pair, ks);
+        const int kb0 = (int)((long)nk * ks / ksplit), nki = (int)((long)nk * (ks + 1) / ksplit) - kb0;
+        for (int kb = 0; kb < nki; ++kb, ++g) {
           const int s = (int)(g % SRC_STAGES);
           const long u = g / SRC_STAGES;
           if (u > 0 && !mbar_wait(src_empty[s], (uint32_t)((u - 1) & 1), err, 11)) { ok = false; break; }
           if (*(volatile int*)&s_abort) { ok = false; break; }
           const uint32_t st = src0 + s * SRC_BYTES;
           mbar_expect_tx(src_full[s], TX_BYTES);
-          tma_load_2d(st, &maps.a, kb * BK, bm * BM, src_full[s]);
-          tma_load_2d(st + A_BYTES, &maps.bh, kb * BK, bn * BM, src_full[s]);
-          tma_load_2d(st + A_BYTES + H_BYTES, &maps.bl, kb * BK, bn * BM, src_full[s]);
-          tma_load_2d(st + W_OFF, &maps.w, kb * BK, 2 * pair, src_full[s]);
+          const int kx = (kb0 + kb) * BK;
+          tma_load_2d(st, &maps.a, kx, bm * BM, src_full[s]);
+          tma_load_2d(st + A_BYTES, &maps.bh, kx, bn * BM, src_full[s]);
+          tma_load_2d(st + A_BYTES + H_BYTES, &maps.bl, kx, bn * BM, src_full[s]);
+          tma_load_2d(st + W_OFF, &maps.w, kx, 2 * pair, src_full[s]);
           issued = g + 1;
         }
       }
@@ -179,10 +194,11 @@ __global__ void __launch_bounds__(THREADS, 1)
       long cf[2] = {0, 0};                 // chunks started per entry
       bool ok = true;
       for (long it = blockIdx.x; it < items && ok; it += gridDim.x) {
-        int bm, bn, pair;
-        decode_item(it, n_tiles, bm, bn, pair);
+        int bm, bn, pair, ks;
+        decode_item(it, n_tiles, ksplit, bm, bn, pair, ks);
         const int nf = min(2, nb - 2 * pair);
-        for (int kb = 0; kb < nk && ok; ++kb, ++g) {
+        const int nki = (int)((long)nk * (ks + 1) / ksplit) - (int)((long)nk * ks / ksplit);
+        for (int kb = 0; kb < nki && ok; ++kb, ++g) {
           const int s = (int)(g % SRC_STAGES), ts = (int)(g % TR_STAGES);
           if (*(volatile int*)&s_abort || !mbar_wait(src_full[s], (uint32_t)((g / SRC_STAGES) & 1), err, 21) ||
               !mbar_wait(tr_full[ts], (uint32_t)((g / TR_STAGES) & 1), err, 22)) {
@@ -212,7 +228,7 @@ __global__ void __launch_bounds__(THREADS, 1)
               mma_bf16(d, ah, bl, IDESC, 1u);
               mma_bf16(d, al, bh, IDESC, 1u);
             }
-            if (chunk_last(f, kb, nk)) mma_commit(acc_full[f]);
+            if (chunk_last(f, kb, nki)) mma_commit(acc_full[f]);
           }
           if (!ok) break;
           mma_commit(src_empty[s]);
@@ -230,10 +246,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     long g = 0;
     bool ok = true;
     for (long it = blockIdx.x; it < items && ok; it += gridDim.x) {
-      int bm, bn, pair;
-      decode_item(it, n_tiles, bm, bn, pair);
+      int bm, bn, pair, ks;
+      decode_item(it, n_tiles, ksplit, bm, bn, pair, ks);
       const int nf = min(2, nb - 2 * pair);
-      for (int kb = 0; kb < nk; ++kb, ++g) {
+      const int nki = (int)((long)nk * (ks + 1) / ksplit) - (int)((long)nk * ks / ksplit);
+      for (int kb = 0; kb < nki; ++kb, ++g) {
         const int s = (int)(g % SRC_STAGES), ts = (int)(g % TR_STAGES);
         bool w_ok = !*(volatile int*)&s_abort && mbar_wait(src_full[s], (uint32_t)((g / SRC_STAGES) & 1), err, 31);
         if (w_ok && g >= TR_STAGES)
@@ -292,24 +309,29 @@ __global__ void __launch_bounds__(THREADS, 1)
     long gd[2] = {0, 0};                  // drains done per entry
     bool ok = true;
     for (long it = blockIdx.x; it < items && ok; it += gridDim.x) {
-      int bm, bn, pair;
-      decode_item(it, n_tiles, bm, bn, pair);
+      int bm, bn, pair, ks;
+      decode_item(it, n_tiles, ksplit, bm, bn, pair, ks);
       const int nf = min(2, nb - 2 * pair);
+      const int nki = (int)((long)nk * (ks + 1) / ksplit) - (int)((long)nk * ks / ksplit);
       const int m0 = bm * BM, n0 = bn * BM;
       const int row = m0 + q * 32 + lane;
-      for (int kb = 0; kb < nk && ok; ++kb) {
+      for (int kb = 0; kb < nki && ok; ++kb) {
         for (int o = 0; o < 2; ++o) {
           const int f = entry_at(kb, o);
-          if (f >= nf || !chunk_last(f, kb, nk)) continue;
+          if (f >= nf || !chunk_last(f, kb, nki)) continue;
           const bool first_of_item = f == 0 ? kb <= 1 : kb == 0;
-          const bool final = kb == nk - 1;
+          const bool final = kb == nki - 1;
           bool w_ok = !*(volatile int*)&s_abort && mbar_wait(acc_full[f], (uint32_t)(gd[f] & 1), err, 41);
           if (!__all_sync(0xffffffffu, w_ok)) { ok = false; break; }
           tc_fence_after();
           const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
           const int b = 2 * pair + f;
-          const int mode = (b & 1) ? mode_odd : mode_even;
-          float* ob = out + (long)b * out_bstride;
+          // split K: the raw partial goes to its slot of `part` (mode 0, row length n); the reduction applies
+          // the mode
+          const bool raw = ksplit > 1;
+          const int mode = raw ? 0 : ((b & 1) ? mode_odd : mode_even);
+          float* ob = raw ? part + ((long)ks * nb + b) * n * n : out + (long)b * out_bstride;
+          const int ld = raw ? n : ldo;
 #pragma unroll 1
           for (int c = 0; c < 4; ++c) {
             uint32_t v[32], w[32];
@@ -333,7 +355,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const int col = c0 + j;
                 if (col > row || col >= n) continue;
                 const float x = __uint_as_float(v[j]);
-                ob[(long)row * ldo + col] = mode == 0 ? x : (mode == 1 ? ((col == row ? 1.f : 0.f) - x) : -x);
+                ob[(long)row * ld + col] = mode == 0 ? x : (mode == 1 ? ((col == row ? 1.f : 0.f) - x) : -x);
               }
             }
 #pragma unroll
@@ -341,7 +363,7 @@ __global__ void __launch_bounds__(THREADS, 1)
               const int col = c0 + j;
               if (row < n && col < row && col < n) {
                 const float x = __uint_as_float(v[j]);
-                ob[(long)col * ldo + row] = mode == 0 ? x : -x;
+                ob[(long)col * ld + row] = mode == 0 ? x : -x;
               }
             }
           }
@@ -361,6 +383,21 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (warp == 0) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// out_b[i][j] = mode(sum_s part[s][b][i][j]) in the fixed order s = 0, 1, ... (split-K reduction).
+__global__ void pf_reduce_kernel(const float* __restrict__ part, int ksplit, int nb, int n, int mode_even,
+                                 int mode_odd, float* __restrict__ out, long out_bstride, int ldo) {
+  const long nn = (long)n * n, N = nn * nb;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < N; idx += (long)gridDim.x * blockDim.x) {
+    const int b = (int)(idx / nn);
+    const long e = idx - (long)b * nn;
+    const int i = (int)(e / n), j = (int)(e - (long)i * n);
+    float v = 0.f;
+    for (int s = 0; s < ksplit; ++s) v += part[((long)s * nb + b) * nn + e];
+    const int mode = (b & 1) ? mode_odd : mode_even;
+    out[(long)b * out_bstride + (long)i * ldo + j] = mode == 0 ? v : (mode == 1 ? ((i == j ? 1.f : 0.f) - v) : -v);
   }
 }
 
@@ -441,9 +478,41 @@ cudaError_t tc_pair_weights(const double* eps, int n_occ, int n_virt, int K, con
   return cudaGetLastError();
 }
 
+namespace {
+
+cudaError_t pf_launch(const PfMaps& maps, int n, int K, int nb, int mode_even, int mode_odd, float* out,
+                      long out_bstride, int ldo, int ksplit, float* part, int* err, cudaStream_t s, int max_ctas) {
+  const int nbt = (n + BM - 1) / BM;
+  const long items = (long)nbt * (nbt + 1) / 2 * ((nb + 1) / 2) * ksplit;
+  int grid = sm_count();
+  if (max_ctas > 0 && max_ctas < grid) grid = max_ctas;
+  if (items < grid) grid = (int)items;
+  pi_fused_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(maps, n, K, nb, mode_even, mode_odd, out, out_bstride, ldo,
+                                                     ksplit, part, err);
+  if (ksplit > 1) {
+    const long N = (long)n * n * nb;
+    pf_reduce_kernel<<<(int)std::min<long>((N + 255) / 256, 4096), 256, 0, s>>>(part, ksplit, nb, n, mode_even,
+                                                                               mode_odd, out, out_bstride, ldo);
+  }
+  return cudaGetLastError();
+}
+
+// Split-K choices measured per problem shape (n, K, nb, grid cap), kept for the process.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, int> g_tune;
+
+}  // namespace
+
+int tc_pi_fused_ksplit(int n, int K, int nb, int max_ctas) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(std::make_tuple(n, K, nb, max_ctas));
+  return it == g_tune.end() ? 0 : it->second;
+}
+
 cudaError_t tc_pi_fused(const float* B, long ldb, int n, int K, const float* w, int nb, const __nv_bfloat16* Bhi,
                         const __nv_bfloat16* Blo, int mode_even, int mode_odd, float* out, long out_bstride, int ldo,
-                        int* err, cudaStream_t s, int max_ctas) {
+                        int* err, cudaStream_t s, int max_ctas, int ksplit, float* part, size_t part_bytes,
+                        int* chosen) {
   if (nb <= 0 || n <= 0 || K <= 0) return cudaSuccess;
   PfMaps maps;
   const int ldh = tc_ld(K), ldw = pf_ldw(K);
@@ -458,13 +527,53 @@ cudaError_t tc_pi_fused(const float* B, long ldb, int n, int K, const float* w, 
     if (e != cudaSuccess) return e;
     attr = true;
   }
+  const int nk = (K + BK - 1) / BK;
+  const size_t per_split = (size_t)nb * n * n * sizeof(float);
+  auto feasible = [&](int ks) {
+    return ks == 1 || (part && (size_t)ks * per_split <= part_bytes && nk / ks >= 4);
+  };
+  if (ksplit > 0) {                        // forced
+    if (!feasible(ksplit)) return cudaErrorInvalidValue;
+    if (chosen) *chosen = ksplit;
+    return pf_launch(maps, n, K, nb, mode_even, mode_odd, out, out_bstride, ldo, ksplit, part, err, s, max_ctas);
+  }
+  // Autotuning over the K split: the persistent grid only fills the GPU when (tiles x entry pairs) reaches the SM
+  // count, so small problems (few 128-row tiles) split K; each feasible split is timed once per shape (the
+  // result of every trial is the same product) and the fastest is kept.
   const int nbt = (n + BM - 1) / BM;
-  const long items = (long)nbt * (nbt + 1) / 2 * ((nb + 1) / 2);
-  int grid = sm_count();
-  if (max_ctas > 0 && max_ctas < grid) grid = max_ctas;
-  if (items < grid) grid = (int)items;
-  pi_fused_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(maps, n, K, nb, mode_even, mode_odd, out, out_bstride, ldo, err);
-  return cudaGetLastError();
+  const long items1 = (long)nbt * (nbt + 1) / 2 * ((nb + 1) / 2);
+  int best = tc_pi_fused_ksplit(n, K, nb, max_ctas);
+  if (best == 0) {
+    std::vector<int> cand{1};
+    for (int ks : {2, 4, 8})
+      if (items1 * (ks / 2) < 2L * sm_count() && feasible(ks)) cand.push_back(ks);
+    if (cand.size() == 1) {
+      best = 1;
+    } else {
+      cudaEvent_t e0, e1;
+      if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return cudaErrorUnknown;
+      float best_ms = 1e30f;
+      for (int ks : cand) {
+        float ms = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {          // the first launch of a configuration warms it up
+          cudaEventRecord(e0, s);
+          cudaError_t e = pf_launch(maps, n, K, nb, mode_even, mode_odd, out, out_bstride, ldo, ks, part, err, s,
+                                    max_ctas);
+          cudaEventRecord(e1, s);
+          if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return e; }
+          if (cudaEventSynchronize(e1) != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return cudaErrorUnknown; }
+          cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (ms < best_ms) { best_ms = ms; best = ks; }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[std::make_tuple(n, K, nb, max_ctas)] = best;
+  }
+  if (chosen) *chosen = best;
+  return pf_launch(maps, n, K, nb, mode_even, mode_odd, out, out_bstride, ldo, best, part, err, s, max_ctas);
 }
 
 }  // namespace gw

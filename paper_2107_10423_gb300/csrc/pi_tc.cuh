@@ -53,9 +53,15 @@ cudaError_t tc_pair_weights(const double* eps, int n_occ, int n_virt, int K, con
 // B FP32 [n][ldb] (ldb a multiple of 4), its BF16 hi/lo split Bhi/Blo [n][tc_ld(K)], w from tc_pair_weights;
 // out [nb][n][ldo] FP32 at batch stride out_bstride, full symmetric (lower tiles computed and mirrored);
 // mode_even / mode_odd for even / odd b: 0 v, 1 delta - v, 2 -v.  max_ctas > 0 caps the persistent grid.
+// ksplit > 0 forces that many K ranges per (tile, pair); ksplit = 0 autotunes it per shape (n, K, nb, max_ctas):
+// every feasible split (partials [ksplit][nb][n][n] FP32 fit in part_bytes of `part`) is timed once and the
+// fastest kept for the process.  *chosen (if not NULL) receives the split used.
 cudaError_t tc_pi_fused(const float* B, long ldb, int n, int K, const float* w, int nb, const __nv_bfloat16* Bhi,
                         const __nv_bfloat16* Blo, int mode_even, int mode_odd, float* out, long out_bstride, int ldo,
-                        int* err, cudaStream_t s, int max_ctas = 0);
+                        int* err, cudaStream_t s, int max_ctas = 0, int ksplit = 1, float* part = nullptr,
+                        size_t part_bytes = 0, int* chosen = nullptr);
+// The split the autotuner chose for a shape, or 0 if it has not seen it.
+int tc_pi_fused_ksplit(int n, int K, int nb, int max_ctas);
 // A_b[m][k] = B[m][k] * w(kinds[b], D_k, params[b]) split into BF16 hi/lo, [batch][M][tc_ld(K)].
 // kinds: 0 Pi(i xi) weight -4D/(D^2+xi^2) (param xi); 1 Re c(x); 2 Im c(x) (param x, broadening eta);
 // 3 unit weight.  kinds/params are device arrays of length batch.  B is FP32 [M][K].  The weights are evaluated

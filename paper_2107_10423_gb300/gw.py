@@ -34,7 +34,7 @@ class Config(ctypes.Structure):
                 ("minres_fallback_tol", ctypes.c_double), ("qp_maxit", ctypes.c_int), ("qp_tol", ctypes.c_double),
                 ("static_subtraction", ctypes.c_int), ("max_rhs_batch", ctypes.c_int), ("workspace_mb", ctypes.c_int),
                 ("refine_tol", ctypes.c_double), ("op_parts", ctypes.c_int), ("deriv_fp64", ctypes.c_int), ("refine_df", ctypes.c_int),
-                ("tc_max_ctas", ctypes.c_int)]
+                ("tc_max_ctas", ctypes.c_int), ("pi_ksplit", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -45,7 +45,7 @@ class Stats(ctypes.Structure):
                 ("ms_kernel", ctypes.c_double * 9), ("flops_kernel", ctypes.c_double * 9),
                 ("launches_kernel", ctypes.c_longlong * 9), ("n_refine_fp64", ctypes.c_longlong),
                 ("bytes_device", ctypes.c_longlong), ("bytes_device_peak", ctypes.c_longlong),
-                ("n_graph_launches", ctypes.c_longlong)]
+                ("n_graph_launches", ctypes.c_longlong), ("pi_ksplit_last", ctypes.c_int)]
 
 
 KERNEL_CLASSES = ["pi_tcgen05", "pi_simt", "w_table_factor", "w_table_reduce", "minres_operator_gemm", "minres_recurrence",

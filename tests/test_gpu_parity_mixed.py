@@ -188,3 +188,25 @@ def test_fused_pi_tiles_and_entries(gw, n, seed, xi, ctas):
         err = np.abs(Pi[g] - ref).max()
         assert err < 2e-5 * np.abs(ref).max(), (g, x, err, np.abs(ref).max())
         assert np.array_equal(Pi[g], Pi[g].T)
+
+
+@pytest.mark.parametrize("n,ks", [(1, 2), (1, 4), (3, 2), (3, 8), (2, 0)])
+def test_fused_pi_split_k(gw, n, ks):
+    """The K split of the fused Pi kernel (forced, or ks = 0: autotuned for the shape) against the oracle, and the
+    split product against the unsplit one (partials added in a fixed order)."""
+    s = synth.workload(0) if n == 1 else synth.water_cluster(n, 9)
+    B, Bn = s.b_ia(), s.b_nm()
+    xi = np.array([0.0, 0.4, 3.0])
+    with gw.Plan(s.eps, s.n_occ, B, Bn, s.targets, precision=gw.GW_PREC_MIXED, pi_ksplit=ks) as p:
+        Pi = p.polarizability(xi)
+        Pi2 = p.polarizability(xi)
+        used = p.stats()["pi_ksplit_last"]
+    with gw.Plan(s.eps, s.n_occ, B, Bn, s.targets, precision=gw.GW_PREC_MIXED, pi_ksplit=1) as p:
+        Pi1 = p.polarizability(xi)
+    assert used == ks if ks else used in (1, 2, 4, 8)
+    np.testing.assert_array_equal(Pi, Pi2)                       # deterministic
+    for g, x in enumerate(xi):
+        ref = O.pi_imag(s.eps, s.n_occ, B, x)
+        assert np.abs(Pi[g] - ref).max() < 2e-5 * np.abs(ref).max()
+        assert np.abs(Pi[g] - Pi1[g]).max() < 2e-6 * np.abs(ref).max()
+        assert np.array_equal(Pi[g], Pi[g].T)
