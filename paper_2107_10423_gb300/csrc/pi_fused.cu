@@ -49,7 +49,8 @@ constexpr int TR_BYTES = 4 * H_BYTES;           // transformed tiles [entry][hi,
 constexpr int TX_BYTES = A_BYTES + 2 * H_BYTES + 2 * BK * 4;
 constexpr int N_BARS = 4 * 3 + 2 + 2 + 1;       // src full/empty, tr full/empty, acc full/empty, final
 constexpr int SMEM_BYTES = SRC_STAGES * SRC_BYTES + TR_STAGES * TR_BYTES + 256 + 1024;
-constexpr int THREADS = 320;                    // warps 0-3 drain + epilogue, 4-7 transform, 8 TMA, 9 MMA
+constexpr int THREADS = 448;                    // warps 0-3 drain + epilogue, 4-11 transform, 12 TMA, 13 MMA
+constexpr int TR_WARPS = 8;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t SBO64 = 8 * 64;              // 8-row groups of 64-byte rows
 constexpr uint32_t SWZ64 = 4;                   // descriptor swizzle mode: 64-byte
@@ -131,10 +132,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     s_abort = 0;
     for (int s = 0; s < SRC_STAGES; ++s) {
       mbar_init(src_full[s], 1);
-      mbar_init(src_empty[s], 5);       // four transform warps + the MMA thread's commit
+      mbar_init(src_empty[s], TR_WARPS + 1);   // the transform warps + the MMA thread's commit
     }
     for (int s = 0; s < TR_STAGES; ++s) {
-      mbar_init(tr_full[s], 4);         // one arrival per transform warp
+      mbar_init(tr_full[s], TR_WARPS);         // one arrival per transform warp
       mbar_init(tr_empty[s], 1);
     }
     for (int f = 0; f < 2; ++f) {
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 8) {
+  if (warp == 12) {
     if (lane == 0) {
       // ------------------------------------------------------------ TMA producer
       long g = 0, issued = 0;
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           mbar_wait(src_full[q % SRC_STAGES], (uint32_t)((q / SRC_STAGES) & 1), err, 12);
       }
     }
-  } else if (warp == 9) {
+  } else if (warp == 13) {
     if (lane == 0) {
       // ------------------------------------------------------------ MMA issuer
       long g = 0;
@@ -241,8 +242,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_wait(fin, 0, err, 24);
     }
   } else if (warp >= 4) {
-    // -------------------------------------------------------------- transform: one thread per row of the tile
-    const int r = threadIdx.x - 128;
+    // -------------------------------------------------------------- transform: two threads per row of the tile,
+    // each over 16 of the k-block's 32 columns
+    const int t = threadIdx.x - 128;
+    const int r = t & (BM - 1), h = t >> 7;
     long g = 0;
     bool ok = true;
     for (long it = blockIdx.x; it < items && ok; it += gridDim.x) {
@@ -258,10 +261,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (!__all_sync(0xffffffffu, w_ok)) { ok = false; break; }
         const uint8_t* sp = smem + s * SRC_BYTES;
         const float* wrow = reinterpret_cast<const float*>(sp + W_OFF);
-        float a[BK];
+        constexpr int HK = BK / 2;
+        float a[HK];
 #pragma unroll
-        for (int c = 0; c < BK / 4; ++c) {   // 128-byte swizzle: 16-byte chunk c of row r sits at c ^ (r & 7)
-          const float4 v = *reinterpret_cast<const float4*>(sp + r * 128 + ((c ^ (r & 7)) << 4));
+        for (int c = 0; c < HK / 4; ++c) {   // 128-byte swizzle: 16-byte chunk cc of row r sits at cc ^ (r & 7)
+          const int cc = h * (HK / 4) + c;
+          const float4 v = *reinterpret_cast<const float4*>(sp + r * 128 + ((cc ^ (r & 7)) << 4));
           a[4 * c] = v.x;
           a[4 * c + 1] = v.y;
           a[4 * c + 2] = v.z;
@@ -269,25 +274,26 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         uint8_t* tp = smem + SRC_STAGES * SRC_BYTES + ts * TR_BYTES;
         for (int f = 0; f < nf; ++f) {
-          float wv[BK];                        // the entry's weights for this k-block (broadcast reads)
+          float wv[HK];                        // the entry's weights for these columns (broadcast reads)
 #pragma unroll
-          for (int c = 0; c < BK / 4; ++c) {
-            const float4 t = *reinterpret_cast<const float4*>(wrow + f * BK + 4 * c);
-            wv[4 * c] = t.x;
-            wv[4 * c + 1] = t.y;
-            wv[4 * c + 2] = t.z;
-            wv[4 * c + 3] = t.w;
+          for (int c = 0; c < HK / 4; ++c) {
+            const float4 q = *reinterpret_cast<const float4*>(wrow + f * BK + h * HK + 4 * c);
+            wv[4 * c] = q.x;
+            wv[4 * c + 1] = q.y;
+            wv[4 * c + 2] = q.z;
+            wv[4 * c + 3] = q.w;
           }
 #pragma unroll
-          for (int j = 0; j < BK / 8; ++j) {  // 64-byte swizzle: 16-byte chunk j of row r sits at j ^ ((r >> 1) & 3)
+          for (int jj = 0; jj < HK / 8; ++jj) {  // 64-byte swizzle: 16-byte chunk j of row r sits at j ^ ((r >> 1) & 3)
+            const int j = h * (HK / 8) + jj;
             uint32_t hi[4], lo[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-              const int k = 8 * j + 2 * e;
+              const int k = 8 * jj + 2 * e;
               const float v0 = a[k] * wv[k], v1 = a[k + 1] * wv[k + 1];
               hi[e] = pack_bf16(v0, v1);
-              const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&hi[e]);
-              lo[e] = pack_bf16(v0 - __low2float(h), v1 - __high2float(h));
+              const __nv_bfloat162 hh = *reinterpret_cast<const __nv_bfloat162*>(&hi[e]);
+              lo[e] = pack_bf16(v0 - __low2float(hh), v1 - __high2float(hh));
             }
             const int off = r * 64 + ((j ^ ((r >> 1) & 3)) << 4);
             *reinterpret_cast<uint4*>(tp + (2 * f) * H_BYTES + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);

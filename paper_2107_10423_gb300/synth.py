@@ -171,13 +171,14 @@ def water64_mixed(seed: int = 2) -> System:
     return s
 
 
-def esca_like(seed: int = 3) -> System:
+def esca_like(seed: int = 3, n_virt: int = 552, n_aux: int = 1800) -> System:
     """ESCA-shaped core-level system: 3 F1s (-25.6 +- 0.05), 3 O1s (-19.3 +- 0.05), 6 C1s in [-11.4,-10.6],
-    36 valence in [-1.6,-0.4]; 552 virtuals in [0.03, 8]; N_aux = 1800.  Targets: the 6 C1s levels."""
+    36 valence in [-1.6,-0.4]; 552 virtuals in [0.03, 8]; N_aux = 1800.  Targets: the 6 C1s levels.
+    ``n_virt`` and ``n_aux`` give the same level structure at a smaller size."""
     occ = np.concatenate([_lin(-25.65, -25.55, 3), _lin(-19.35, -19.25, 3), _lin(-11.4, -10.6, 6),
                           _lin(-1.6, -0.4, 36)])
-    eps = np.concatenate([occ, _lin(0.03, 8.0, 552)])
-    return System("esca", eps, 48, 1800, 0.6 / np.sqrt(1800), seed, np.arange(6, 12), {})
+    eps = np.concatenate([occ, _lin(0.03, 8.0, n_virt)])
+    return System("esca", eps, 48, n_aux, 0.6 / np.sqrt(n_aux), seed, np.arange(6, 12), {})
 
 
 def workload(k: int) -> System:

@@ -1,0 +1,30 @@
+"""The core-level batch (ESCA-shaped: 6 C1s states by the step tree, all residue right-hand sides of a QP iteration
+in one batched MINRES launch sequence) at a reduced size the oracle finishes in about a minute: mixed precision
+against the oracle's step tree, per state."""
+import numpy as np
+import pytest
+
+from oracle import gw_oracle as O
+from paper_2107_10423_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+MEV = 3.6749322175655e-5
+
+
+def test_c1s_batch_steptree_vs_oracle(gwlib):
+    from paper_2107_10423_gb300 import gw
+    s = synth.esca_like(3, n_virt=40, n_aux=120)
+    B, Bn = s.b_ia(), s.b_nm()
+    ref = O.g0w0_cd(s.eps, s.n_occ, B, Bn, s.targets, eta=1e-3, qp_tol=1e-6)
+    with gw.Plan(s.eps, s.n_occ, B, Bn, s.targets, precision=gw.GW_PREC_MIXED, qp_tol=1e-6) as p:
+        e, z, st = p.qp_solve(gw.GW_QP_STEPTREE)
+        stats = p.stats()
+    err = np.abs(e - ref["e_qp"]) / MEV
+    print("C1s step tree |mixed - oracle| meV:", np.round(err, 4), " Sigma evaluations:", stats["n_sigma_evals"],
+          " MINRES graph launches:", stats["n_graph_launches"])
+    assert np.all(st != 1) and np.all(ref["status"] == 0)
+    assert np.all(err < 5.0), err
+    # one batched MINRES launch sequence (one graph) per QP iteration, shared by every state still active: fewer
+    # graph launches than per-state Sigma evaluations, at most one per iteration
+    assert 1 <= stats["n_graph_launches"] <= 50
+    assert stats["n_sigma_evals"] > 2 * stats["n_graph_launches"]
