@@ -97,7 +97,7 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 __global__ void __launch_bounds__(THREADS, 1)
     pi_fused_kernel(const __grid_constant__ PfMaps maps, int n, int K, int nb, int mode_even, int mode_odd,
                     float* __restrict__ out, long out_bstride, int ldo, int ksplit, float* __restrict__ part,
-                    int* __restrict__ err) {
+                    long out_limit, long part_limit, int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -336,8 +336,10 @@ __global__ void __launch_bounds__(THREADS, 1)
           // the mode
           const bool raw = ksplit > 1;
           const int mode = raw ? 0 : ((b & 1) ? mode_odd : mode_even);
-          float* ob = raw ? part + ((long)ks * nb + b) * n * n : out + (long)b * out_bstride;
+          const long ob0 = raw ? ((long)ks * nb + b) * n * n : (long)b * out_bstride;
+          float* ob = (raw ? part : out) + ob0;
           const int ld = raw ? n : ldo;
+          const long lim = (raw ? part_limit : out_limit) - ob0;   // elements writable from ob
 #pragma unroll 1
           for (int c = 0; c < 4; ++c) {
             uint32_t v[32], w[32];
@@ -361,7 +363,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const int col = c0 + j;
                 if (col > row || col >= n) continue;
                 const float x = __uint_as_float(v[j]);
-                ob[(long)row * ld + col] = mode == 0 ? x : (mode == 1 ? ((col == row ? 1.f : 0.f) - x) : -x);
+                const long o = (long)row * ld + col;
+                if (o >= lim) { atomicCAS(err, 0, 51); continue; }    // outside the caller's buffer: record, skip
+                ob[o] = mode == 0 ? x : (mode == 1 ? ((col == row ? 1.f : 0.f) - x) : -x);
               }
             }
 #pragma unroll
@@ -369,7 +373,9 @@ __global__ void __launch_bounds__(THREADS, 1)
               const int col = c0 + j;
               if (row < n && col < row && col < n) {
                 const float x = __uint_as_float(v[j]);
-                ob[(long)col * ld + row] = mode == 0 ? x : -x;
+                const long o = (long)col * ld + row;
+                if (o >= lim) { atomicCAS(err, 0, 52); continue; }
+                ob[o] = mode == 0 ? x : -x;
               }
             }
           }
@@ -394,16 +400,20 @@ __global__ void __launch_bounds__(THREADS, 1)
 
 // out_b[i][j] = mode(sum_s part[s][b][i][j]) in the fixed order s = 0, 1, ... (split-K reduction).
 __global__ void pf_reduce_kernel(const float* __restrict__ part, int ksplit, int nb, int n, int mode_even,
-                                 int mode_odd, float* __restrict__ out, long out_bstride, int ldo) {
+                                 int mode_odd, float* __restrict__ out, long out_bstride, int ldo, long out_limit,
+                                 long part_limit, int* __restrict__ err) {
   const long nn = (long)n * n, N = nn * nb;
   for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < N; idx += (long)gridDim.x * blockDim.x) {
     const int b = (int)(idx / nn);
     const long e = idx - (long)b * nn;
     const int i = (int)(e / n), j = (int)(e - (long)i * n);
+    if (((long)(ksplit - 1) * nb + b) * nn + e >= part_limit) { atomicCAS(err, 0, 53); continue; }
     float v = 0.f;
     for (int s = 0; s < ksplit; ++s) v += part[((long)s * nb + b) * nn + e];
     const int mode = (b & 1) ? mode_odd : mode_even;
-    out[(long)b * out_bstride + (long)i * ldo + j] = mode == 0 ? v : (mode == 1 ? ((i == j ? 1.f : 0.f) - v) : -v);
+    const long o = (long)b * out_bstride + (long)i * ldo + j;
+    if (o >= out_limit) { atomicCAS(err, 0, 54); continue; }
+    out[o] = mode == 0 ? v : (mode == 1 ? ((i == j ? 1.f : 0.f) - v) : -v);
   }
 }
 
@@ -493,12 +503,15 @@ cudaError_t pf_launch(const PfMaps& maps, int n, int K, int nb, int mode_even, i
   int grid = sm_count();
   if (max_ctas > 0 && max_ctas < grid) grid = max_ctas;
   if (items < grid) grid = (int)items;
+  // elements the kernels may write: the nb output matrices, and the ksplit x nb partials
+  const long out_limit = (long)(nb - 1) * out_bstride + (long)n * ldo;
+  const long part_limit = (long)ksplit * nb * n * n;
   pi_fused_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(maps, n, K, nb, mode_even, mode_odd, out, out_bstride, ldo,
-                                                     ksplit, part, err);
+                                                     ksplit, part, out_limit, part_limit, err);
   if (ksplit > 1) {
     const long N = (long)n * n * nb;
-    pf_reduce_kernel<<<(int)std::min<long>((N + 255) / 256, 4096), 256, 0, s>>>(part, ksplit, nb, n, mode_even,
-                                                                               mode_odd, out, out_bstride, ldo);
+    pf_reduce_kernel<<<(int)std::min<long>((N + 255) / 256, 4096), 256, 0, s>>>(
+        part, ksplit, nb, n, mode_even, mode_odd, out, out_bstride, ldo, out_limit, part_limit, err);
   }
   return cudaGetLastError();
 }
