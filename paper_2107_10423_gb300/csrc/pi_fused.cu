@@ -16,8 +16,8 @@
 //     3-stage ring.  The weight never round-trips through HBM and the source tile serves both entries, which
 //     halves the L2 bytes per tensor-core flop against one entry per pass.
 //   * One thread issues tcgen05.mma (M128 N128 K16, BF16 in, FP32 accumulate in TMEM): hi*hi + hi*lo + lo*hi.
-//   * Every CHUNK = 2 k-blocks an entry's TMEM partial is added (round to nearest) into its FP32 sum, also kept
-//     in TMEM, by the drain warpgroup, so no partial runs through more than 12 tensor-core accumulates.  The two
+//   * Every CHUNK = 4 k-blocks an entry's TMEM partial is added (round to nearest) into its FP32 sum, also kept
+//     in TMEM, by the drain warpgroup, so no partial runs through more than 24 tensor-core accumulates.  The two
 //     entries' chunks are staggered by one k-block: while one entry's partial drains, the tensor core works on the
 //     other entry.
 //   * TMEM: partials of entries 0/1 in columns [0, 256), FP32 sums in [256, 512).
@@ -62,15 +62,21 @@ struct PfMaps {
   CUtensorMap a, bh, bl, w;
 };
 
-// Chunk bookkeeping of entry f at k-block kb (nk k-blocks per item).  Entry 0: chunks {0,1}, {2,3}, ...;
-// entry 1: {0}, {1,2}, {3,4}, ...; both end at the last k-block.
-__device__ __forceinline__ bool chunk_first(int f, int kb) { return f == 0 ? (kb % 2 == 0) : (kb == 0 || kb % 2 == 1); }
-__device__ __forceinline__ bool chunk_last(int f, int kb, int nk) {
-  return kb == nk - 1 || (f == 0 ? (kb % 2 == 1) : (kb % 2 == 0));
+// Chunk bookkeeping of entry f at k-block kb (nk k-blocks per item), CHUNK k-blocks per chunk.  Entry 0's chunks
+// start at multiples of CHUNK, entry 1's half a chunk later (its first chunk is CHUNK/2 long); both end at the last
+// k-block.  The staggering means that the two entries never drain at the same k-block.
+constexpr int CHUNK = 4;
+__device__ __forceinline__ bool chunk_first(int f, int kb) {
+  return f == 0 ? (kb % CHUNK == 0) : (kb == 0 || kb % CHUNK == CHUNK / 2);
 }
+__device__ __forceinline__ bool chunk_last(int f, int kb, int nk) {
+  return kb == nk - 1 || (f == 0 ? (kb % CHUNK == CHUNK - 1) : (kb % CHUNK == CHUNK / 2 - 1));
+}
+// The first chunk of the item ends at k-block kb (no running sum to add yet).
+__device__ __forceinline__ bool chunk_first_of_item(int f, int kb) { return kb < (f == 0 ? CHUNK : CHUNK / 2); }
 // Issue order within k-block kb: the entry that does not start a chunk first (the other one may still be
 // draining its previous partial).
-__device__ __forceinline__ int entry_at(int kb, int o) { return (kb % 2 == 0 && kb > 0) ? 1 - o : o; }
+__device__ __forceinline__ int entry_at(int kb, int o) { return (kb % CHUNK == 0 && kb > 0) ? 1 - o : o; }
 
 // Work item -> (lower tile (bm, bn), entry pair, K split ks).
 __device__ __forceinline__ void decode_item(long item, int n_tiles, int ksplit, int& bm, int& bn, int& pair,
@@ -325,7 +331,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int o = 0; o < 2; ++o) {
           const int f = entry_at(kb, o);
           if (f >= nf || !chunk_last(f, kb, nki)) continue;
-          const bool first_of_item = f == 0 ? kb <= 1 : kb == 0;
+          const bool first_of_item = chunk_first_of_item(f, kb);
           const bool final = kb == nki - 1;
           bool w_ok = !*(volatile int*)&s_abort && mbar_wait(acc_full[f], (uint32_t)(gd[f] & 1), err, 41);
           if (!__all_sync(0xffffffffu, w_ok)) { ok = false; break; }
@@ -497,15 +503,17 @@ cudaError_t tc_pair_weights(const double* eps, int n_occ, int n_virt, int K, con
 namespace {
 
 cudaError_t pf_launch(const PfMaps& maps, int n, int K, int nb, int mode_even, int mode_odd, float* out,
-                      long out_bstride, int ldo, int ksplit, float* part, int* err, cudaStream_t s, int max_ctas) {
+                      long out_bstride, int ldo, int ksplit, float* part, size_t part_bytes, int* err, cudaStream_t s,
+                      int max_ctas) {
   const int nbt = (n + BM - 1) / BM;
   const long items = (long)nbt * (nbt + 1) / 2 * ((nb + 1) / 2) * ksplit;
   int grid = sm_count();
   if (max_ctas > 0 && max_ctas < grid) grid = max_ctas;
   if (items < grid) grid = (int)items;
-  // elements the kernels may write: the nb output matrices, and the ksplit x nb partials
+  // elements the kernels may write: the nb output matrices, and the capacity of the partials buffer
   const long out_limit = (long)(nb - 1) * out_bstride + (long)n * ldo;
-  const long part_limit = (long)ksplit * nb * n * n;
+  const long part_limit = part ? (long)(part_bytes / sizeof(float)) : 0;
+  if (ksplit > 1 && (long)ksplit * nb * n * n > part_limit) return cudaErrorInvalidValue;
   pi_fused_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(maps, n, K, nb, mode_even, mode_odd, out, out_bstride, ldo,
                                                      ksplit, part, out_limit, part_limit, err);
   if (ksplit > 1) {
@@ -516,15 +524,16 @@ cudaError_t pf_launch(const PfMaps& maps, int n, int K, int nb, int mode_even, i
   return cudaGetLastError();
 }
 
-// Split-K choices measured per problem shape (n, K, nb, grid cap), kept for the process.
+// Split-K choices measured per problem shape (n, K, nb, grid cap) and largest split the caller's partials buffer
+// allows (a choice made with a larger buffer is never reused with a smaller one), kept for the process.
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int>, int> g_tune;
+std::map<std::tuple<int, int, int, int, int>, int> g_tune;
 
 }  // namespace
 
-int tc_pi_fused_ksplit(int n, int K, int nb, int max_ctas) {
+int tc_pi_fused_ksplit(int n, int K, int nb, int max_ctas, int max_split) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  auto it = g_tune.find(std::make_tuple(n, K, nb, max_ctas));
+  auto it = g_tune.find(std::make_tuple(n, K, nb, max_ctas, max_split));
   return it == g_tune.end() ? 0 : it->second;
 }
 
@@ -554,18 +563,20 @@ cudaError_t tc_pi_fused(const float* B, long ldb, int n, int K, const float* w, 
   if (ksplit > 0) {                        // forced
     if (!feasible(ksplit)) return cudaErrorInvalidValue;
     if (chosen) *chosen = ksplit;
-    return pf_launch(maps, n, K, nb, mode_even, mode_odd, out, out_bstride, ldo, ksplit, part, err, s, max_ctas);
+    return pf_launch(maps, n, K, nb, mode_even, mode_odd, out, out_bstride, ldo, ksplit, part, part_bytes, err, s,
+                     max_ctas);
   }
   // Autotuning over the K split: the persistent grid only fills the GPU when (tiles x entry pairs) reaches the SM
   // count, so small problems (few 128-row tiles) split K; each feasible split is timed once per shape (the
   // result of every trial is the same product) and the fastest is kept.
   const int nbt = (n + BM - 1) / BM;
   const long items1 = (long)nbt * (nbt + 1) / 2 * ((nb + 1) / 2);
-  int best = tc_pi_fused_ksplit(n, K, nb, max_ctas);
+  std::vector<int> cand{1};
+  for (int ks : {2, 4, 8})
+    if (items1 * (ks / 2) < 2L * sm_count() && feasible(ks)) cand.push_back(ks);
+  const int max_split = cand.back();
+  int best = tc_pi_fused_ksplit(n, K, nb, max_ctas, max_split);
   if (best == 0) {
-    std::vector<int> cand{1};
-    for (int ks : {2, 4, 8})
-      if (items1 * (ks / 2) < 2L * sm_count() && feasible(ks)) cand.push_back(ks);
     if (cand.size() == 1) {
       best = 1;
     } else {
@@ -576,8 +587,8 @@ cudaError_t tc_pi_fused(const float* B, long ldb, int n, int K, const float* w, 
         float ms = 0.f;
         for (int rep = 0; rep < 2; ++rep) {          // the first launch of a configuration warms it up
           cudaEventRecord(e0, s);
-          cudaError_t e = pf_launch(maps, n, K, nb, mode_even, mode_odd, out, out_bstride, ldo, ks, part, err, s,
-                                    max_ctas);
+          cudaError_t e = pf_launch(maps, n, K, nb, mode_even, mode_odd, out, out_bstride, ldo, ks, part, part_bytes,
+                                    err, s, max_ctas);
           cudaEventRecord(e1, s);
           if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return e; }
           if (cudaEventSynchronize(e1) != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return cudaErrorUnknown; }
@@ -589,10 +600,11 @@ cudaError_t tc_pi_fused(const float* B, long ldb, int n, int K, const float* w, 
       cudaEventDestroy(e1);
     }
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[std::make_tuple(n, K, nb, max_ctas)] = best;
+    g_tune[std::make_tuple(n, K, nb, max_ctas, max_split)] = best;
   }
   if (chosen) *chosen = best;
-  return pf_launch(maps, n, K, nb, mode_even, mode_odd, out, out_bstride, ldo, best, part, err, s, max_ctas);
+  return pf_launch(maps, n, K, nb, mode_even, mode_odd, out, out_bstride, ldo, best, part, part_bytes, err, s,
+                   max_ctas);
 }
 
 }  // namespace gw

@@ -60,8 +60,8 @@ cudaError_t tc_pi_fused(const float* B, long ldb, int n, int K, const float* w, 
                         const __nv_bfloat16* Blo, int mode_even, int mode_odd, float* out, long out_bstride, int ldo,
                         int* err, cudaStream_t s, int max_ctas = 0, int ksplit = 1, float* part = nullptr,
                         size_t part_bytes = 0, int* chosen = nullptr);
-// The split the autotuner chose for a shape, or 0 if it has not seen it.
-int tc_pi_fused_ksplit(int n, int K, int nb, int max_ctas);
+// The split the autotuner chose for a shape with the given largest feasible split, or 0 if it has not seen it.
+int tc_pi_fused_ksplit(int n, int K, int nb, int max_ctas, int max_split);
 // A_b[m][k] = B[m][k] * w(kinds[b], D_k, params[b]) split into BF16 hi/lo, [batch][M][tc_ld(K)].
 // kinds: 0 Pi(i xi) weight -4D/(D^2+xi^2) (param xi); 1 Re c(x); 2 Im c(x) (param x, broadening eta);
 // 3 unit weight.  kinds/params are device arrays of length batch.  B is FP32 [M][K].  The weights are evaluated
