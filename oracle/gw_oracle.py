@@ -453,26 +453,74 @@ def _golden_point(br):
 # Driver: G0W0 QP energies of the targets (Algorithm 1 with maxeviter = 0)
 # --------------------------------------------------------------------------
 def g0w0_cd(eps, n_occ, B_ia, B_nm, targets, n_freq=128, x0=0.5, eta=1e-3, mode="steptree",
-            vxc=None, qp_tol=1e-8, qp_maxit=50, static_subtraction=True):
-    """CD-G0W0 QP energies.  Returns dict with e_qp, Z, status, sigma_x, n_residue_solves."""
+            vxc=None, qp_tol=1e-8, qp_maxit=50, static_subtraction=True, cluster_gap=0.0, window=0.5,
+            n_window=64):
+    """CD-G0W0 QP energies.  ``mode``: "linearised", "steptree" or "graphical" (window of +-``window`` Ha around
+    the starting point, ``n_window`` points).  ``cluster_gap`` > 0 turns on the cluster layer of Sec. 3.4: targets
+    within cluster_gap of each other in KS energy form a cluster; its first member is solved from its KS energy,
+    the others start from their KS energy shifted by the first member's QP correction.
+    Returns dict with e_qp, Z, status, sigma_x, n_residue_solves, n_sigma (Sigma evaluations per target)."""
     xi, wt = mgl_grid(n_freq, x0)
     cd = CDSelfEnergy(eps, n_occ, B_ia, B_nm, targets, xi, wt, eta)
-    e_qp, Zs, st, sx = [], [], [], []
-    for t, n in enumerate(targets):
-        sxn = cd.sigma_x(t)
-        shift = 0.0 if vxc is None else sxn - vxc[t]
-        fn = lambda w, t=t: cd.sigma_c(t, w, static_subtraction)
-        if mode == "linearised":
-            e, Z = qp_linearised(eps[n], shift, fn)
-            s = 0
-        else:
-            e, Z, s, _, _ = qp_steptree(eps[n], shift, fn, tol=qp_tol, maxit=qp_maxit)
-        e_qp.append(e)
-        Zs.append(Z)
-        st.append(s)
-        sx.append(sxn)
+    nt = len(targets)
+    e_qp, Zs, st, sx, nsig = [0.0] * nt, [1.0] * nt, [0] * nt, [0.0] * nt, [0] * nt
+    groups = clusters([eps[n] for n in targets], cluster_gap) if cluster_gap > 0 else [[t] for t in range(nt)]
+    for grp in groups:
+        for k, t in enumerate(grp):
+            n = targets[t]
+            sxn = cd.sigma_x(t)
+            shift = 0.0 if vxc is None else sxn - vxc[t]
+            fn = lambda w, t=t: cd.sigma_c(t, w, static_subtraction)
+            start = eps[n] if k == 0 else eps[n] + (e_qp[grp[0]] - eps[targets[grp[0]]])
+            if mode == "linearised":
+                e, Z = qp_linearised(eps[n], shift, fn)
+                s, ne = 0, 1
+            elif mode == "graphical":
+                e, Z, s, ne = qp_graphical(eps[n], shift, fn, start, window, n_window, tol=qp_tol, maxit=qp_maxit)
+            else:
+                e, Z, s, ne, _ = qp_steptree(start, eps[n] + shift - start, fn, tol=qp_tol, maxit=qp_maxit)
+            e_qp[t], Zs[t], st[t], sx[t], nsig[t] = e, Z, s, sxn, ne
     return {"e_qp": np.array(e_qp), "Z": np.array(Zs), "status": np.array(st), "sigma_x": np.array(sx),
-            "n_residue_solves": cd.n_residue_solves, "cd": cd}
+            "n_residue_solves": cd.n_residue_solves, "n_sigma": np.array(nsig), "cd": cd}
+
+
+# --------------------------------------------------------------------------
+# Graphical solution and cluster guesses (Sec. 3.4)
+# --------------------------------------------------------------------------
+def qp_graphical(e_n, shift, sigma_fn, center, half_width=0.5, n_pts=64, tol=1e-8, maxit=50):
+    """Graphical solution of e_QP = e_n + shift + Re Sigma_c(e_QP) (Sec. 3.4): f(w) = e_n + shift + Sigma_c(w) - w
+    on n_pts evenly spaced points of [center - half_width, center + half_width]; every sign change of f between
+    neighbouring points with f decreasing across it (a root of the QP equation, not a pole of Sigma, where f jumps
+    upwards) is a candidate, located by linear interpolation; the candidate closest to ``center`` is refined by the
+    step tree started there.  Returns (omega, Z, status, n_grid_evaluations) with status 0 converged, 1 step tree
+    not converged, 3 no root in the window."""
+    ws = center + half_width * np.linspace(-1.0, 1.0, n_pts)
+    fs = np.array([e_n + shift + sigma_fn(w)[0] - w for w in ws])
+    best = None
+    for k in range(n_pts - 1):
+        f0, f1 = fs[k], fs[k + 1]
+        if f0 > 0.0 >= f1 or (f0 == 0.0 and f1 < 0.0):
+            r = ws[k] + (ws[k + 1] - ws[k]) * f0 / (f0 - f1)
+            if best is None or abs(r - center) < abs(best - center):
+                best = r
+    if best is None:
+        return center, float("nan"), 3, n_pts
+    w, Z, st, n, _ = qp_steptree(best, e_n + shift - best, sigma_fn, tol=tol, maxit=maxit)
+    return w, Z, st, n_pts + n
+
+
+def clusters(eps_t, gap):
+    """Targets grouped by KS energy (Sec. 3.4, cluster layer): sorted energies split wherever two neighbours are
+    more than ``gap`` apart.  Returns lists of positions into eps_t; each cluster's representative is its first
+    member in energy order."""
+    order = sorted(range(len(eps_t)), key=lambda t: eps_t[t])
+    out = []
+    for t in order:
+        if out and eps_t[t] - eps_t[out[-1][-1]] <= gap:
+            out[-1].append(t)
+        else:
+            out.append([t])
+    return out
 
 
 # --------------------------------------------------------------------------

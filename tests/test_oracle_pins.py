@@ -442,3 +442,50 @@ def test_scissor_energies():
     np.testing.assert_allclose(out, [-10.3, -1.2, -0.8, 0.5, 1.2, 3.3], atol=1e-15)
     out = O.scissor_energies(eps, 3, [4], [1.0])
     np.testing.assert_allclose(out, [-10.0, -1.0, -0.5, 0.3, 1.0, 3.1], atol=1e-15)
+
+
+# ---------------------------------------------------------------- graphical solver and cluster guesses (Sec. 3.4)
+def test_graphical_solver_finds_the_nearest_root_of_the_pole_model():
+    """f(w) = e + Sigma_c(w) - w on the one-pair pole model is a rational function: e + A/(w - p1) + B/(w - p2) - w
+    with p1 = e_i - Omega, p2 = e_a + Omega.  Its roots are those of a cubic (numpy.roots); the graphical solver
+    must return the root with f' < 0 closest to the window centre."""
+    eps, B_ia, B_nm, D, Om, bs = _pole_model()
+    b, b_ii, b_aa = bs
+    pref = 2 * b * b * D / Om
+    for t in (0, 1):
+        ni, na = (b_ii, b) if t == 0 else (b, b_aa)
+        A, Bc = pref * ni ** 2, pref * na ** 2
+        p1, p2 = eps[0] - Om, eps[1] + Om
+        e = eps[t]
+        # (e - w)(w - p1)(w - p2) + A (w - p2) + B (w - p1) = 0
+        poly = np.polymul(np.polymul([-1.0, e], [1.0, -p1]), [1.0, -p2])
+        poly = np.polyadd(poly, np.polyadd(A * np.array([1.0, -p2]), Bc * np.array([1.0, -p1])))
+        fn = lambda w: _pole_sigma(w, t, eps, D, Om, bs)
+        f = lambda w: e + fn(w)[0] - w
+        df = lambda w: fn(w)[1] - 1.0
+        roots = [r.real for r in np.roots(poly) if abs(r.imag) < 1e-12 and df(r.real) < 0]
+        for center in (e, e - 0.7, e + 0.9):
+            inside = [r for r in roots if abs(r - center) <= 1.5]
+            w, Z, st, n = O.qp_graphical(e, 0.0, fn, center, half_width=1.5, n_pts=301, tol=1e-12)
+            if not inside:
+                assert st == 3
+                continue
+            ref = min(inside, key=lambda r: abs(r - center))
+            assert st == 0 and abs(w - ref) < 1e-10 and abs(f(w)) < 1e-12, (t, center, w, ref)
+
+
+def test_cluster_guesses_reach_the_same_roots_with_fewer_evaluations():
+    s = synth.water_cluster(2, 31, targets=[0, 1])           # the two O1s-like core levels, 0.2 Ha apart
+    B, Bn = s.b_ia(), s.b_nm()
+    plain = O.g0w0_cd(s.eps, s.n_occ, B, Bn, s.targets, eta=1e-3, qp_tol=1e-7)
+    grouped = O.g0w0_cd(s.eps, s.n_occ, B, Bn, s.targets, eta=1e-3, qp_tol=1e-7, cluster_gap=0.5)
+    assert O.clusters([s.eps[0], s.eps[1]], 0.5) == [[0, 1]]
+    assert np.all(plain["status"] == 0) and np.all(grouped["status"] == 0)
+    np.testing.assert_allclose(grouped["e_qp"], plain["e_qp"], rtol=0, atol=1e-6)
+    assert grouped["n_sigma"][1] < plain["n_sigma"][1]       # the second state started from the first's shift
+
+
+def test_clusters_split_on_gaps():
+    assert O.clusters([-20.5, -20.4, -1.0, -0.9, -0.2, 3.0], 0.15) == [[0, 1], [2, 3], [4], [5]]
+    assert O.clusters([0.3, -0.1, 0.0], 0.2) == [[1, 2], [0]]
+    assert O.clusters([0.3, -0.1, 0.0], 0.35) == [[1, 2, 0]]
