@@ -52,7 +52,12 @@ typedef enum {
 
 typedef enum {
   GW_QP_LINEARISED = 0,        /* one Newton step from eps_n (Sec. 3.4) */
-  GW_QP_STEPTREE = 1           /* iterative solver with the step-selection tree (Sec. 3.4, Fig. "steptree") */
+  GW_QP_STEPTREE = 1,          /* iterative solver with the step-selection tree (Sec. 3.4, Fig. "steptree") */
+  GW_QP_GRAPHICAL = 2          /* graphical solution (Sec. 3.4): f(w) = e_n + Sigma_x - V_xc + Re Sigma_c(w) - w on
+                                  qp_window_points evenly spaced points of [e - qp_window, e + qp_window] around the
+                                  starting point e (all points of all targets in one batched evaluation); the sign
+                                  change with f decreasing closest to e, by linear interpolation, refined by the
+                                  step tree; a state whose window holds no such change is not converged */
 } gw_qp_mode;
 
 /* Flags for gw_plan_create. */
@@ -89,6 +94,12 @@ typedef struct {
                                   pairs, 48-bit, on the FP32 pipes: 1, default) or in FP64 (0) */
   int tc_max_ctas;             /* mixed: cap on the persistent grid of the Pi kernel (CTAs, one per SM at most);
                                   0 = every SM.  A smaller grid leaves SMs to work that runs beside it */
+  double qp_window;            /* graphical mode: half width of the search window (Ha), default 0.5 */
+  int qp_window_points;        /* graphical mode: points per window (>= 2), default 64 */
+  double qp_cluster_gap;       /* cluster layer (Sec. 3.4; step tree and graphical modes): targets whose KS energies are
+                                  within this distance (Ha) of a neighbour in energy form a cluster; the member with the
+                                  lowest KS energy is solved first and the others start from their KS energy shifted
+                                  by its QP correction.  0 = off (default) */
   int pi_ksplit;               /* mixed: K ranges per (tile, frequency pair) of the Pi kernel: 0 = autotuned per
                                   problem shape (n_aux, n_occ n_virt, batch; every feasible split timed once per
                                   process, the fastest kept; only shapes whose tiles do not fill the GPU split),
@@ -98,7 +109,8 @@ typedef struct {
 typedef struct gw_plan* gw_plan_t;
 
 /* Fill *cfg with defaults: n_freq 128, x0 0.5, eta 1e-3, FP64, MINRES 25 / 5e-5 / 1e-4,
- * qp_maxit 50, qp_tol 1e-8, static_subtraction 1, refine_tol 1e-6, op_parts 2, deriv_fp64 0, refine_df 1.
+ * qp_maxit 50, qp_tol 1e-8, static_subtraction 1, refine_tol 1e-6, op_parts 2, deriv_fp64 0, refine_df 1,
+ * qp_window 0.5, qp_window_points 64, qp_cluster_gap 0, tc_max_ctas 0, pi_ksplit 0.
  * Sizes are set to 0. */
 void gw_config_default(gw_config* cfg);
 

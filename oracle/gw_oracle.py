@@ -458,7 +458,7 @@ def g0w0_cd(eps, n_occ, B_ia, B_nm, targets, n_freq=128, x0=0.5, eta=1e-3, mode=
     """CD-G0W0 QP energies.  ``mode``: "linearised", "steptree" or "graphical" (window of +-``window`` Ha around
     the starting point, ``n_window`` points).  ``cluster_gap`` > 0 turns on the cluster layer of Sec. 3.4: targets
     within cluster_gap of each other in KS energy form a cluster; its first member is solved from its KS energy,
-    the others start from their KS energy shifted by the first member's QP correction.
+    the others start from their KS energy shifted by the first member's QP correction (if it converged).
     Returns dict with e_qp, Z, status, sigma_x, n_residue_solves, n_sigma (Sigma evaluations per target)."""
     xi, wt = mgl_grid(n_freq, x0)
     cd = CDSelfEnergy(eps, n_occ, B_ia, B_nm, targets, xi, wt, eta)
@@ -471,7 +471,8 @@ def g0w0_cd(eps, n_occ, B_ia, B_nm, targets, n_freq=128, x0=0.5, eta=1e-3, mode=
             sxn = cd.sigma_x(t)
             shift = 0.0 if vxc is None else sxn - vxc[t]
             fn = lambda w, t=t: cd.sigma_c(t, w, static_subtraction)
-            start = eps[n] if k == 0 else eps[n] + (e_qp[grp[0]] - eps[targets[grp[0]]])
+            rep = grp[0]
+            start = eps[n] + (e_qp[rep] - eps[targets[rep]]) if k > 0 and st[rep] == 0 else eps[n]
             if mode == "linearised":
                 e, Z = qp_linearised(eps[n], shift, fn)
                 s, ne = 0, 1

@@ -63,9 +63,10 @@ void launch_op_gemm2(const T* U, const T* B, int n_aux, int n_ov, int nr, const 
 void launch_sigma_x(const double* B_nm, int n_t, int n_bas, int n_aux, int n_occ, double* sx, cudaStream_t s);
 
 // I term (eq. "inn") with optional static subtraction, per target t at omega[t].
+// n_t evaluation points; point t reads the W rows of target tmap[t] (t itself when tmap is NULL).
 void launch_sigma_imag(const double* W, int n_t, int n_bas, int n_g, const double* eps, const double* xi,
                        const double* wt, const double* omega, int static_sub, double* I, double* dI,
-                       const unsigned char* active, cudaStream_t s);
+                       const unsigned char* active, cudaStream_t s, const int* tmap = nullptr);
 
 struct MinresState {
   double beta, c2, s2, c1, s1, phibar, beta1, pad;

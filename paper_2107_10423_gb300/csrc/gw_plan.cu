@@ -77,7 +77,7 @@ struct gw_plan {
       ns_E0, ns_vec;
   DevBuf mr_V, mr_U, mr_S, mr_vprev, mr_v, mr_d1, mr_d2, mr_x, mr_st, mr_rt, mr_rm, mr_xf, mr_wre, mr_wim,
       mr_dwre, mr_it, mr_res, mr_cnt, mr_Vhi, mr_Vlo, mr_Uhi, mr_Ulo, mr_Vlo2, mr_Ulo2, mr_V64;
-  DevBuf sg_I, sg_dI, sg_R, sg_dR, sg_om, sg_start, sg_coef, sg_act, qp_st, qp_om0;
+  DevBuf sg_I, sg_dI, sg_R, sg_dR, sg_om, sg_start, sg_coef, sg_act, sg_tmap, qp_st, qp_om0;
   DevBuf fb_A, fb_y, fb_piv, fb_info, fb_idx, fb_y64, fb_V32, fb_S32, fb_Vp, fb_Up, fb_x, fb_V64, fb_U64, fb_S64, fb_sel,
       fb_pos, fb_rho, fb_xs, fb_Bh, fb_Bl;
   int* h_cnt = nullptr;       // pinned
@@ -94,7 +94,7 @@ struct gw_plan {
     DevBuf* all[] = {&ws_mat, &ws_info, &ws_scratch, &ws_gout, &ws_xi, &tc_part, &tc_kind, &tc_par, &tc_err, &tc_w, &ns_E, &ns_X, &ns_X2, &ns_Xa, &ns_Xb, &ns_T, &ns_lam, &ns_E0, &ns_vec, &mr_V, &mr_U, &mr_S, &mr_vprev,
                      &mr_v, &mr_d1, &mr_d2, &mr_x, &mr_st, &mr_rt, &mr_rm, &mr_xf, &mr_wre, &mr_wim,
                      &mr_dwre, &mr_it, &mr_res, &mr_cnt, &mr_Vhi, &mr_Vlo, &mr_Uhi, &mr_Ulo, &mr_Vlo2, &mr_Ulo2, &mr_V64, &sg_I, &sg_dI, &sg_R, &sg_dR, &sg_om, &sg_start,
-                     &sg_coef, &sg_act, &qp_st, &qp_om0, &fb_A, &fb_y, &fb_piv, &fb_info, &fb_idx, &fb_y64, &fb_V32, &fb_S32, &fb_Vp, &fb_Up, &fb_x, &fb_V64, &fb_U64, &fb_S64, &fb_sel, &fb_pos, &fb_rho, &fb_xs, &fb_Bh, &fb_Bl};
+                     &sg_coef, &sg_act, &sg_tmap, &qp_st, &qp_om0, &fb_A, &fb_y, &fb_piv, &fb_info, &fb_idx, &fb_y64, &fb_V32, &fb_S32, &fb_Vp, &fb_Up, &fb_x, &fb_V64, &fb_U64, &fb_S64, &fb_sel, &fb_pos, &fb_rho, &fb_xs, &fb_Bh, &fb_Bl};
     bufs.assign(all, all + sizeof(all) / sizeof(all[0]));
   }
 };
@@ -1003,15 +1003,19 @@ gw_status residues(gw_plan* P, int nr, const int* d_rt, const int* d_rm, const d
 }
 
 // Residues of eq. "rnn" at omega_t for the active targets: (t, m, x = e_m - omega_t, coef = sign * theta).
+// Evaluation points p (target tmap[p], or p without a map) at omega[p]; start[p] .. start[p + 1] are point p's
+// entries.
 void build_residue_list(gw_plan* P, const std::vector<double>& omega, const std::vector<unsigned char>& active,
                         std::vector<int>& rt, std::vector<int>& rm, std::vector<double>& xf,
-                        std::vector<double>& coef, std::vector<int>& start) {
+                        std::vector<double>& coef, std::vector<int>& start, const std::vector<int>* tmap = nullptr) {
   rt.clear(); rm.clear(); xf.clear(); coef.clear();
-  start.assign(P->n_t + 1, 0);
-  for (int t = 0; t < P->n_t; ++t) {
-    start[t] = (int)rt.size();
-    if (!active[t]) continue;
-    const double w = omega[t];
+  const int np = (int)omega.size();
+  start.assign(np + 1, 0);
+  for (int pt = 0; pt < np; ++pt) {
+    start[pt] = (int)rt.size();
+    if (!active[pt]) continue;
+    const int t = tmap ? (*tmap)[pt] : pt;
+    const double w = omega[pt];
     for (int m = 0; m < P->n_bas; ++m) {
       const double e = P->h_eps_g[m];
       double th;
@@ -1030,13 +1034,15 @@ void build_residue_list(gw_plan* P, const std::vector<double>& omega, const std:
       coef.push_back(sg * th);
     }
   }
-  start[P->n_t] = (int)rt.size();
+  start[np] = (int)rt.size();
 }
 
 // Sigma_c = R - I (and derivative) at omega for active targets, into sg_R/sg_dR/sg_I/sg_dI.
+// Sigma_c = R - I (and derivative) at evaluation points p: target tmap[p] (p itself without a map) at omega[p],
+// for the active points, into sg_R/sg_dR/sg_I/sg_dI [n points].  Every point's residues share one batched solve.
 gw_status sigma_eval(gw_plan* P, const std::vector<double>& omega, const std::vector<unsigned char>& active,
-                     int* n_fallback_out) {
-  const int n_t = P->n_t;
+                     int* n_fallback_out, const std::vector<int>* tmap = nullptr) {
+  const int n_t = (int)omega.size();
   TRY(ensure(P, P->sg_I, sizeof(double) * n_t));
   TRY(ensure(P, P->sg_dI, sizeof(double) * n_t));
   TRY(ensure(P, P->sg_R, sizeof(double) * n_t));
@@ -1050,19 +1056,25 @@ gw_status sigma_eval(gw_plan* P, const std::vector<double>& omega, const std::ve
   CK(cudaEventCreate(&a));
   CK(cudaEventCreate(&b));
   CK(cudaEventRecord(a, P->stream));
+  const int* d_tmap = nullptr;
+  if (tmap) {
+    TRY(ensure(P, P->sg_tmap, sizeof(int) * n_t));
+    CK(cudaMemcpyAsync(P->sg_tmap.p, tmap->data(), sizeof(int) * n_t, cudaMemcpyHostToDevice, P->stream));
+    d_tmap = as<int>(P->sg_tmap);
+  }
   LAUNCH(gw::launch_sigma_imag(P->d_W, n_t, P->n_bas, P->n_g, P->d_eps_g, P->d_xi, P->d_wt, as<double>(P->sg_om),
                                P->cfg.static_subtraction, as<double>(P->sg_I), as<double>(P->sg_dI),
-                               as<unsigned char>(P->sg_act), P->stream));
+                               as<unsigned char>(P->sg_act), P->stream, d_tmap));
   CK(cudaEventRecord(b, P->stream));
   std::vector<int> rt, rm, start;
   std::vector<double> xf, coef;
-  build_residue_list(P, omega, active, rt, rm, xf, coef, start);
+  build_residue_list(P, omega, active, rt, rm, xf, coef, start, tmap);
   if (P->sh_world > 1) {
     // this rank's right-hand sides: entry j of the full list with j % world == rank (the per-target sums of R
     // and dR are then added across ranks)
-    std::vector<int> rt2, rm2, start2(P->n_t + 1, 0);
+    std::vector<int> rt2, rm2, start2(n_t + 1, 0);
     std::vector<double> xf2, coef2;
-    for (int t = 0; t < P->n_t; ++t) {
+    for (int t = 0; t < n_t; ++t) {
       start2[t] = (int)rt2.size();
       for (int j = start[t]; j < start[t + 1]; ++j)
         if (j % P->sh_world == P->sh_rank) {
@@ -1072,7 +1084,7 @@ gw_status sigma_eval(gw_plan* P, const std::vector<double>& omega, const std::ve
           coef2.push_back(coef[j]);
         }
     }
-    start2[P->n_t] = (int)rt2.size();
+    start2[n_t] = (int)rt2.size();
     rt.swap(rt2); rm.swap(rm2); xf.swap(xf2); coef.swap(coef2); start.swap(start2);
   }
   const int nr = (int)rt.size();
@@ -1199,6 +1211,8 @@ void gw_config_default(gw_config* c) {
   c->refine_tol = 1e-6;
   c->op_parts = 2;
   c->refine_df = 1;
+  c->qp_window = 0.5;
+  c->qp_window_points = 64;
 }
 
 static void free_plan(gw_plan* P) {
@@ -1355,6 +1369,9 @@ gw_status gw_plan_create(const gw_config* cfg, const double* eps, const double* 
   if (!(cfg->eta >= 0.0)) return fail(nullptr, GW_ERR_ARG, "eta must be >= 0");
   if (cfg->minres_maxit < 0 || cfg->qp_maxit <= 0) return fail(nullptr, GW_ERR_ARG, "bad iteration caps");
   if (cfg->tc_max_ctas < 0) return fail(nullptr, GW_ERR_ARG, "tc_max_ctas must be >= 0");
+  if (!(cfg->qp_window > 0.0) || cfg->qp_window_points < 2 || !(cfg->qp_cluster_gap >= 0.0))
+    return fail(nullptr, GW_ERR_ARG, "bad graphical window (%g Ha, %d points) or cluster gap %g", cfg->qp_window,
+                cfg->qp_window_points, cfg->qp_cluster_gap);
   if (cfg->pi_ksplit != 0 && cfg->pi_ksplit != 1 && cfg->pi_ksplit != 2 && cfg->pi_ksplit != 4 && cfg->pi_ksplit != 8)
     return fail(nullptr, GW_ERR_ARG, "pi_ksplit must be 0 (autotune), 1, 2, 4 or 8 (got %d)", cfg->pi_ksplit);
   if (cfg->op_parts != 2 && cfg->op_parts != 3)
@@ -1481,30 +1498,23 @@ gw_status gw_residues_minres(gw_plan_t P, int n_rhs, const int* target_idx, cons
 
 namespace {
 
-// QP loop (Sec. 3.4): every active state's Sigma(omega) per evaluation (one batched residue solve for all of them),
-// then one step of the linearised update or of the step tree.  omega0 (host [n_targets]) is the starting point, or
-// NULL for the KS energies.
-gw_status qp_solve_impl(gw_plan* P, gw_qp_mode mode, const double* omega0, double* e_qp, double* z_factor,
-                        int* state_status) {
-  cudaEvent_t a, b;
-  CK(cudaEventCreate(&a));
-  CK(cudaEventCreate(&b));
-  CK(cudaEventRecord(a, P->stream));
-  TRY(ensure_screening(P));
+// QP loop (Sec. 3.4) for the targets with run[t] != 0, started at om0[t]: every running state's Sigma(omega) per
+// evaluation (one batched residue solve for all of them), then one step of the linearised update or of the step
+// tree.  Final states go to hs (states not run keep status 1 and om0); any_fb[t] is set when an evaluation of a
+// running state used the dense fallback.
+gw_status qp_loop(gw_plan* P, int lin, const std::vector<double>& om0, const std::vector<unsigned char>& run,
+                  std::vector<QPState>& hs, std::vector<int>& any_fb) {
   const int n_t = P->n_t;
   TRY(ensure(P, P->qp_st, sizeof(QPState) * n_t));
-  const double* d_om0 = P->d_en;
-  if (omega0) {
-    TRY(ensure(P, P->qp_om0, sizeof(double) * n_t));
-    CK(cudaMemcpyAsync(P->qp_om0.p, omega0, sizeof(double) * n_t, cudaMemcpyHostToDevice, P->stream));
-    d_om0 = as<double>(P->qp_om0);
+  hs.assign(n_t, QPState{});
+  for (int t = 0; t < n_t; ++t) {
+    hs[t].omega = om0[t];
+    hs[t].Z = 1.0;
+    hs[t].status = run[t] ? 0 : 1;
   }
-  LAUNCH(gw::launch_qp_init(as<QPState>(P->qp_st), d_om0, n_t, P->stream));
-  std::vector<QPState> hs(n_t);
+  CK(cudaMemcpyAsync(P->qp_st.p, hs.data(), sizeof(QPState) * n_t, cudaMemcpyHostToDevice, P->stream));
   std::vector<double> om(n_t);
   std::vector<unsigned char> act(n_t);
-  std::vector<int> any_fb(n_t, 0);
-  const int lin = (mode == GW_QP_LINEARISED) ? 1 : 0;
   const int maxit = lin ? 1 : P->cfg.qp_maxit;
   for (int it = 0; it < maxit; ++it) {
     CK(cudaMemcpyAsync(hs.data(), P->qp_st.p, sizeof(QPState) * n_t, cudaMemcpyDeviceToHost, P->stream));
@@ -1526,6 +1536,124 @@ gw_status qp_solve_impl(gw_plan* P, gw_qp_mode mode, const double* omega0, doubl
                               P->cfg.qp_maxit, n_t, lin, P->stream));
   }
   CK(cudaMemcpyAsync(hs.data(), P->qp_st.p, sizeof(QPState) * n_t, cudaMemcpyDeviceToHost, P->stream));
+  CK(cudaStreamSynchronize(P->stream));
+  for (int t = 0; t < n_t; ++t)
+    if (!run[t]) hs[t].omega = om0[t];
+  return GW_OK;
+}
+
+// Graphical search (Sec. 3.4): f(w) = e_n + shift + Sigma_c(w) - w on qp_window_points evenly spaced points of
+// [c_t - qp_window, c_t + qp_window] for every target with run[t], all points of all targets in one batched
+// evaluation.  root[t] = the sign change of f with f decreasing (a root of the QP equation, not a pole of Sigma)
+// closest to c_t, by linear interpolation; found[t] = 0 if the window holds none.
+gw_status graphical_scan(gw_plan* P, const std::vector<double>& c, const std::vector<unsigned char>& run,
+                         std::vector<double>& root, std::vector<unsigned char>& found, std::vector<int>& any_fb) {
+  const int n_t = P->n_t, np = std::max(2, P->cfg.qp_window_points);
+  const double hw = P->cfg.qp_window;
+  std::vector<int> tmap;
+  std::vector<double> om;
+  for (int t = 0; t < n_t; ++t)
+    if (run[t])
+      for (int j = 0; j < np; ++j) {
+        tmap.push_back(t);
+        om.push_back(c[t] + hw * (-1.0 + 2.0 * j / (np - 1)));
+      }
+  root = c;
+  found.assign(n_t, 0);
+  if (om.empty()) return GW_OK;
+  std::vector<unsigned char> act(om.size(), 1);
+  int nf = 0;
+  TRY(sigma_eval(P, om, act, &nf, &tmap));
+  std::vector<double> R(om.size()), I(om.size());
+  CK(cudaMemcpyAsync(R.data(), P->sg_R.p, sizeof(double) * om.size(), cudaMemcpyDeviceToHost, P->stream));
+  CK(cudaMemcpyAsync(I.data(), P->sg_I.p, sizeof(double) * om.size(), cudaMemcpyDeviceToHost, P->stream));
+  CK(cudaStreamSynchronize(P->stream));
+  for (size_t k = 0; k < om.size(); ++k) {
+    const int t = tmap[k];
+    if (nf > 0) any_fb[t] = 1;
+    if (k + 1 >= om.size() || tmap[k + 1] != t) continue;
+    const double f0 = P->h_en[t] + P->h_shift[t] + R[k] - I[k] - om[k];
+    const double f1 = P->h_en[t] + P->h_shift[t] + R[k + 1] - I[k + 1] - om[k + 1];
+    if (f0 > 0.0 >= f1 || (f0 == 0.0 && f1 < 0.0)) {
+      const double r = om[k] + (om[k + 1] - om[k]) * f0 / (f0 - f1);
+      if (!found[t] || std::fabs(r - c[t]) < std::fabs(root[t] - c[t])) root[t] = r;
+      found[t] = 1;
+    }
+  }
+  return GW_OK;
+}
+
+// QP energies of the targets with run[t] from the starting points / window centres start[t]: linearised, step
+// tree, or graphical search followed by the step tree from the root it found.
+gw_status qp_solve_set(gw_plan* P, gw_qp_mode mode, const std::vector<double>& start,
+                       const std::vector<unsigned char>& run, std::vector<QPState>& hs, std::vector<int>& any_fb,
+                       std::vector<unsigned char>& no_root) {
+  const int n_t = P->n_t;
+  no_root.assign(n_t, 0);
+  if (mode != GW_QP_GRAPHICAL) return qp_loop(P, mode == GW_QP_LINEARISED, start, run, hs, any_fb);
+  std::vector<double> root;
+  std::vector<unsigned char> found;
+  TRY(graphical_scan(P, start, run, root, found, any_fb));
+  std::vector<unsigned char> run2(n_t, 0);
+  for (int t = 0; t < n_t; ++t) {
+    run2[t] = run[t] && found[t];
+    no_root[t] = run[t] && !found[t];
+  }
+  return qp_loop(P, 0, root, run2, hs, any_fb);
+}
+
+// QP equation of every target (Sec. 3.4), with the cluster layer when qp_cluster_gap > 0 (not in the linearised
+// mode): targets whose KS energies are within qp_cluster_gap of a neighbour in energy form a cluster; the first
+// member of each cluster (lowest KS energy) is solved first, then every other member starts from its KS energy
+// shifted by that member's QP correction (the step tree's start, or the centre of the graphical window).
+// omega0 (host [n_targets]) replaces the KS energies as starting points, or NULL.
+gw_status qp_solve_impl(gw_plan* P, gw_qp_mode mode, const double* omega0, double* e_qp, double* z_factor,
+                        int* state_status) {
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  CK(cudaEventRecord(a, P->stream));
+  TRY(ensure_screening(P));
+  const int n_t = P->n_t;
+  std::vector<double> start(n_t);
+  for (int t = 0; t < n_t; ++t) start[t] = omega0 ? omega0[t] : P->h_en[t];
+  std::vector<QPState> hs;
+  std::vector<int> any_fb(n_t, 0);
+  std::vector<unsigned char> no_root;
+  const bool cluster = P->cfg.qp_cluster_gap > 0.0 && mode != GW_QP_LINEARISED;
+  if (!cluster) {
+    std::vector<unsigned char> run(n_t, 1);
+    TRY(qp_solve_set(P, mode, start, run, hs, any_fb, no_root));
+  } else {
+    std::vector<int> order(n_t);
+    for (int t = 0; t < n_t; ++t) order[t] = t;
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return P->h_en[x] < P->h_en[y]; });
+    std::vector<int> rep(n_t);
+    std::vector<unsigned char> first(n_t, 0), rest(n_t, 0);
+    for (int k = 0; k < n_t; ++k) {
+      const int t = order[k];
+      if (k == 0 || P->h_en[t] - P->h_en[order[k - 1]] > P->cfg.qp_cluster_gap) {
+        rep[t] = t;
+        first[t] = 1;
+      } else {
+        rep[t] = rep[order[k - 1]];
+        rest[t] = 1;
+      }
+    }
+    std::vector<QPState> h1;
+    std::vector<unsigned char> nr1;
+    TRY(qp_solve_set(P, mode, start, first, h1, any_fb, nr1));
+    std::vector<double> start2(start);
+    for (int t = 0; t < n_t; ++t)
+      if (rest[t] && h1[rep[t]].status == 1 && !nr1[rep[t]])
+        start2[t] = start[t] + (h1[rep[t]].omega - P->h_en[rep[t]]);
+    TRY(qp_solve_set(P, mode, start2, rest, hs, any_fb, no_root));
+    for (int t = 0; t < n_t; ++t)
+      if (first[t]) {
+        hs[t] = h1[t];
+        no_root[t] = nr1[t];
+      }
+  }
   CK(cudaEventRecord(b, P->stream));
   CK(cudaStreamSynchronize(P->stream));
   P->stats.ms_qp = now_ms(P, a, b);
@@ -1533,11 +1661,11 @@ gw_status qp_solve_impl(gw_plan* P, gw_qp_mode mode, const double* omega0, doubl
   cudaEventDestroy(b);
   bool all_ok = true;
   for (int t = 0; t < n_t; ++t) {
+    const bool conv = hs[t].status == 1 && !no_root[t];
     if (e_qp) e_qp[t] = hs[t].omega;
-    if (z_factor) z_factor[t] = hs[t].Z;
-    int s = hs[t].status == 1 ? (any_fb[t] ? 2 : 0) : 1;
-    if (hs[t].status != 1) all_ok = false;
-    if (state_status) state_status[t] = s;
+    if (z_factor) z_factor[t] = no_root[t] ? NAN : hs[t].Z;
+    if (!conv) all_ok = false;
+    if (state_status) state_status[t] = conv ? (any_fb[t] ? 2 : 0) : 1;
   }
   return all_ok ? GW_OK : GW_ERR_NOT_CONVERGED;
 }
@@ -1565,14 +1693,16 @@ extern "C" {
 
 gw_status gw_qp_solve(gw_plan_t P, gw_qp_mode mode, double* e_qp, double* z_factor, int* state_status) {
   if (!P) return GW_ERR_ARG;
-  if (mode != GW_QP_LINEARISED && mode != GW_QP_STEPTREE) return fail(P, GW_ERR_ARG, "unknown QP mode %d", (int)mode);
+  if (mode != GW_QP_LINEARISED && mode != GW_QP_STEPTREE && mode != GW_QP_GRAPHICAL)
+    return fail(P, GW_ERR_ARG, "unknown QP mode %d", (int)mode);
   return qp_solve_impl(P, mode, nullptr, e_qp, z_factor, state_status);
 }
 
 gw_status gw_evgw(gw_plan_t P, int update_w, gw_qp_mode mode, int max_iter, double tol, double* e_qp,
                   double* z_factor, int* state_status, int* iterations) {
   if (!P) return GW_ERR_ARG;
-  if (mode != GW_QP_LINEARISED && mode != GW_QP_STEPTREE) return fail(P, GW_ERR_ARG, "unknown QP mode %d", (int)mode);
+  if (mode != GW_QP_LINEARISED && mode != GW_QP_STEPTREE && mode != GW_QP_GRAPHICAL)
+    return fail(P, GW_ERR_ARG, "unknown QP mode %d", (int)mode);
   if (max_iter <= 0 || !(tol > 0.0)) return fail(P, GW_ERR_ARG, "max_iter must be positive and tol > 0");
   const int n_t = P->n_t;
   std::vector<double> prev(n_t), cur(n_t), z(n_t);

@@ -46,10 +46,12 @@ __global__ void sigma_x_kernel(const double* __restrict__ B_nm, int n_bas, int n
 __global__ void sigma_imag_kernel(const double* __restrict__ W, int n_bas, int n_g, const double* __restrict__ eps,
                                   const double* __restrict__ xi, const double* __restrict__ wt,
                                   const double* __restrict__ omega, int static_sub, double* __restrict__ I,
-                                  double* __restrict__ dI, const unsigned char* __restrict__ active) {
+                                  double* __restrict__ dI, const unsigned char* __restrict__ active,
+                                  const int* __restrict__ tmap) {
   __shared__ double buf[32];
-  const int t = blockIdx.x;
+  const int t = blockIdx.x;                 // evaluation point; its target's W rows are tw's
   if (active && !active[t]) return;
+  const int tw = tmap ? tmap[t] : t;
   const double w0 = omega[t];
   const int ld = n_g + 1;
   double si = 0.0, sd = 0.0, sj = 0.0;
@@ -57,7 +59,7 @@ __global__ void sigma_imag_kernel(const double* __restrict__ W, int n_bas, int n
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int m = wid; m < n_bas; m += nw) {
     const double a = w0 - eps[m];
-    const double* Wm = W + ((long)t * n_bas + m) * ld;
+    const double* Wm = W + ((long)tw * n_bas + m) * ld;
     const double Ws = static_sub ? Wm[n_g] : 0.0;
     double pi_acc = 0.0, pd_acc = 0.0;
     for (int g = lane; g < n_g; g += 32) {
@@ -498,8 +500,9 @@ void launch_sigma_x(const double* B_nm, int n_t, int n_bas, int n_aux, int n_occ
 
 void launch_sigma_imag(const double* W, int n_t, int n_bas, int n_g, const double* eps, const double* xi,
                        const double* wt, const double* omega, int static_sub, double* I, double* dI,
-                       const unsigned char* active, cudaStream_t s) {
-  if (n_t > 0) sigma_imag_kernel<<<n_t, RT, 0, s>>>(W, n_bas, n_g, eps, xi, wt, omega, static_sub, I, dI, active);
+                       const unsigned char* active, cudaStream_t s, const int* tmap) {
+  if (n_t > 0)
+    sigma_imag_kernel<<<n_t, RT, 0, s>>>(W, n_bas, n_g, eps, xi, wt, omega, static_sub, I, dI, active, tmap);
 }
 
 template <typename T>

@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(_HERE, "libgw.so")
 GW_OK, GW_ERR_ARG, GW_ERR_OOM, GW_ERR_CUDA, GW_ERR_NOT_CONVERGED, GW_ERR_TIMEOUT, GW_ERR_UNIMPLEMENTED, \
     GW_ERR_NUMERIC = range(8)
 GW_PREC_FP64, GW_PREC_MIXED = 0, 1
-GW_QP_LINEARISED, GW_QP_STEPTREE = 0, 1
+GW_QP_LINEARISED, GW_QP_STEPTREE, GW_QP_GRAPHICAL = 0, 1, 2
 GW_INPUT_ON_DEVICE, GW_BORROW_DEVICE_PTRS = 1, 2
 
 EXPORTED = ["gw_config_default", "gw_plan_create", "gw_polarizability", "gw_sigma_cd", "gw_residues_minres",
@@ -34,7 +34,8 @@ class Config(ctypes.Structure):
                 ("minres_fallback_tol", ctypes.c_double), ("qp_maxit", ctypes.c_int), ("qp_tol", ctypes.c_double),
                 ("static_subtraction", ctypes.c_int), ("max_rhs_batch", ctypes.c_int), ("workspace_mb", ctypes.c_int),
                 ("refine_tol", ctypes.c_double), ("op_parts", ctypes.c_int), ("deriv_fp64", ctypes.c_int), ("refine_df", ctypes.c_int),
-                ("tc_max_ctas", ctypes.c_int), ("pi_ksplit", ctypes.c_int)]
+                ("tc_max_ctas", ctypes.c_int), ("qp_window", ctypes.c_double), ("qp_window_points", ctypes.c_int),
+                ("qp_cluster_gap", ctypes.c_double), ("pi_ksplit", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

@@ -1,0 +1,45 @@
+"""QP solvers of Sec. 3.4 beyond the linearised equation and the step tree: the graphical solution over a window
+(all window points of all states in one batched Sigma evaluation) and the cluster layer (the first state of each
+KS-energy cluster solved first, the others started from its QP shift), against the oracle's versions."""
+import numpy as np
+import pytest
+
+from oracle import gw_oracle as O
+from paper_2107_10423_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+TIGHT = dict(minres_tol=1e-12, minres_maxit=600, minres_fallback_tol=1e-9)
+
+
+@pytest.fixture(scope="module")
+def gw(gwlib):
+    from paper_2107_10423_gb300 import gw as m
+    return m
+
+
+def test_graphical_fp64_vs_oracle(gw):
+    s = synth.water_cluster(2, 21, targets=[6, 8, 9, 10, 11])
+    B, Bn = s.b_ia(), s.b_nm()
+    ref = O.g0w0_cd(s.eps, s.n_occ, B, Bn, s.targets, eta=1e-3, mode="graphical", window=0.5, n_window=48)
+    with gw.Plan(s.eps, s.n_occ, B, Bn, s.targets, qp_window=0.5, qp_window_points=48, **TIGHT) as p:
+        e, z, st = p.qp_solve(gw.GW_QP_GRAPHICAL)
+    print("graphical e_qp", e, "oracle", ref["e_qp"], "status", st, ref["status"])
+    np.testing.assert_array_equal(st == 1, ref["status"] != 0)
+    ok = ref["status"] == 0
+    np.testing.assert_allclose(e[ok], ref["e_qp"][ok], rtol=0, atol=1e-5)
+
+
+def test_cluster_layer_fp64_vs_oracle(gw):
+    s = synth.water_cluster(3, 33, targets=[0, 1, 2, 13, 14])      # three O1s-like levels and two valence ones
+    B, Bn = s.b_ia(), s.b_nm()
+    ref = O.g0w0_cd(s.eps, s.n_occ, B, Bn, s.targets, eta=1e-3, qp_tol=1e-7, cluster_gap=0.5)
+    with gw.Plan(s.eps, s.n_occ, B, Bn, s.targets, qp_tol=1e-7, qp_cluster_gap=0.5, **TIGHT) as p:
+        e, z, st = p.qp_solve(gw.GW_QP_STEPTREE)
+        n_clu = p.stats()["n_sigma_evals"]
+    with gw.Plan(s.eps, s.n_occ, B, Bn, s.targets, qp_tol=1e-7, **TIGHT) as p:
+        e0, _, _ = p.qp_solve(gw.GW_QP_STEPTREE)
+        n_plain = p.stats()["n_sigma_evals"]
+    print("cluster layer: Sigma evaluations", n_clu, "without", n_plain, "e", e, "oracle", ref["e_qp"])
+    np.testing.assert_array_equal(st == 1, ref["status"] != 0)
+    np.testing.assert_allclose(e, ref["e_qp"], rtol=0, atol=1e-5)
+    assert n_clu < n_plain
