@@ -7,15 +7,16 @@
 namespace gw {
 
 // ---------------------------------------------------------------- dense kernels (kernels_dense.cu)
+// Every kernel below takes the pair energies D_k (k < n_ov, the columns of B) as an array Dk.
 // Pi_PQ(i xi_g) = -4 sum_k B[P][k] B[Q][k] D_k/(D_k^2 + xi_g^2)  (Sec. 3.3, eta = 0), for n_xi points.
 // mode 0 writes Pi, mode 1 writes eps = 1 - Pi.  out: [n_xi][n_aux][n_aux] full symmetric.
 template <typename T>
-void launch_pi_syrk(const T* B, const double* eps, int n_occ, int n_virt, int n_aux, const double* xi, int n_xi,
-                    T* out, int mode, cudaStream_t s);
+void launch_pi_syrk(const T* B, const double* Dk, long n_ov, int n_aux, const double* xi, int n_xi, T* out, int mode,
+                    cudaStream_t s);
 
 // Dense complex real-axis matrix A = 1 - Pi(x) as two real [n_aux][n_aux] halves (dense fallback).
-void launch_pi_complex_dense(const double* B, const double* eps, int n_occ, int n_virt, int n_aux, double x,
-                             double eta, double* Ar, double* Ai, cudaStream_t s);
+void launch_pi_complex_dense(const double* B, const double* Dk, long n_ov, int n_aux, double x, double eta, double* Ar,
+                             double* Ai, cudaStream_t s);
 
 // In-place lower Cholesky of `batch` SPD matrices A[b] = base + b*stride (row-major n x n).
 // info[b] = 0 on success, j+1 if pivot j was not positive.
@@ -39,15 +40,15 @@ int trsm_w_default_ctas();
 // gemm2: S[r][P] = sum_k U[r][k] B[P][k]; mode 0 writes S (= [Re; Im] of Pi z),
 //   mode 1 writes the real embedding [u - S_re; -v - S_im] of (1 - Pi) z.
 template <typename T>
-void launch_op_gemm1(const T* V, const T* B, const double* eps, int n_occ, int n_virt, int n_aux, const double* x,
-                     double eta, int nr, T* U, int mode, cudaStream_t s, double* dw = nullptr,
-                     double cut = 0.0, long ldb = 0,    // ldb: row length of B (0 = n_occ * n_virt)
+void launch_op_gemm1(const T* V, const T* B, const double* Dk, long n_ov, int n_aux, const double* x, double eta,
+                     int nr, T* U, int mode, cudaStream_t s, double* dw = nullptr,
+                     double cut = 0.0, long ldb = 0,    // ldb: row length of B (0 = n_ov)
                      const int* run_if = nullptr);      // device flag: the launch does nothing if *run_if == 0
 // Double-float (FP32 pair, 48-bit) versions of op_gemm1 mode 0 and op_gemm2 mode 1 for the refinement residual:
 // V, U, out FP64; B as its split Bh + Bl (launch_df_split of the FP64 B_ia).
 void launch_df_split(const double* x, long n, float* h, float* l, cudaStream_t s);
-void launch_op_gemm1_df(const double* V, const float* Bh, const float* Bl, const double* eps, int n_occ, int n_virt,
-                        int n_aux, const double* x, double eta, int nr, double* U, cudaStream_t s);
+void launch_op_gemm1_df(const double* V, const float* Bh, const float* Bl, const double* Dk, long n_ov, int n_aux,
+                        const double* x, double eta, int nr, double* U, cudaStream_t s);
 void launch_op_gemm2_df(const double* U, const float* Bh, const float* Bl, int n_aux, int n_ov, int nr,
                         const double* V, double* out, cudaStream_t s);
 // The pairs that mode 2 skips, in FP64: dw[j] += Re(c'_k(x_j) t_k^2) with t from the FP64 rows of V64 and the FP64

@@ -220,7 +220,7 @@ gw_status tc_weighted_syrk(gw_plan* P, const int* kinds, const double* params, i
   CK(cudaMemcpyAsync(P->tc_par.p, params, sizeof(double) * nb, cudaMemcpyHostToDevice, P->stream));
   if (reset_err) CK(cudaMemsetAsync(P->tc_err.p, 0, sizeof(int), P->stream));
   const size_t t0 = tick(P);
-  CK(gw::tc_pair_weights(P->d_eps, P->cfg.n_occ, P->cfg.n_virt, K, as<int>(P->tc_kind), as<double>(P->tc_par),
+  CK(gw::tc_pair_weights(P->d_D, K, as<int>(P->tc_kind), as<double>(P->tc_par),
                          P->cfg.eta, nb, as<float>(P->tc_w), P->stream));
   // split-K partials (only small problems, whose tiles x entry pairs do not fill the GPU, consider a split)
   const long nbt = (n + 127) / 128;
@@ -506,7 +506,7 @@ gw_status screening_T(gw_plan* P, const T* B, const T* Bn) {
       TRY(tc_weighted_syrk(P, kinds.data(), xi_all.data() + g0, nc, 1, 1, reinterpret_cast<float*>(P->ws_mat.p), 0));
     } else {
       const size_t t0 = tick(P);
-      LAUNCH(gw::launch_pi_syrk<T>(B, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, as<double>(P->ws_xi) + g0, nc,
+      LAUNCH(gw::launch_pi_syrk<T>(B, P->d_D, P->n_ov, n, as<double>(P->ws_xi) + g0, nc,
                                    as<T>(P->ws_mat), 1, P->stream));
       mark(P, 1, t0, (double)nc * n * n * P->n_ov);
     }
@@ -639,7 +639,7 @@ gw_status dense_fallback(gw_plan* P, const std::vector<int>& need, const int* rt
     } else {
       const size_t t0 = tick(P);
       for (int k = 0; k < nf; ++k)
-        LAUNCH(gw::launch_pi_complex_dense(P->d_B_ia, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, hx[k0 + k],
+        LAUNCH(gw::launch_pi_complex_dense(P->d_B_ia, P->d_D, P->n_ov, n, hx[k0 + k],
                                            P->cfg.eta, reinterpret_cast<double*>(A) + 2 * mat * k,
                                            reinterpret_cast<double*>(A) + 2 * mat * k + mat, P->stream));
       mark(P, 6, t0, 4.0 * nf * (double)mat * P->n_ov);
@@ -710,14 +710,12 @@ gw_status dense_fallback(gw_plan* P, const std::vector<int>& need, const int* rt
               TRY(ensure(P, P->fb_Bl, sizeof(float) * nb));
               LAUNCH(gw::launch_df_split(P->d_B_ia, (long)nb, as<float>(P->fb_Bh), as<float>(P->fb_Bl), P->stream));
             }
-            LAUNCH(gw::launch_op_gemm1_df(as<double>(P->fb_V64), as<float>(P->fb_Bh), as<float>(P->fb_Bl), P->d_eps,
-                                          P->cfg.n_occ, P->cfg.n_virt, n, as<double>(P->fb_xs), P->cfg.eta, m,
+            LAUNCH(gw::launch_op_gemm1_df(as<double>(P->fb_V64), as<float>(P->fb_Bh), as<float>(P->fb_Bl), P->d_D, P->n_ov, n, as<double>(P->fb_xs), P->cfg.eta, m,
                                           as<double>(P->fb_U64), P->stream));
             LAUNCH(gw::launch_op_gemm2_df(as<double>(P->fb_U64), as<float>(P->fb_Bh), as<float>(P->fb_Bl), n,
                                           P->n_ov, m, as<double>(P->fb_V64), as<double>(P->fb_S64), P->stream));
           } else {
-            LAUNCH(gw::launch_op_gemm1<double>(as<double>(P->fb_V64), P->d_B_ia, P->d_eps, P->cfg.n_occ,
-                                               P->cfg.n_virt, n, as<double>(P->fb_xs), P->cfg.eta, m,
+            LAUNCH(gw::launch_op_gemm1<double>(as<double>(P->fb_V64), P->d_B_ia, P->d_D, P->n_ov, n, as<double>(P->fb_xs), P->cfg.eta, m,
                                                as<double>(P->fb_U64), 0, P->stream));
             LAUNCH(gw::launch_op_gemm2<double>(as<double>(P->fb_U64), P->d_B_ia, n, P->n_ov, m,
                                                as<double>(P->fb_V64), as<double>(P->fb_S64), 1, P->stream));
@@ -877,7 +875,7 @@ gw_status residues_T(gw_plan* P, int nr_total, const int* d_rt, const int* d_rm,
     if (tcop) {
       TRY(tc_operator(P, nr, xf, reinterpret_cast<const float*>(P->mr_V.p), reinterpret_cast<float*>(P->mr_S.p), 0));
     } else {
-      LAUNCH(gw::launch_op_gemm1<T>(as<T>(P->mr_V), B, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, xf, eta, nr,
+      LAUNCH(gw::launch_op_gemm1<T>(as<T>(P->mr_V), B, P->d_D, P->n_ov, n, xf, eta, nr,
                                     as<T>(P->mr_U), 0, P->stream));
       LAUNCH(gw::launch_op_gemm2<T>(as<T>(P->mr_U), B, n, n_ov, nr, as<T>(P->mr_V), as<T>(P->mr_S), 0, P->stream));
     }
@@ -901,7 +899,7 @@ gw_status residues_T(gw_plan* P, int nr_total, const int* d_rt, const int* d_rm,
           cap = tc_operator(P, nr, xf, reinterpret_cast<const float*>(P->mr_V.p),
                             reinterpret_cast<float*>(P->mr_S.p), 1, cnt);
         } else {
-          gw::launch_op_gemm1<T>(as<T>(P->mr_V), B, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, xf, eta, nr,
+          gw::launch_op_gemm1<T>(as<T>(P->mr_V), B, P->d_D, P->n_ov, n, xf, eta, nr,
                                  as<T>(P->mr_U), 0, P->stream, nullptr, 0.0, 0, cnt);
           gw::launch_op_gemm2<T>(as<T>(P->mr_U), B, n, n_ov, nr, as<T>(P->mr_V), as<T>(P->mr_S), 1, P->stream,
                                  cnt);
@@ -967,15 +965,15 @@ gw_status residues_T(gw_plan* P, int nr_total, const int* d_rt, const int* d_rm,
     CK(cudaMemsetAsync(dw_re + j0, 0, sizeof(double) * nr, P->stream));
     const size_t td = tick(P);
     if (d64) {
-      LAUNCH(gw::launch_op_gemm1<double>(V64, P->d_B_ia, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, xf, eta, nr,
+      LAUNCH(gw::launch_op_gemm1<double>(V64, P->d_B_ia, P->d_D, P->n_ov, n, xf, eta, nr,
                                          nullptr, 2, P->stream, dw_re + j0));
     } else if (sizeof(T) == 4) {
-      LAUNCH(gw::launch_op_gemm1<T>(as<T>(P->mr_V), B, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, xf, eta, nr,
+      LAUNCH(gw::launch_op_gemm1<T>(as<T>(P->mr_V), B, P->d_D, P->n_ov, n, xf, eta, nr,
                                     nullptr, 2, P->stream, dw_re + j0, kResonantCut, P->ld_f));
       LAUNCH(gw::launch_deriv_resonant(V64, P->d_B_ia, n_ov, n, P->d_Dsort, P->d_Dkidx, xf, nr, eta, kResonantCut,
                                        dw_re + j0, P->stream));
     } else {
-      LAUNCH(gw::launch_op_gemm1<T>(as<T>(P->mr_V), B, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, xf, eta, nr,
+      LAUNCH(gw::launch_op_gemm1<T>(as<T>(P->mr_V), B, P->d_D, P->n_ov, n, xf, eta, nr,
                                     nullptr, 2, P->stream, dw_re + j0));
     }
     mark(P, 4, td, 2.0 * (2.0 * nr) * n * (double)n_ov);
@@ -1133,26 +1131,36 @@ gw_status sigma_eval(gw_plan* P, const std::vector<double>& omega, const std::ve
   return GW_OK;
 }
 
-// W's energies: d_eps and, in mixed precision, the pair energies D_ia, their ascending order and the smallest one.
-gw_status set_pair_energies(gw_plan* P, const double* eps) {
-  CK(cudaMemcpyAsync(P->d_eps, eps, sizeof(double) * P->n_bas, cudaMemcpyHostToDevice, P->stream));
-  if (P->d_D) {
-    const int n_occ = P->cfg.n_occ, n_virt = P->cfg.n_virt;
-    std::vector<double> D((size_t)P->n_ov);
-    for (int i = 0; i < n_occ; ++i)
-      for (int a = 0; a < n_virt; ++a) D[(size_t)i * n_virt + a] = eps[n_occ + a] - eps[i];
+// Pair-energy table D [n_ov] (the columns of B_ia) on the device; in mixed precision also its ascending order with
+// the pair index of each entry (for the resonance windows of the derivative pass) and its minimum.
+gw_status set_pair_table(gw_plan* P, const std::vector<double>& D) {
+  CK(cudaMemcpyAsync(P->d_D, D.data(), sizeof(double) * P->n_ov, cudaMemcpyHostToDevice, P->stream));
+  double dmin = D.empty() ? 0.0 : D[0];
+  for (double v : D) dmin = std::min(dmin, v);
+  P->D_min = dmin;
+  if (P->d_Dsort) {
     std::vector<int> order((size_t)P->n_ov);
     for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
     std::sort(order.begin(), order.end(), [&](int a, int b) { return D[a] < D[b]; });
     std::vector<double> Ds(order.size());
     for (size_t k = 0; k < order.size(); ++k) Ds[k] = D[order[k]];
-    P->D_min = Ds.empty() ? 0.0 : Ds[0];
-    CK(cudaMemcpyAsync(P->d_D, D.data(), sizeof(double) * P->n_ov, cudaMemcpyHostToDevice, P->stream));
     CK(cudaMemcpyAsync(P->d_Dsort, Ds.data(), sizeof(double) * P->n_ov, cudaMemcpyHostToDevice, P->stream));
     CK(cudaMemcpyAsync(P->d_Dkidx, order.data(), sizeof(int) * P->n_ov, cudaMemcpyHostToDevice, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
   }
   CK(cudaStreamSynchronize(P->stream));
   return GW_OK;
+}
+
+// W's energies: d_eps, the pair energies D_ia = e_a - e_i (ia = i n_virt + a) and, in mixed precision, their
+// ascending order and the smallest one.
+gw_status set_pair_energies(gw_plan* P, const double* eps) {
+  CK(cudaMemcpyAsync(P->d_eps, eps, sizeof(double) * P->n_bas, cudaMemcpyHostToDevice, P->stream));
+  const int n_occ = P->cfg.n_occ, n_virt = P->cfg.n_virt;
+  std::vector<double> D((size_t)P->n_ov);
+  for (int i = 0; i < n_occ; ++i)
+    for (int a = 0; a < n_virt; ++a) D[(size_t)i * n_virt + a] = eps[n_occ + a] - eps[i];
+  return set_pair_table(P, D);
 }
 
 // G's energies (host copy for the residue list, device copy for the I term).
@@ -1291,6 +1299,7 @@ static gw_status plan_create_impl(gw_plan* P, const gw_config* cfg, const double
   TRY(dmalloc(P, &P->d_shift, sizeof(double) * std::max(1, n_targets)));
   TRY(dmalloc(P, &P->d_en, sizeof(double) * std::max(1, n_targets)));
   TRY(dmalloc(P, &P->d_W, sizeof(double) * (size_t)n_targets * P->n_bas * (P->n_g + 1)));
+  TRY(dmalloc(P, &P->d_D, sizeof(double) * (size_t)P->n_ov));
   CK(cudaMemcpyAsync(P->d_eps, eps, sizeof(double) * P->n_bas, cudaMemcpyHostToDevice, P->stream));
   CK(cudaMemcpyAsync(P->d_eps_g, eps, sizeof(double) * P->n_bas, cudaMemcpyHostToDevice, P->stream));
   CK(cudaMemcpyAsync(P->d_xi, xi_all.data(), sizeof(double) * (P->n_g + 1), cudaMemcpyHostToDevice, P->stream));
@@ -1329,12 +1338,11 @@ static gw_status plan_create_impl(gw_plan* P, const gw_config* cfg, const double
     TRY(dmalloc(P, &P->d_BThi, sizeof(__nv_bfloat16) * nsplitT));
     TRY(dmalloc(P, &P->d_BTlo, sizeof(__nv_bfloat16) * nsplitT));
     CK(gw::tc_transpose_split(P->d_B_ia_f, n, P->n_ov, P->d_BThi, P->d_BTlo, P->stream, nullptr, P->ld_f));
-    TRY(dmalloc(P, &P->d_D, sizeof(double) * P->n_ov));
     TRY(dmalloc(P, &P->d_Dsort, sizeof(double) * P->n_ov));
     TRY(dmalloc(P, &P->d_Dkidx, sizeof(int) * P->n_ov));
-    TRY(set_pair_energies(P, eps));
     CK(cudaStreamSynchronize(P->stream));
   }
+  TRY(set_pair_energies(P, eps));
   LAUNCH(gw::launch_sigma_x(P->d_B_nm, n_targets, P->n_bas, n, cfg->n_occ, P->d_sx, P->stream));
   P->h_sx.resize(n_targets);
   CK(cudaMemcpyAsync(P->h_sx.data(), P->d_sx, sizeof(double) * n_targets, cudaMemcpyDeviceToHost, P->stream));
@@ -1426,7 +1434,7 @@ gw_status gw_polarizability(gw_plan_t P, const double* xi, int n_xi, double* pi_
     }
   } else {
     TRY(ensure(P, P->ws_mat, sizeof(double) * (size_t)n * n * n_xi));
-    LAUNCH(gw::launch_pi_syrk<double>(P->d_B_ia, P->d_eps, P->cfg.n_occ, P->cfg.n_virt, n, as<double>(dxi), n_xi,
+    LAUNCH(gw::launch_pi_syrk<double>(P->d_B_ia, P->d_D, P->n_ov, n, as<double>(dxi), n_xi,
                                       as<double>(P->ws_mat), 0, P->stream));
     CK(cudaEventRecord(P->ev1, P->stream));
     if (pi_out)
@@ -1782,8 +1790,9 @@ gw_status gw_plan_footprint(const gw_config* c, int n_t, unsigned flags, unsigne
   if (mixed) {
     b += 4 * (n * ldf + nBn);                                                // FP32 copies
     b += 6 * (n * ldo + rows * ldn + n_ov * ldn);                             // three BF16 parts of B, B_nm, B^T
-    b += 20 * n_ov;                                                          // D, sorted D, pair index
+    b += 12 * n_ov;                                                          // sorted D and its pair index
   }
+  b += 8 * n_ov;                                                             // pair energies D_ia
   // imaginary-axis stage: frequency matrices, info/index lists
   b += capped(n * n * ts, n * n * ts * n_g1) + 24 * n_g1;
   if (mixed) {

@@ -18,21 +18,14 @@ constexpr int TN = 64;     // tile cols
 constexpr int TK = 16;     // k step
 constexpr int NT = 256;    // threads per CTA (16 x 16, 4 x 4 outputs each)
 
-__device__ __forceinline__ double pair_energy(const double* eps, int n_occ, int n_virt, long k) {
-  int i = (int)(k / n_virt);
-  int a = (int)(k - (long)i * n_virt);
-  return eps[n_occ + a] - eps[i];
-}
-
 // ------------------------------------------------------------------ Pi(i xi) SYRK
 // grid.x: lower-triangular tile index (bi >= bj), grid.y: frequency index.
 template <typename T>
-__global__ void __launch_bounds__(NT) pi_syrk_kernel(const T* __restrict__ B, const double* __restrict__ eps,
-                                                     int n_occ, int n_virt, int n_aux,
+__global__ void __launch_bounds__(NT) pi_syrk_kernel(const T* __restrict__ B, const double* __restrict__ Dk,
+                                                     long n_ov, int n_aux,
                                                      const double* __restrict__ xi, T* __restrict__ out, int mode) {
   __shared__ T As[TK][TM + 4];
   __shared__ T Bs[TK][TN + 4];
-  const long n_ov = (long)n_occ * n_virt;
   // decode lower tile (bi, bj) from linear index t = bi*(bi+1)/2 + bj
   int t = blockIdx.x;
   int bi = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
@@ -55,7 +48,7 @@ __global__ void __launch_bounds__(NT) pi_syrk_kernel(const T* __restrict__ B, co
       long k = k0 + lk + u;
       T wa = T(0), va = T(0), vb = T(0);
       if (k < n_ov) {
-        double D = pair_energy(eps, n_occ, n_virt, k);
+        const double D = Dk[k];
         wa = (T)(-4.0 * D / (D * D + x2));
         if (p0 + lr < n_aux) va = B[(long)(p0 + lr) * n_ov + k];
         if (q0 + lr < n_aux) vb = B[(long)(q0 + lr) * n_ov + k];
@@ -96,13 +89,12 @@ __global__ void __launch_bounds__(NT) pi_syrk_kernel(const T* __restrict__ B, co
 }
 
 // Complex real-axis Pi(x) as A = 1 - Pi, two real halves (dense fallback only).
-__global__ void __launch_bounds__(NT) pi_complex_kernel(const double* __restrict__ B, const double* __restrict__ eps,
-                                                        int n_occ, int n_virt, int n_aux, double x, double eta,
+__global__ void __launch_bounds__(NT) pi_complex_kernel(const double* __restrict__ B, const double* __restrict__ Dk,
+                                                        long n_ov, int n_aux, double x, double eta,
                                                         double* __restrict__ Ar, double* __restrict__ Ai) {
   __shared__ double Asr[TK][TM + 4];
   __shared__ double Asi[TK][TM + 4];
   __shared__ double Bs[TK][TN + 4];
-  const long n_ov = (long)n_occ * n_virt;
   const int p0 = blockIdx.y * TM, q0 = blockIdx.x * TN;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   double accr[4][4], acci[4][4];
@@ -115,7 +107,7 @@ __global__ void __launch_bounds__(NT) pi_complex_kernel(const double* __restrict
       long k = k0 + lk + u;
       double cr = 0, ci = 0, va = 0, vb = 0;
       if (k < n_ov) {
-        double D = pair_energy(eps, n_occ, n_virt, k);
+        const double D = Dk[k];
         double a1 = x - D, a2 = -x - D;
         double d1 = a1 * a1 + e2, d2 = a2 * a2 + e2;
         cr = 2.0 * (a1 / d1 + a2 / d2);
@@ -360,14 +352,13 @@ __global__ void __launch_bounds__(NT) trsm_w_kernel(const T* __restrict__ Lbase,
 // gemm1: rows r in [0, 2nr), cols k in [0, n_ov): acc = sum_P V[r][P] B[P][k]  (B is N-contiguous here)
 template <typename T>
 __global__ void __launch_bounds__(NT) op_gemm1_kernel(const T* __restrict__ V, const T* __restrict__ B,
-                                                      const double* __restrict__ eps, int n_occ, int n_virt,
+                                                      const double* __restrict__ Dk, long n_ov,
                                                       int n_aux, const double* __restrict__ xs, double eta, int nr,
                                                       T* __restrict__ U, int mode, double* __restrict__ dw,
                                                       double cut, long ldb, const int* __restrict__ run_if) {
   if (run_if && *run_if == 0) return;
   __shared__ T As[TK][TM + 4];
   __shared__ T Bs[TK][TN + 4];
-  const long n_ov = (long)n_occ * n_virt;
   const int M = 2 * nr;
   const int m0 = blockIdx.y * TM;
   const long k0c = (long)blockIdx.x * TN;
@@ -423,7 +414,7 @@ __global__ void __launch_bounds__(NT) op_gemm1_kernel(const T* __restrict__ V, c
           const long k = k0c + tx + 16 * j;
           if (k >= n_ov) continue;
           const double tr = (double)acc[2 * ip][j], ti = -(double)acc[2 * ip + 1][j];
-          const double D = pair_energy(eps, n_occ, n_virt, k);
+          const double D = Dk[k];
           const double a1 = x - D, a2 = -x - D;
           if (fabs(a1) < cut || fabs(a2) < cut) continue;   // near resonance: FP64 pass (deriv_resonant)
           const double d1 = a1 * a1 + e2, d2 = a2 * a2 + e2;
@@ -451,7 +442,7 @@ __global__ void __launch_bounds__(NT) op_gemm1_kernel(const T* __restrict__ V, c
       long k = k0c + tx + 16 * j;
       if (k >= n_ov) continue;
       double tr = (double)acc[2 * ip][j], ti = -(double)acc[2 * ip + 1][j];
-      double D = pair_energy(eps, n_occ, n_virt, k);
+      const double D = Dk[k];
       double a1 = x - D, a2 = -x - D;
       double d1 = a1 * a1 + e2, d2 = a2 * a2 + e2;
       const double cr = 2.0 * (a1 / d1 + a2 / d2);
@@ -621,13 +612,12 @@ __device__ __forceinline__ void df_mac(float ah, float al, float bh, float bl, f
 // df gemm1: U[r][k] for rows r of V [2nr][n_aux] (FP64) against B = Bh + Bl [n_aux][n_ov], then the complex
 // weights c_k(x_j) of the pair (2j, 2j+1) as in op_gemm1 mode 0; U in FP64.
 __global__ void __launch_bounds__(NT) op_gemm1_df_kernel(const double* __restrict__ V, const float* __restrict__ Bh,
-                                                         const float* __restrict__ Bl, const double* __restrict__ eps,
-                                                         int n_occ, int n_virt, int n_aux,
+                                                         const float* __restrict__ Bl, const double* __restrict__ Dk,
+                                                         long n_ov, int n_aux,
                                                          const double* __restrict__ xs, double eta, int nr,
                                                          double* __restrict__ U) {
   __shared__ float Ah_s[TK][TM + 4], Al_s[TK][TM + 4];
   __shared__ float Bh_s[TK][TN + 4], Bl_s[TK][TN + 4];
-  const long n_ov = (long)n_occ * n_virt;
   const int M = 2 * nr;
   const int m0 = blockIdx.y * TM;
   const long k0c = (long)blockIdx.x * TN;
@@ -692,7 +682,7 @@ __global__ void __launch_bounds__(NT) op_gemm1_df_kernel(const double* __restric
       if (k >= n_ov) continue;
       const double tr = (double)ah_[2 * ip][j] + (double)al_[2 * ip][j];
       const double ti = -((double)ah_[2 * ip + 1][j] + (double)al_[2 * ip + 1][j]);
-      const double D = pair_energy(eps, n_occ, n_virt, k);
+      const double D = Dk[k];
       const double a1 = x - D, a2 = -x - D;
       const double d1 = a1 * a1 + e2, d2 = a2 * a2 + e2;
       const double cr = 2.0 * (a1 / d1 + a2 / d2);
@@ -779,11 +769,10 @@ void launch_df_split(const double* x, long n, float* h, float* l, cudaStream_t s
   if (n > 0) df_split_kernel<<<1216, 256, 0, s>>>(x, n, h, l);
 }
 
-void launch_op_gemm1_df(const double* V, const float* Bh, const float* Bl, const double* eps, int n_occ, int n_virt,
-                        int n_aux, const double* x, double eta, int nr, double* U, cudaStream_t s) {
-  const long n_ov = (long)n_occ * n_virt;
+void launch_op_gemm1_df(const double* V, const float* Bh, const float* Bl, const double* Dk, long n_ov, int n_aux,
+                        const double* x, double eta, int nr, double* U, cudaStream_t s) {
   const dim3 grid((unsigned)((n_ov + TN - 1) / TN), (2 * nr + TM - 1) / TM);
-  if (nr > 0) op_gemm1_df_kernel<<<grid, NT, 0, s>>>(V, Bh, Bl, eps, n_occ, n_virt, n_aux, x, eta, nr, U);
+  if (nr > 0) op_gemm1_df_kernel<<<grid, NT, 0, s>>>(V, Bh, Bl, Dk, n_ov, n_aux, x, eta, nr, U);
 }
 
 void launch_op_gemm2_df(const double* U, const float* Bh, const float* Bl, int n_aux, int n_ov, int nr,
@@ -800,18 +789,18 @@ void launch_deriv_resonant(const double* V64, const double* B, long n_ov, int n_
 
 // ------------------------------------------------------------------ launchers
 template <typename T>
-void launch_pi_syrk(const T* B, const double* eps, int n_occ, int n_virt, int n_aux, const double* xi, int n_xi,
-                    T* out, int mode, cudaStream_t s) {
+void launch_pi_syrk(const T* B, const double* Dk, long n_ov, int n_aux, const double* xi, int n_xi, T* out, int mode,
+                    cudaStream_t s) {
   int nb = (n_aux + TM - 1) / TM;
   dim3 grid(nb * (nb + 1) / 2, n_xi);
-  pi_syrk_kernel<T><<<grid, NT, 0, s>>>(B, eps, n_occ, n_virt, n_aux, xi, out, mode);
+  pi_syrk_kernel<T><<<grid, NT, 0, s>>>(B, Dk, n_ov, n_aux, xi, out, mode);
 }
 
-void launch_pi_complex_dense(const double* B, const double* eps, int n_occ, int n_virt, int n_aux, double x,
-                             double eta, double* Ar, double* Ai, cudaStream_t s) {
+void launch_pi_complex_dense(const double* B, const double* Dk, long n_ov, int n_aux, double x, double eta, double* Ar,
+                             double* Ai, cudaStream_t s) {
   int nb = (n_aux + TM - 1) / TM;
   dim3 grid(nb, nb);
-  pi_complex_kernel<<<grid, NT, 0, s>>>(B, eps, n_occ, n_virt, n_aux, x, eta, Ar, Ai);
+  pi_complex_kernel<<<grid, NT, 0, s>>>(B, Dk, n_ov, n_aux, x, eta, Ar, Ai);
 }
 
 template <typename T>
@@ -847,12 +836,10 @@ cudaError_t launch_trsm_w(const T* Lbase, long Lstride, int n, int n_g, const in
 }
 
 template <typename T>
-void launch_op_gemm1(const T* V, const T* B, const double* eps, int n_occ, int n_virt, int n_aux, const double* x,
-                     double eta, int nr, T* U, int mode, cudaStream_t s, double* dw, double cut, long ldb,
-                     const int* run_if) {
-  long n_ov = (long)n_occ * n_virt;
+void launch_op_gemm1(const T* V, const T* B, const double* Dk, long n_ov, int n_aux, const double* x, double eta,
+                     int nr, T* U, int mode, cudaStream_t s, double* dw, double cut, long ldb, const int* run_if) {
   dim3 grid((unsigned)((n_ov + TN - 1) / TN), (2 * nr + TM - 1) / TM);
-  op_gemm1_kernel<T><<<grid, NT, 0, s>>>(V, B, eps, n_occ, n_virt, n_aux, x, eta, nr, U, mode, dw, cut,
+  op_gemm1_kernel<T><<<grid, NT, 0, s>>>(V, B, Dk, n_ov, n_aux, x, eta, nr, U, mode, dw, cut,
                                          ldb > 0 ? ldb : n_ov, run_if);
 }
 
@@ -864,13 +851,13 @@ void launch_op_gemm2(const T* U, const T* B, int n_aux, int n_ov, int nr, const 
 }
 
 #define GW_INST(T)                                                                                              \
-  template void launch_pi_syrk<T>(const T*, const double*, int, int, int, const double*, int, T*, int,          \
+  template void launch_pi_syrk<T>(const T*, const double*, long, int, const double*, int, T*, int,             \
                                   cudaStream_t);                                                                \
   template void launch_cholesky<T>(T*, int, long, int, int*, cudaStream_t);                                     \
   template size_t trsm_w_scratch_elems<T>(int, int);                                                            \
   template cudaError_t launch_trsm_w<T>(const T*, long, int, int, const int*, const T*, int, double*, int, T*,   \
                                         int, cudaStream_t);                                                     \
-  template void launch_op_gemm1<T>(const T*, const T*, const double*, int, int, int, const double*, double, int, \
+  template void launch_op_gemm1<T>(const T*, const T*, const double*, long, int, const double*, double, int,    \
                                    T*, int, cudaStream_t, double*, double, long, const int*);                   \
   template void launch_op_gemm2<T>(const T*, const T*, int, int, int, const T*, T*, int, cudaStream_t,          \
                                    const int*);

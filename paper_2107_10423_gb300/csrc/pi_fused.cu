@@ -435,17 +435,11 @@ __device__ __forceinline__ double pair_weight(int kind, double D, double p, doub
   return -2.0 * eta * (1.0 / d1 + 1.0 / d2);
 }
 
-__global__ void pf_weight_kernel(const double* __restrict__ eps, int n_occ, int n_virt, int K,
-                                 const int* __restrict__ kinds, const double* __restrict__ params, double eta,
-                                 float* __restrict__ w, int ldw) {
+__global__ void pf_weight_kernel(const double* __restrict__ Dk, int K, const int* __restrict__ kinds,
+                                 const double* __restrict__ params, double eta, float* __restrict__ w, int ldw) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
   if (k >= ldw) return;
-  float v = 0.f;
-  if (k < K) {
-    const int i = k / n_virt, a = k - i * n_virt;
-    v = (float)pair_weight(kinds[b], eps[n_occ + a] - eps[i], params[b], eta);
-  }
-  w[(long)b * ldw + k] = v;
+  w[(long)b * ldw + k] = k < K ? (float)pair_weight(kinds[b], Dk[k], params[b], eta) : 0.f;
 }
 
 typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -492,11 +486,11 @@ int sm_count() {
 
 int pf_ldw(int K) { return (K + 3) / 4 * 4; }
 
-cudaError_t tc_pair_weights(const double* eps, int n_occ, int n_virt, int K, const int* kinds, const double* params,
-                            double eta, int nb, float* w, cudaStream_t s) {
+cudaError_t tc_pair_weights(const double* Dk, int K, const int* kinds, const double* params, double eta, int nb,
+                            float* w, cudaStream_t s) {
   const int ldw = pf_ldw(K);
   if (nb <= 0) return cudaSuccess;
-  pf_weight_kernel<<<dim3((ldw + 255) / 256, nb), 256, 0, s>>>(eps, n_occ, n_virt, K, kinds, params, eta, w, ldw);
+  pf_weight_kernel<<<dim3((ldw + 255) / 256, nb), 256, 0, s>>>(Dk, K, kinds, params, eta, w, ldw);
   return cudaGetLastError();
 }
 

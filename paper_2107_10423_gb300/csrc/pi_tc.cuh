@@ -46,9 +46,11 @@ int tc_ld(int K);
 // Row length (elements) of FP32 arrays read by TMA with contraction length K (multiple of 4: 16-byte rows).
 int pf_ldw(int K);
 // Weight table w [nb][pf_ldw(K)] (device, FP32, zero padded): w[b][k] = weight(kinds[b], D_k, params[b]) evaluated
-// in FP64, with the kinds of tc_scale_split below (0 Pi(i xi), 1 Re c(x), 2 Im c(x), 3 unit, 4 Pi(i xi) - Pi(0)).
-cudaError_t tc_pair_weights(const double* eps, int n_occ, int n_virt, int K, const int* kinds, const double* params,
-                            double eta, int nb, float* w, cudaStream_t s);
+// in FP64 from the pair energies Dk [K].  kinds (device [nb]): 0 Pi(i xi): -4D/(D^2 + xi^2) (param xi); 1 Re c(x),
+// 2 Im c(x), c = 2[1/(x - D + i eta) + 1/(-x - D + i eta)] (param x); 3 unit; 4 Pi(i xi) - Pi(0):
+// 4 xi^2/(D (D^2 + xi^2)).
+cudaError_t tc_pair_weights(const double* Dk, int K, const int* kinds, const double* params, double eta, int nb,
+                            float* w, cudaStream_t s);
 // out_b = f(B diag(w_b) B^T) for b < nb on the tensor cores with the weight applied in the kernel (pi_fused.cu):
 // B FP32 [n][ldb] (ldb a multiple of 4), its BF16 hi/lo split Bhi/Blo [n][tc_ld(K)], w from tc_pair_weights;
 // out [nb][n][ldo] FP32 at batch stride out_bstride, full symmetric (lower tiles computed and mirrored);
@@ -62,13 +64,6 @@ cudaError_t tc_pi_fused(const float* B, long ldb, int n, int K, const float* w, 
                         size_t part_bytes = 0, int* chosen = nullptr);
 // The split the autotuner chose for a shape with the given largest feasible split, or 0 if it has not seen it.
 int tc_pi_fused_ksplit(int n, int K, int nb, int max_ctas, int max_split);
-// A_b[m][k] = B[m][k] * w(kinds[b], D_k, params[b]) split into BF16 hi/lo, [batch][M][tc_ld(K)].
-// kinds: 0 Pi(i xi) weight -4D/(D^2+xi^2) (param xi); 1 Re c(x); 2 Im c(x) (param x, broadening eta);
-// 3 unit weight.  kinds/params are device arrays of length batch.  B is FP32 [M][K].  The weights are evaluated
-// once per (entry, k) in FP64 into wtab [batch][K] (device scratch), then applied in FP32 while splitting.
-cudaError_t tc_scale_split(const float* B, const double* eps, int n_occ, int n_virt, int M, int K, const int* kinds,
-                           const double* params, double eta, int batch, float* wtab, __nv_bfloat16* hi,
-                           __nv_bfloat16* lo, cudaStream_t s);
 // out_b = f(A_b Bm^T) for b < batch, out [batch][M][N] FP32; lower != 0 computes lower tiles and mirrors.
 // mode_even / mode_odd for even / odd b: 0 v, 1 delta - v, 2 -v.  *err (device) receives a nonzero code if a
 // bounded wait inside the kernel ran out.

@@ -375,53 +375,6 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
-// ---------------------------------------------------------------- operand preparation (HBM-bound)
-__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
-  hi = __float2bfloat16_rn(v);
-  lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-}
-
-// Weight kinds: 0 Pi(i xi): -4D/(D^2+xi^2);  1: Re c(x);  2: Im c(x);  3: 1 (plain split);
-// 4 Pi(i xi) - Pi(0): 4 xi^2/(D (D^2+xi^2))
-__device__ __forceinline__ double weight(int kind, double D, double p, double eta) {
-  if (kind == 0) return -4.0 * D / (D * D + p * p);
-  if (kind == 3) return 1.0;
-  if (kind == 4) return 4.0 * p * p / (D * (D * D + p * p));
-  const double a1 = p - D, a2 = -p - D, e2 = eta * eta;
-  const double d1 = a1 * a1 + e2, d2 = a2 * a2 + e2;
-  if (kind == 1) return 2.0 * (a1 / d1 + a2 / d2);
-  return -2.0 * eta * (1.0 / d1 + 1.0 / d2);
-}
-
-// w[b][k] = w(kind_b, D_k, param_b) in FP64, stored FP32: one evaluation per (entry, pair), not per element.
-__global__ void weight_table_kernel(const double* __restrict__ eps, int n_occ, int n_virt, int K,
-                                    const int* __restrict__ kinds, const double* __restrict__ params, double eta,
-                                    float* __restrict__ w) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
-  if (k >= K) return;
-  const int i = k / n_virt, a = k - i * n_virt;
-  w[(long)b * K + k] = (float)weight(kinds[b], eps[n_occ + a] - eps[i], params[b], eta);
-}
-
-// A_b[m][k] = B[m][k] * w[b][k], split into BF16 hi/lo; rows padded to ld (ld even).  Two columns per thread.
-// grid: (ceil(ld/512), M, batch); block 256.
-__global__ void scale_split_kernel(const float* __restrict__ B, int M, int K, int ld, const float* __restrict__ w,
-                                   __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
-  const int k = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-  const int m = blockIdx.y, b = blockIdx.z;
-  if (k >= ld) return;
-  const float* Bm = B + (long)m * K;
-  const float* wb = w + (long)b * K;
-  const float v0 = k < K ? Bm[k] * wb[k] : 0.f;
-  const float v1 = k + 1 < K ? Bm[k + 1] * wb[k + 1] : 0.f;
-  __nv_bfloat16 h0, l0, h1, l1;
-  split_bf16(v0, h0, l0);
-  split_bf16(v1, h1, l1);
-  const long o = ((long)b * M + m) * ld + k;
-  *reinterpret_cast<__nv_bfloat162*>(hi + o) = __halves2bfloat162(h0, h1);
-  *reinterpret_cast<__nv_bfloat162*>(lo + o) = __halves2bfloat162(l0, l1);
-}
-
 typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                     const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                     CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -455,16 +408,6 @@ bool make_map(CUtensorMap* map, const void* ptr, int rows, int K, int ld, int ba
 }  // namespace
 
 int tc_ld(int K) { return (K + 7) / 8 * 8; }
-
-cudaError_t tc_scale_split(const float* B, const double* eps, int n_occ, int n_virt, int M, int K, const int* kinds,
-                           const double* params, double eta, int batch, float* wtab, __nv_bfloat16* hi,
-                           __nv_bfloat16* lo, cudaStream_t s) {
-  const int ld = tc_ld(K);
-  weight_table_kernel<<<dim3((K + 255) / 256, batch), 256, 0, s>>>(eps, n_occ, n_virt, K, kinds, params, eta, wtab);
-  dim3 grid((ld / 2 + 255) / 256, M, batch);
-  scale_split_kernel<<<grid, 256, 0, s>>>(B, M, K, ld, wtab, hi, lo);
-  return cudaGetLastError();
-}
 
 cudaError_t tc_gemm_ex(const TcOperand& A, int batch, const TcOperand& B, int b_batched, int nsplit, int M, int N,
                        int K, int lower, const TcEpi& ep, int* err, cudaStream_t s) {
