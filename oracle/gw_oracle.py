@@ -486,6 +486,99 @@ def g0w0_cd(eps, n_occ, B_ia, B_nm, targets, n_freq=128, x0=0.5, eta=1e-3, mode=
 
 
 # --------------------------------------------------------------------------
+# Open shell (spin-unrestricted, Sec. 2.2/3.3: the sum over sigma in Pi and spin-resolved Sigma)
+# --------------------------------------------------------------------------
+def pi_imag_uks(channels, xi):
+    """Pi_PQ(i xi) = sum_sigma sum_{ia in sigma} B^s_P,ia [1/(i xi - D) + 1/(-i xi - D)] B^s_Q,ia
+                  = -2 sum_sigma sum_ia B B D/(D^2 + xi^2).  channels = [(eps_sigma, n_occ_sigma, B_ia_sigma), ...]."""
+    out = 0.0
+    for eps, n_occ, B in channels:
+        D = pair_energies(eps, n_occ)
+        out = out + (B * (-2.0 * D / (D * D + xi * xi))) @ B.T
+    return out
+
+
+def pi_complex_uks(channels, z, eta):
+    """Pi_PQ(z) = sum_sigma sum_ia B B [1/(z - D + i eta) + 1/(-z - D + i eta)] (one spin channel per term)."""
+    out = 0.0
+    for eps, n_occ, B in channels:
+        D = pair_energies(eps, n_occ)
+        c = 1.0 / (z - D + 1j * eta) + 1.0 / (-z - D + 1j * eta)
+        out = out + (B * c) @ B.T
+    return out
+
+
+def dpi_complex_uks(channels, z, eta):
+    out = 0.0
+    for eps, n_occ, B in channels:
+        D = pair_energies(eps, n_occ)
+        c = -1.0 / (z - D + 1j * eta) ** 2 + 1.0 / (-z - D + 1j * eta) ** 2
+        out = out + (B * c) @ B.T
+    return out
+
+
+class CDSelfEnergyUKS:
+    """Sigma^c_nn,sigma(omega) by contour deformation for an open-shell system: W from the spin-summed Pi, G of the
+    target's own spin (its energies and occupations), b_nm the target's rows.  ``targets`` = [(spin, n), ...],
+    ``B_nm`` [n_t][n_bas][n_aux] rows of each target's spin."""
+
+    def __init__(self, channels, B_nm, targets, xi, wt, eta=1e-3):
+        self.ch = [(np.asarray(e, dtype=np.float64), int(o), B) for e, o, B in channels]
+        self.B_nm = B_nm
+        self.targets = list(targets)
+        self.xi = np.asarray(xi, dtype=np.float64)
+        self.wt = np.asarray(wt, dtype=np.float64)
+        self.eta = float(eta)
+        n_t, n_bas, _ = B_nm.shape
+        self.W = np.empty((n_t, n_bas, len(self.xi)))
+        self.W0 = np.empty((n_t, n_bas))
+        for g, x in enumerate(self.xi):
+            Pi = pi_imag_uks(self.ch, x)
+            for t in range(n_t):
+                self.W[t, :, g] = w_corr(Pi, B_nm[t].T)
+        Pi0 = pi_imag_uks(self.ch, 0.0)
+        for t in range(n_t):
+            self.W0[t] = w_corr(Pi0, B_nm[t].T)
+
+    def sigma_x(self, t):
+        sp, _ = self.targets[t]
+        return sigma_x(self.B_nm[t], self.ch[sp][1])
+
+    def sigma_c(self, t, omega, static_subtraction=True):
+        sp, _ = self.targets[t]
+        eps, n_occ, _ = self.ch[sp]
+        a = omega - eps
+        xi2 = self.xi[None, :] ** 2
+        a2 = a[:, None] ** 2
+        Wg = self.W[t] - self.W0[t][:, None] if static_subtraction else self.W[t]
+        I = np.sum(self.wt[None, :] * Wg * a[:, None] / (a2 + xi2)) / math.pi
+        dI = np.sum(self.wt[None, :] * Wg * (xi2 - a2) / (a2 + xi2) ** 2) / math.pi
+        if static_subtraction:
+            I += np.sum(self.W0[t] * np.sign(a)) / 2.0
+        R = dR = 0.0
+        for m, sgn, th in residue_set(eps, n_occ, omega):
+            x = eps[m] - omega
+            w, dw = w_corr_and_deriv(pi_complex_uks(self.ch, x, self.eta), dpi_complex_uks(self.ch, x, self.eta),
+                                     self.B_nm[t, m])
+            R += sgn * th * w.real
+            dR -= sgn * th * dw.real
+        return R - I, dR - dI
+
+
+def casida_uks(channels):
+    """Casida form with two spin blocks: M = D^1/2 (D + 2K) D^1/2 over the pairs of both spins, K = B^T B with the
+    spin blocks' B side by side (each spin channel carries its own factor 1 where the closed shell has 2).
+    Returns Omega and V = sqrt(2) B D^1/2 T (W^c as in ``casida``)."""
+    D = np.concatenate([pair_energies(e, o) for e, o, _ in channels])
+    B = np.concatenate([b for _, _, b in channels], axis=1)
+    K = B.T @ B
+    sD = np.sqrt(D)
+    M = sD[:, None] * (np.diag(D) + 2.0 * K) * sD[None, :]
+    Om2, T = np.linalg.eigh(M)
+    return np.sqrt(Om2), (math.sqrt(2.0) * B * sD[None, :]) @ T
+
+
+# --------------------------------------------------------------------------
 # Graphical solution and cluster guesses (Sec. 3.4)
 # --------------------------------------------------------------------------
 def qp_graphical(e_n, shift, sigma_fn, center, half_width=0.5, n_pts=64, tol=1e-8, maxit=50):

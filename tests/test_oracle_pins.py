@@ -489,3 +489,48 @@ def test_clusters_split_on_gaps():
     assert O.clusters([-20.5, -20.4, -1.0, -0.9, -0.2, 3.0], 0.15) == [[0, 1], [2, 3], [4], [5]]
     assert O.clusters([0.3, -0.1, 0.0], 0.2) == [[1, 2], [0]]
     assert O.clusters([0.3, -0.1, 0.0], 0.35) == [[1, 2, 0]]
+
+
+# ---------------------------------------------------------------- open shell
+def _uks_system(seed, n_bas=7, n_occ=(3, 2), n_aux=5):
+    rng = np.random.default_rng(seed)
+    chans = []
+    for o in n_occ:
+        eps = np.sort(np.concatenate([rng.uniform(-1.6, -0.3, o), rng.uniform(0.1, 2.2, n_bas - o)]))
+        chans.append((eps, o, rng.normal(0, 0.3, (n_aux, o * (n_bas - o)))))
+    return chans, rng
+
+
+def test_uks_with_equal_spins_is_the_closed_shell():
+    s = synth.workload(0)
+    B, Bn = s.b_ia(), s.b_nm()
+    xi, wt = O.mgl_grid(64, 0.5)
+    cs = O.CDSelfEnergy(s.eps, s.n_occ, B, Bn, s.targets, xi, wt, eta=1e-3)
+    chans = [(s.eps, s.n_occ, B), (s.eps, s.n_occ, B)]
+    us = O.CDSelfEnergyUKS(chans, Bn, [(0, n) for n in s.targets], xi, wt, eta=1e-3)
+    for x in (0.0, 0.7):
+        np.testing.assert_allclose(O.pi_imag_uks(chans, x), O.pi_imag(s.eps, s.n_occ, B, x), atol=1e-14)
+    for t, n in enumerate(s.targets):
+        for w in (s.eps[n], s.eps[n] - 0.3):
+            a, b = us.sigma_c(t, w), cs.sigma_c(t, w)
+            assert abs(a[0] - b[0]) < 1e-12 and abs(a[1] - b[1]) < 1e-11
+        assert us.sigma_x(t) == cs.sigma_x(t)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_uks_cd_matches_spectral_route(seed):
+    """Open shell, different occupations per spin: CD (spin-summed Pi, spin-resolved G) against the spectral
+    decomposition with two spin blocks, at eta = 0 and omega = e_n (as the closed-shell SD/CD pin)."""
+    chans, rng = _uks_system(seed)
+    n_bas, n_aux = len(chans[0][0]), chans[0][2].shape[0]
+    targets = [(0, 2), (0, 3), (1, 1), (1, 2)]
+    Bn = rng.normal(0, 0.3, (len(targets), n_bas, n_aux))
+    xi, wt = O.mgl_grid(256, 0.5)
+    cd = O.CDSelfEnergyUKS(chans, Bn, targets, xi, wt, eta=0.0)
+    Omega, V = O.casida_uks(chans)
+    for t, (sp, n) in enumerate(targets):
+        eps, n_occ, _ = chans[sp]
+        s_sd, ds_sd = O.sigma_c_sd(eps, n_occ, Bn[t], Omega, V, eps[n], 0.0)
+        s_cd, ds_cd = cd.sigma_c(t, eps[n])
+        assert abs(s_cd - s_sd) < 1e-8, (t, s_cd, s_sd)
+        assert abs(ds_cd - ds_sd) < 1e-6 * max(1.0, abs(ds_sd)), (t, ds_cd, ds_sd)
