@@ -127,6 +127,24 @@ gw_status gw_plan_create(const gw_config* cfg, const double* eps, const double* 
                          const int* targets, int n_targets, const double* vxc, const double* xi,
                          const double* wt, unsigned flags, void* stream, gw_plan_t* out);
 
+/* Create a plan for an open-shell (spin-unrestricted) system.  Both spins share the orbital basis
+ * (n_bas = cfg->n_occ + cfg->n_virt) and the auxiliary basis; cfg->n_occ is the alpha occupation, n_occ_b the
+ * beta one (cfg->n_virt = n_bas - n_occ_alpha).
+ *   eps_a, eps_b  [n_bas] host, ascending per spin.
+ *   B_ia_a        [n_aux][n_occ_a * (n_bas - n_occ_a)], B_ia_b [n_aux][n_occ_b * (n_bas - n_occ_b)]: the
+ *                 occupied-virtual blocks of each spin (pair index i * n_virt + a within the spin).
+ *   B_nm          [n_targets][n_bas][n_aux]: each target's rows b_nm in its own spin.
+ *   targets, spins [n_targets] host: state index and spin (0 alpha, 1 beta) of every target.
+ *   vxc, xi, wt, flags, stream, out as in gw_plan_create (GW_BORROW_DEVICE_PTRS is not accepted: the plan keeps its
+ *   own copy of the two B_ia blocks side by side).
+ * The polarizability sums the spin channels, Pi = sum_sigma sum_{ia in sigma} B B [1/(z - D + i eta) +
+ * 1/(-z - D + i eta)] (Sec. 3.3; the closed shell is the case of two equal channels); Sigma_c, Sigma_x and the QP
+ * equation of a target use the energies and occupations of its spin.  Every other call is as for gw_plan_create. */
+gw_status gw_plan_create_uks(const gw_config* cfg, const double* eps_a, const double* eps_b, int n_occ_b,
+                             const double* B_ia_a, const double* B_ia_b, const double* B_nm, const int* targets,
+                             const int* spins, int n_targets, const double* vxc, const double* xi, const double* wt,
+                             unsigned flags, void* stream, gw_plan_t* out);
+
 /* Polarizability on the imaginary axis (Sec. 3.3, equation after "wauxbas", eta = 0):
  *   Pi_PQ(i xi) = -4 sum_ia B_P,ia B_Q,ia D_ia / (D_ia^2 + xi^2),  D_ia = e_a - e_i.
  * With xi != NULL: builds Pi for the n_xi given frequencies and, if pi_out != NULL, writes

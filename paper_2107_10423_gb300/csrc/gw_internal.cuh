@@ -61,13 +61,17 @@ void launch_op_gemm2(const T* U, const T* B, int n_aux, int n_ov, int nr, const 
                      cudaStream_t s, const int* run_if = nullptr);
 
 // ---------------------------------------------------------------- CD kernels (kernels_cd.cu)
-void launch_sigma_x(const double* B_nm, int n_t, int n_bas, int n_aux, int n_occ, double* sx, cudaStream_t s);
+// Sigma_x of each target; occ_t (device [n_t], or NULL for n_occ everywhere): occupied states of its spin.
+void launch_sigma_x(const double* B_nm, int n_t, int n_bas, int n_aux, int n_occ, double* sx, cudaStream_t s,
+                    const int* occ_t = nullptr);
 
 // I term (eq. "inn") with optional static subtraction, per target t at omega[t].
-// n_t evaluation points; point t reads the W rows of target tmap[t] (t itself when tmap is NULL).
+// n_t evaluation points; point t reads the W rows of target tmap[t] (t itself when tmap is NULL) and the G energies
+// eps + spin[target] * n_bas (eps [n_spin][n_bas]; spin NULL: one set).
 void launch_sigma_imag(const double* W, int n_t, int n_bas, int n_g, const double* eps, const double* xi,
                        const double* wt, const double* omega, int static_sub, double* I, double* dI,
-                       const unsigned char* active, cudaStream_t s, const int* tmap = nullptr);
+                       const unsigned char* active, cudaStream_t s, const int* tmap = nullptr,
+                       const int* spin = nullptr);
 
 struct MinresState {
   double beta, c2, s2, c1, s1, phibar, beta1, pad;

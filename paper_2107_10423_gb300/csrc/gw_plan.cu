@@ -33,8 +33,15 @@ struct gw_plan {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::vector<double> h_eps, h_xi, h_wt, h_shift, h_sx, h_en;
-  std::vector<double> h_eps_g;   // poles of G (the KS energies, or the updated ones inside gw_evgw)
-  double* d_eps_g = nullptr;
+  // open shell: n_spin = 2, per-spin KS energies and occupations, each target's spin; closed shell: n_spin = 1
+  int n_spin = 1;
+  int occ_s[2] = {0, 0};
+  std::vector<double> h_eps_s[2];
+  std::vector<int> h_spin;
+  int* d_spin = nullptr;        // [n_targets] (open shell only)
+  int* d_occ_t = nullptr;       // [n_targets] occupied states of each target's spin (open shell only)
+  std::vector<double> h_eps_g[2];   // poles of G per spin (the KS energies, or the updated ones inside gw_evgw)
+  double* d_eps_g = nullptr;        // [n_spin][n_bas]
   std::vector<int> h_targets;
   double* d_eps = nullptr;     // energies of W: the pair energies D_ia of Pi
   double* d_B_ia = nullptr;
@@ -1013,12 +1020,13 @@ void build_residue_list(gw_plan* P, const std::vector<double>& omega, const std:
     start[pt] = (int)rt.size();
     if (!active[pt]) continue;
     const int t = tmap ? (*tmap)[pt] : pt;
+    const int sp = P->h_spin[t];
     const double w = omega[pt];
     for (int m = 0; m < P->n_bas; ++m) {
-      const double e = P->h_eps_g[m];
+      const double e = P->h_eps_g[sp][m];
       double th;
       double sg;
-      if (m < P->cfg.n_occ) {
+      if (m < P->occ_s[sp]) {
         th = (e > w) ? 1.0 : (e == w ? 0.5 : 0.0);
         sg = -1.0;
       } else {
@@ -1035,7 +1043,6 @@ void build_residue_list(gw_plan* P, const std::vector<double>& omega, const std:
   start[np] = (int)rt.size();
 }
 
-// Sigma_c = R - I (and derivative) at omega for active targets, into sg_R/sg_dR/sg_I/sg_dI.
 // Sigma_c = R - I (and derivative) at evaluation points p: target tmap[p] (p itself without a map) at omega[p],
 // for the active points, into sg_R/sg_dR/sg_I/sg_dI [n points].  Every point's residues share one batched solve.
 gw_status sigma_eval(gw_plan* P, const std::vector<double>& omega, const std::vector<unsigned char>& active,
@@ -1062,7 +1069,7 @@ gw_status sigma_eval(gw_plan* P, const std::vector<double>& omega, const std::ve
   }
   LAUNCH(gw::launch_sigma_imag(P->d_W, n_t, P->n_bas, P->n_g, P->d_eps_g, P->d_xi, P->d_wt, as<double>(P->sg_om),
                                P->cfg.static_subtraction, as<double>(P->sg_I), as<double>(P->sg_dI),
-                               as<unsigned char>(P->sg_act), P->stream, d_tmap));
+                               as<unsigned char>(P->sg_act), P->stream, d_tmap, P->d_spin));
   CK(cudaEventRecord(b, P->stream));
   std::vector<int> rt, rm, start;
   std::vector<double> xf, coef;
@@ -1154,19 +1161,24 @@ gw_status set_pair_table(gw_plan* P, const std::vector<double>& D) {
 
 // W's energies: d_eps, the pair energies D_ia = e_a - e_i (ia = i n_virt + a) and, in mixed precision, their
 // ascending order and the smallest one.
-gw_status set_pair_energies(gw_plan* P, const double* eps) {
+gw_status set_pair_energies(gw_plan* P, const double* eps, const double* eps_b = nullptr) {
   CK(cudaMemcpyAsync(P->d_eps, eps, sizeof(double) * P->n_bas, cudaMemcpyHostToDevice, P->stream));
-  const int n_occ = P->cfg.n_occ, n_virt = P->cfg.n_virt;
-  std::vector<double> D((size_t)P->n_ov);
-  for (int i = 0; i < n_occ; ++i)
-    for (int a = 0; a < n_virt; ++a) D[(size_t)i * n_virt + a] = eps[n_occ + a] - eps[i];
+  std::vector<double> D;
+  D.reserve((size_t)P->n_ov);
+  for (int sp = 0; sp < P->n_spin; ++sp) {      // spin blocks side by side: the columns of the (open-shell) B_ia
+    const double* e = sp == 0 ? eps : eps_b;
+    const int n_occ = P->occ_s[sp], n_virt = P->n_bas - n_occ;
+    for (int i = 0; i < n_occ; ++i)
+      for (int a = 0; a < n_virt; ++a) D.push_back(e[n_occ + a] - e[i]);
+  }
   return set_pair_table(P, D);
 }
 
 // G's energies (host copy for the residue list, device copy for the I term).
-gw_status set_g_energies(gw_plan* P, const double* eps) {
-  P->h_eps_g.assign(eps, eps + P->n_bas);
-  CK(cudaMemcpyAsync(P->d_eps_g, eps, sizeof(double) * P->n_bas, cudaMemcpyHostToDevice, P->stream));
+gw_status set_g_energies(gw_plan* P, int spin, const double* eps) {
+  P->h_eps_g[spin].assign(eps, eps + P->n_bas);
+  CK(cudaMemcpyAsync(P->d_eps_g + (size_t)spin * P->n_bas, eps, sizeof(double) * P->n_bas, cudaMemcpyHostToDevice,
+                     P->stream));
   CK(cudaStreamSynchronize(P->stream));
   return GW_OK;
 }
@@ -1174,6 +1186,10 @@ gw_status set_g_energies(gw_plan* P, const double* eps) {
 __global__ void convert_f64_f32_kernel(const double* __restrict__ a, float* __restrict__ b, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     b[i] = (float)a[i];
+}
+
+__global__ void scale_kernel(double* __restrict__ a, size_t n, double f) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) a[i] *= f;
 }
 
 // rows x cols FP64 (contiguous) to FP32 rows of ldb elements, zero padded.
@@ -1229,6 +1245,8 @@ static void free_plan(gw_plan* P) {
   for (DevBuf* b : P->bufs)
     if (b->p) cudaFree(b->p);
   double* owned[] = {P->d_eps, P->d_eps_g, P->d_xi, P->d_wt, P->d_sx, P->d_shift, P->d_en, P->d_W};
+  if (P->d_spin) cudaFree(P->d_spin);
+  if (P->d_occ_t) cudaFree(P->d_occ_t);
   for (double* p : owned)
     if (p) cudaFree(p);
   if (P->own_B) {
@@ -1258,13 +1276,28 @@ static void free_plan(gw_plan* P) {
   delete P;
 }
 
+// Open-shell inputs of gw_plan_create_uks: the beta channel (its energies, occupations and B_ia block) and the
+// spin of every target; the alpha channel comes through the closed-shell arguments.
+struct UksInput {
+  const double* eps_b;
+  int n_occ_b;
+  const double* B_ia_b;
+  const int* spins;
+};
+
 static gw_status plan_create_impl(gw_plan* P, const gw_config* cfg, const double* eps, const double* B_ia,
                                   const double* B_nm, const int* targets, int n_targets, const double* vxc,
-                                  const double* xi, const double* wt, unsigned flags, void* stream) {
+                                  const double* xi, const double* wt, unsigned flags, void* stream,
+                                  const UksInput* uks = nullptr) {
   P->cfg = *cfg;
   P->flags = flags;
   P->n_bas = cfg->n_occ + cfg->n_virt;
-  P->n_ov = cfg->n_occ * cfg->n_virt;
+  P->n_spin = uks ? 2 : 1;
+  P->occ_s[0] = cfg->n_occ;
+  P->occ_s[1] = uks ? uks->n_occ_b : cfg->n_occ;
+  const long n_ov_a = (long)cfg->n_occ * cfg->n_virt;
+  const long n_ov_b = uks ? (long)uks->n_occ_b * (P->n_bas - uks->n_occ_b) : 0;
+  P->n_ov = (int)(n_ov_a + n_ov_b);
   P->n_t = n_targets;
   P->n_g = cfg->n_freq;
   if (stream) {
@@ -1279,8 +1312,14 @@ static gw_status plan_create_impl(gw_plan* P, const gw_config* cfg, const double
   CK(cudaMallocHost(&P->h_cnt, sizeof(int)));
   const int n = cfg->n_aux;
   P->h_eps.assign(eps, eps + P->n_bas);
-  P->h_eps_g = P->h_eps;
+  P->h_eps_s[0] = P->h_eps;
+  P->h_eps_s[1] = uks ? std::vector<double>(uks->eps_b, uks->eps_b + P->n_bas) : P->h_eps;
+  P->h_eps_g[0] = P->h_eps_s[0];
+  P->h_eps_g[1] = P->h_eps_s[1];
   P->h_targets.assign(targets, targets + n_targets);
+  P->h_spin.assign(n_targets, 0);
+  if (uks)
+    for (int t = 0; t < n_targets; ++t) P->h_spin[t] = uks->spins[t];
   // grid
   P->h_xi.resize(P->n_g);
   P->h_wt.resize(P->n_g);
@@ -1292,7 +1331,7 @@ static gw_status plan_create_impl(gw_plan* P, const gw_config* cfg, const double
   std::vector<double> xi_all(P->h_xi);
   xi_all.push_back(0.0);
   TRY(dmalloc(P, &P->d_eps, sizeof(double) * P->n_bas));
-  TRY(dmalloc(P, &P->d_eps_g, sizeof(double) * P->n_bas));
+  TRY(dmalloc(P, &P->d_eps_g, sizeof(double) * P->n_spin * P->n_bas));
   TRY(dmalloc(P, &P->d_xi, sizeof(double) * (P->n_g + 1)));
   TRY(dmalloc(P, &P->d_wt, sizeof(double) * std::max(1, P->n_g)));
   TRY(dmalloc(P, &P->d_sx, sizeof(double) * std::max(1, n_targets)));
@@ -1300,12 +1339,34 @@ static gw_status plan_create_impl(gw_plan* P, const gw_config* cfg, const double
   TRY(dmalloc(P, &P->d_en, sizeof(double) * std::max(1, n_targets)));
   TRY(dmalloc(P, &P->d_W, sizeof(double) * (size_t)n_targets * P->n_bas * (P->n_g + 1)));
   TRY(dmalloc(P, &P->d_D, sizeof(double) * (size_t)P->n_ov));
-  CK(cudaMemcpyAsync(P->d_eps, eps, sizeof(double) * P->n_bas, cudaMemcpyHostToDevice, P->stream));
-  CK(cudaMemcpyAsync(P->d_eps_g, eps, sizeof(double) * P->n_bas, cudaMemcpyHostToDevice, P->stream));
+  for (int sp = 0; sp < P->n_spin; ++sp) TRY(set_g_energies(P, sp, P->h_eps_s[sp].data()));
   CK(cudaMemcpyAsync(P->d_xi, xi_all.data(), sizeof(double) * (P->n_g + 1), cudaMemcpyHostToDevice, P->stream));
   CK(cudaMemcpyAsync(P->d_wt, P->h_wt.data(), sizeof(double) * P->n_g, cudaMemcpyHostToDevice, P->stream));
+  if (uks) {
+    std::vector<int> occ_t(n_targets);
+    for (int t = 0; t < n_targets; ++t) occ_t[t] = P->occ_s[P->h_spin[t]];
+    TRY(dmalloc(P, &P->d_spin, sizeof(int) * n_targets));
+    TRY(dmalloc(P, &P->d_occ_t, sizeof(int) * n_targets));
+    CK(cudaMemcpyAsync(P->d_spin, P->h_spin.data(), sizeof(int) * n_targets, cudaMemcpyHostToDevice, P->stream));
+    CK(cudaMemcpyAsync(P->d_occ_t, occ_t.data(), sizeof(int) * n_targets, cudaMemcpyHostToDevice, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+  }
   const size_t nB = (size_t)n * P->n_ov, nBn = (size_t)n_targets * P->n_bas * n;
-  if (flags & GW_BORROW_DEVICE_PTRS) {
+  cudaMemcpyKind kind = (flags & GW_INPUT_ON_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (uks) {
+    // the two spin channels side by side along the pair axis, each scaled by 1/sqrt(2): the closed-shell formulas
+    // (factor 2 for the two spins) then give sum over sigma with factor 1 per channel (Sec. 3.3, Pi with Sigma_s)
+    P->own_B = true;
+    TRY(dmalloc(P, &P->d_B_ia, sizeof(double) * nB));
+    TRY(dmalloc(P, &P->d_B_nm, sizeof(double) * nBn));
+    CK(cudaMemcpy2DAsync(P->d_B_ia, sizeof(double) * P->n_ov, B_ia, sizeof(double) * n_ov_a, sizeof(double) * n_ov_a,
+                         n, kind, P->stream));
+    if (n_ov_b > 0)
+      CK(cudaMemcpy2DAsync(P->d_B_ia + n_ov_a, sizeof(double) * P->n_ov, uks->B_ia_b, sizeof(double) * n_ov_b,
+                           sizeof(double) * n_ov_b, n, kind, P->stream));
+    LAUNCH((scale_kernel<<<1024, 256, 0, P->stream>>>(P->d_B_ia, nB, 0.70710678118654752440)));
+    CK(cudaMemcpyAsync(P->d_B_nm, B_nm, sizeof(double) * nBn, kind, P->stream));
+  } else if (flags & GW_BORROW_DEVICE_PTRS) {
     P->own_B = false;
     P->d_B_ia = const_cast<double*>(B_ia);
     P->d_B_nm = const_cast<double*>(B_nm);
@@ -1313,7 +1374,6 @@ static gw_status plan_create_impl(gw_plan* P, const gw_config* cfg, const double
     P->own_B = true;
     TRY(dmalloc(P, &P->d_B_ia, sizeof(double) * nB));
     TRY(dmalloc(P, &P->d_B_nm, sizeof(double) * nBn));
-    cudaMemcpyKind kind = (flags & GW_INPUT_ON_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     CK(cudaMemcpyAsync(P->d_B_ia, B_ia, sizeof(double) * nB, kind, P->stream));
     CK(cudaMemcpyAsync(P->d_B_nm, B_nm, sizeof(double) * nBn, kind, P->stream));
   }
@@ -1342,8 +1402,8 @@ static gw_status plan_create_impl(gw_plan* P, const gw_config* cfg, const double
     TRY(dmalloc(P, &P->d_Dkidx, sizeof(int) * P->n_ov));
     CK(cudaStreamSynchronize(P->stream));
   }
-  TRY(set_pair_energies(P, eps));
-  LAUNCH(gw::launch_sigma_x(P->d_B_nm, n_targets, P->n_bas, n, cfg->n_occ, P->d_sx, P->stream));
+  TRY(set_pair_energies(P, P->h_eps_s[0].data(), P->h_eps_s[1].data()));
+  LAUNCH(gw::launch_sigma_x(P->d_B_nm, n_targets, P->n_bas, n, cfg->n_occ, P->d_sx, P->stream, P->d_occ_t));
   P->h_sx.resize(n_targets);
   CK(cudaMemcpyAsync(P->h_sx.data(), P->d_sx, sizeof(double) * n_targets, cudaMemcpyDeviceToHost, P->stream));
   CK(cudaStreamSynchronize(P->stream));
@@ -1351,7 +1411,7 @@ static gw_status plan_create_impl(gw_plan* P, const gw_config* cfg, const double
   P->h_en.resize(n_targets);
   for (int t = 0; t < n_targets; ++t) {
     P->h_shift[t] = vxc ? P->h_sx[t] - vxc[t] : 0.0;
-    P->h_en[t] = eps[targets[t]];
+    P->h_en[t] = P->h_eps_s[P->h_spin[t]][targets[t]];
   }
   CK(cudaMemcpyAsync(P->d_shift, P->h_shift.data(), sizeof(double) * n_targets, cudaMemcpyHostToDevice, P->stream));
   CK(cudaMemcpyAsync(P->d_en, P->h_en.data(), sizeof(double) * n_targets, cudaMemcpyHostToDevice, P->stream));
@@ -1398,6 +1458,56 @@ gw_status gw_plan_create(const gw_config* cfg, const double* eps, const double* 
   P = new (std::nothrow) gw_plan();
   if (!P) return fail(nullptr, GW_ERR_OOM, "host allocation failed");
   gw_status st = plan_create_impl(P, cfg, eps, B_ia, B_nm, targets, n_targets, vxc, xi, wt, flags, stream);
+  if (st != GW_OK) {
+    g_create_error = P->err;
+    free_plan(P);
+    return st;
+  }
+  *out = P;
+  return GW_OK;
+}
+
+gw_status gw_plan_create_uks(const gw_config* cfg, const double* eps_a, const double* eps_b, int n_occ_b,
+                             const double* B_ia_a, const double* B_ia_b, const double* B_nm, const int* targets,
+                             const int* spins, int n_targets, const double* vxc, const double* xi, const double* wt,
+                             unsigned flags, void* stream, gw_plan_t* out) {
+  if (!out) return fail(nullptr, GW_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!cfg || !eps_a || !eps_b || !B_ia_a || !B_nm || !targets || !spins)
+    return fail(nullptr, GW_ERR_ARG, "NULL input pointer");
+  if (flags & GW_BORROW_DEVICE_PTRS) return fail(nullptr, GW_ERR_ARG, "open shell: B cannot be borrowed");
+  const int n_bas = cfg->n_occ + cfg->n_virt;
+  if (cfg->n_occ <= 0 || cfg->n_virt <= 0 || n_occ_b < 0 || n_occ_b >= n_bas || cfg->n_aux <= 0 || n_targets <= 0 ||
+      cfg->n_freq <= 0)
+    return fail(nullptr, GW_ERR_ARG, "bad sizes (n_occ %d/%d n_bas %d n_aux %d n_targets %d)", cfg->n_occ, n_occ_b,
+                n_bas, cfg->n_aux, n_targets);
+  if (n_occ_b > 0 && !B_ia_b) return fail(nullptr, GW_ERR_ARG, "B_ia_b is NULL");
+  if ((long)cfg->n_occ * cfg->n_virt + (long)n_occ_b * (n_bas - n_occ_b) > 2147483647L)
+    return fail(nullptr, GW_ERR_ARG, "too many pairs");
+  if (cfg->precision != GW_PREC_FP64 && cfg->precision != GW_PREC_MIXED)
+    return fail(nullptr, GW_ERR_ARG, "unknown precision %d", cfg->precision);
+  if ((xi == nullptr) != (wt == nullptr)) return fail(nullptr, GW_ERR_ARG, "xi and wt must both be given or both NULL");
+  if (!(cfg->x0 > 0.0) && !xi) return fail(nullptr, GW_ERR_ARG, "x0 must be positive");
+  if (!(cfg->eta >= 0.0) || cfg->minres_maxit < 0 || cfg->qp_maxit <= 0 || (cfg->op_parts != 2 && cfg->op_parts != 3))
+    return fail(nullptr, GW_ERR_ARG, "bad solver settings");
+  const double* e2[2] = {eps_a, eps_b};
+  const int occ[2] = {cfg->n_occ, n_occ_b};
+  for (int sp = 0; sp < 2; ++sp) {
+    for (int i = 0; i < n_bas; ++i) {
+      if (!std::isfinite(e2[sp][i])) return fail(nullptr, GW_ERR_ARG, "spin %d: eps[%d] is not finite", sp, i);
+      if (i > 0 && e2[sp][i] < e2[sp][i - 1]) return fail(nullptr, GW_ERR_ARG, "spin %d: eps not ascending", sp);
+    }
+    if (occ[sp] > 0 && e2[sp][occ[sp]] <= e2[sp][occ[sp] - 1])
+      return fail(nullptr, GW_ERR_ARG, "spin %d: no gap between HOMO and LUMO", sp);
+  }
+  for (int t = 0; t < n_targets; ++t) {
+    if (targets[t] < 0 || targets[t] >= n_bas) return fail(nullptr, GW_ERR_ARG, "target %d out of range", targets[t]);
+    if (spins[t] != 0 && spins[t] != 1) return fail(nullptr, GW_ERR_ARG, "spin of target %d must be 0 or 1", t);
+  }
+  gw_plan* P = new (std::nothrow) gw_plan();
+  if (!P) return fail(nullptr, GW_ERR_OOM, "host allocation failed");
+  const UksInput uks{eps_b, n_occ_b, B_ia_b, spins};
+  gw_status st = plan_create_impl(P, cfg, eps_a, B_ia_a, B_nm, targets, n_targets, vxc, xi, wt, flags, stream, &uks);
   if (st != GW_OK) {
     g_create_error = P->err;
     free_plan(P);
@@ -1678,20 +1788,24 @@ gw_status qp_solve_impl(gw_plan* P, gw_qp_mode mode, const double* omega0, doubl
   return all_ok ? GW_OK : GW_ERR_NOT_CONVERGED;
 }
 
-// Energies of the next eigenvalue cycle: targets take their QP energies, every other occupied state moves by the
-// correction of the highest occupied target, every other virtual state by that of the lowest virtual target.
-std::vector<double> scissor(const gw_plan* P, const std::vector<double>& e_qp) {
-  const int n_occ = P->cfg.n_occ;
-  std::vector<double> out(P->h_eps);
+// Energies of the next eigenvalue cycle, per spin: targets take their QP energies, every other occupied state moves
+// by the correction of the highest occupied target of its spin, every other virtual state by that of the lowest
+// virtual target of its spin.
+std::vector<double> scissor(const gw_plan* P, int spin, const std::vector<double>& e_qp) {
+  const int n_occ = P->occ_s[spin];
+  const std::vector<double>& ks = P->h_eps_s[spin];
+  std::vector<double> out(ks);
   double e_o = -INFINITY, d_o = 0.0, e_v = INFINITY, d_v = 0.0;
   for (int t = 0; t < P->n_t; ++t) {
+    if (P->h_spin[t] != spin) continue;
     const int n = P->h_targets[t];
-    const double e = P->h_eps[n], d = e_qp[t] - e;
+    const double e = ks[n], d = e_qp[t] - e;
     if (n < n_occ && (e > e_o || (e == e_o && d > d_o))) { e_o = e; d_o = d; }
     if (n >= n_occ && (e < e_v || (e == e_v && d < d_v))) { e_v = e; d_v = d; }
   }
   for (int m = 0; m < P->n_bas; ++m) out[m] += m < n_occ ? d_o : d_v;
-  for (int t = 0; t < P->n_t; ++t) out[P->h_targets[t]] = e_qp[t];
+  for (int t = 0; t < P->n_t; ++t)
+    if (P->h_spin[t] == spin) out[P->h_targets[t]] = e_qp[t];
   return out;
 }
 
@@ -1716,14 +1830,14 @@ gw_status gw_evgw(gw_plan_t P, int update_w, gw_qp_mode mode, int max_iter, doub
   std::vector<double> prev(n_t), cur(n_t), z(n_t);
   std::vector<int> st(n_t);
   for (int t = 0; t < n_t; ++t) prev[t] = P->h_en[t];
-  std::vector<double> eps_cur(P->h_eps);
+  std::vector<double> eps_cur[2] = {P->h_eps_s[0], P->h_eps_s[1]};
   gw_status last = GW_OK;
   bool conv = false;
   int it = 0;
   for (it = 1; it <= max_iter; ++it) {
-    TRY(set_g_energies(P, eps_cur.data()));
+    for (int sp = 0; sp < P->n_spin; ++sp) TRY(set_g_energies(P, sp, eps_cur[sp].data()));
     if (update_w && it > 1) {            // evGW: W from the current energies (cycle 1 is G0W0)
-      TRY(set_pair_energies(P, eps_cur.data()));
+      TRY(set_pair_energies(P, eps_cur[0].data(), eps_cur[1].data()));
       P->screening_done = false;
     }
     last = qp_solve_impl(P, mode, prev.data(), cur.data(), z.data(), st.data());
@@ -1731,13 +1845,14 @@ gw_status gw_evgw(gw_plan_t P, int update_w, gw_qp_mode mode, int max_iter, doub
     double delta = 0.0;
     for (int t = 0; t < n_t; ++t) delta = std::max(delta, std::fabs(cur[t] - prev[t]));
     prev = cur;
-    eps_cur = scissor(P, cur);
+    for (int sp = 0; sp < P->n_spin; ++sp) eps_cur[sp] = scissor(P, sp, cur);
     if (delta < tol) { conv = true; break; }
   }
   // the plan goes back to G0W0: G and W from the KS energies (W is rebuilt on the next call that needs it)
-  gw_status rs = set_g_energies(P, P->h_eps.data());
+  gw_status rs = GW_OK;
+  for (int sp = 0; sp < P->n_spin && rs == GW_OK; ++sp) rs = set_g_energies(P, sp, P->h_eps_s[sp].data());
   if (rs == GW_OK && update_w) {
-    rs = set_pair_energies(P, P->h_eps.data());
+    rs = set_pair_energies(P, P->h_eps_s[0].data(), P->h_eps_s[1].data());
     P->screening_done = false;
   }
   if (last != GW_OK && last != GW_ERR_NOT_CONVERGED) return last;

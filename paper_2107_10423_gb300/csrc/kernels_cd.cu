@@ -31,8 +31,9 @@ __device__ double block_sum(double v, double* buf) {
 
 // Sigma_x_nn = -sum_{m < n_occ} sum_P B_nm[t][m][P]^2  (Algorithm 1, Init)
 __global__ void sigma_x_kernel(const double* __restrict__ B_nm, int n_bas, int n_aux, int n_occ,
-                               double* __restrict__ sx) {
+                               double* __restrict__ sx, const int* __restrict__ occ_t) {
   __shared__ double buf[32];
+  if (occ_t) n_occ = occ_t[blockIdx.x];
   const double* b = B_nm + (long)blockIdx.x * n_bas * n_aux;
   double acc = 0.0;
   for (long i = threadIdx.x; i < (long)n_occ * n_aux; i += blockDim.x) acc += b[i] * b[i];
@@ -47,11 +48,12 @@ __global__ void sigma_imag_kernel(const double* __restrict__ W, int n_bas, int n
                                   const double* __restrict__ xi, const double* __restrict__ wt,
                                   const double* __restrict__ omega, int static_sub, double* __restrict__ I,
                                   double* __restrict__ dI, const unsigned char* __restrict__ active,
-                                  const int* __restrict__ tmap) {
+                                  const int* __restrict__ tmap, const int* __restrict__ spin) {
   __shared__ double buf[32];
   const int t = blockIdx.x;                 // evaluation point; its target's W rows are tw's
   if (active && !active[t]) return;
   const int tw = tmap ? tmap[t] : t;
+  eps += spin ? (long)spin[tw] * n_bas : 0;   // the target's own spin (G energies [n_spin][n_bas])
   const double w0 = omega[t];
   const int ld = n_g + 1;
   double si = 0.0, sd = 0.0, sj = 0.0;
@@ -494,15 +496,16 @@ __global__ void qp_step_kernel(QPState* st, const double* __restrict__ R, const 
 
 }  // namespace
 
-void launch_sigma_x(const double* B_nm, int n_t, int n_bas, int n_aux, int n_occ, double* sx, cudaStream_t s) {
-  if (n_t > 0) sigma_x_kernel<<<n_t, RT, 0, s>>>(B_nm, n_bas, n_aux, n_occ, sx);
+void launch_sigma_x(const double* B_nm, int n_t, int n_bas, int n_aux, int n_occ, double* sx, cudaStream_t s,
+                    const int* occ_t) {
+  if (n_t > 0) sigma_x_kernel<<<n_t, RT, 0, s>>>(B_nm, n_bas, n_aux, n_occ, sx, occ_t);
 }
 
 void launch_sigma_imag(const double* W, int n_t, int n_bas, int n_g, const double* eps, const double* xi,
                        const double* wt, const double* omega, int static_sub, double* I, double* dI,
-                       const unsigned char* active, cudaStream_t s, const int* tmap) {
+                       const unsigned char* active, cudaStream_t s, const int* tmap, const int* spin) {
   if (n_t > 0)
-    sigma_imag_kernel<<<n_t, RT, 0, s>>>(W, n_bas, n_g, eps, xi, wt, omega, static_sub, I, dI, active, tmap);
+    sigma_imag_kernel<<<n_t, RT, 0, s>>>(W, n_bas, n_g, eps, xi, wt, omega, static_sub, I, dI, active, tmap, spin);
 }
 
 template <typename T>

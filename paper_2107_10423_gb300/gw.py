@@ -18,7 +18,7 @@ GW_INPUT_ON_DEVICE, GW_BORROW_DEVICE_PTRS = 1, 2
 
 EXPORTED = ["gw_config_default", "gw_plan_create", "gw_polarizability", "gw_sigma_cd", "gw_residues_minres",
             "gw_qp_solve", "gw_grid", "gw_w_table", "gw_w_table_noalloc", "gw_get_stats", "gw_plan_destroy", "gw_last_error",
-            "gw_plan_footprint", "gw_evgw", "gw_set_shard", "gw_shard_columns"]
+            "gw_plan_footprint", "gw_evgw", "gw_set_shard", "gw_shard_columns", "gw_plan_create_uks"]
 
 
 class GWError(RuntimeError):
@@ -71,6 +71,9 @@ def load(path: str = LIB_PATH):
     lib.gw_config_default.restype = None
     lib.gw_plan_create.argtypes = [ctypes.POINTER(Config), _P, _P, _P, _P, ctypes.c_int, _P, _P, _P, ctypes.c_uint,
                                    _P, ctypes.POINTER(_P)]
+    lib.gw_plan_create_uks.argtypes = [ctypes.POINTER(Config), _P, _P, ctypes.c_int, _P, _P, _P, _P, _P,
+                                       ctypes.c_int, _P, _P, _P, ctypes.c_uint, _P, ctypes.POINTER(_P)]
+    lib.gw_plan_create_uks.restype = ctypes.c_int
     lib.gw_polarizability.argtypes = [_P, _P, ctypes.c_int, _P]
     lib.gw_sigma_cd.argtypes = [_P, _P, _P, _P, _P]
     lib.gw_residues_minres.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P, _P, _P]
@@ -180,6 +183,41 @@ class Plan:
         if st != GW_OK:
             raise GWError(st, lib.gw_last_error(None).decode())
         self._h = h
+
+    @classmethod
+    def open_shell(cls, eps_a, eps_b, n_occ_a, n_occ_b, B_ia_a, B_ia_b, B_nm, targets, spins, vxc=None, xi=None,
+                   wt=None, stream=None, **config):
+        """Open-shell plan (gw_plan_create_uks): host float64 arrays (B_ia_a [n_aux, n_occ_a*n_virt_a], B_ia_b
+        [n_aux, n_occ_b*n_virt_b], B_nm [n_targets, n_bas, n_aux] in each target's spin), spins 0/1 per target."""
+        self = cls.__new__(cls)
+        lib = load()
+        self._lib = lib
+        self.eps = np.ascontiguousarray(eps_a, dtype=np.float64)
+        eb = np.ascontiguousarray(eps_b, dtype=np.float64)
+        n_bas = len(self.eps)
+        cfg = default_config(n_occ=int(n_occ_a), n_virt=int(n_bas - n_occ_a), n_aux=int(B_ia_a.shape[0]), **config)
+        self.cfg = cfg
+        self.targets = np.ascontiguousarray(targets, dtype=np.int32)
+        sp = np.ascontiguousarray(spins, dtype=np.int32)
+        self.n_t = len(self.targets)
+        ba = np.ascontiguousarray(B_ia_a, dtype=np.float64)
+        bb = np.ascontiguousarray(B_ia_b, dtype=np.float64)
+        bn = np.ascontiguousarray(B_nm, dtype=np.float64)
+        vx = None if vxc is None else np.ascontiguousarray(vxc, dtype=np.float64)
+        xa = None if xi is None else np.ascontiguousarray(xi, dtype=np.float64)
+        wa = None if wt is None else np.ascontiguousarray(wt, dtype=np.float64)
+        if xa is not None:
+            cfg.n_freq = len(xa)
+        self._keep = (ba, bb, bn, eb, sp)
+        self._grid = (vx, xa, wa)
+        h = ctypes.c_void_p()
+        st = lib.gw_plan_create_uks(ctypes.byref(cfg), _ptr(self.eps), _ptr(eb), int(n_occ_b), _ptr(ba), _ptr(bb),
+                                    _ptr(bn), _ptr(self.targets), _ptr(sp), self.n_t, _ptr(vx), _ptr(xa), _ptr(wa), 0,
+                                    ctypes.c_void_p(stream) if stream else None, ctypes.byref(h))
+        if st != GW_OK:
+            raise GWError(st, lib.gw_last_error(None).decode())
+        self._h = h
+        return self
 
     def _check(self, st, allow=()):
         if st != GW_OK and st not in allow:

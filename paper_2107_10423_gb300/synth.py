@@ -181,6 +181,42 @@ def esca_like(seed: int = 3, n_virt: int = 552, n_aux: int = 1800) -> System:
     return System("esca", eps, 48, n_aux, 0.6 / np.sqrt(n_aux), seed, np.arange(6, 12), {})
 
 
+@dataclass
+class OpenShellSystem:
+    """A spin-unrestricted problem: per-spin energies and occupations on a shared orbital and auxiliary basis, B
+    drawn per spin (alpha with ``seed``, beta with ``seed + 1``), targets as (spin, state) pairs."""
+    name: str
+    eps: tuple               # (eps_alpha, eps_beta), each [n_bas] ascending
+    n_occ: tuple             # (n_occ_alpha, n_occ_beta)
+    n_aux: int
+    sigma_b: float
+    seed: int
+    targets: list            # [(spin, state), ...]
+
+    @property
+    def n_bas(self) -> int:
+        return len(self.eps[0])
+
+    def b_ia(self, spin: int) -> np.ndarray:
+        o = self.n_occ[spin]
+        return b_ia(self.seed + spin, self.sigma_b, self.n_aux, o, self.n_bas - o)
+
+    def b_nm(self) -> np.ndarray:
+        """Rows of every target in its own spin, [n_targets, n_bas, n_aux]."""
+        return np.stack([b_nm(self.seed + sp, self.sigma_b, self.n_aux, self.n_bas, [n])[0] for sp, n in self.targets])
+
+
+def water_cation(n: int, seed: int) -> OpenShellSystem:
+    """(H2O)_n^+-shaped doublet: the levels of ``water_cluster(n)`` for both spins, the beta HOMO emptied and the
+    beta levels raised by 0.05 Ha; targets the alpha HOMO and LUMO and the beta HOMO and LUMO."""
+    base = water_cluster(n, seed)
+    ea = base.eps.copy()
+    eb = base.eps + 0.05
+    oa, ob = base.n_occ, base.n_occ - 1
+    return OpenShellSystem(f"water{n}+", (ea, eb), (oa, ob), base.n_aux, base.sigma_b, seed,
+                           [(0, oa - 1), (0, oa), (1, ob - 1), (1, ob)])
+
+
 def workload(k: int) -> System:
     """The four fixed workloads: 0 single water (FP64, SD and CD), 1 (H2O)_16 valence (FP64 CD+MINRES),
     2 (H2O)_64 (mixed precision), 3 ESCA-shaped C1s batch."""
