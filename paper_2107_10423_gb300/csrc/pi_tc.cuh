@@ -55,7 +55,8 @@ cudaError_t tc_pair_weights(const double* Dk, int K, const int* kinds, const dou
 // B FP32 [n][ldb] (ldb a multiple of 4), its BF16 hi/lo split Bhi/Blo [n][tc_ld(K)], w from tc_pair_weights;
 // out [nb][n][ldo] FP32 at batch stride out_bstride, full symmetric (lower tiles computed and mirrored);
 // mode_even / mode_odd for even / odd b: 0 v, 1 delta - v, 2 -v.  max_ctas > 0 caps the persistent grid.
-// ksplit > 0 forces that many K ranges per (tile, pair); ksplit = 0 autotunes it per shape (n, K, nb, max_ctas):
+// ksplit > 0 asks for that many K ranges per (tile, pair), lowered by halving to the largest feasible split (every
+// range at least 4 K blocks of 32, partials within part_bytes); ksplit = 0 autotunes it per shape (n, K, nb, max_ctas):
 // every feasible split (partials [ksplit][nb][n][n] FP32 fit in part_bytes of `part`) is timed once and the
 // fastest kept for the process.  *chosen (if not NULL) receives the split used.
 cudaError_t tc_pi_fused(const float* B, long ldb, int n, int K, const float* w, int nb, const __nv_bfloat16* Bhi,

@@ -190,11 +190,12 @@ def test_fused_pi_tiles_and_entries(gw, n, seed, xi, ctas):
         assert np.array_equal(Pi[g], Pi[g].T)
 
 
-@pytest.mark.parametrize("n,ks", [(1, 2), (1, 4), (3, 2), (3, 8), (2, 0)])
+@pytest.mark.parametrize("n,ks", [(2, 2), (2, 4), (3, 2), (3, 8), (2, 0), (0, 2)])
 def test_fused_pi_split_k(gw, n, ks):
     """The K split of the fused Pi kernel (forced, or ks = 0: autotuned for the shape) against the oracle, and the
-    split product against the unsplit one (partials added in a fixed order)."""
-    s = synth.workload(0) if n == 1 else synth.water_cluster(n, 9)
+    split product against the unsplit one (partials added in a fixed order).  n = 0 is the single water, whose
+    N_ov = 95 (3 K blocks) admits no split: the request falls back to one K range."""
+    s = synth.workload(0) if n == 0 else synth.water_cluster(n, 9)
     B, Bn = s.b_ia(), s.b_nm()
     xi = np.array([0.0, 0.4, 3.0])
     with gw.Plan(s.eps, s.n_occ, B, Bn, s.targets, precision=gw.GW_PREC_MIXED, pi_ksplit=ks) as p:
@@ -203,7 +204,10 @@ def test_fused_pi_split_k(gw, n, ks):
         used = p.stats()["pi_ksplit_last"]
     with gw.Plan(s.eps, s.n_occ, B, Bn, s.targets, precision=gw.GW_PREC_MIXED, pi_ksplit=1) as p:
         Pi1 = p.polarizability(xi)
-    assert used == ks if ks else used in (1, 2, 4, 8)
+    if n == 0:
+        assert used == 1
+    else:
+        assert used == ks if ks else used in (1, 2, 4, 8)
     np.testing.assert_array_equal(Pi, Pi2)                       # deterministic
     for g, x in enumerate(xi):
         ref = O.pi_imag(s.eps, s.n_occ, B, x)
