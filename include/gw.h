@@ -165,6 +165,13 @@ gw_status gw_polarizability(gw_plan_t plan, const double* xi, int n_xi, double* 
 gw_status gw_sigma_cd(gw_plan_t plan, const double* omega, double* sigma_c, double* dsigma_c,
                       double* sigma_x);
 
+/* Sigma_c and its omega-derivative at n_points arbitrary (target, frequency) pairs, all in one batched evaluation
+ * (the same I term, residue list and batched MINRES as gw_sigma_cd; the graphical solution of Sec. 3.4 samples its
+ * windows this way).  target_idx[p] in [0, n_targets), omega[p] in Ha (host, [n_points]); sigma_c, dsigma_c host
+ * [n_points], either may be NULL.  GW_ERR_ARG for a bad index or a non-finite frequency. */
+gw_status gw_sigma_points(gw_plan_t plan, int n_points, const int* target_idx, const double* omega, double* sigma_c,
+                          double* dsigma_c);
+
 /* Residue terms (eq. "rnn") for an explicit list of n_rhs right-hand sides:
  *   W_nm(x) = b_nm^T [(1 - Pi(x))^-1 - 1] b_nm,  Pi(x) = 2 sum_ia B B [1/(x-D+i eta) + 1/(-x-D+i eta)]
  * solved matrix-free by MINRES on the real symmetric 2 n_aux embedding of the complex-symmetric

@@ -2,6 +2,7 @@
 // Not part of the public ABI (include/gw.h).
 #pragma once
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 #include <cstdint>
 
 namespace gw {
@@ -100,6 +101,12 @@ void launch_minres_finish(const double* B_nm, int n_bas, int n_aux, const int* r
 // Batched complex LU with partial pivoting (kernels_lu.cu): matrices b at Ar + b*stride, Ai + b*stride.
 template <typename T>
 void launch_zlu(T* Ar, T* Ai, long stride, int n, int batch, int* piv, int* info, cudaStream_t s);
+// Blocked FP32 LU of `batch` complex matrices (planes A and A + plane, matrix stride `stride`) with the trailing
+// updates on the tensor cores; same factors and pivot convention as launch_zlu.  work: work_elems BF16, at least
+// zlu_tc_work_elems(n, 1) (one matrix's split panel operands); the updates run in sub-batches that fit it.
+size_t zlu_tc_work_elems(int n, int batch);
+cudaError_t launch_zlu_tc(float* A, long stride, long plane, int n, int batch, int* piv, int* info,
+                          __nv_bfloat16* work, size_t work_elems, int* err, cudaStream_t s);
 template <typename T>
 void launch_zlu_solve(const T* Ar, const T* Ai, long stride, int n, int batch, const int* piv, T* yr, T* yi,
                       long ystride, cudaStream_t s);

@@ -86,7 +86,7 @@ struct gw_plan {
       mr_dwre, mr_it, mr_res, mr_cnt, mr_Vhi, mr_Vlo, mr_Uhi, mr_Ulo, mr_Vlo2, mr_Ulo2, mr_V64;
   DevBuf sg_I, sg_dI, sg_R, sg_dR, sg_om, sg_start, sg_coef, sg_act, sg_tmap, qp_st, qp_om0;
   DevBuf fb_A, fb_y, fb_piv, fb_info, fb_idx, fb_y64, fb_V32, fb_S32, fb_Vp, fb_Up, fb_x, fb_V64, fb_U64, fb_S64, fb_sel,
-      fb_pos, fb_rho, fb_xs, fb_Bh, fb_Bl;
+      fb_pos, fb_rho, fb_xs, fb_Bh, fb_Bl, fb_lu;
   int* h_cnt = nullptr;       // pinned
   std::string err;
   gw_stats stats{};
@@ -101,7 +101,7 @@ struct gw_plan {
     DevBuf* all[] = {&ws_mat, &ws_info, &ws_scratch, &ws_gout, &ws_xi, &tc_part, &tc_kind, &tc_par, &tc_err, &tc_w, &ns_E, &ns_X, &ns_X2, &ns_Xa, &ns_Xb, &ns_T, &ns_lam, &ns_E0, &ns_vec, &mr_V, &mr_U, &mr_S, &mr_vprev,
                      &mr_v, &mr_d1, &mr_d2, &mr_x, &mr_st, &mr_rt, &mr_rm, &mr_xf, &mr_wre, &mr_wim,
                      &mr_dwre, &mr_it, &mr_res, &mr_cnt, &mr_Vhi, &mr_Vlo, &mr_Uhi, &mr_Ulo, &mr_Vlo2, &mr_Ulo2, &mr_V64, &sg_I, &sg_dI, &sg_R, &sg_dR, &sg_om, &sg_start,
-                     &sg_coef, &sg_act, &sg_tmap, &qp_st, &qp_om0, &fb_A, &fb_y, &fb_piv, &fb_info, &fb_idx, &fb_y64, &fb_V32, &fb_S32, &fb_Vp, &fb_Up, &fb_x, &fb_V64, &fb_U64, &fb_S64, &fb_sel, &fb_pos, &fb_rho, &fb_xs, &fb_Bh, &fb_Bl};
+                     &sg_coef, &sg_act, &sg_tmap, &qp_st, &qp_om0, &fb_A, &fb_y, &fb_piv, &fb_info, &fb_idx, &fb_y64, &fb_V32, &fb_S32, &fb_Vp, &fb_Up, &fb_x, &fb_V64, &fb_U64, &fb_S64, &fb_sel, &fb_pos, &fb_rho, &fb_xs, &fb_Bh, &fb_Bl, &fb_lu};
     bufs.assign(all, all + sizeof(all) / sizeof(all[0]));
   }
 };
@@ -584,6 +584,14 @@ gw_status ensure_third_parts(gw_plan* P);
 // Half-width (Ha) of the window around each resonance x = +-D_ia whose derivative terms are computed in FP64.
 constexpr double kResonantCut = 0.1;
 
+// BF16 elements of the blocked LU's split panel operands for a fallback batch of fb matrices: the whole batch, or
+// as many matrices as fit in 1 GiB (at least one); the panel updates then run in sub-batches.
+size_t lu_work_elems(int n, long fb) {
+  const size_t one = gw::zlu_tc_work_elems(n, 1);
+  const size_t cap = std::max(one, ((size_t)1 << 29) / std::max<size_t>(one, 1) * one);
+  return std::min(one * (size_t)std::max(1L, fb), cap);
+}
+
 // Dense solves for the MINRES batch slots in `need` (Sec. 3.3: build the dielectric matrix and factorise).
 // A_j = 1 - Pi(x_j) is built on the tensor cores (mixed) or by the FP64 SIMT kernel, then factorised by the
 // batched complex LU; W and the derivative-pass vectors are written into the slot.
@@ -615,6 +623,7 @@ gw_status dense_fallback(gw_plan* P, const std::vector<int>& need, const int* rt
     TRY(ensure(P, P->fb_rho, sizeof(double) * fb));
     TRY(ensure(P, P->fb_sel, sizeof(int) * fb));
     TRY(ensure(P, P->fb_pos, sizeof(int) * fb));
+    TRY(ensure(P, P->fb_lu, sizeof(__nv_bfloat16) * lu_work_elems(n, fb)));
   }
   CK(cudaMemcpyAsync(P->fb_idx.p, need.data(), sizeof(int) * nneed, cudaMemcpyHostToDevice, P->stream));
   std::vector<double> hx(nneed);
@@ -654,8 +663,18 @@ gw_status dense_fallback(gw_plan* P, const std::vector<int>& need, const int* rt
     LAUNCH(gw::launch_fallback_rhs<T>(P->d_B_nm, P->n_bas, n, rt, rm, as<int>(P->fb_idx) + k0, nf, as<T>(P->fb_y),
                                       P->stream));
     const size_t tl = tick(P);
-    LAUNCH(gw::launch_zlu<T>(A, A + mat, (long)(2 * mat), n, nf, as<int>(P->fb_piv), as<int>(P->fb_info),
-                             P->stream));
+    if (sizeof(T) == 4) {
+      // FP32 factors, trailing updates on the tensor cores (about FP32-accurate six-product split); a bounded
+      // wait that runs out in its GEMMs is reported by the refinement operator's check below
+      CK(cudaMemsetAsync(P->tc_err.p, 0, sizeof(int), P->stream));
+      CK(gw::launch_zlu_tc(reinterpret_cast<float*>(A), (long)(2 * mat), (long)mat, n, nf, as<int>(P->fb_piv),
+                           as<int>(P->fb_info), as<__nv_bfloat16>(P->fb_lu), P->fb_lu.bytes / sizeof(__nv_bfloat16),
+                           as<int>(P->tc_err), P->stream));
+      P->stats.n_kernel_launches += 5 * ((n + 63) / 64);
+    } else {
+      LAUNCH(gw::launch_zlu<T>(A, A + mat, (long)(2 * mat), n, nf, as<int>(P->fb_piv), as<int>(P->fb_info),
+                               P->stream));
+    }
     LAUNCH(gw::launch_zlu_solve<T>(A, A + mat, (long)(2 * mat), n, nf, as<int>(P->fb_piv), as<T>(P->fb_y),
                                    as<T>(P->fb_y) + n, 2L * n, P->stream));
     mark(P, 7, tl, nf * (8.0 / 3.0 * (double)n * n * n + 8.0 * (double)n * n));
@@ -802,7 +821,7 @@ gw_status tc_operator3(gw_plan* P, int nf, const double* xf, const float* V32, f
   const size_t sv = 2 * (size_t)nf * gw::tc_ld(n), su = 2 * (size_t)nf * gw::tc_ld(n_ov);
   __nv_bfloat16* vp = as<__nv_bfloat16>(P->fb_Vp);
   __nv_bfloat16* up = as<__nv_bfloat16>(P->fb_Up);
-  CK(cudaMemsetAsync(P->tc_err.p, 0, sizeof(int), P->stream));
+  // tc_err is not reset here: the caller clears it before the blocked LU, whose bounded waits this check covers too
   CK(gw::tc_split_rows(V32, 2 * nf, n, n, vp, vp + sv, P->stream, vp + 2 * sv));
   gw::TcEpi e1{};
   e1.kind = gw::TC_EPI_CPAIR;
@@ -1578,6 +1597,33 @@ gw_status gw_sigma_cd(gw_plan_t P, const double* omega, double* sigma_c, double*
   return GW_OK;
 }
 
+gw_status gw_sigma_points(gw_plan_t P, int n_points, const int* target_idx, const double* omega, double* sigma_c,
+                          double* dsigma_c) {
+  if (!P) return GW_ERR_ARG;
+  if (n_points < 0 || (n_points > 0 && (!target_idx || !omega))) return fail(P, GW_ERR_ARG, "bad point list");
+  if (n_points == 0) return GW_OK;
+  for (int p = 0; p < n_points; ++p) {
+    if (target_idx[p] < 0 || target_idx[p] >= P->n_t) return fail(P, GW_ERR_ARG, "target_idx[%d] out of range", p);
+    if (!std::isfinite(omega[p])) return fail(P, GW_ERR_ARG, "omega[%d] not finite", p);
+  }
+  TRY(ensure_screening(P));
+  std::vector<double> om(omega, omega + n_points);
+  std::vector<int> tmap(target_idx, target_idx + n_points);
+  std::vector<unsigned char> act(n_points, 1);
+  int nf = 0;
+  TRY(sigma_eval(P, om, act, &nf, &tmap));
+  std::vector<double> R(n_points), dR(n_points), I(n_points), dI(n_points);
+  CK(cudaMemcpy(R.data(), P->sg_R.p, sizeof(double) * n_points, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(dR.data(), P->sg_dR.p, sizeof(double) * n_points, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(I.data(), P->sg_I.p, sizeof(double) * n_points, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(dI.data(), P->sg_dI.p, sizeof(double) * n_points, cudaMemcpyDeviceToHost));
+  for (int p = 0; p < n_points; ++p) {
+    if (sigma_c) sigma_c[p] = R[p] - I[p];
+    if (dsigma_c) dsigma_c[p] = dR[p] - dI[p];
+  }
+  return GW_OK;
+}
+
 gw_status gw_residues_minres(gw_plan_t P, int n_rhs, const int* target_idx, const int* m, const double* x,
                              double* w_re, double* w_im, double* dw_re, int* iters, double* resnorm,
                              int* used_fallback) {
@@ -1938,6 +1984,7 @@ gw_status gw_plan_footprint(const gw_config* c, int n_t, unsigned flags, unsigne
   if (mixed) {
     b += fb * (16 * n + 16 * n + 12 * ldn + 12 * ldo + 40);                  // FP64 solutions, V/S, split parts
     b += fb * (32 * n + 16 * n_ov) + 8 * n * n_ov;                           // FP64-residual vectors, df split of B
+    b += 2 * (u64)lu_work_elems(c->n_aux, (long)std::min<u64>(fb, 1u << 30));            // blocked-LU split operands
   }
   *bytes = b;
   return GW_OK;

@@ -9,9 +9,11 @@
 //   * the difference-form products Pi(i xi) - Pi(0): w = 4 xi^2/(D (D^2 + xi^2)).
 //
 // Design (one CTA per SM, persistent over work items = (lower tile, pair of batch entries)):
-//   * TMA streams, per 32-wide k-block, the FP32 rows of the weighted side (128 x 32), the BF16 hi/lo parts of
-//     the unweighted side (2 x 128 x 32) and the two weight rows (2 x 32) into a 3-stage source ring.
-//   * A transform warpgroup (one thread per row) multiplies the FP32 rows by the weights of both entries and
+//   * TMA streams, per 32-wide k-block, the FP32 rows of the weighted side (128 x 32) with the two weight rows
+//     (2 x 32) into a 3-stage A ring that the transform releases, and the BF16 hi/lo parts of the unweighted side
+//     (2 x 128 x 32) into a 4-stage B ring that the tensor core releases: the FP32 rows are refilled as soon as
+//     they are transformed instead of staying held until the tensor core has finished with the k-block.
+//   * Two transform warpgroups (two threads per row) multiply the FP32 rows by the weights of both entries and
 //     splits the products into BF16 hi/lo tiles (64-byte swizzle, the tensor core's K-major layout) in a
 //     3-stage ring.  The weight never round-trips through HBM and the source tile serves both entries, which
 //     halves the L2 bytes per tensor-core flop against one entry per pass.
@@ -40,15 +42,22 @@ namespace {
 using namespace ptx;
 
 constexpr int BM = 128, BK = 32;
-constexpr int SRC_STAGES = 3, TR_STAGES = 3;
+constexpr int A_STAGES = 3, B_STAGES = 4, TR_STAGES = 3;
 constexpr int A_BYTES = BM * BK * 4;            // FP32 rows of the weighted side: 16 KiB
+constexpr int W_OFF = A_BYTES;                  // the two weight rows [2][BK] FP32 follow the FP32 tile
+constexpr int AS_BYTES = A_BYTES + 1024;        // 17 KiB per A stage (keeps every stage 1 KiB aligned)
 constexpr int H_BYTES = BM * BK * 2;            // one BF16 tile (128 rows x 64 bytes): 8 KiB
-constexpr int W_OFF = A_BYTES + 2 * H_BYTES;    // the two weight rows [2][BK] FP32 follow the tiles
-constexpr int SRC_BYTES = W_OFF + 1024;         // 33 KiB per source stage (keeps every stage 1 KiB aligned)
+constexpr int BS_BYTES = 2 * H_BYTES;           // B stage: hi and lo tiles of the unweighted side
 constexpr int TR_BYTES = 4 * H_BYTES;           // transformed tiles [entry][hi, lo]: 32 KiB
-constexpr int TX_BYTES = A_BYTES + 2 * H_BYTES + 2 * BK * 4;
-constexpr int N_BARS = 4 * 3 + 2 + 2 + 1;       // src full/empty, tr full/empty, acc full/empty, final
-constexpr int SMEM_BYTES = SRC_STAGES * SRC_BYTES + TR_STAGES * TR_BYTES + 256 + 1024;
+constexpr int A_TX = A_BYTES + 2 * BK * 4;
+constexpr int B_TX = 2 * H_BYTES;
+// mbarrier indices: A ring full/empty, B ring full/empty, transform ring full/empty, accumulators, final
+constexpr int BAR_AF = 0, BAR_AE = BAR_AF + A_STAGES, BAR_BF = BAR_AE + A_STAGES, BAR_BE = BAR_BF + B_STAGES,
+              BAR_TF = BAR_BE + B_STAGES, BAR_TE = BAR_TF + TR_STAGES, BAR_ACCF = BAR_TE + TR_STAGES,
+              BAR_ACCE = BAR_ACCF + 2, BAR_FIN = BAR_ACCE + 2, N_BARS = BAR_FIN + 1;
+static_assert(N_BARS * 8 + 4 <= 256, "barrier area");
+constexpr int SMEM_BYTES = A_STAGES * AS_BYTES + B_STAGES * BS_BYTES + TR_STAGES * TR_BYTES + 256 + 1024;
+static_assert(SMEM_BYTES <= 232448, "shared memory per block");
 constexpr int THREADS = 448;                    // warps 0-3 drain + epilogue, 4-11 transform, 12 TMA, 13 MMA
 constexpr int TR_WARPS = 8;
 constexpr uint32_t TMEM_COLS = 512;
@@ -108,9 +117,14 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* smem = smem_raw + (base - raw);
-  const uint32_t src0 = base, tr0 = base + SRC_STAGES * SRC_BYTES;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SRC_STAGES * SRC_BYTES + TR_STAGES * TR_BYTES);
+  constexpr int B_OFF = A_STAGES * AS_BYTES, TR_OFF = B_OFF + B_STAGES * BS_BYTES,
+                BAR_OFF = TR_OFF + TR_STAGES * TR_BYTES;
+  const uint32_t b0 = base + B_OFF, tr0 = base + TR_OFF;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + BAR_OFF);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + N_BARS);
+  const uint32_t bar0 = base + BAR_OFF;
+  // barrier i at bar0 + 8 i (addresses computed, not held in an indexed array)
+  auto bar = [bar0](int i) { return bar0 + 8u * (uint32_t)i; };
   __shared__ int s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -120,35 +134,25 @@ __global__ void __launch_bounds__(THREADS, 1)
   const long items = (long)n_tiles * n_pairs * ksplit;
   const int nk = (K + BK - 1) / BK;
 
-  uint32_t src_full[SRC_STAGES], src_empty[SRC_STAGES], tr_full[TR_STAGES], tr_empty[TR_STAGES];
-  for (int s = 0; s < SRC_STAGES; ++s) {
-    src_full[s] = smem_u32(&bars[s]);
-    src_empty[s] = smem_u32(&bars[SRC_STAGES + s]);
-  }
-  for (int s = 0; s < TR_STAGES; ++s) {
-    tr_full[s] = smem_u32(&bars[2 * SRC_STAGES + s]);
-    tr_empty[s] = smem_u32(&bars[2 * SRC_STAGES + TR_STAGES + s]);
-  }
-  const int ab = 2 * SRC_STAGES + 2 * TR_STAGES;
-  const uint32_t acc_full[2] = {smem_u32(&bars[ab]), smem_u32(&bars[ab + 1])};
-  const uint32_t acc_empty[2] = {smem_u32(&bars[ab + 2]), smem_u32(&bars[ab + 3])};
-  const uint32_t fin = smem_u32(&bars[ab + 4]);
-
   if (threadIdx.x == 0) {
     s_abort = 0;
-    for (int s = 0; s < SRC_STAGES; ++s) {
-      mbar_init(src_full[s], 1);
-      mbar_init(src_empty[s], TR_WARPS + 1);   // the transform warps + the MMA thread's commit
+    for (int s = 0; s < A_STAGES; ++s) {
+      mbar_init(bar(BAR_AF + s), 1);
+      mbar_init(bar(BAR_AE + s), TR_WARPS);    // one arrival per transform warp
+    }
+    for (int s = 0; s < B_STAGES; ++s) {
+      mbar_init(bar(BAR_BF + s), 1);
+      mbar_init(bar(BAR_BE + s), 1);           // the MMA thread's commit
     }
     for (int s = 0; s < TR_STAGES; ++s) {
-      mbar_init(tr_full[s], TR_WARPS);         // one arrival per transform warp
-      mbar_init(tr_empty[s], 1);
+      mbar_init(bar(BAR_TF + s), TR_WARPS);    // one arrival per transform warp
+      mbar_init(bar(BAR_TE + s), 1);
     }
     for (int f = 0; f < 2; ++f) {
-      mbar_init(acc_full[f], 1);
-      mbar_init(acc_empty[f], 4);       // one arrival per drain warp
+      mbar_init(bar(BAR_ACCF + f), 1);
+      mbar_init(bar(BAR_ACCE + f), 4);         // one arrival per drain warp
     }
-    mbar_init(fin, 1);
+    mbar_init(bar(BAR_FIN), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     fence_async_smem();
   }
@@ -166,39 +170,50 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (warp == 12) {
     if (lane == 0) {
       // ------------------------------------------------------------ TMA producer
-      long g = 0, issued = 0;
+      // A ring (FP32 rows + weights): released by the transform warps; B ring (BF16 hi/lo of the unweighted
+      // side): released by the tensor core.  The A ring therefore refills as soon as a k-block is transformed.
+      long g = 0, issued_a = 0, issued_b = 0;
       bool ok = true;
       for (long it = blockIdx.x; it < items && ok; it += gridDim.x) {
         int bm, bn, pair, ks;
         decode_item(it, n_tiles, ksplit, bm, bn, pair, ks);
         const int kb0 = (int)((long)nk * ks / ksplit), nki = (int)((long)nk * (ks + 1) / ksplit) - kb0;
         for (int kb = 0; kb < nki; ++kb, ++g) {
-          const int s = (int)(g % SRC_STAGES);
-          const long u = g / SRC_STAGES;
-          if (u > 0 && !mbar_wait(src_empty[s], (uint32_t)((u - 1) & 1), err, 11)) { ok = false; break; }
-          if (*(volatile int*)&s_abort) { ok = false; break; }
-          const uint32_t st = src0 + s * SRC_BYTES;
-          mbar_expect_tx(src_full[s], TX_BYTES);
           const int kx = (kb0 + kb) * BK;
-          tma_load_2d(st, &maps.a, kx, bm * BM, src_full[s]);
-          tma_load_2d(st + A_BYTES, &maps.bh, kx, bn * BM, src_full[s]);
-          tma_load_2d(st + A_BYTES + H_BYTES, &maps.bl, kx, bn * BM, src_full[s]);
-          tma_load_2d(st + W_OFF, &maps.w, kx, 2 * pair, src_full[s]);
-          issued = g + 1;
+          const int sa = (int)(g % A_STAGES);
+          const long ua = g / A_STAGES;
+          if (ua > 0 && !mbar_wait(bar(BAR_AE + sa), (uint32_t)((ua - 1) & 1), err, 11)) { ok = false; break; }
+          if (*(volatile int*)&s_abort) { ok = false; break; }
+          const uint32_t as = base + sa * AS_BYTES;
+          mbar_expect_tx(bar(BAR_AF + sa), A_TX);
+          tma_load_2d(as, &maps.a, kx, bm * BM, bar(BAR_AF + sa));
+          tma_load_2d(as + W_OFF, &maps.w, kx, 2 * pair, bar(BAR_AF + sa));
+          issued_a = g + 1;
+          const int sb = (int)(g % B_STAGES);
+          const long ub = g / B_STAGES;
+          if (ub > 0 && !mbar_wait(bar(BAR_BE + sb), (uint32_t)((ub - 1) & 1), err, 13)) { ok = false; break; }
+          if (*(volatile int*)&s_abort) { ok = false; break; }
+          const uint32_t bs = b0 + sb * BS_BYTES;
+          mbar_expect_tx(bar(BAR_BF + sb), B_TX);
+          tma_load_2d(bs, &maps.bh, kx, bn * BM, bar(BAR_BF + sb));
+          tma_load_2d(bs + H_BYTES, &maps.bl, kx, bn * BM, bar(BAR_BF + sb));
+          issued_b = g + 1;
         }
       }
       if (!ok) {
         s_abort = 1;
         // wait for the copies that may still be in flight (the latest phase of each stage)
-        for (long q = issued > SRC_STAGES ? issued - SRC_STAGES : 0; q < issued; ++q)
-          mbar_wait(src_full[q % SRC_STAGES], (uint32_t)((q / SRC_STAGES) & 1), err, 12);
+        for (long q = issued_a > A_STAGES ? issued_a - A_STAGES : 0; q < issued_a; ++q)
+          mbar_wait(bar(BAR_AF + (int)(q % A_STAGES)), (uint32_t)((q / A_STAGES) & 1), err, 12);
+        for (long q = issued_b > B_STAGES ? issued_b - B_STAGES : 0; q < issued_b; ++q)
+          mbar_wait(bar(BAR_BF + (int)(q % B_STAGES)), (uint32_t)((q / B_STAGES) & 1), err, 14);
       }
     }
   } else if (warp == 13) {
     if (lane == 0) {
       // ------------------------------------------------------------ MMA issuer
       long g = 0;
-      long cf[2] = {0, 0};                 // chunks started per entry
+      long cf0 = 0, cf1 = 0;               // chunks started per entry
       bool ok = true;
       for (long it = blockIdx.x; it < items && ok; it += gridDim.x) {
         int bm, bn, pair, ks;
@@ -206,21 +221,23 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int nf = min(2, nb - 2 * pair);
         const int nki = (int)((long)nk * (ks + 1) / ksplit) - (int)((long)nk * ks / ksplit);
         for (int kb = 0; kb < nki && ok; ++kb, ++g) {
-          const int s = (int)(g % SRC_STAGES), ts = (int)(g % TR_STAGES);
-          if (*(volatile int*)&s_abort || !mbar_wait(src_full[s], (uint32_t)((g / SRC_STAGES) & 1), err, 21) ||
-              !mbar_wait(tr_full[ts], (uint32_t)((g / TR_STAGES) & 1), err, 22)) {
+          const int sb = (int)(g % B_STAGES), ts = (int)(g % TR_STAGES);
+          if (*(volatile int*)&s_abort ||
+              !mbar_wait(bar(BAR_BF + sb), (uint32_t)((g / B_STAGES) & 1), err, 21) ||
+              !mbar_wait(bar(BAR_TF + ts), (uint32_t)((g / TR_STAGES) & 1), err, 22)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t sb = src0 + s * SRC_BYTES, tb = tr0 + ts * TR_BYTES;
+          const uint32_t bb = b0 + sb * BS_BYTES, tb = tr0 + ts * TR_BYTES;
           for (int o = 0; o < 2 && ok; ++o) {
             const int f = entry_at(kb, o);
             if (f >= nf) continue;
             const bool first = chunk_first(f, kb);
             if (first) {
-              if (cf[f] > 0 && !mbar_wait(acc_empty[f], (uint32_t)((cf[f] - 1) & 1), err, 23)) { ok = false; break; }
-              ++cf[f];
+              const long cf = f ? cf1 : cf0;
+              if (cf > 0 && !mbar_wait(bar(BAR_ACCE + f), (uint32_t)((cf - 1) & 1), err, 23)) { ok = false; break; }
+              if (f) ++cf1; else ++cf0;
               tc_fence_after();
             }
             const uint32_t d = tmem + (uint32_t)(f * 128);
@@ -229,23 +246,23 @@ __global__ void __launch_bounds__(THREADS, 1)
               const uint32_t off = k * 32;
               const uint64_t ah = sdesc(tb + (2 * f) * H_BYTES + off, SBO64, SWZ64);
               const uint64_t al = sdesc(tb + (2 * f + 1) * H_BYTES + off, SBO64, SWZ64);
-              const uint64_t bh = sdesc(sb + A_BYTES + off, SBO64, SWZ64);
-              const uint64_t bl = sdesc(sb + A_BYTES + H_BYTES + off, SBO64, SWZ64);
+              const uint64_t bh = sdesc(bb + off, SBO64, SWZ64);
+              const uint64_t bl = sdesc(bb + H_BYTES + off, SBO64, SWZ64);
               mma_bf16(d, ah, bh, IDESC, (first && k == 0) ? 0u : 1u);
               mma_bf16(d, ah, bl, IDESC, 1u);
               mma_bf16(d, al, bh, IDESC, 1u);
             }
-            if (chunk_last(f, kb, nki)) mma_commit(acc_full[f]);
+            if (chunk_last(f, kb, nki)) mma_commit(bar(BAR_ACCF + f));
           }
           if (!ok) break;
-          mma_commit(src_empty[s]);
-          mma_commit(tr_empty[ts]);
+          mma_commit(bar(BAR_BE + sb));
+          mma_commit(bar(BAR_TE + ts));
         }
       }
       if (!ok) s_abort = 1;
-      // every tensor-core operation issued above has completed once `fin` flips
-      mma_commit(fin);
-      mbar_wait(fin, 0, err, 24);
+      // every tensor-core operation issued above has completed once the final barrier flips
+      mma_commit(bar(BAR_FIN));
+      mbar_wait(bar(BAR_FIN), 0, err, 24);
     }
   } else if (warp >= 4) {
     // -------------------------------------------------------------- transform: two threads per row of the tile,
@@ -260,12 +277,12 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int nf = min(2, nb - 2 * pair);
       const int nki = (int)((long)nk * (ks + 1) / ksplit) - (int)((long)nk * ks / ksplit);
       for (int kb = 0; kb < nki; ++kb, ++g) {
-        const int s = (int)(g % SRC_STAGES), ts = (int)(g % TR_STAGES);
-        bool w_ok = !*(volatile int*)&s_abort && mbar_wait(src_full[s], (uint32_t)((g / SRC_STAGES) & 1), err, 31);
+        const int sa = (int)(g % A_STAGES), ts = (int)(g % TR_STAGES);
+        bool w_ok = !*(volatile int*)&s_abort && mbar_wait(bar(BAR_AF + sa), (uint32_t)((g / A_STAGES) & 1), err, 31);
         if (w_ok && g >= TR_STAGES)
-          w_ok = mbar_wait(tr_empty[ts], (uint32_t)((g / TR_STAGES - 1) & 1), err, 32);
+          w_ok = mbar_wait(bar(BAR_TE + ts), (uint32_t)((g / TR_STAGES - 1) & 1), err, 32);
         if (!__all_sync(0xffffffffu, w_ok)) { ok = false; break; }
-        const uint8_t* sp = smem + s * SRC_BYTES;
+        const uint8_t* sp = smem + sa * AS_BYTES;
         const float* wrow = reinterpret_cast<const float*>(sp + W_OFF);
         constexpr int HK = BK / 2;
         float a[HK];
@@ -278,7 +295,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           a[4 * c + 2] = v.z;
           a[4 * c + 3] = v.w;
         }
-        uint8_t* tp = smem + SRC_STAGES * SRC_BYTES + ts * TR_BYTES;
+        uint8_t* tp = smem + TR_OFF + ts * TR_BYTES;
         for (int f = 0; f < nf; ++f) {
           float wv[HK];                        // the entry's weights for these columns (broadcast reads)
 #pragma unroll
@@ -309,8 +326,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         fence_async_smem();
         __syncwarp();
         if (lane == 0) {
-          mbar_arrive(tr_full[ts]);
-          mbar_arrive(src_empty[s]);
+          mbar_arrive(bar(BAR_TF + ts));
+          mbar_arrive(bar(BAR_AE + sa));
         }
       }
     }
@@ -318,7 +335,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else {
     // -------------------------------------------------------------- drain + epilogue (TMEM lane quarter = warp)
     const int q = warp;
-    long gd[2] = {0, 0};                  // drains done per entry
+    long gd0 = 0, gd1 = 0;                // drains done per entry
     bool ok = true;
     for (long it = blockIdx.x; it < items && ok; it += gridDim.x) {
       int bm, bn, pair, ks;
@@ -333,7 +350,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           if (f >= nf || !chunk_last(f, kb, nki)) continue;
           const bool first_of_item = chunk_first_of_item(f, kb);
           const bool final = kb == nki - 1;
-          bool w_ok = !*(volatile int*)&s_abort && mbar_wait(acc_full[f], (uint32_t)(gd[f] & 1), err, 41);
+          bool w_ok = !*(volatile int*)&s_abort && mbar_wait(bar(BAR_ACCF + f), (uint32_t)((f ? gd1 : gd0) & 1), err, 41);
           if (!__all_sync(0xffffffffu, w_ok)) { ok = false; break; }
           tc_fence_after();
           const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
@@ -388,8 +405,8 @@ __global__ void __launch_bounds__(THREADS, 1)
           if (!final) tmem_wait_st();
           tc_fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive(acc_empty[f]);
-          ++gd[f];
+          if (lane == 0) mbar_arrive(bar(BAR_ACCE + f));
+          if (f) ++gd1; else ++gd0;
         }
       }
     }
@@ -554,8 +571,8 @@ cudaError_t tc_pi_fused(const float* B, long ldb, int n, int K, const float* w, 
   auto feasible = [&](int ks) {
     return ks == 1 || (part && (size_t)ks * per_split <= part_bytes && nk / ks >= 4);
   };
-  if (ksplit > 0) {                        // forced
-    if (!feasible(ksplit)) return cudaErrorInvalidValue;
+  if (ksplit > 0) {                        // forced: the largest feasible split not above the request
+    while (ksplit > 1 && !feasible(ksplit)) ksplit /= 2;
     if (chosen) *chosen = ksplit;
     return pf_launch(maps, n, K, nb, mode_even, mode_odd, out, out_bstride, ldo, ksplit, part, part_bytes, err, s,
                      max_ctas);

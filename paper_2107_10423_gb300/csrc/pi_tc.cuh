@@ -4,7 +4,7 @@
 #include <cuda_bf16.h>
 
 namespace gw {
-enum { TC_EPI_STORE = 0, TC_EPI_CPAIR = 1, TC_EPI_EMBED = 2, TC_EPI_AXPBY = 3, TC_EPI_WRED = 4 };
+enum { TC_EPI_STORE = 0, TC_EPI_CPAIR = 1, TC_EPI_EMBED = 2, TC_EPI_AXPBY = 3, TC_EPI_WRED = 4, TC_EPI_SUB2 = 5 };
 
 // Epilogue of the tensor-core GEMM (passed by value to the kernel).
 struct TcEpi {
@@ -37,6 +37,12 @@ struct TcEpi {
   const int* gidx;
   const float* bvec;
   int ldb;
+  // TC_EPI_SUB2: out_b[r][c] -= v[r][c] for rows r < half and out_b[plane + (r - half) * ldo + c] -= v[r][c] for
+  // the rows below (the two planes of a complex matrix updated by one stacked real product), batch stride
+  // out_bstride, row length ldo
+  long plane;
+  int half;
+  long limit;                 // TC_EPI_SUB2: elements writable from out (an index beyond it is recorded, code 66)
   // if not NULL: the whole launch does nothing when *run_if == 0 (device flag, read once at kernel start)
   const int* run_if;
 };

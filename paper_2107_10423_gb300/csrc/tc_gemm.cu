@@ -130,7 +130,8 @@ __device__ __forceinline__ void split_store(float v, __nv_bfloat16* hi, __nv_bfl
   if (lo2) lo2[o] = __float2bfloat16_rn(r - __bfloat162float(m));
 }
 
-__device__ void epilogue(const TcEpi& ep, const float* stg, int m0, int n0, int M, int N, int b, int lower) {
+__device__ void epilogue(const TcEpi& ep, const float* stg, int m0, int n0, int M, int N, int b, int lower,
+                         int* err) {
   if (ep.kind == TC_EPI_STORE) {
     const int mode = (b & 1) ? ep.mode_odd : ep.mode_even;
     float* o = ep.out + (long)b * ep.out_bstride;
@@ -190,6 +191,16 @@ __device__ void epilogue(const TcEpi& ep, const float* stg, int m0, int n0, int 
         for (int rr = 0; rr < BM && m0 + rr < M; ++rr) acc += (double)bv[m0 + rr] * stg[rr * (BN + 1) + cc];
         atomicAdd(ep.W + (long)n * ep.wld + ep.gidx[b], acc);
       }
+    }
+  } else if (ep.kind == TC_EPI_SUB2) {
+    float* o = ep.out + (long)b * ep.out_bstride;
+    for (int idx = threadIdx.x; idx < BM * BN; idx += THREADS) {
+      const int rr = idx / BN, cc = idx % BN;
+      const int m = m0 + rr, n = n0 + cc;
+      if (m >= M || n >= N) continue;
+      const long off = m < ep.half ? (long)m * ep.ldo + n : ep.plane + (long)(m - ep.half) * ep.ldo + n;
+      if ((long)b * ep.out_bstride + off >= ep.limit || off < 0) { atomicCAS(err, 0, 66); continue; }
+      o[off] -= stg[rr * (BN + 1) + cc];
     }
   } else if (ep.kind == TC_EPI_EMBED) {
     // real 2n embedding of (1 - Pi) z: rows 2j: u - (B w)_r, rows 2j+1: -v - (B w)_i
@@ -366,7 +377,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int j = 0; j < BN; ++j) stg[r * (BN + 1) + j] = acc[j];
   }
   __syncthreads();
-  if (all_ok) epilogue(ep, stg, m0, n0, M, N, b, lower);
+  if (all_ok) epilogue(ep, stg, m0, n0, M, N, b, lower, err);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {

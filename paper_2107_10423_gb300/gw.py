@@ -18,7 +18,8 @@ GW_INPUT_ON_DEVICE, GW_BORROW_DEVICE_PTRS = 1, 2
 
 EXPORTED = ["gw_config_default", "gw_plan_create", "gw_polarizability", "gw_sigma_cd", "gw_residues_minres",
             "gw_qp_solve", "gw_grid", "gw_w_table", "gw_w_table_noalloc", "gw_get_stats", "gw_plan_destroy", "gw_last_error",
-            "gw_plan_footprint", "gw_evgw", "gw_set_shard", "gw_shard_columns", "gw_plan_create_uks"]
+            "gw_plan_footprint", "gw_evgw", "gw_set_shard", "gw_shard_columns", "gw_plan_create_uks",
+            "gw_sigma_points"]
 
 
 class GWError(RuntimeError):
@@ -77,6 +78,7 @@ def load(path: str = LIB_PATH):
     lib.gw_polarizability.argtypes = [_P, _P, ctypes.c_int, _P]
     lib.gw_sigma_cd.argtypes = [_P, _P, _P, _P, _P]
     lib.gw_residues_minres.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P, _P, _P]
+    lib.gw_sigma_points.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P]
     lib.gw_qp_solve.argtypes = [_P, ctypes.c_int, _P, _P, _P]
     lib.gw_evgw.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P, _P, _P]
     lib.gw_evgw.restype = ctypes.c_int
@@ -244,6 +246,14 @@ class Plan:
         sc, dsc, sx = (np.empty(self.n_t) for _ in range(3))
         self._check(self._lib.gw_sigma_cd(self._h, _ptr(om), _ptr(sc), _ptr(dsc), _ptr(sx)))
         return sc, dsc, sx
+
+    def sigma_points(self, target_idx, omega):
+        """Sigma_c and dSigma_c/domega at arbitrary (target, omega) pairs in one batched evaluation."""
+        t = np.ascontiguousarray(target_idx, dtype=np.int32)
+        om = np.ascontiguousarray(omega, dtype=np.float64)
+        sc, dsc = np.empty(len(t)), np.empty(len(t))
+        self._check(self._lib.gw_sigma_points(self._h, len(t), _ptr(t), _ptr(om), _ptr(sc), _ptr(dsc)))
+        return sc, dsc
 
     def residues(self, target_idx, m, x):
         t = np.ascontiguousarray(target_idx, dtype=np.int32)

@@ -122,6 +122,29 @@ def test_double_float_refinement_residual_matches_fp64(gw):
     assert np.abs(out[1] - ref["e_qp"]).max() < 1 * MEV, np.abs(out[1] - ref["e_qp"]).max() / MEV
 
 
+@pytest.mark.parametrize("n", [1, 3])
+def test_mixed_dense_fallback_blocked_lu(gw, n):
+    """Residues forced through the mixed dense fallback, whose FP32 LU runs in 64-column panels with the trailing
+    updates on the tensor cores (N_aux 126: one update of 62 rows; N_aux 378: five updates and a ragged last
+    panel), refined against the FP64 operator: W and dW against the oracle's dense complex solve (Sec. 3.3)."""
+    s = synth.water_cluster(n, 9)
+    B, Bn = s.b_ia(), s.b_nm()
+    ti = np.array([0, 1, 1, 0])
+    m = np.array([2, 7, 4, s.n_occ])
+    x = np.array([0.3, -0.9, 1.7, 0.62])
+    with gw.Plan(s.eps, s.n_occ, B, Bn, s.targets, precision=gw.GW_PREC_MIXED, minres_maxit=2, minres_tol=1e-14,
+                 minres_fallback_tol=1e-13) as p:
+        r = p.residues(ti, m, x)
+    assert np.all(r["used_fallback"] == 1)
+    for j in range(len(ti)):
+        w, dw = O.w_corr_and_deriv(O.pi_complex(s.eps, s.n_occ, B, x[j], 1e-3),
+                                   O.dpi_complex(s.eps, s.n_occ, B, x[j], 1e-3), Bn[ti[j], m[j]])
+        print("fallback W error", abs(r["w_re"][j] - w.real), " dW error", abs(r["dw_re"][j] - dw.real))
+        assert abs(r["w_re"][j] - w.real) < 2e-6 * max(1, abs(w)), (j, r["w_re"][j], w)
+        assert abs(r["w_im"][j] - w.imag) < 2e-6 * max(1, abs(w)), (j, r["w_im"][j], w)
+        assert abs(r["dw_re"][j] - dw.real) < 1e-4 * max(1, abs(dw)), (j, r["dw_re"][j], dw)
+
+
 def test_chunked_workspace_mixed_vs_oracle(gw):
     """The chunked code that full-size mixed jobs run, forced on (H2O)_3 by a 12 MiB workspace cap: two frequency
     matrices per Newton-Schulz chunk (65 chunks), so the difference-form columns of the lowest grid points span many

@@ -30,7 +30,10 @@ def test_graphical_fp64_vs_oracle(gw):
 
 
 def test_cluster_layer_fp64_vs_oracle(gw):
-    s = synth.water_cluster(3, 33, targets=[0, 1, 2, 13, 14])      # three O1s-like levels and two valence ones
+    # three O1s-like levels (one cluster), a valence level alone and the two lowest virtuals (one cluster); each
+    # of them converges well inside qp_maxit in the oracle (22-27 Sigma evaluations), so the comparison does not
+    # depend on rounding-sensitive paths of states with tiny |Z|
+    s = synth.water_cluster(3, 33, targets=[0, 1, 2, 9, 16, 17])
     B, Bn = s.b_ia(), s.b_nm()
     ref = O.g0w0_cd(s.eps, s.n_occ, B, Bn, s.targets, eta=1e-3, qp_tol=1e-7, cluster_gap=0.5)
     with gw.Plan(s.eps, s.n_occ, B, Bn, s.targets, qp_tol=1e-7, qp_cluster_gap=0.5, **TIGHT) as p:
