@@ -165,6 +165,19 @@ gw_status gw_polarizability(gw_plan_t plan, const double* xi, int n_xi, double* 
 gw_status gw_sigma_cd(gw_plan_t plan, const double* omega, double* sigma_c, double* dsigma_c,
                       double* sigma_x);
 
+/* Sigma_c and its omega-derivative by spectral decomposition (Sec. 2.2 and 3.2, the Casida route the paper uses
+ * for small systems): the Hermitian Casida problem D^1/2 (D + 4 B_ia^T B_ia) D^1/2 T = T Omega^2 over the pairs
+ * (both spin channels for an open-shell plan) is diagonalised once per plan in FP64 (cyclic Jacobi, to 1e-13
+ * relative off-diagonal norm), then
+ *   Sigma_c(omega) = sum_m sum_s w_nms^2 / (omega - e_m +/- Omega_s -/+ i eta)  (upper signs for occupied m),
+ *   w_nms = b_nm . V_s / sqrt(2 Omega_s),  V = 2 B_ia D^1/2 T.
+ * target_idx[p] (or NULL: point p is target p, n_points = n_targets) and omega[p] (host); sigma_c, dsigma_c host
+ * [n_points] (real parts), either may be NULL.  O(N_ov^3) work and 2 N_ov^2 doubles: GW_ERR_ARG above
+ * N_ov = 16384; GW_ERR_NOT_CONVERGED if 40 Jacobi sweeps do not converge.  The Casida solution is kept until W's
+ * energies change (evGW). */
+gw_status gw_sigma_sd(gw_plan_t plan, int n_points, const int* target_idx, const double* omega, double* sigma_c,
+                      double* dsigma_c);
+
 /* Sigma_c and its omega-derivative at n_points arbitrary (target, frequency) pairs, all in one batched evaluation
  * (the same I term, residue list and batched MINRES as gw_sigma_cd; the graphical solution of Sec. 3.4 samples its
  * windows this way).  target_idx[p] in [0, n_targets), omega[p] in Ha (host, [n_points]); sigma_c, dsigma_c host

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgw.so")
-CU_SOURCES = ["gw_plan.cu", "kernels_dense.cu", "kernels_cd.cu", "kernels_lu.cu", "tc_gemm.cu", "pi_fused.cu"]
+CU_SOURCES = ["gw_plan.cu", "kernels_dense.cu", "kernels_cd.cu", "kernels_lu.cu", "tc_gemm.cu", "pi_fused.cu", "kernels_sd.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
 

@@ -101,6 +101,20 @@ void launch_minres_finish(const double* B_nm, int n_bas, int n_aux, const int* r
 // Batched complex LU with partial pivoting (kernels_lu.cu): matrices b at Ar + b*stride, Ai + b*stride.
 template <typename T>
 void launch_zlu(T* Ar, T* Ai, long stride, int n, int batch, int* piv, int* info, cudaStream_t s);
+// Spectral-decomposition route (kernels_sd.cu): the Casida matrix M = D^1/2 (D + 4 B^T B) D^1/2 [Np][Np] (Np = N
+// rounded up to even, identity padding) and T = I; one cyclic Jacobi sweep of M (rotations accumulated in T, cs [Np]
+// work space); off[0] / off[1] = squared off-diagonal / diagonal Frobenius norms; Omega [N], V = 2 B D^1/2 T
+// [n_aux][N] and the pole weights w2[r][s] = (Bn_r . V_s)^2 / (2 Omega_s) for the R rows of Bn; Sigma_c and its
+// derivative at evaluation points (target tmap[p] at omega[p]) from those weights.
+cudaError_t sd_casida_matrix(const double* B, const double* Dk, int n_aux, int N, int Np, double* M, double* T,
+                             cudaStream_t s);
+cudaError_t sd_jacobi_sweep(double* M, double* T, int Np, double* cs, cudaStream_t s);
+cudaError_t sd_offdiag(const double* M, int Np, double* off, cudaStream_t s);
+cudaError_t sd_weights(const double* B, const double* Dk, const double* M, const double* T, const double* Bn,
+                       int n_aux, int N, int Np, int R, double* Om, double* V, double* w2, cudaStream_t s);
+cudaError_t sd_sigma(const double* w2, const double* Om, int N, int n_bas, const double* eps, const int* tmap,
+                     const int* spin, const int* occ_t, int n_occ, const double* omega, int npts, double eta,
+                     double* S, double* dS, cudaStream_t s);
 // Blocked FP32 LU of `batch` complex matrices (planes A and A + plane, matrix stride `stride`) with the trailing
 // updates on the tensor cores; same factors and pivot convention as launch_zlu.  work: work_elems BF16, at least
 // zlu_tc_work_elems(n, 1) (one matrix's split panel operands); the updates run in sub-batches that fit it.

@@ -70,6 +70,10 @@ struct gw_plan {
   __nv_bfloat16* d_Bnlo = nullptr;
   __nv_bfloat16* d_Bnlo2 = nullptr;
   bool screening_done = false;
+  // spectral-decomposition route (gw_sigma_sd): Casida matrix and eigenvectors, pole weights; valid while sd_done
+  DevBuf sd_M, sd_T, sd_cs, sd_off, sd_Om, sd_V, sd_w2, sd_tmap, sd_om, sd_S, sd_dS;
+  bool sd_done = false;
+  int sd_sweeps = 0;
   // sharding across ranks (gw_set_shard): frequency positions [sh_p0, sh_p1) of the imaginary-axis stage and the
   // residue right-hand sides j with j % sh_world == sh_rank; sums across ranks through sh_reduce
   int sh_rank = 0, sh_world = 1;
@@ -101,7 +105,7 @@ struct gw_plan {
     DevBuf* all[] = {&ws_mat, &ws_info, &ws_scratch, &ws_gout, &ws_xi, &tc_part, &tc_kind, &tc_par, &tc_err, &tc_w, &ns_E, &ns_X, &ns_X2, &ns_Xa, &ns_Xb, &ns_T, &ns_lam, &ns_E0, &ns_vec, &mr_V, &mr_U, &mr_S, &mr_vprev,
                      &mr_v, &mr_d1, &mr_d2, &mr_x, &mr_st, &mr_rt, &mr_rm, &mr_xf, &mr_wre, &mr_wim,
                      &mr_dwre, &mr_it, &mr_res, &mr_cnt, &mr_Vhi, &mr_Vlo, &mr_Uhi, &mr_Ulo, &mr_Vlo2, &mr_Ulo2, &mr_V64, &sg_I, &sg_dI, &sg_R, &sg_dR, &sg_om, &sg_start,
-                     &sg_coef, &sg_act, &sg_tmap, &qp_st, &qp_om0, &fb_A, &fb_y, &fb_piv, &fb_info, &fb_idx, &fb_y64, &fb_V32, &fb_S32, &fb_Vp, &fb_Up, &fb_x, &fb_V64, &fb_U64, &fb_S64, &fb_sel, &fb_pos, &fb_rho, &fb_xs, &fb_Bh, &fb_Bl, &fb_lu};
+                     &sg_coef, &sg_act, &sg_tmap, &qp_st, &qp_om0, &fb_A, &fb_y, &fb_piv, &fb_info, &fb_idx, &fb_y64, &fb_V32, &fb_S32, &fb_Vp, &fb_Up, &fb_x, &fb_V64, &fb_U64, &fb_S64, &fb_sel, &fb_pos, &fb_rho, &fb_xs, &fb_Bh, &fb_Bl, &fb_lu, &sd_M, &sd_T, &sd_cs, &sd_off, &sd_Om, &sd_V, &sd_w2, &sd_tmap, &sd_om, &sd_S, &sd_dS};
     bufs.assign(all, all + sizeof(all) / sizeof(all[0]));
   }
 };
@@ -1190,6 +1194,7 @@ gw_status set_pair_energies(gw_plan* P, const double* eps, const double* eps_b =
     for (int i = 0; i < n_occ; ++i)
       for (int a = 0; a < n_virt; ++a) D.push_back(e[n_occ + a] - e[i]);
   }
+  P->sd_done = false;             // the Casida poles follow W's energies
   return set_pair_table(P, D);
 }
 
@@ -1597,6 +1602,81 @@ gw_status gw_sigma_cd(gw_plan_t P, const double* omega, double* sigma_c, double*
   return GW_OK;
 }
 
+// Spectral decomposition (Sec. 2.2, 3.2): the Hermitian Casida matrix M = D^1/2 (D + 4K) D^1/2 (K = B^T B over the
+// pairs of every spin channel side by side; an open-shell plan stores each channel scaled by 1/sqrt 2, which turns
+// the factor 4 into the 2 of each spin block) diagonalised by cyclic Jacobi sweeps in FP64 until the off-diagonal
+// Frobenius norm is below 1e-13 of the diagonal one, then Omega_s and the pole weights of every (target, state).
+constexpr long kSdMaxPairs = 16384;       // O(N_ov^3) work and 2 N_ov^2 doubles of storage
+gw_status ensure_sd(gw_plan* P) {
+  if (P->sd_done) return GW_OK;
+  const long N = P->n_ov;
+  if (N > kSdMaxPairs)
+    return fail(P, GW_ERR_ARG, "spectral decomposition needs N_ov <= %ld (got %ld): O(N_ov^3)", kSdMaxPairs, N);
+  const int n = P->cfg.n_aux, Np = (int)(N + (N & 1));
+  TRY(ensure(P, P->sd_M, sizeof(double) * (size_t)Np * Np));
+  TRY(ensure(P, P->sd_T, sizeof(double) * (size_t)Np * Np));
+  TRY(ensure(P, P->sd_cs, sizeof(double) * (size_t)Np));
+  TRY(ensure(P, P->sd_off, sizeof(double) * 2));
+  TRY(ensure(P, P->sd_Om, sizeof(double) * (size_t)N));
+  TRY(ensure(P, P->sd_V, sizeof(double) * (size_t)n * N));
+  const int R = P->n_t * P->n_bas;
+  TRY(ensure(P, P->sd_w2, sizeof(double) * (size_t)R * N));
+  LAUNCH(CK(gw::sd_casida_matrix(P->d_B_ia, P->d_D, n, (int)N, Np, as<double>(P->sd_M), as<double>(P->sd_T),
+                                 P->stream)));
+  double off[2] = {1.0, 1.0};
+  int sweeps = 0;
+  for (; sweeps < 40; ++sweeps) {
+    CK(gw::sd_offdiag(as<double>(P->sd_M), Np, as<double>(P->sd_off), P->stream));
+    CK(cudaMemcpyAsync(off, P->sd_off.p, sizeof(off), cudaMemcpyDeviceToHost, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+    if (!(off[0] > 1e-26 * off[1])) break;
+    CK(gw::sd_jacobi_sweep(as<double>(P->sd_M), as<double>(P->sd_T), Np, as<double>(P->sd_cs), P->stream));
+    P->stats.n_kernel_launches += 4 * (Np - 1) + 1;
+  }
+  if (!(off[0] <= 1e-26 * off[1]))
+    return fail(P, GW_ERR_NOT_CONVERGED, "Jacobi sweeps of the Casida matrix did not converge (off/diag %g)",
+                std::sqrt(off[0] / off[1]));
+  LAUNCH(CK(gw::sd_weights(P->d_B_ia, P->d_D, as<double>(P->sd_M), as<double>(P->sd_T), P->d_B_nm, n, (int)N, Np, R,
+                           as<double>(P->sd_Om), as<double>(P->sd_V), as<double>(P->sd_w2), P->stream)));
+  CK(cudaStreamSynchronize(P->stream));
+  P->sd_sweeps = sweeps;
+  P->sd_done = true;
+  return GW_OK;
+}
+
+gw_status gw_sigma_sd(gw_plan_t P, int n_points, const int* target_idx, const double* omega, double* sigma_c,
+                      double* dsigma_c) {
+  if (!P) return GW_ERR_ARG;
+  if (n_points < 0 || (n_points > 0 && !omega)) return fail(P, GW_ERR_ARG, "bad point list");
+  if (n_points == 0) return GW_OK;
+  std::vector<int> tmap(n_points);
+  for (int p = 0; p < n_points; ++p) {
+    tmap[p] = target_idx ? target_idx[p] : p;
+    if (tmap[p] < 0 || tmap[p] >= P->n_t) return fail(P, GW_ERR_ARG, "target_idx[%d] out of range", p);
+    if (!std::isfinite(omega[p])) return fail(P, GW_ERR_ARG, "omega[%d] not finite", p);
+  }
+  if (!target_idx && n_points != P->n_t) return fail(P, GW_ERR_ARG, "without target_idx, n_points = n_targets");
+  TRY(ensure_sd(P));
+  TRY(ensure(P, P->sd_tmap, sizeof(int) * n_points));
+  TRY(ensure(P, P->sd_om, sizeof(double) * n_points));
+  TRY(ensure(P, P->sd_S, sizeof(double) * n_points));
+  TRY(ensure(P, P->sd_dS, sizeof(double) * n_points));
+  CK(cudaMemcpyAsync(P->sd_tmap.p, tmap.data(), sizeof(int) * n_points, cudaMemcpyHostToDevice, P->stream));
+  CK(cudaMemcpyAsync(P->sd_om.p, omega, sizeof(double) * n_points, cudaMemcpyHostToDevice, P->stream));
+  LAUNCH(CK(gw::sd_sigma(as<double>(P->sd_w2), as<double>(P->sd_Om), (int)P->n_ov, P->n_bas, P->d_eps_g,
+                         as<int>(P->sd_tmap), P->d_spin, P->d_occ_t, P->cfg.n_occ, as<double>(P->sd_om), n_points,
+                         P->cfg.eta, as<double>(P->sd_S), as<double>(P->sd_dS), P->stream)));
+  std::vector<double> S(n_points), dS(n_points);
+  CK(cudaMemcpyAsync(S.data(), P->sd_S.p, sizeof(double) * n_points, cudaMemcpyDeviceToHost, P->stream));
+  CK(cudaMemcpyAsync(dS.data(), P->sd_dS.p, sizeof(double) * n_points, cudaMemcpyDeviceToHost, P->stream));
+  CK(cudaStreamSynchronize(P->stream));
+  for (int p = 0; p < n_points; ++p) {
+    if (sigma_c) sigma_c[p] = S[p];
+    if (dsigma_c) dsigma_c[p] = dS[p];
+  }
+  return GW_OK;
+}
+
 gw_status gw_sigma_points(gw_plan_t P, int n_points, const int* target_idx, const double* omega, double* sigma_c,
                           double* dsigma_c) {
   if (!P) return GW_ERR_ARG;
@@ -1738,7 +1818,7 @@ gw_status graphical_scan(gw_plan* P, const std::vector<double>& c, const std::ve
     if (k + 1 >= om.size() || tmap[k + 1] != t) continue;
     const double f0 = P->h_en[t] + P->h_shift[t] + R[k] - I[k] - om[k];
     const double f1 = P->h_en[t] + P->h_shift[t] + R[k + 1] - I[k + 1] - om[k + 1];
-    if (f0 > 0.0 >= f1 || (f0 == 0.0 && f1 < 0.0)) {
+    if ((f0 > 0.0 && f1 <= 0.0) || (f0 == 0.0 && f1 < 0.0)) {
       const double r = om[k] + (om[k + 1] - om[k]) * f0 / (f0 - f1);
       if (!found[t] || std::fabs(r - c[t]) < std::fabs(root[t] - c[t])) root[t] = r;
       found[t] = 1;

@@ -19,7 +19,7 @@ GW_INPUT_ON_DEVICE, GW_BORROW_DEVICE_PTRS = 1, 2
 EXPORTED = ["gw_config_default", "gw_plan_create", "gw_polarizability", "gw_sigma_cd", "gw_residues_minres",
             "gw_qp_solve", "gw_grid", "gw_w_table", "gw_w_table_noalloc", "gw_get_stats", "gw_plan_destroy", "gw_last_error",
             "gw_plan_footprint", "gw_evgw", "gw_set_shard", "gw_shard_columns", "gw_plan_create_uks",
-            "gw_sigma_points"]
+            "gw_sigma_points", "gw_sigma_sd"]
 
 
 class GWError(RuntimeError):
@@ -79,6 +79,7 @@ def load(path: str = LIB_PATH):
     lib.gw_sigma_cd.argtypes = [_P, _P, _P, _P, _P]
     lib.gw_residues_minres.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P, _P, _P]
     lib.gw_sigma_points.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P]
+    lib.gw_sigma_sd.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P]
     lib.gw_qp_solve.argtypes = [_P, ctypes.c_int, _P, _P, _P]
     lib.gw_evgw.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P, _P, _P]
     lib.gw_evgw.restype = ctypes.c_int
@@ -253,6 +254,16 @@ class Plan:
         om = np.ascontiguousarray(omega, dtype=np.float64)
         sc, dsc = np.empty(len(t)), np.empty(len(t))
         self._check(self._lib.gw_sigma_points(self._h, len(t), _ptr(t), _ptr(om), _ptr(sc), _ptr(dsc)))
+        return sc, dsc
+
+    def sigma_sd(self, omega, target_idx=None):
+        """Sigma_c and dSigma_c/domega by spectral decomposition (Casida), at omega[t] for every target, or at
+        (target_idx[p], omega[p]) pairs."""
+        om = np.ascontiguousarray(omega, dtype=np.float64)
+        t = None if target_idx is None else np.ascontiguousarray(target_idx, dtype=np.int32)
+        sc, dsc = np.empty(len(om)), np.empty(len(om))
+        self._check(self._lib.gw_sigma_sd(self._h, len(om), None if t is None else _ptr(t), _ptr(om), _ptr(sc),
+                                          _ptr(dsc)))
         return sc, dsc
 
     def residues(self, target_idx, m, x):
