@@ -172,32 +172,33 @@ __global__ void __launch_bounds__(THREADS, 1)
       // ------------------------------------------------------------ TMA producer
       // A ring (FP32 rows + weights): released by the transform warps; B ring (BF16 hi/lo of the unweighted
       // side): released by the tensor core.  The A ring therefore refills as soon as a k-block is transformed.
-      long g = 0, issued_a = 0, issued_b = 0;
+      // ring positions kept as stage indices and phase bits (no divisions in the loop)
+      long issued_a = 0, issued_b = 0;
+      uint32_t sa = 0, pa = 0, sb = 0, pbb = 0;
+      bool a_wrapped = false, b_wrapped = false;
       bool ok = true;
       for (long it = blockIdx.x; it < items && ok; it += gridDim.x) {
         int bm, bn, pair, ks;
         decode_item(it, n_tiles, ksplit, bm, bn, pair, ks);
         const int kb0 = (int)((long)nk * ks / ksplit), nki = (int)((long)nk * (ks + 1) / ksplit) - kb0;
-        for (int kb = 0; kb < nki; ++kb, ++g) {
+        for (int kb = 0; kb < nki; ++kb) {
           const int kx = (kb0 + kb) * BK;
-          const int sa = (int)(g % A_STAGES);
-          const long ua = g / A_STAGES;
-          if (ua > 0 && !mbar_wait(bar(BAR_AE + sa), (uint32_t)((ua - 1) & 1), err, 11)) { ok = false; break; }
+          if (a_wrapped && !mbar_wait(bar(BAR_AE + sa), pa ^ 1u, err, 11)) { ok = false; break; }
           if (*(volatile int*)&s_abort) { ok = false; break; }
           const uint32_t as = base + sa * AS_BYTES;
           mbar_expect_tx(bar(BAR_AF + sa), A_TX);
           tma_load_2d(as, &maps.a, kx, bm * BM, bar(BAR_AF + sa));
           tma_load_2d(as + W_OFF, &maps.w, kx, 2 * pair, bar(BAR_AF + sa));
-          issued_a = g + 1;
-          const int sb = (int)(g % B_STAGES);
-          const long ub = g / B_STAGES;
-          if (ub > 0 && !mbar_wait(bar(BAR_BE + sb), (uint32_t)((ub - 1) & 1), err, 13)) { ok = false; break; }
+          ++issued_a;
+          if (++sa == A_STAGES) { sa = 0; pa ^= 1u; a_wrapped = true; }
+          if (b_wrapped && !mbar_wait(bar(BAR_BE + sb), pbb ^ 1u, err, 13)) { ok = false; break; }
           if (*(volatile int*)&s_abort) { ok = false; break; }
           const uint32_t bs = b0 + sb * BS_BYTES;
           mbar_expect_tx(bar(BAR_BF + sb), B_TX);
           tma_load_2d(bs, &maps.bh, kx, bn * BM, bar(BAR_BF + sb));
           tma_load_2d(bs + H_BYTES, &maps.bl, kx, bn * BM, bar(BAR_BF + sb));
-          issued_b = g + 1;
+          ++issued_b;
+          if (++sb == B_STAGES) { sb = 0; pbb ^= 1u; b_wrapped = true; }
         }
       }
       if (!ok) {
@@ -212,51 +213,54 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp == 13) {
     if (lane == 0) {
       // ------------------------------------------------------------ MMA issuer
-      long g = 0;
-      long cf0 = 0, cf1 = 0;               // chunks started per entry
+      // The issuing thread's work between MMAs limits the tensor core's throughput as soon as it exceeds one MMA's
+      // 64 cycles, so the loop keeps it minimal: ring positions as stage indices and phase bits, and shared-memory
+      // descriptors formed once and advanced by adding the byte offset >> 4 to their start-address field.
+      uint32_t sb = 0, pbb = 0, ts = 0, pt = 0;
+      uint32_t cf0 = 0, cf1 = 0;           // chunks started per entry
+      const uint64_t dB = sdesc(b0, SBO64, SWZ64), dT = sdesc(tr0, SBO64, SWZ64);
       bool ok = true;
       for (long it = blockIdx.x; it < items && ok; it += gridDim.x) {
         int bm, bn, pair, ks;
         decode_item(it, n_tiles, ksplit, bm, bn, pair, ks);
         const int nf = min(2, nb - 2 * pair);
         const int nki = (int)((long)nk * (ks + 1) / ksplit) - (int)((long)nk * ks / ksplit);
-        for (int kb = 0; kb < nki && ok; ++kb, ++g) {
-          const int sb = (int)(g % B_STAGES), ts = (int)(g % TR_STAGES);
-          if (*(volatile int*)&s_abort ||
-              !mbar_wait(bar(BAR_BF + sb), (uint32_t)((g / B_STAGES) & 1), err, 21) ||
-              !mbar_wait(bar(BAR_TF + ts), (uint32_t)((g / TR_STAGES) & 1), err, 22)) {
+        for (int kb = 0; kb < nki && ok; ++kb) {
+          if (*(volatile int*)&s_abort || !mbar_wait(bar(BAR_BF + sb), pbb, err, 21) ||
+              !mbar_wait(bar(BAR_TF + ts), pt, err, 22)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t bb = b0 + sb * BS_BYTES, tb = tr0 + ts * TR_BYTES;
-          for (int o = 0; o < 2 && ok; ++o) {
+          const uint64_t bh = dB + (uint64_t)((sb * BS_BYTES) >> 4), bl = bh + (uint64_t)(H_BYTES >> 4);
+          const uint64_t td = dT + (uint64_t)((ts * TR_BYTES) >> 4);
+#pragma unroll
+          for (int o = 0; o < 2; ++o) {
             const int f = entry_at(kb, o);
             if (f >= nf) continue;
             const bool first = chunk_first(f, kb);
             if (first) {
-              const long cf = f ? cf1 : cf0;
-              if (cf > 0 && !mbar_wait(bar(BAR_ACCE + f), (uint32_t)((cf - 1) & 1), err, 23)) { ok = false; break; }
+              const uint32_t cf = f ? cf1 : cf0;
+              if (cf > 0 && !mbar_wait(bar(BAR_ACCE + f), (cf - 1) & 1u, err, 23)) { ok = false; break; }
               if (f) ++cf1; else ++cf0;
               tc_fence_after();
             }
             const uint32_t d = tmem + (uint32_t)(f * 128);
+            const uint64_t ah = td + (uint64_t)((2 * f * H_BYTES) >> 4), al = ah + (uint64_t)(H_BYTES >> 4);
 #pragma unroll
-            for (int k = 0; k < BK / 16; ++k) {
-              const uint32_t off = k * 32;
-              const uint64_t ah = sdesc(tb + (2 * f) * H_BYTES + off, SBO64, SWZ64);
-              const uint64_t al = sdesc(tb + (2 * f + 1) * H_BYTES + off, SBO64, SWZ64);
-              const uint64_t bh = sdesc(bb + off, SBO64, SWZ64);
-              const uint64_t bl = sdesc(bb + H_BYTES + off, SBO64, SWZ64);
-              mma_bf16(d, ah, bh, IDESC, (first && k == 0) ? 0u : 1u);
-              mma_bf16(d, ah, bl, IDESC, 1u);
-              mma_bf16(d, al, bh, IDESC, 1u);
+            for (int k = 0; k < BK / 16; ++k) {        // K16 step k: 32 bytes further along each 64-byte row
+              const uint64_t o2 = (uint64_t)(2 * k);
+              mma_bf16(d, ah + o2, bh + o2, IDESC, (first && k == 0) ? 0u : 1u);
+              mma_bf16(d, ah + o2, bl + o2, IDESC, 1u);
+              mma_bf16(d, al + o2, bh + o2, IDESC, 1u);
             }
             if (chunk_last(f, kb, nki)) mma_commit(bar(BAR_ACCF + f));
           }
           if (!ok) break;
           mma_commit(bar(BAR_BE + sb));
           mma_commit(bar(BAR_TE + ts));
+          if (++sb == B_STAGES) { sb = 0; pbb ^= 1u; }
+          if (++ts == TR_STAGES) { ts = 0; pt ^= 1u; }
         }
       }
       if (!ok) s_abort = 1;
@@ -269,18 +273,17 @@ __global__ void __launch_bounds__(THREADS, 1)
     // each over 16 of the k-block's 32 columns
     const int t = threadIdx.x - 128;
     const int r = t & (BM - 1), h = t >> 7;
-    long g = 0;
+    uint32_t sa = 0, pa = 0, ts = 0, pt = 0;
+    bool t_wrapped = false;
     bool ok = true;
     for (long it = blockIdx.x; it < items && ok; it += gridDim.x) {
       int bm, bn, pair, ks;
       decode_item(it, n_tiles, ksplit, bm, bn, pair, ks);
       const int nf = min(2, nb - 2 * pair);
       const int nki = (int)((long)nk * (ks + 1) / ksplit) - (int)((long)nk * ks / ksplit);
-      for (int kb = 0; kb < nki; ++kb, ++g) {
-        const int sa = (int)(g % A_STAGES), ts = (int)(g % TR_STAGES);
-        bool w_ok = !*(volatile int*)&s_abort && mbar_wait(bar(BAR_AF + sa), (uint32_t)((g / A_STAGES) & 1), err, 31);
-        if (w_ok && g >= TR_STAGES)
-          w_ok = mbar_wait(bar(BAR_TE + ts), (uint32_t)((g / TR_STAGES - 1) & 1), err, 32);
+      for (int kb = 0; kb < nki; ++kb) {
+        bool w_ok = !*(volatile int*)&s_abort && mbar_wait(bar(BAR_AF + sa), pa, err, 31);
+        if (w_ok && t_wrapped) w_ok = mbar_wait(bar(BAR_TE + ts), pt ^ 1u, err, 32);
         if (!__all_sync(0xffffffffu, w_ok)) { ok = false; break; }
         const uint8_t* sp = smem + sa * AS_BYTES;
         const float* wrow = reinterpret_cast<const float*>(sp + W_OFF);
@@ -329,6 +332,8 @@ __global__ void __launch_bounds__(THREADS, 1)
           mbar_arrive(bar(BAR_TF + ts));
           mbar_arrive(bar(BAR_AE + sa));
         }
+        if (++sa == A_STAGES) { sa = 0; pa ^= 1u; }
+        if (++ts == TR_STAGES) { ts = 0; pt ^= 1u; t_wrapped = true; }
       }
     }
     if (!ok) s_abort = 1;

@@ -19,6 +19,7 @@ namespace gw {
 namespace {
 
 constexpr int BM = 128, BN = 128, BK = 64, THREADS = 192;
+constexpr int EPI_U = 8;         // epilogue elements per thread whose global reads are in flight together
 constexpr int TILE_BYTES = BM * BK * 2;               // one 128 x 64 BF16 tile = 16 KiB
 
 // NSP split parts per operand: 2 (hi, lo: products hh, hl, lh) or 3 (hi, mid, lo: the six products with
@@ -172,14 +173,23 @@ __device__ void epilogue(const TcEpi& ep, const float* stg, int m0, int n0, int 
       split_store(cr * ti + ci * tr, ep.ohi, ep.olo, (long)(m + 1) * ep.ldh + n, ep.olo2);
     }
   } else if (ep.kind == TC_EPI_AXPBY) {
-    for (int idx = threadIdx.x; idx < BM * BN; idx += THREADS) {
-      const int rr = idx / BN, cc = idx % BN;
-      const int m = m0 + rr, n = n0 + cc;
-      if (m >= M || n >= N) continue;
-      float y = ep.gamma * stg[rr * (BN + 1) + cc] + (m == n ? ep.beta : 0.f);
-      if (ep.xin) y += ep.alpha * ep.xin[(long)b * ep.x_bstride + (long)m * ep.ldo + n];
-      if (ep.out) ep.out[(long)b * ep.out_bstride + (long)m * ep.ldo + n] = y;
-      if (ep.ohi) split_store(y, ep.ohi, ep.olo, (long)b * ep.oh_bstride + (long)m * ep.ldh + n, ep.olo2);
+    // EPI_U elements per thread and pass: their global reads are issued together before any store
+    for (int base = threadIdx.x; base < BM * BN; base += THREADS * EPI_U) {
+      float xv[EPI_U];
+#pragma unroll
+      for (int u = 0; u < EPI_U; ++u) {
+        const int idx = base + u * THREADS, rr = idx / BN, cc = idx % BN, m = m0 + rr, n = n0 + cc;
+        xv[u] = (ep.xin && idx < BM * BN && m < M && n < N)
+                    ? ep.xin[(long)b * ep.x_bstride + (long)m * ep.ldo + n] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < EPI_U; ++u) {
+        const int idx = base + u * THREADS, rr = idx / BN, cc = idx % BN, m = m0 + rr, n = n0 + cc;
+        if (idx >= BM * BN || m >= M || n >= N) continue;
+        const float y = ep.gamma * stg[rr * (BN + 1) + cc] + (m == n ? ep.beta : 0.f) + ep.alpha * xv[u];
+        if (ep.out) ep.out[(long)b * ep.out_bstride + (long)m * ep.ldo + n] = y;
+        if (ep.ohi) split_store(y, ep.ohi, ep.olo, (long)b * ep.oh_bstride + (long)m * ep.ldh + n, ep.olo2);
+      }
     }
   } else if (ep.kind == TC_EPI_WRED) {
     // column n of the tile: sum over the tile's rows m of bvec[n][m] * v[m][n], added into W
@@ -194,22 +204,41 @@ __device__ void epilogue(const TcEpi& ep, const float* stg, int m0, int n0, int 
     }
   } else if (ep.kind == TC_EPI_SUB2) {
     float* o = ep.out + (long)b * ep.out_bstride;
-    for (int idx = threadIdx.x; idx < BM * BN; idx += THREADS) {
-      const int rr = idx / BN, cc = idx % BN;
-      const int m = m0 + rr, n = n0 + cc;
-      if (m >= M || n >= N) continue;
-      const long off = m < ep.half ? (long)m * ep.ldo + n : ep.plane + (long)(m - ep.half) * ep.ldo + n;
-      if ((long)b * ep.out_bstride + off >= ep.limit || off < 0) { atomicCAS(err, 0, 66); continue; }
-      o[off] -= stg[rr * (BN + 1) + cc];
+    for (int base = threadIdx.x; base < BM * BN; base += THREADS * EPI_U) {
+      long off[EPI_U];
+      float cv[EPI_U];
+#pragma unroll
+      for (int u = 0; u < EPI_U; ++u) {
+        const int idx = base + u * THREADS, rr = idx / BN, cc = idx % BN, m = m0 + rr, n = n0 + cc;
+        off[u] = -1;
+        if (idx < BM * BN && m < M && n < N) {
+          const long o1 = m < ep.half ? (long)m * ep.ldo + n : ep.plane + (long)(m - ep.half) * ep.ldo + n;
+          if ((long)b * ep.out_bstride + o1 >= ep.limit || o1 < 0) atomicCAS(err, 0, 66);
+          else off[u] = o1;
+        }
+        cv[u] = off[u] >= 0 ? o[off[u]] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < EPI_U; ++u) {
+        const int idx = base + u * THREADS, rr = idx / BN, cc = idx % BN;
+        if (off[u] >= 0) o[off[u]] = cv[u] - stg[rr * (BN + 1) + cc];
+      }
     }
   } else if (ep.kind == TC_EPI_EMBED) {
     // real 2n embedding of (1 - Pi) z: rows 2j: u - (B w)_r, rows 2j+1: -v - (B w)_i
-    for (int idx = threadIdx.x; idx < BM * BN; idx += THREADS) {
-      const int rr = idx / BN, cc = idx % BN;
-      const int m = m0 + rr, n = n0 + cc;
-      if (m >= M || n >= N) continue;
-      const float vin = ep.vin[(long)m * ep.ldv + n];
-      ep.out[(long)m * ep.ldo + n] = ((m & 1) ? -vin : vin) - stg[rr * (BN + 1) + cc];
+    for (int base = threadIdx.x; base < BM * BN; base += THREADS * EPI_U) {
+      float vv[EPI_U];
+#pragma unroll
+      for (int u = 0; u < EPI_U; ++u) {
+        const int idx = base + u * THREADS, rr = idx / BN, cc = idx % BN, m = m0 + rr, n = n0 + cc;
+        vv[u] = (idx < BM * BN && m < M && n < N) ? ep.vin[(long)m * ep.ldv + n] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < EPI_U; ++u) {
+        const int idx = base + u * THREADS, rr = idx / BN, cc = idx % BN, m = m0 + rr, n = n0 + cc;
+        if (idx >= BM * BN || m >= M || n >= N) continue;
+        ep.out[(long)m * ep.ldo + n] = ((m & 1) ? -vv[u] : vv[u]) - stg[rr * (BN + 1) + cc];
+      }
     }
   }
 }
