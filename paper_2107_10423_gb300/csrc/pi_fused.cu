@@ -10,9 +10,10 @@
 //
 // Design (one CTA per SM, persistent over work items = (lower tile, pair of batch entries)):
 //   * TMA streams, per 32-wide k-block, the FP32 rows of the weighted side (128 x 32) with the two weight rows
-//     (2 x 32) into a 3-stage A ring that the transform releases, and the BF16 hi/lo parts of the unweighted side
-//     (2 x 128 x 32) into a 4-stage B ring that the tensor core releases: the FP32 rows are refilled as soon as
-//     they are transformed instead of staying held until the tensor core has finished with the k-block.
+//     (2 x 32) into a 4-stage A ring that the transform releases, and the BF16 hi/lo tiles of the unweighted side
+//     (2 x 128 x 32) into a 3-stage S ring whose stages also hold the transformed tiles: one barrier tells the
+//     tensor core that a stage's B tiles have landed and its transformed tiles are written, and one commit frees
+//     both, so the issuing thread does one wait and one commit per k-block.
 //   * Two transform warpgroups (two threads per row) multiply the FP32 rows by the weights of both entries and
 //     splits the products into BF16 hi/lo tiles (64-byte swizzle, the tensor core's K-major layout) in a
 //     3-stage ring.  The weight never round-trips through HBM and the source tile serves both entries, which
@@ -42,21 +43,21 @@ namespace {
 using namespace ptx;
 
 constexpr int BM = 128, BK = 32;
-constexpr int A_STAGES = 3, B_STAGES = 4, TR_STAGES = 3;
+constexpr int A_STAGES = 4, S_STAGES = 3;
 constexpr int A_BYTES = BM * BK * 4;            // FP32 rows of the weighted side: 16 KiB
 constexpr int W_OFF = A_BYTES;                  // the two weight rows [2][BK] FP32 follow the FP32 tile
 constexpr int AS_BYTES = A_BYTES + 1024;        // 17 KiB per A stage (keeps every stage 1 KiB aligned)
 constexpr int H_BYTES = BM * BK * 2;            // one BF16 tile (128 rows x 64 bytes): 8 KiB
-constexpr int BS_BYTES = 2 * H_BYTES;           // B stage: hi and lo tiles of the unweighted side
-constexpr int TR_BYTES = 4 * H_BYTES;           // transformed tiles [entry][hi, lo]: 32 KiB
+// S stage: the BF16 hi/lo tiles of the unweighted side (TMA), then the transformed tiles [entry][hi, lo]
+constexpr int ST_OFF = 2 * H_BYTES;
+constexpr int SS_BYTES = 6 * H_BYTES;           // 48 KiB
 constexpr int A_TX = A_BYTES + 2 * BK * 4;
 constexpr int B_TX = 2 * H_BYTES;
-// mbarrier indices: A ring full/empty, B ring full/empty, transform ring full/empty, accumulators, final
-constexpr int BAR_AF = 0, BAR_AE = BAR_AF + A_STAGES, BAR_BF = BAR_AE + A_STAGES, BAR_BE = BAR_BF + B_STAGES,
-              BAR_TF = BAR_BE + B_STAGES, BAR_TE = BAR_TF + TR_STAGES, BAR_ACCF = BAR_TE + TR_STAGES,
-              BAR_ACCE = BAR_ACCF + 2, BAR_FIN = BAR_ACCE + 2, N_BARS = BAR_FIN + 1;
+// mbarrier indices: A ring full/empty, S ring full/empty, accumulators, final
+constexpr int BAR_AF = 0, BAR_AE = BAR_AF + A_STAGES, BAR_SF = BAR_AE + A_STAGES, BAR_SE = BAR_SF + S_STAGES,
+              BAR_ACCF = BAR_SE + S_STAGES, BAR_ACCE = BAR_ACCF + 2, BAR_FIN = BAR_ACCE + 2, N_BARS = BAR_FIN + 1;
 static_assert(N_BARS * 8 + 4 <= 256, "barrier area");
-constexpr int SMEM_BYTES = A_STAGES * AS_BYTES + B_STAGES * BS_BYTES + TR_STAGES * TR_BYTES + 256 + 1024;
+constexpr int SMEM_BYTES = A_STAGES * AS_BYTES + S_STAGES * SS_BYTES + 256 + 1024;
 static_assert(SMEM_BYTES <= 232448, "shared memory per block");
 constexpr int THREADS = 448;                    // warps 0-3 drain + epilogue, 4-11 transform, 12 TMA, 13 MMA
 constexpr int TR_WARPS = 8;
@@ -117,9 +118,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* smem = smem_raw + (base - raw);
-  constexpr int B_OFF = A_STAGES * AS_BYTES, TR_OFF = B_OFF + B_STAGES * BS_BYTES,
-                BAR_OFF = TR_OFF + TR_STAGES * TR_BYTES;
-  const uint32_t b0 = base + B_OFF, tr0 = base + TR_OFF;
+  constexpr int S_OFF = A_STAGES * AS_BYTES, BAR_OFF = S_OFF + S_STAGES * SS_BYTES;
+  const uint32_t s0 = base + S_OFF;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + BAR_OFF);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + N_BARS);
   const uint32_t bar0 = base + BAR_OFF;
@@ -140,13 +140,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(bar(BAR_AF + s), 1);
       mbar_init(bar(BAR_AE + s), TR_WARPS);    // one arrival per transform warp
     }
-    for (int s = 0; s < B_STAGES; ++s) {
-      mbar_init(bar(BAR_BF + s), 1);
-      mbar_init(bar(BAR_BE + s), 1);           // the MMA thread's commit
-    }
-    for (int s = 0; s < TR_STAGES; ++s) {
-      mbar_init(bar(BAR_TF + s), TR_WARPS);    // one arrival per transform warp
-      mbar_init(bar(BAR_TE + s), 1);
+    for (int s = 0; s < S_STAGES; ++s) {
+      mbar_init(bar(BAR_SF + s), TR_WARPS + 1);   // the producer's expect_tx arrival + one per transform warp
+      mbar_init(bar(BAR_SE + s), 1);              // the MMA thread's commit
     }
     for (int f = 0; f < 2; ++f) {
       mbar_init(bar(BAR_ACCF + f), 1);
@@ -173,9 +169,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       // A ring (FP32 rows + weights): released by the transform warps; B ring (BF16 hi/lo of the unweighted
       // side): released by the tensor core.  The A ring therefore refills as soon as a k-block is transformed.
       // ring positions kept as stage indices and phase bits (no divisions in the loop)
-      long issued_a = 0, issued_b = 0;
-      uint32_t sa = 0, pa = 0, sb = 0, pbb = 0;
-      bool a_wrapped = false, b_wrapped = false;
+      long issued_a = 0, issued_s = 0;
+      uint32_t sa = 0, pa = 0, ss = 0, ps = 0;
+      bool a_wrapped = false, s_wrapped = false;
       bool ok = true;
       for (long it = blockIdx.x; it < items && ok; it += gridDim.x) {
         int bm, bn, pair, ks;
@@ -191,23 +187,24 @@ __global__ void __launch_bounds__(THREADS, 1)
           tma_load_2d(as + W_OFF, &maps.w, kx, 2 * pair, bar(BAR_AF + sa));
           ++issued_a;
           if (++sa == A_STAGES) { sa = 0; pa ^= 1u; a_wrapped = true; }
-          if (b_wrapped && !mbar_wait(bar(BAR_BE + sb), pbb ^ 1u, err, 13)) { ok = false; break; }
+          if (s_wrapped && !mbar_wait(bar(BAR_SE + ss), ps ^ 1u, err, 13)) { ok = false; break; }
           if (*(volatile int*)&s_abort) { ok = false; break; }
-          const uint32_t bs = b0 + sb * BS_BYTES;
-          mbar_expect_tx(bar(BAR_BF + sb), B_TX);
-          tma_load_2d(bs, &maps.bh, kx, bn * BM, bar(BAR_BF + sb));
-          tma_load_2d(bs + H_BYTES, &maps.bl, kx, bn * BM, bar(BAR_BF + sb));
-          ++issued_b;
-          if (++sb == B_STAGES) { sb = 0; pbb ^= 1u; b_wrapped = true; }
+          const uint32_t st = s0 + ss * SS_BYTES;
+          mbar_expect_tx(bar(BAR_SF + ss), B_TX);
+          tma_load_2d(st, &maps.bh, kx, bn * BM, bar(BAR_SF + ss));
+          tma_load_2d(st + H_BYTES, &maps.bl, kx, bn * BM, bar(BAR_SF + ss));
+          ++issued_s;
+          if (++ss == S_STAGES) { ss = 0; ps ^= 1u; s_wrapped = true; }
         }
       }
       if (!ok) {
         s_abort = 1;
-        // wait for the copies that may still be in flight (the latest phase of each stage)
+        // wait for the copies that may still be in flight (the latest phase of each stage; an S stage's phase
+        // also needs the transform's arrivals, so that wait may run out after the copy itself has landed)
         for (long q = issued_a > A_STAGES ? issued_a - A_STAGES : 0; q < issued_a; ++q)
           mbar_wait(bar(BAR_AF + (int)(q % A_STAGES)), (uint32_t)((q / A_STAGES) & 1), err, 12);
-        for (long q = issued_b > B_STAGES ? issued_b - B_STAGES : 0; q < issued_b; ++q)
-          mbar_wait(bar(BAR_BF + (int)(q % B_STAGES)), (uint32_t)((q / B_STAGES) & 1), err, 14);
+        for (long q = issued_s > S_STAGES ? issued_s - S_STAGES : 0; q < issued_s; ++q)
+          mbar_wait(bar(BAR_SF + (int)(q % S_STAGES)), (uint32_t)((q / S_STAGES) & 1), err, 14);
       }
     }
   } else if (warp == 13) {
@@ -216,9 +213,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       // The issuing thread's work between MMAs limits the tensor core's throughput as soon as it exceeds one MMA's
       // 64 cycles, so the loop keeps it minimal: ring positions as stage indices and phase bits, and shared-memory
       // descriptors formed once and advanced by adding the byte offset >> 4 to their start-address field.
-      uint32_t sb = 0, pbb = 0, ts = 0, pt = 0;
+      uint32_t ss = 0, ps = 0;
       uint32_t cf0 = 0, cf1 = 0;           // chunks started per entry
-      const uint64_t dB = sdesc(b0, SBO64, SWZ64), dT = sdesc(tr0, SBO64, SWZ64);
+      const uint64_t dS = sdesc(s0, SBO64, SWZ64);
       bool ok = true;
       for (long it = blockIdx.x; it < items && ok; it += gridDim.x) {
         int bm, bn, pair, ks;
@@ -226,14 +223,14 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int nf = min(2, nb - 2 * pair);
         const int nki = (int)((long)nk * (ks + 1) / ksplit) - (int)((long)nk * ks / ksplit);
         for (int kb = 0; kb < nki && ok; ++kb) {
-          if (*(volatile int*)&s_abort || !mbar_wait(bar(BAR_BF + sb), pbb, err, 21) ||
-              !mbar_wait(bar(BAR_TF + ts), pt, err, 22)) {
+          // one wait: the stage's B tiles have landed and every transform warp has written its tiles
+          if (*(volatile int*)&s_abort || !mbar_wait(bar(BAR_SF + ss), ps, err, 21)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint64_t bh = dB + (uint64_t)((sb * BS_BYTES) >> 4), bl = bh + (uint64_t)(H_BYTES >> 4);
-          const uint64_t td = dT + (uint64_t)((ts * TR_BYTES) >> 4);
+          const uint64_t bh = dS + (uint64_t)((ss * SS_BYTES) >> 4), bl = bh + (uint64_t)(H_BYTES >> 4);
+          const uint64_t td = bh + (uint64_t)(ST_OFF >> 4);
 #pragma unroll
           for (int o = 0; o < 2; ++o) {
             const int f = entry_at(kb, o);
@@ -257,10 +254,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (chunk_last(f, kb, nki)) mma_commit(bar(BAR_ACCF + f));
           }
           if (!ok) break;
-          mma_commit(bar(BAR_BE + sb));
-          mma_commit(bar(BAR_TE + ts));
-          if (++sb == B_STAGES) { sb = 0; pbb ^= 1u; }
-          if (++ts == TR_STAGES) { ts = 0; pt ^= 1u; }
+          mma_commit(bar(BAR_SE + ss));        // frees the stage's B tiles and transformed tiles together
+          if (++ss == S_STAGES) { ss = 0; ps ^= 1u; }
         }
       }
       if (!ok) s_abort = 1;
@@ -273,8 +268,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     // each over 16 of the k-block's 32 columns
     const int t = threadIdx.x - 128;
     const int r = t & (BM - 1), h = t >> 7;
-    uint32_t sa = 0, pa = 0, ts = 0, pt = 0;
-    bool t_wrapped = false;
+    uint32_t sa = 0, pa = 0, ss = 0, ps = 0;
+    bool s_wrapped = false;
     bool ok = true;
     for (long it = blockIdx.x; it < items && ok; it += gridDim.x) {
       int bm, bn, pair, ks;
@@ -283,7 +278,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int nki = (int)((long)nk * (ks + 1) / ksplit) - (int)((long)nk * ks / ksplit);
       for (int kb = 0; kb < nki; ++kb) {
         bool w_ok = !*(volatile int*)&s_abort && mbar_wait(bar(BAR_AF + sa), pa, err, 31);
-        if (w_ok && t_wrapped) w_ok = mbar_wait(bar(BAR_TE + ts), pt ^ 1u, err, 32);
+        if (w_ok && s_wrapped) w_ok = mbar_wait(bar(BAR_SE + ss), ps ^ 1u, err, 32);
         if (!__all_sync(0xffffffffu, w_ok)) { ok = false; break; }
         const uint8_t* sp = smem + sa * AS_BYTES;
         const float* wrow = reinterpret_cast<const float*>(sp + W_OFF);
@@ -298,7 +293,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           a[4 * c + 2] = v.z;
           a[4 * c + 3] = v.w;
         }
-        uint8_t* tp = smem + TR_OFF + ts * TR_BYTES;
+        uint8_t* tp = smem + S_OFF + ss * SS_BYTES + ST_OFF;
         for (int f = 0; f < nf; ++f) {
           float wv[HK];                        // the entry's weights for these columns (broadcast reads)
 #pragma unroll
@@ -329,11 +324,11 @@ __global__ void __launch_bounds__(THREADS, 1)
         fence_async_smem();
         __syncwarp();
         if (lane == 0) {
-          mbar_arrive(bar(BAR_TF + ts));
+          mbar_arrive(bar(BAR_SF + ss));
           mbar_arrive(bar(BAR_AE + sa));
         }
         if (++sa == A_STAGES) { sa = 0; pa ^= 1u; }
-        if (++ts == TR_STAGES) { ts = 0; pt ^= 1u; t_wrapped = true; }
+        if (++ss == S_STAGES) { ss = 0; ps ^= 1u; s_wrapped = true; }
       }
     }
     if (!ok) s_abort = 1;
