@@ -46,11 +46,13 @@ void launch_op_gemm1(const T* V, const T* B, const double* Dk, long n_ov, int n_
                      double cut = 0.0, long ldb = 0,    // ldb: row length of B (0 = n_ov)
                      const int* run_if = nullptr);      // device flag: the launch does nothing if *run_if == 0
 // Double-float (FP32 pair, 48-bit) versions of op_gemm1 mode 0 and op_gemm2 mode 1 for the refinement residual:
-// V, U, out FP64; B as its split Bh + Bl (launch_df_split of the FP64 B_ia).
+// V, U, out FP64; B as its split Bh + Bl (launch_df_split of the FP64 B_ia): Bh [n_aux][ldh] is the FP32 rounding
+// of B (the plan's FP32 copy), Bl [n_aux][n_ov] the rounding of the remainder.  launch_df_split writes h only if it
+// is not NULL.
 void launch_df_split(const double* x, long n, float* h, float* l, cudaStream_t s);
-void launch_op_gemm1_df(const double* V, const float* Bh, const float* Bl, const double* Dk, long n_ov, int n_aux,
-                        const double* x, double eta, int nr, double* U, cudaStream_t s);
-void launch_op_gemm2_df(const double* U, const float* Bh, const float* Bl, int n_aux, int n_ov, int nr,
+void launch_op_gemm1_df(const double* V, const float* Bh, const float* Bl, long ldh, const double* Dk, long n_ov,
+                        int n_aux, const double* x, double eta, int nr, double* U, cudaStream_t s);
+void launch_op_gemm2_df(const double* U, const float* Bh, const float* Bl, long ldh, int n_aux, int n_ov, int nr,
                         const double* V, double* out, cudaStream_t s);
 // The pairs that mode 2 skips, in FP64: dw[j] += Re(c'_k(x_j) t_k^2) with t from the FP64 rows of V64 and the FP64
 // B_ia [n_aux][n_ov]; Dsort ascending pair energies with their pair indices kidx.

@@ -61,6 +61,9 @@ struct gw_plan {
   __nv_bfloat16* d_BThi = nullptr;  // mixed: BF16 hi/lo split of B_ia^T, [n_ov][tc_ld(n_aux)]
   __nv_bfloat16* d_BTlo = nullptr;
   __nv_bfloat16* d_Blo2 = nullptr;  // mixed: third split parts of B_ia and B_ia^T (refinement operator)
+  __nv_bfloat16* d_Bp_hi = nullptr; // mixed: BF16 hi/lo split of B_ia in the K-panel layout of the Pi kernel,
+                                    // [P][n_aux][256]
+  __nv_bfloat16* d_Bp_lo = nullptr;
   __nv_bfloat16* d_BTlo2 = nullptr;
   double* d_D = nullptr;            // pair energies D_ia [n_ov]
   double* d_Dsort = nullptr;        // mixed: D_ia ascending, with the pair index of each entry in d_Dkidx
@@ -84,13 +87,14 @@ struct gw_plan {
   int ns_kmax = 0;
   int ns_ndiff = 0;           // lowest grid points whose W column is built in the difference form
   std::vector<DevBuf*> bufs;
-  DevBuf ws_mat, ws_info, ws_scratch, ws_gout, ws_xi, tc_part, tc_kind, tc_par, tc_err, tc_w, ns_E, ns_X, ns_X2, ns_Xa, ns_Xb, ns_T, ns_lam,
+  int tc_tiles_n = 0;          // N_aux the tile-order table of the Pi kernel was built for
+  DevBuf ws_mat, ws_info, ws_scratch, ws_gout, ws_xi, tc_part, tc_kind, tc_par, tc_err, tc_w, tc_tiles, ns_E, ns_X, ns_X2, ns_Xa, ns_Xb, ns_T, ns_lam,
       ns_E0, ns_vec;
   DevBuf mr_V, mr_U, mr_S, mr_vprev, mr_v, mr_d1, mr_d2, mr_x, mr_st, mr_rt, mr_rm, mr_xf, mr_wre, mr_wim,
       mr_dwre, mr_it, mr_res, mr_cnt, mr_Vhi, mr_Vlo, mr_Uhi, mr_Ulo, mr_Vlo2, mr_Ulo2, mr_V64;
   DevBuf sg_I, sg_dI, sg_R, sg_dR, sg_om, sg_start, sg_coef, sg_act, sg_tmap, qp_st, qp_om0;
   DevBuf fb_A, fb_y, fb_piv, fb_info, fb_idx, fb_y64, fb_V32, fb_S32, fb_Vp, fb_Up, fb_x, fb_V64, fb_U64, fb_S64, fb_sel,
-      fb_pos, fb_rho, fb_xs, fb_Bh, fb_Bl, fb_lu;
+      fb_pos, fb_rho, fb_xs, fb_Bl, fb_lu;
   int* h_cnt = nullptr;       // pinned
   std::string err;
   gw_stats stats{};
@@ -102,10 +106,10 @@ struct gw_plan {
   std::vector<Mark> marks;
 
   gw_plan() {
-    DevBuf* all[] = {&ws_mat, &ws_info, &ws_scratch, &ws_gout, &ws_xi, &tc_part, &tc_kind, &tc_par, &tc_err, &tc_w, &ns_E, &ns_X, &ns_X2, &ns_Xa, &ns_Xb, &ns_T, &ns_lam, &ns_E0, &ns_vec, &mr_V, &mr_U, &mr_S, &mr_vprev,
+    DevBuf* all[] = {&ws_mat, &ws_info, &ws_scratch, &ws_gout, &ws_xi, &tc_part, &tc_kind, &tc_par, &tc_err, &tc_w, &tc_tiles, &ns_E, &ns_X, &ns_X2, &ns_Xa, &ns_Xb, &ns_T, &ns_lam, &ns_E0, &ns_vec, &mr_V, &mr_U, &mr_S, &mr_vprev,
                      &mr_v, &mr_d1, &mr_d2, &mr_x, &mr_st, &mr_rt, &mr_rm, &mr_xf, &mr_wre, &mr_wim,
                      &mr_dwre, &mr_it, &mr_res, &mr_cnt, &mr_Vhi, &mr_Vlo, &mr_Uhi, &mr_Ulo, &mr_Vlo2, &mr_Ulo2, &mr_V64, &sg_I, &sg_dI, &sg_R, &sg_dR, &sg_om, &sg_start,
-                     &sg_coef, &sg_act, &sg_tmap, &qp_st, &qp_om0, &fb_A, &fb_y, &fb_piv, &fb_info, &fb_idx, &fb_y64, &fb_V32, &fb_S32, &fb_Vp, &fb_Up, &fb_x, &fb_V64, &fb_U64, &fb_S64, &fb_sel, &fb_pos, &fb_rho, &fb_xs, &fb_Bh, &fb_Bl, &fb_lu, &sd_M, &sd_T, &sd_cs, &sd_off, &sd_Om, &sd_V, &sd_w2, &sd_tmap, &sd_om, &sd_S, &sd_dS};
+                     &sg_coef, &sg_act, &sg_tmap, &qp_st, &qp_om0, &fb_A, &fb_y, &fb_piv, &fb_info, &fb_idx, &fb_y64, &fb_V32, &fb_S32, &fb_Vp, &fb_Up, &fb_x, &fb_V64, &fb_U64, &fb_S64, &fb_sel, &fb_pos, &fb_rho, &fb_xs, &fb_Bl, &fb_lu, &sd_M, &sd_T, &sd_cs, &sd_off, &sd_Om, &sd_V, &sd_w2, &sd_tmap, &sd_om, &sd_S, &sd_dS};
     bufs.assign(all, all + sizeof(all) / sizeof(all[0]));
   }
 };
@@ -227,6 +231,13 @@ gw_status tc_weighted_syrk(gw_plan* P, const int* kinds, const double* params, i
   TRY(ensure(P, P->tc_par, sizeof(double) * nb));
   TRY(ensure(P, P->tc_err, sizeof(int)));
   TRY(ensure(P, P->tc_w, sizeof(float) * (size_t)nb * gw::pf_ldw(K)));
+  if (P->tc_tiles_n != n) {                  // tile order of the Pi kernel, uploaded once per plan
+    std::vector<uint32_t> order;
+    gw::tc_pi_fused_tile_order(n, order);
+    TRY(ensure(P, P->tc_tiles, sizeof(uint32_t) * order.size()));
+    CK(cudaMemcpy(P->tc_tiles.p, order.data(), sizeof(uint32_t) * order.size(), cudaMemcpyHostToDevice));
+    P->tc_tiles_n = n;
+  }
   CK(cudaMemcpyAsync(P->tc_kind.p, kinds, sizeof(int) * nb, cudaMemcpyHostToDevice, P->stream));
   CK(cudaMemcpyAsync(P->tc_par.p, params, sizeof(double) * nb, cudaMemcpyHostToDevice, P->stream));
   if (reset_err) CK(cudaMemsetAsync(P->tc_err.p, 0, sizeof(int), P->stream));
@@ -234,16 +245,15 @@ gw_status tc_weighted_syrk(gw_plan* P, const int* kinds, const double* params, i
   CK(gw::tc_pair_weights(P->d_D, K, as<int>(P->tc_kind), as<double>(P->tc_par),
                          P->cfg.eta, nb, as<float>(P->tc_w), P->stream));
   // split-K partials (only small problems, whose tiles x entry pairs do not fill the GPU, consider a split)
-  const long nbt = (n + 127) / 128;
   float* part = nullptr;
   size_t part_bytes = 0;
-  if (P->cfg.pi_ksplit != 1 && nbt * (nbt + 1) / 2 * ((nb + 1) / 2) < 2L * 152) {
+  if (P->cfg.pi_ksplit != 1 && gw::tc_pi_fused_items(n, nb) < 2L * 152) {
     part_bytes = std::min(ws_bytes(P), (size_t)(P->cfg.pi_ksplit > 0 ? P->cfg.pi_ksplit : 8) * nb * n * n * 4);
     TRY(ensure(P, P->tc_part, part_bytes));
     part = as<float>(P->tc_part);
   }
   int chosen = 1;
-  CK(gw::tc_pi_fused(P->d_B_ia_f, P->ld_f, n, K, as<float>(P->tc_w), nb, P->d_Bhi, P->d_Blo, mode_even, mode_odd,
+  CK(gw::tc_pi_fused(n, K, as<float>(P->tc_w), nb, as<uint32_t>(P->tc_tiles), P->d_Bp_hi, P->d_Bp_lo, mode_even, mode_odd,
                      out, (long)n * n, n, as<int>(P->tc_err), P->stream, P->cfg.tc_max_ctas, P->cfg.pi_ksplit, part,
                      part_bytes, &chosen));
   P->stats.pi_ksplit_last = chosen;
@@ -734,15 +744,16 @@ gw_status dense_fallback(gw_plan* P, const std::vector<int>& need, const int* rt
                                        P->stream));
           if (P->cfg.refine_df) {
             // double-float (FP32 pair) residual: 48-bit products and sums on the FP32 pipes
-            if (!P->fb_Bh.p) {
+            // the hi part of the split is the FP32 copy of B_ia already held by the plan; only the lo part is made
+            if (!P->fb_Bl.p) {
               const size_t nb = (size_t)n * P->n_ov;
-              TRY(ensure(P, P->fb_Bh, sizeof(float) * nb));
               TRY(ensure(P, P->fb_Bl, sizeof(float) * nb));
-              LAUNCH(gw::launch_df_split(P->d_B_ia, (long)nb, as<float>(P->fb_Bh), as<float>(P->fb_Bl), P->stream));
+              LAUNCH(gw::launch_df_split(P->d_B_ia, (long)nb, nullptr, as<float>(P->fb_Bl), P->stream));
             }
-            LAUNCH(gw::launch_op_gemm1_df(as<double>(P->fb_V64), as<float>(P->fb_Bh), as<float>(P->fb_Bl), P->d_D, P->n_ov, n, as<double>(P->fb_xs), P->cfg.eta, m,
-                                          as<double>(P->fb_U64), P->stream));
-            LAUNCH(gw::launch_op_gemm2_df(as<double>(P->fb_U64), as<float>(P->fb_Bh), as<float>(P->fb_Bl), n,
+            LAUNCH(gw::launch_op_gemm1_df(as<double>(P->fb_V64), P->d_B_ia_f, as<float>(P->fb_Bl), P->ld_f, P->d_D,
+                                          P->n_ov, n, as<double>(P->fb_xs), P->cfg.eta, m, as<double>(P->fb_U64),
+                                          P->stream));
+            LAUNCH(gw::launch_op_gemm2_df(as<double>(P->fb_U64), P->d_B_ia_f, as<float>(P->fb_Bl), P->ld_f, n,
                                           P->n_ov, m, as<double>(P->fb_V64), as<double>(P->fb_S64), P->stream));
           } else {
             LAUNCH(gw::launch_op_gemm1<double>(as<double>(P->fb_V64), P->d_B_ia, P->d_D, P->n_ov, n, as<double>(P->fb_xs), P->cfg.eta, m,
@@ -1284,6 +1295,8 @@ static void free_plan(gw_plan* P) {
   if (P->d_BThi) cudaFree(P->d_BThi);
   if (P->d_BTlo) cudaFree(P->d_BTlo);
   if (P->d_Blo2) cudaFree(P->d_Blo2);
+  if (P->d_Bp_hi) cudaFree(P->d_Bp_hi);
+  if (P->d_Bp_lo) cudaFree(P->d_Bp_lo);
   if (P->d_BTlo2) cudaFree(P->d_BTlo2);
   if (P->d_D) cudaFree(P->d_D);
   if (P->d_Dsort) cudaFree(P->d_Dsort);
@@ -1413,6 +1426,10 @@ static gw_status plan_create_impl(gw_plan* P, const gw_config* cfg, const double
     TRY(dmalloc(P, &P->d_Bhi, sizeof(__nv_bfloat16) * nsplit));
     TRY(dmalloc(P, &P->d_Blo, sizeof(__nv_bfloat16) * nsplit));
     CK(gw::tc_split_rows(P->d_B_ia_f, n, P->n_ov, (int)P->ld_f, P->d_Bhi, P->d_Blo, P->stream));
+    const size_t npanel = (size_t)n * gw::tc_pi_panel_cols(P->n_ov);
+    TRY(dmalloc(P, &P->d_Bp_hi, sizeof(__nv_bfloat16) * npanel));
+    TRY(dmalloc(P, &P->d_Bp_lo, sizeof(__nv_bfloat16) * npanel));
+    CK(gw::tc_pi_panel_split(P->d_B_ia_f, P->ld_f, n, P->n_ov, P->d_Bp_hi, P->d_Bp_lo, P->stream));
     const size_t nsplitN = (size_t)n_targets * P->n_bas * gw::tc_ld(n);
     TRY(dmalloc(P, &P->d_Bnhi, sizeof(__nv_bfloat16) * nsplitN));
     TRY(dmalloc(P, &P->d_Bnlo, sizeof(__nv_bfloat16) * nsplitN));
@@ -2032,6 +2049,7 @@ gw_status gw_plan_footprint(const gw_config* c, int n_t, unsigned flags, unsigne
     b += 4 * (n * ldf + nBn);                                                // FP32 copies
     b += 6 * (n * ldo + rows * ldn + n_ov * ldn);                             // three BF16 parts of B, B_nm, B^T
     b += 12 * n_ov;                                                          // sorted D and its pair index
+    b += 4 * n * (u64)gw::tc_pi_panel_cols((int)std::min<u64>(n_ov, 2147483647ull));   // K-panel hi/lo of B
   }
   b += 8 * n_ov;                                                             // pair energies D_ia
   // imaginary-axis stage: frequency matrices, info/index lists
@@ -2063,7 +2081,7 @@ gw_status gw_plan_footprint(const gw_config* c, int n_t, unsigned flags, unsigne
   b += capped(mat2, mat2 * fb) + fb * (2 * n * ts + 8 * n + 8);
   if (mixed) {
     b += fb * (16 * n + 16 * n + 12 * ldn + 12 * ldo + 40);                  // FP64 solutions, V/S, split parts
-    b += fb * (32 * n + 16 * n_ov) + 8 * n * n_ov;                           // FP64-residual vectors, df split of B
+    b += fb * (32 * n + 16 * n_ov) + 4 * n * n_ov;                           // FP64-residual vectors, df lo part of B
     b += 2 * (u64)lu_work_elems(c->n_aux, (long)std::min<u64>(fb, 1u << 30));            // blocked-LU split operands
   }
   *bytes = b;

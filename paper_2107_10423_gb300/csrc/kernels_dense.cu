@@ -612,7 +612,8 @@ __device__ __forceinline__ void df_mac(float ah, float al, float bh, float bl, f
 // df gemm1: U[r][k] for rows r of V [2nr][n_aux] (FP64) against B = Bh + Bl [n_aux][n_ov], then the complex
 // weights c_k(x_j) of the pair (2j, 2j+1) as in op_gemm1 mode 0; U in FP64.
 __global__ void __launch_bounds__(NT) op_gemm1_df_kernel(const double* __restrict__ V, const float* __restrict__ Bh,
-                                                         const float* __restrict__ Bl, const double* __restrict__ Dk,
+                                                         const float* __restrict__ Bl, long ldh,
+                                                         const double* __restrict__ Dk,
                                                          long n_ov, int n_aux,
                                                          const double* __restrict__ xs, double eta, int nr,
                                                          double* __restrict__ U) {
@@ -644,7 +645,7 @@ __global__ void __launch_bounds__(NT) op_gemm1_df_kernel(const double* __restric
       for (int u = 0; u < 4; ++u) {
         const long k = k0c + c4 + u;
         const bool in = P < n_aux && k < n_ov;
-        Bh_s[kr][c4 + u] = in ? Bh[(long)P * n_ov + k] : 0.f;
+        Bh_s[kr][c4 + u] = in ? Bh[(long)P * ldh + k] : 0.f;
         Bl_s[kr][c4 + u] = in ? Bl[(long)P * n_ov + k] : 0.f;
       }
     }
@@ -695,7 +696,8 @@ __global__ void __launch_bounds__(NT) op_gemm1_df_kernel(const double* __restric
 
 // df gemm2: acc[r][P] = sum_k U[r][k] B[P][k]; out = the real embedding [u - acc_re; -v - acc_im] (op_gemm2 mode 1).
 __global__ void __launch_bounds__(NT) op_gemm2_df_kernel(const double* __restrict__ U, const float* __restrict__ Bh,
-                                                         const float* __restrict__ Bl, int n_aux, long n_ov, int nr,
+                                                         const float* __restrict__ Bl, long ldh, int n_aux, long n_ov,
+                                                         int nr,
                                                          const double* __restrict__ V, double* __restrict__ out) {
   __shared__ float Ah_s[TK][TM + 4], Al_s[TK][TM + 4];
   __shared__ float Bh_s[TK][TN + 4], Bl_s[TK][TN + 4];
@@ -718,7 +720,7 @@ __global__ void __launch_bounds__(NT) op_gemm2_df_kernel(const double* __restric
       Ah_s[lk + u][lr] = h;
       Al_s[lk + u][lr] = l;
       const bool in = q0 + lr < n_aux && k < n_ov;
-      Bh_s[lk + u][lr] = in ? Bh[(long)(q0 + lr) * n_ov + k] : 0.f;
+      Bh_s[lk + u][lr] = in ? Bh[(long)(q0 + lr) * ldh + k] : 0.f;
       Bl_s[lk + u][lr] = in ? Bl[(long)(q0 + lr) * n_ov + k] : 0.f;
     }
     __syncthreads();
@@ -759,8 +761,12 @@ __global__ void __launch_bounds__(NT) op_gemm2_df_kernel(const double* __restric
 }
 
 __global__ void df_split_kernel(const double* __restrict__ x, long n, float* __restrict__ h, float* __restrict__ l) {
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-    df_split(x[i], h[i], l[i]);
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    float hh, ll;
+    df_split(x[i], hh, ll);
+    if (h) h[i] = hh;
+    l[i] = ll;
+  }
 }
 
 }  // namespace
@@ -769,16 +775,16 @@ void launch_df_split(const double* x, long n, float* h, float* l, cudaStream_t s
   if (n > 0) df_split_kernel<<<1216, 256, 0, s>>>(x, n, h, l);
 }
 
-void launch_op_gemm1_df(const double* V, const float* Bh, const float* Bl, const double* Dk, long n_ov, int n_aux,
-                        const double* x, double eta, int nr, double* U, cudaStream_t s) {
+void launch_op_gemm1_df(const double* V, const float* Bh, const float* Bl, long ldh, const double* Dk, long n_ov,
+                        int n_aux, const double* x, double eta, int nr, double* U, cudaStream_t s) {
   const dim3 grid((unsigned)((n_ov + TN - 1) / TN), (2 * nr + TM - 1) / TM);
-  if (nr > 0) op_gemm1_df_kernel<<<grid, NT, 0, s>>>(V, Bh, Bl, Dk, n_ov, n_aux, x, eta, nr, U);
+  if (nr > 0) op_gemm1_df_kernel<<<grid, NT, 0, s>>>(V, Bh, Bl, ldh, Dk, n_ov, n_aux, x, eta, nr, U);
 }
 
-void launch_op_gemm2_df(const double* U, const float* Bh, const float* Bl, int n_aux, int n_ov, int nr,
+void launch_op_gemm2_df(const double* U, const float* Bh, const float* Bl, long ldh, int n_aux, int n_ov, int nr,
                         const double* V, double* out, cudaStream_t s) {
   const dim3 grid((n_aux + TN - 1) / TN, (2 * nr + TM - 1) / TM);
-  if (nr > 0) op_gemm2_df_kernel<<<grid, NT, 0, s>>>(U, Bh, Bl, n_aux, (long)n_ov, nr, V, out);
+  if (nr > 0) op_gemm2_df_kernel<<<grid, NT, 0, s>>>(U, Bh, Bl, ldh, n_aux, (long)n_ov, nr, V, out);
 }
 
 void launch_deriv_resonant(const double* V64, const double* B, long n_ov, int n_aux, const double* Dsort,

@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cstdint>
+#include <vector>
 
 namespace gw {
 enum { TC_EPI_STORE = 0, TC_EPI_CPAIR = 1, TC_EPI_EMBED = 2, TC_EPI_AXPBY = 3, TC_EPI_WRED = 4, TC_EPI_SUB2 = 5 };
@@ -58,17 +60,30 @@ int pf_ldw(int K);
 cudaError_t tc_pair_weights(const double* Dk, int K, const int* kinds, const double* params, double eta, int nb,
                             float* w, cudaStream_t s);
 // out_b = f(B diag(w_b) B^T) for b < nb on the tensor cores with the weight applied in the kernel (pi_fused.cu):
-// B FP32 [n][ldb] (ldb a multiple of 4), its BF16 hi/lo split Bhi/Blo [n][tc_ld(K)], w from tc_pair_weights;
+// B as its BF16 hi/lo split Bhi/Blo in the K-panel layout of tc_pi_panel_split ([P][n][256],
+// P = tc_pi_panel_cols(K) / 256), w from tc_pair_weights, tiles (device) the table of tc_pi_fused_tile_order(n);
 // out [nb][n][ldo] FP32 at batch stride out_bstride, full symmetric (lower tiles computed and mirrored);
 // mode_even / mode_odd for even / odd b: 0 v, 1 delta - v, 2 -v.  max_ctas > 0 caps the persistent grid.
-// ksplit > 0 asks for that many K ranges per (tile, pair), lowered by halving to the largest feasible split (every
+// ksplit > 0 asks for that many K ranges per (tile, entry), lowered by halving to the largest feasible split (every
 // range at least 4 K blocks of 32, partials within part_bytes); ksplit = 0 autotunes it per shape (n, K, nb, max_ctas):
 // every feasible split (partials [ksplit][nb][n][n] FP32 fit in part_bytes of `part`) is timed once and the
 // fastest kept for the process.  *chosen (if not NULL) receives the split used.
-cudaError_t tc_pi_fused(const float* B, long ldb, int n, int K, const float* w, int nb, const __nv_bfloat16* Bhi,
+cudaError_t tc_pi_fused(int n, int K, const float* w, int nb, const uint32_t* tiles,
+                        const __nv_bfloat16* Bhi,
                         const __nv_bfloat16* Blo, int mode_even, int mode_odd, float* out, long out_bstride, int ldo,
                         int* err, cudaStream_t s, int max_ctas = 0, int ksplit = 1, float* part = nullptr,
                         size_t part_bytes = 0, int* chosen = nullptr);
+// Work items of one unsplit tc_pi_fused launch (lower 128 x 256 tiles x entries); fewer than about two per SM
+// leave the persistent grid partly idle, which is when a K split pays.
+long tc_pi_fused_items(int n, int nb);
+// Columns of the K-panel layout (K rounded up to the 256-column panel width) and the conversion to it: the BF16
+// hi/lo split hp/lp[p][r][c] of B[r][256 p + c] (zero beyond K), from B FP32 [n][ldb] (n <= 65535).
+long tc_pi_panel_cols(int K);
+cudaError_t tc_pi_panel_split(const float* B, long ldb, int n, int K, __nv_bfloat16* hp, __nv_bfloat16* lp,
+                              cudaStream_t s);
+// The order in which tc_pi_fused visits its lower 128 x 256 tiles (bm | bn2 << 16, one entry per tile); the caller
+// uploads it and passes it as `tiles`.
+void tc_pi_fused_tile_order(int n, std::vector<uint32_t>& tiles);
 // The split the autotuner chose for a shape with the given largest feasible split, or 0 if it has not seen it.
 int tc_pi_fused_ksplit(int n, int K, int nb, int max_ctas, int max_split);
 // out_b = f(A_b Bm^T) for b < batch, out [batch][M][N] FP32; lower != 0 computes lower tiles and mirrors.
