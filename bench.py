@@ -428,17 +428,20 @@ def main():
         stream_jobs = synth.serving_stream()
         jobs = serve.make_jobs(stream_jobs, n_max=args.serve_nmax, limit=args.serve_jobs)
 
-        def served(slots, at_zero):
+        def served(slots, at_zero, keep=None):
             js = serve.make_jobs(stream_jobs, n_max=args.serve_nmax, limit=args.serve_jobs)
             if at_zero:
                 for j in js:
                     j.arrival = 0.0
             t0 = time.perf_counter()
             done = serve.Server(max_slots=slots).run(js)
+            if keep is not None:
+                keep.extend(done)
             return serve.summarize(done, makespan=time.perf_counter() - t0)
 
         rnd = lambda d: {k: (round(v, 4) if isinstance(v, float) else v) for k, v in d.items()}
-        live4, live1 = served(4, False), served(1, False)
+        done4 = []
+        live4, live1 = served(4, False, done4), served(1, False)
         cap4, cap1 = served(4, True), served(1, True)
         out["serving"] = {"sample": f"first {len(jobs)} jobs with n <= {args.serve_nmax} of the 256-job stream "
                                     f"(Poisson arrivals over {jobs[-1].arrival:.1f} s), mixed precision, linearised QP",
@@ -446,6 +449,26 @@ def main():
                           "capacity_jobs_per_s_4_slots": round(cap4["jobs_per_s"], 3),
                           "capacity_jobs_per_s_1_slot": round(cap1["jobs_per_s"], 3),
                           "capacity_p99_latency_s_4_slots": round(cap4["p99_latency_s"], 3)}
+        # serial plain-FP64 baseline: the sample's small jobs ((H2O)_n, n <= 3; an FP64 (H2O)_16 job alone takes
+        # minutes) solved one after another in FP64, against their latency in the 4-slot mixed run above
+        try:
+            small = [j for j in done4 if j.system.meta.get("n_water", 99) <= 3 and "error" not in j.result]
+            t64 = []
+            for j in small:
+                t0 = time.perf_counter()
+                r = serve.run_job(j, precision="fp64")
+                if "error" in r:
+                    raise RuntimeError(r["error"])
+                t64.append(time.perf_counter() - t0)
+            if t64:
+                lat = np.array([j.latency for j in small])
+                out["serving"]["fp64_serial_small_jobs"] = {
+                    "jobs": len(t64), "n_max": 3, "jobs_per_s": round(len(t64) / sum(t64), 3),
+                    "p50_s": round(float(np.percentile(t64, 50)), 4), "p99_s": round(float(np.percentile(t64, 99)), 4),
+                    "mixed_served_p50_s": round(float(np.percentile(lat, 50)), 4),
+                    "mixed_served_p99_s": round(float(np.percentile(lat, 99)), 4)}
+        except Exception as e:            # the baseline is a side measurement: report, do not lose the line
+            out["serving"]["fp64_serial_small_jobs"] = {"error": repr(e)[:200]}
 
     if rank == 0 and not args.no_cpu_baseline:
         job, desc = oracle_sample(s, count_residues(s))
