@@ -100,7 +100,7 @@ typedef struct {
                                   within this distance (Ha) of a neighbour in energy form a cluster; the member with the
                                   lowest KS energy is solved first and the others start from their KS energy shifted
                                   by its QP correction.  0 = off (default) */
-  int pi_ksplit;               /* mixed: K ranges per (tile, frequency pair) of the Pi kernel: 0 = autotuned per
+  int pi_ksplit;               /* mixed: K ranges per (tile, frequency) of the Pi kernel: 0 = autotuned per
                                   problem shape (n_aux, n_occ n_virt, batch; every feasible split timed once per
                                   process, the fastest kept; only shapes whose tiles do not fill the GPU split),
                                   or 1, 2, 4, 8 forced.  Default 0 */

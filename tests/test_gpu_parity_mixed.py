@@ -193,14 +193,14 @@ def test_footprint_bound_holds(gw):
 
 
 @pytest.mark.parametrize("n,seed,xi,ctas", [
-    (1, 3, [0.7], 0),                           # one 128-row tile holding 84 rows, K = 95 (ragged k-block), one entry
-    (1, 3, [0.0, 0.2, 1.0, 4.0, 30.0], 1),      # odd entry count on a single persistent CTA (items in sequence)
-    (3, 5, [0.0, 0.05, 2.0, 9.0], 2),           # 378 rows: 6 lower tiles with a ragged last row of tiles, 2 CTAs
-    (4, 6, [0.01, 0.3, 1.1], 0)])               # 504 rows, K = 7600
+    (1, 3, [0.7], 0),                           # one 128 x 256 tile holding 84 rows, K = 95 (ragged k-block), one entry
+    (1, 3, [0.0, 0.2, 1.0, 4.0, 30.0], 1),      # five entries on a single persistent CTA (items in sequence)
+    (3, 5, [0.0, 0.05, 2.0, 9.0], 2),           # 378 rows: 4 lower 128 x 256 tiles, ragged in rows and columns, 2 CTAs
+    (4, 6, [0.01, 0.3, 1.1], 0)])               # 504 rows, K = 7600 (30 K panels)
 def test_fused_pi_tiles_and_entries(gw, n, seed, xi, ctas):
-    """Pi(i xi) from the fused-weight tensor-core kernel against the oracle, element by element: ragged row and k
-    tails, an odd number of batch entries (a lone entry in the last pair) and persistent CTAs that each take many
-    (tile, entry pair) items in sequence.  Bar: 2e-5 of max |Pi| (BF16x3 with FP32 sums)."""
+    """Pi(i xi) from the fused-weight tensor-core kernel against the oracle, element by element: ragged row, column
+    and k tails, several batch entries and persistent CTAs that each take many (tile, entry) items in sequence.
+    Bar: 2e-5 of max |Pi| (BF16x3 with FP32 sums)."""
     s = synth.workload(0) if n == 1 else synth.water_cluster(n, seed)
     B, Bn = s.b_ia(), s.b_nm()
     xi = np.array(xi)
